@@ -1,0 +1,32 @@
+"""Parameters of the oracle (its own copy; nothing is shared with the CUDA path)."""
+from __future__ import annotations
+
+from dataclasses import dataclass, replace
+
+
+@dataclass
+class Params:
+    # objective (Sec. 2): regulariser weights, penalty weight
+    alpha: float = 0.02        # spatial diffusion weight
+    alpha_t: float = 0.0       # temporal first-difference weight (the paper uses none)
+    lam: float = 1.0           # lambda of the mean-transform penalty P
+    # predictor (eq. 2) and temporal stopping rule (eq. 3)
+    beta: float = 1e-5
+    eps_stop: float = 1e-3
+    stop_rule: bool = True
+    # multilevel structure
+    n_levels: int = 2          # spatial levels
+    n_tlevels: int = 2         # temporal levels Q (q = 0..Q-1)
+    # Gauss-Newton / PCG / Armijo
+    tol_J: float = 1e-3
+    tol_Y: float = 1e-2
+    tol_G: float = 5e-2
+    max_gn: int = 10
+    tol_cg: float = 1e-1
+    max_cg: int = 20
+    max_ls: int = 10
+    armijo_c: float = 1e-4
+    g_abs: float = 1e-12       # ||g|| below g_abs (1 + |J0|) counts as stationary
+
+    def with_(self, **kw) -> "Params":
+        return replace(self, **kw)

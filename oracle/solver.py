@@ -1,0 +1,133 @@
+"""Gauss-Newton / PCG / Armijo: the registration scheme GIR on a frame subset.
+
+The paper registers with FAIR's L-BFGS (Sec. 2) and allows "any numerical
+optimization scheme".  This oracle (like the library) uses a matrix-free
+Gauss-Newton method on the displacement fields of all frames in K:
+
+1. evaluate J and its gradient g at u;
+2. stop (the three FAIR-style tests below) or continue;
+3. solve H d = -g approximately by Jacobi-preconditioned conjugate gradients
+   started at 0 (stop when ||r|| <= tol_cg ||g|| or after max_cg steps; if a
+   search direction has p^T H p <= 0 the iterate so far is returned, or the
+   preconditioned gradient step when that happens on the first step);
+4. Armijo back-tracking on t in {1, 1/2, 1/4, ...}:
+   accept the first t with J(u + t d) <= J(u) + c t g^T d (at most max_ls trials);
+5. u <- u + t d, go to 1.
+
+Stopping after iteration i >= 1 when all of
+|J_old - J| <= tol_J (1 + |J0|), ||t d|| <= tol_Y (1 + ||u||),
+||g|| <= tol_G (1 + |J0|) hold, or at once when ||g|| <= g_abs (1 + |J0|),
+or when max_gn iterations were taken.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, Sequence
+
+import numpy as np
+
+from . import objective
+from .params import Params
+
+
+def pcg(apply_H: Callable[[np.ndarray], np.ndarray], b: np.ndarray, Minv: np.ndarray,
+        tol: float, maxit: int):
+    """Jacobi-preconditioned CG for H x = b from x = 0; returns (x, steps, flag)."""
+    x = np.zeros_like(b)
+    bnorm = float(np.sqrt(np.sum(b * b)))
+    if bnorm == 0.0:
+        return x, 0, "zero-rhs"
+    r = b.copy()
+    z = Minv * r
+    p = z.copy()
+    rho = float(np.sum(r * z))
+    steps = 0
+    flag = "maxit"
+    while steps < maxit:
+        q = apply_H(p)
+        pq = float(np.sum(p * q))
+        if pq <= 0.0:
+            if steps == 0:
+                x = z.copy()
+            flag = "breakdown"
+            break
+        alpha = rho / pq
+        x += alpha * p
+        r -= alpha * q
+        steps += 1
+        if float(np.sqrt(np.sum(r * r))) <= tol * bnorm:
+            flag = "converged"
+            break
+        z = Minv * r
+        rho_new = float(np.sum(r * z))
+        beta = rho_new / rho
+        rho = rho_new
+        p = z + beta * p
+    return x, steps, flag
+
+
+@dataclass
+class GirStats:
+    J: float = 0.0
+    D: float = 0.0
+    S: float = 0.0
+    P: float = 0.0
+    J0: float = 0.0
+    gn_iters: int = 0
+    cg_iters: int = 0
+    ls_trials: int = 0
+    status: str = "ok"
+    history: list = field(default_factory=list)
+
+
+def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float, p: Params):
+    """GIR(K): minimise eq. (1) over the fields of the frames in K, from u0."""
+    u = np.array(u0, dtype=np.float64, copy=True)
+    ev = objective.evaluate(T, u, frames, h, p)
+    J0 = ev["J"]
+    st = GirStats(J0=J0)
+    J, g = ev["J"], ev["g"]
+    J_old = None
+    step_norm = None
+    it = 0
+    while True:
+        gnorm = float(np.sqrt(np.sum(g * g)))
+        st.history.append((J, gnorm))
+        if it > 0:
+            c1 = abs(J_old - J) <= p.tol_J * (1.0 + abs(J0))
+            c2 = step_norm <= p.tol_Y * (1.0 + float(np.sqrt(np.sum(u * u))))
+            c3 = gnorm <= p.tol_G * (1.0 + abs(J0))
+            if c1 and c2 and c3:
+                break
+        if gnorm <= p.g_abs * (1.0 + abs(J0)) or it >= p.max_gn:
+            break
+        Minv = 1.0 / objective.jacobi_diag(ev["dT"], frames, h, p)
+        dT = ev["dT"]
+        d, steps, _ = pcg(lambda v: objective.hessvec(dT, v, frames, h, p), -g, Minv,
+                          p.tol_cg, p.max_cg)
+        st.cg_iters += steps
+        gTd = float(np.sum(g * d))
+        if not gTd < 0.0:
+            st.status = "no-descent"
+            break
+        t = 1.0
+        accepted = False
+        for _ in range(p.max_ls):
+            st.ls_trials += 1
+            Jt = objective.evaluate(T, u + t * d, frames, h, p, want_grad=False)["J"]
+            if Jt <= J + p.armijo_c * t * gTd:
+                accepted = True
+                break
+            t *= 0.5
+        if not accepted:
+            st.status = "line-search"
+            break
+        u = u + t * d
+        step_norm = t * float(np.sqrt(np.sum(d * d)))
+        J_old = J
+        ev = objective.evaluate(T, u, frames, h, p)
+        J, g = ev["J"], ev["g"]
+        it += 1
+    st.J, st.D, st.S, st.P = ev["J"], ev["D"], ev["S"], ev["P"]
+    st.gn_iters = it
+    return u, st
