@@ -1,0 +1,378 @@
+"""Benchmark: frames registered per second by spatio-temporal multilevel (STML)
+registration of a 200-frame 256x256 OCT-like sequence (4 spatial x 3 temporal
+levels), with the Gauss-Newton Hessian-product kernel's HBM throughput.
+
+One step = one full registration of the sequence through the C ABI
+(pyramid build, predictor-corrector sweep over all levels, Gauss-Newton/PCG),
+inputs resident in device memory.  Run with no flags for 1 GPU; under
+torchrun every rank registers its own replica (no data-path collective).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (the method has no other reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames registered/s at fixed objective tol; GN-matvec HBM GB/s vs peak"
+
+WORKLOADS = {
+    # name: (n, shape, levels, tlevels, spec factory name)
+    "paper-scale": (200, (256, 256), 4, 3, "spec_paper_scale"),
+    "tiny": (16, (64, 64), 2, 2, "spec_tiny"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="paper-scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="stml", choices=["stml", "spml"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-spml", action="store_true")
+    ap.add_argument("--cpu-sample-frames", type=int, default=9)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def matvec_traffic_per_pixel_frame():
+    """DRAM bytes per pixel-frame of the Hessian-product kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "gn_matvec_paper_scale.md")
+    src = os.path.join(ROOT, "paper_2001_06613_gb300", "csrc", "k_hessian.cu")
+    try:
+        txt = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for ln in txt.splitlines():
+            if ":" in ln and ln.strip().startswith("- "):
+                k, v = ln.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("k_hessian.cu sha256[:16]") != digest:
+            return None
+        return float(vals["dram bytes per pixel-frame"])
+    except Exception:
+        return None
+
+
+def make_sequence(workload: str, seed_offset: int = 0):
+    from paper_2001_06613_gb300 import synthetic
+    n, shape, L, Q, factory = WORKLOADS[workload]
+    spec = getattr(synthetic, factory)()
+    spec.seed += seed_offset
+    return synthetic.make_sequence(spec), spec
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_sample(R: np.ndarray, workload: str, frames: int):
+    """Register the first `frames` frames (full spatial size, same level
+    structure) with the FP64 oracle; returns (frames/s, seconds)."""
+    from oracle import Params, multilevel
+    n, shape, L, Q, _ = WORKLOADS[workload]
+    p = Params(n_levels=L, n_tlevels=Q)
+    sub = R[:frames].astype(np.float64)
+    t0 = time.perf_counter()
+    multilevel.register(sub, p, "stml")
+    dt = time.perf_counter() - t0
+    return frames / dt, dt
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    R, _ = make_sequence(args.workload)
+    n = WORKLOADS[args.workload][0]
+    frames = min(args.cpu_sample_frames, n)
+    for _ in range(args.warmup):
+        oracle_sample(R, args.workload, frames)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample(R, args.workload, frames)
+        times.append(dt)
+    total = sum(times)
+    value = frames * len(times) / total
+    sample = (f"first {frames} of {n} frames at full size, same spatial/temporal levels, "
+              f"numpy FP64, one registration per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_frames": n, "sample_frames": frames},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_native(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2001_06613_gb300 as S
+    S.load()
+
+    n, shape, L, Q, _ = WORKLOADS[args.workload]
+    R, spec = make_sequence(args.workload, seed_offset=rank)
+    mode = S.MODE_STML if args.mode == "stml" else S.MODE_SPML
+    prm = S.stml_default_params(n_levels=L, n_tlevels=Q)
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(prm, stream.cuda_stream)
+    R_dev = torch.from_numpy(R).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
+
+    def step():
+        S.stml_load_sequence(ctx.ptr, R_dev)          # device-to-device: inputs already in HBM
+        S.stml_build_pyramid(ctx.ptr)
+        return S.stml_register(ctx.ptr, mode)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = S.stml_launch_count()
+    S.stml_profile_enable(ctx.ptr, True)
+    stats = None
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        for i in range(args.steps):
+            flush.zero_()                                 # evict the previous step from L2
+            ev[i][0].record(stream)
+            stats = step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = S.stml_launch_count() - launches0 - 0
+    prof = S.stml_profile_read(ctx.ptr)
+    S.stml_profile_enable(ctx.ptr, False)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms_total = max_over_ranks(sum(ms_steps), world, dev)
+    frames_all = sum_over_ranks(float(n * args.steps), world, dev)
+    value = frames_all / (ms_total / 1e3)
+
+    # final objective over all frames on the finest level
+    y = torch.empty((n, len(shape)) + tuple(shape), dtype=torch.float32, device=dev)
+    S.stml_get_field(ctx.ptr, L - 1, y)
+    outJ = S.stml_eval(ctx.ptr, L - 1, list(range(n)), y)
+
+    # end to end through the public API with host buffers
+    R_host = torch.from_numpy(R).pin_memory()
+    y_host = torch.empty((n, len(shape)) + tuple(shape), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        S.stml_load_sequence(ctx.ptr, R_host)
+        S.stml_build_pyramid(ctx.ptr)
+        S.stml_register(ctx.ptr, mode)
+        S.stml_get_field(ctx.ptr, L - 1, y_host)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = sum_over_ranks(float(n * e2e_steps), world, dev) / e2e_s
+
+    # spatial-only multilevel on the same data (the paper's comparison)
+    spml = None
+    if not args.no_spml and mode == S.MODE_STML:
+        sp_steps = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(sp_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            S.stml_load_sequence(ctx.ptr, R_dev)
+            S.stml_build_pyramid(ctx.ptr)
+            S.stml_register(ctx.ptr, S.MODE_SPML)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(b))
+        S.stml_get_field(ctx.ptr, L - 1, y)
+        outJs = S.stml_eval(ctx.ptr, L - 1, list(range(n)), y)
+        spml_fps = n / (statistics.mean(t) / 1e3)
+        spml = {"frames_per_s": spml_fps, "final_J": outJs[0],
+                "stml_over_spml_speedup": (value / world) / spml_fps if world else None,
+                "paper_speedup": "2.5x average (Sec. 4, Table 1; hardware not stated)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        frames = min(args.cpu_sample_frames, n)
+        fps, dt = oracle_sample(R, args.workload, frames)
+        cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {frames} of {n} frames, full 256x256, same levels; numpy FP64 "
+                         f"single thread; {dt:.1f} s"}
+
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = prof["bytes"] / (prof["ms"] / 1e3) / 1e9 if prof["ms"] > 0 else None
+    tpf = matvec_traffic_per_pixel_frame()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": (tpf * prof["pixel_frames"] / prof["launches"]) if tpf and prof["launches"] else None,
+            "kernel": "GN Hessian product (hv_sums + hv_apply)",
+            "algorithmic_bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
+            "launches": prof["launches"], "ms_total": prof["ms"],
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s (of fallback)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {n} frames {shape[0]}x{shape[1]} fp32, "
+                                       f"{L} spatial x {Q} temporal levels, {args.mode.upper()}",
+                           "n_frames": n, "shape": list(shape), "levels": L, "tlevels": Q,
+                           "mode": args.mode, "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": f"replicas x{world}"},
+                "clocks": clk.summary(), "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": "frames/s",
+                        "h2d_bytes_per_step": int(R.nbytes), "d2h_bytes_per_step": int(y_host.numel() * 4)},
+                "roofline": roof, "cpu_baseline": cpu, "final_J": outJ[0],
+                "per_step_ms": ms_steps,
+                "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
+                                                 "ls_trials", "stopped_early")} for s in stats],
+                "spml": spml}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

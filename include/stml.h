@@ -1,0 +1,228 @@
+/*
+ * stml.h -- C ABI of the GB300 spatio-temporal multilevel (STML) registration library.
+ *
+ * The library registers an image sequence groupwise (Sec. 2, eq. 1 of
+ * Aggrawal & Modersitzki, "Accelerating the Registration of Image Sequences by
+ * Spatio-temporal Multilevel Strategies") with the predictor-corrector sweep
+ * over a spatial pyramid and a temporal binary tree (Sec. 3, Fig. 1, eqs. 2-3).
+ * Every step of the computation runs in CUDA kernels on one GPU; this header
+ * uses plain pointers and sizes only.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Grids are cell-centred.  `shape` lists the cells per axis in C order
+ *   (2-D: {ny, nx}; 3-D: {nz, ny, nx}); x varies fastest in memory.  Level 0 is
+ *   the coarsest of `n_levels` spatial levels; level l has cell width
+ *   h = 2^(n_levels-1-l) finest pixels and shape = finest_shape / h.
+ * - Images: float32, layout [frame][z][y][x].
+ * - Displacement fields: float32, layout [frame][component][z][y][x] in finest
+ *   pixel units; component c moves along axis c of `shape` (2-D: c=0 is y,
+ *   c=1 is x).  The transformation of frame k is y_k(x) = x + u_k(x).
+ * - Frame subsets (`frames`, `K`) are host int arrays of strictly increasing
+ *   0-based frame numbers.
+ * - Pointers documented as "device" must point to device memory of the GPU
+ *   that was current when the context was created; "host" pointers to host
+ *   memory.  The library never takes ownership of caller memory.
+ * - All work is ordered on the CUDA stream given to stml_create (or passed to
+ *   the context-free operators); calls that return host values synchronise
+ *   that stream only.
+ * - No C++ exception crosses this boundary.  Every entry point returns a
+ *   stml_status; on error, stml_last_error() describes it.  A context stays
+ *   usable after STML_EINVAL; after STML_ECUDA it should be destroyed.
+ */
+#ifndef STML_H
+#define STML_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stml_ctx stml_ctx;   /* opaque; owns all device memory it allocates */
+
+typedef enum {
+    STML_OK = 0,
+    STML_EINVAL = -1,        /* bad argument or shape */
+    STML_ENOMEM = -2,        /* device allocation failed */
+    STML_ECUDA = -3,         /* a CUDA call failed */
+    STML_ENONFINITE = -4,    /* a NaN or Inf appeared in the objective */
+    STML_EBREAKDOWN = -5,    /* PCG met p^T H p <= 0 */
+    STML_ELINESEARCH = -6,   /* Armijo found no acceptable step */
+    STML_ETIMEOUT = -7,      /* a bounded device wait expired */
+    STML_ESTATE = -8         /* call out of order (e.g. no sequence loaded) */
+} stml_status;
+
+typedef enum { STML_MODE_STML = 0, STML_MODE_SPML = 1 } stml_mode;
+
+/* Solver parameters.  Objective terms (Sec. 2, eq. 1):
+ *   J = hd/2 sum_k ||a_k - mean_j a_j||^2                       (distance, a_k = R_k o y_k)
+ *     + alpha/2 hd sum_k sum_c sum_i ||d_i u_{k,c}||^2           (spatial diffusion S)
+ *     + alpha_t/2 hd sum_{consecutive k<k' in K} ||u_k' - u_k||^2 / (k'-k)^2
+ *     + lambda hd ||(1/|K|) sum_j u_j||^2                         (penalty P)
+ * with hd the cell volume of the level.  beta weighs eq. (2); eps_stop is the
+ * relative per-frame tolerance of the stopping rule eq. (3). */
+typedef struct {
+    double alpha, alpha_t, lambda;
+    double beta;
+    double eps_stop;
+    int stop_rule;           /* 1: apply eq. (3) for q > 0 */
+    int n_levels;            /* spatial levels L >= 1 */
+    int n_tlevels;           /* temporal levels Q >= 1 (q = 0..Q-1) */
+    double tol_J, tol_Y, tol_G, g_abs;   /* Gauss-Newton stopping tests */
+    int max_gn;
+    double tol_cg;           /* PCG stops when ||r|| <= tol_cg ||g|| */
+    int max_cg;
+    int max_ls;              /* Armijo trials */
+    double armijo_c;
+} stml_params;
+
+typedef struct {
+    int level, tlevel, n_frames;
+    int gn_iters, cg_iters, ls_trials;
+    int stopped_early;       /* eq. (3) ended this level after this temporal level */
+    int status;              /* stml_status of the GIR (0, ELINESEARCH, EBREAKDOWN ...) */
+    double J0, J, D, S, P;   /* objective at start and end of the GIR */
+    double seconds;          /* wall time of the GIR on the stream */
+} stml_stats;
+
+/* Fills *p with the library defaults (alpha 0.02, lambda 1, beta 1e-5, ...). */
+void stml_default_params(stml_params* p);
+
+/* Creates a context that will work on `cuda_stream` (a cudaStream_t, or NULL
+ * for the legacy default stream) of the current device.  Returns STML_EINVAL
+ * for invalid parameters. */
+stml_status stml_create(const stml_params* p, void* cuda_stream, stml_ctx** out);
+
+/* Frees every device allocation of the context. NULL is ignored. */
+void stml_destroy(stml_ctx* ctx);
+
+/* Text of the last error on ctx, or of the last context-free call when ctx is NULL. */
+const char* stml_last_error(const stml_ctx* ctx);
+
+/* Replaces the parameters (level counts must match the loaded sequence, if any). */
+stml_status stml_set_params(stml_ctx* ctx, const stml_params* p);
+
+/* ------------------------------------------------------------------ data */
+
+/* Copies n_frames images of `shape` (dim = 2 or 3) from `frames` (host, or
+ * device when on_device != 0) into library memory.  Every axis must be
+ * divisible by 2^(n_levels-1).  Allocates all level buffers. */
+stml_status stml_load_sequence(stml_ctx* ctx, const float* frames, int on_device,
+                               int n_frames, int dim, const int* shape);
+
+/* Builds the image pyramid by 2^d block means (Sec. 3; Sec. 4: smoothing in
+ * space only) and the temporal sets K_q (Fig. 1). */
+stml_status stml_build_pyramid(stml_ctx* ctx);
+
+/* Shape (3 ints, z first; 1 for a missing axis) and cell width of a level. */
+stml_status stml_level_info(const stml_ctx* ctx, int level, int* shape3, double* h);
+
+/* Frames of K_q (Fig. 1): *count receives |K_q|; up to cap numbers are written. */
+stml_status stml_temporal_set(const stml_ctx* ctx, int tlevel, int* frames, int cap, int* count);
+
+/* Copies the images of all frames at `level` to dst (n * N floats). */
+stml_status stml_get_images(stml_ctx* ctx, int level, float* dst, int dst_on_device);
+
+/* Copies y_{level,all} (n * d * N floats) to dst / from src. */
+stml_status stml_get_field(stml_ctx* ctx, int level, float* dst, int dst_on_device);
+stml_status stml_set_field(stml_ctx* ctx, int level, const float* src, int src_on_device);
+
+/* --------------------------------------------------------------- drivers */
+
+/* Registers the loaded sequence from the coarsest to the finest level.
+ * STML: predictor-corrector sweep over K_0..K_T at every level (Sec. 3) with
+ * the stopping rule eq. (3); SpML: one GIR over all frames per level.
+ * Per-GIR statistics go to stats[0..cap) and their number to *n_written
+ * (either may be NULL).  The result is available via stml_get_field. */
+stml_status stml_register(stml_ctx* ctx, stml_mode mode, stml_stats* stats, int cap,
+                          int* n_written);
+
+/* One predictor step of the STML sweep (Sec. 3): start values z_{l,q} on all
+ * frames -- Id (level 0, q = 0), the prolongated y_{l-1,all} (q = 0), the
+ * linear rule (level 0) or eq. (2) (finer levels) from y_{l,q-1}. */
+stml_status stml_predict(stml_ctx* ctx, int level, int tlevel);
+
+/* One corrector step: y_{l,q} = GIR(l, K_q) from z_{l,q}; applies eq. (3) for
+ * q > 0 and, when it fires or q = T, completes y_{l,all}.  *finished (may be
+ * NULL) is set to 1 when the level is complete. */
+stml_status stml_correct(stml_ctx* ctx, int level, int tlevel, stml_stats* stats, int* finished);
+
+/* --------------------------------------------- building blocks (device) */
+
+/* Objective of eq. (1) with S and P on the level-`level` images of `frames`
+ * at fields u (device, nK * d * N floats).  out (host, 6 doubles) receives
+ * J, D, S, P, ||g||^2, ||u||^2.  g and dT (device, nK * d * N floats each)
+ * receive the gradient and grad T_k(x + u_k(x)); pass NULL for both to
+ * evaluate the objective only (then out[4] = 0). */
+stml_status stml_eval(stml_ctx* ctx, int level, const int* frames, int nK, const float* u,
+                      double* out, float* g, float* dT);
+
+/* Gauss-Newton Hessian product Hv = J^T J v + alpha hd B^T B v + alpha_t hd L_t v
+ * + 2 lambda hd / |K|^2 sum_j v_j (device arrays of nK * d * N floats, dT as
+ * returned by stml_eval).  *vHv (host, may be NULL) receives <v, Hv>. */
+stml_status stml_hessvec(stml_ctx* ctx, int level, const int* frames, int nK,
+                         const float* dT, const float* v, float* Hv, double* vHv);
+
+/* Runs the Gauss-Newton/PCG/Armijo scheme on the frames of K starting from
+ * u (device, nK * d * N floats, overwritten with the result). */
+stml_status stml_gir(stml_ctx* ctx, int level, const int* frames, int nK, float* u,
+                     stml_stats* stats);
+
+/* Correlation coefficients rho_{k,k+1} of consecutive frames at `level`
+ * (Sec. 4, Table 1); rho (host) receives n - 1 doubles. */
+stml_status stml_corr_coeff(stml_ctx* ctx, int level, double* rho);
+
+/* ------------------------------------ context-free operators (device) */
+
+/* 2^d block mean of `planes` images of fine_shape into coarse (Sec. 3). */
+stml_status stml_restrict(const float* fine, float* coarse, int planes, int dim,
+                          const int* fine_shape, void* cuda_stream);
+
+/* Cell-centred multilinear prolongation P (clamp at the border) of `planes`
+ * scalar planes of coarse_shape to 2 * coarse_shape. */
+stml_status stml_prolong(const float* coarse, float* fine, int planes, int dim,
+                         const int* coarse_shape, void* cuda_stream);
+
+/* Transpose P^T of stml_prolong, as a gather with a fixed summation order. */
+stml_status stml_prolong_adjoint(const float* fine, float* coarse, int planes, int dim,
+                                 const int* coarse_shape, void* cuda_stream);
+
+/* Linear temporal predictor (Sec. 3, coarsest level): for every target frame
+ * t in `targets` (host, nT frames) z[t] = yK[t] if t is in K, else the linear
+ * interpolation of its neighbours left(t), right(t) in K.  yK holds nK planes
+ * of plane_elems floats in the order of K, z holds nT planes in the order of
+ * targets (device). */
+stml_status stml_predict_linear(const float* yK, const int* K, int nK, float* z,
+                                const int* targets, int nT, size_t plane_elems,
+                                void* cuda_stream);
+
+/* Least-squares temporal predictor, eq. (2), for n_comp independent
+ * (pixel, component) series: eta (device, nK * n_comp floats, frames of K in
+ * order), omega and zeta (device, n * n_comp floats, frame-major).  Solved by
+ * Thomas' algorithm with one factorisation of D_K + beta L for all series. */
+stml_status stml_predict_ls(const float* eta, const int* K, int nK, const float* omega,
+                            float* zeta, int n, double beta, size_t n_comp,
+                            void* cuda_stream);
+
+/* ------------------------------------------------------------ profiling */
+
+/* Enables (1) or disables (0) CUDA-event timing of every launch of the
+ * Gauss-Newton Hessian-product kernel on the context's stream, and resets
+ * the counters. */
+stml_status stml_profile_enable(stml_ctx* ctx, int enable);
+
+/* Reads the counters: launches, summed device milliseconds, summed
+ * algorithmic bytes (read v, read grad T, write Hv: 12 d bytes per
+ * pixel-frame) and summed pixel-frames.  Synchronises the stream. */
+stml_status stml_profile_read(stml_ctx* ctx, long long* launches, double* ms, double* bytes,
+                              double* pixel_frames);
+
+/* Number of this library's kernel launches since the context was created. */
+long long stml_launch_count(const stml_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STML_H */

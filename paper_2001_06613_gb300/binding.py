@@ -1,0 +1,327 @@
+"""Thin ctypes binding of ``libstml.so`` (include/stml.h).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name.  Device buffers are passed as ``torch`` CUDA tensors (their
+``data_ptr()``), host buffers as numpy arrays.  There is no fallback: if the
+library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstml.so")
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EBREAKDOWN",
+          -6: "ELINESEARCH", -7: "ETIMEOUT", -8: "ESTATE"}
+MODE_STML, MODE_SPML = 0, 1
+
+
+class StmlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"stml error {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("alpha_t", C.c_double), ("lambda_", C.c_double),
+                ("beta", C.c_double), ("eps_stop", C.c_double), ("stop_rule", C.c_int),
+                ("n_levels", C.c_int), ("n_tlevels", C.c_int),
+                ("tol_J", C.c_double), ("tol_Y", C.c_double), ("tol_G", C.c_double),
+                ("g_abs", C.c_double), ("max_gn", C.c_int), ("tol_cg", C.c_double),
+                ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [("level", C.c_int), ("tlevel", C.c_int), ("n_frames", C.c_int),
+                ("gn_iters", C.c_int), ("cg_iters", C.c_int), ("ls_trials", C.c_int),
+                ("stopped_early", C.c_int), ("status", C.c_int),
+                ("J0", C.c_double), ("J", C.c_double), ("D", C.c_double), ("S", C.c_double),
+                ("P", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp, _ip, _dp, _fp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p
+
+_SIGS = {
+    "stml_default_params": (None, [C.POINTER(Params)]),
+    "stml_create": (C.c_int, [C.POINTER(Params), _vp, C.POINTER(_vp)]),
+    "stml_destroy": (None, [_vp]),
+    "stml_last_error": (C.c_char_p, [_vp]),
+    "stml_set_params": (C.c_int, [_vp, C.POINTER(Params)]),
+    "stml_load_sequence": (C.c_int, [_vp, _fp, C.c_int, C.c_int, C.c_int, _ip]),
+    "stml_build_pyramid": (C.c_int, [_vp]),
+    "stml_level_info": (C.c_int, [_vp, C.c_int, _ip, _dp]),
+    "stml_temporal_set": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _ip]),
+    "stml_get_images": (C.c_int, [_vp, C.c_int, _fp, C.c_int]),
+    "stml_get_field": (C.c_int, [_vp, C.c_int, _fp, C.c_int]),
+    "stml_set_field": (C.c_int, [_vp, C.c_int, _fp, C.c_int]),
+    "stml_register": (C.c_int, [_vp, C.c_int, C.POINTER(Stats), C.c_int, _ip]),
+    "stml_predict": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "stml_correct": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(Stats), _ip]),
+    "stml_eval": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, _dp, _fp, _fp]),
+    "stml_hessvec": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, _fp, _fp, _dp]),
+    "stml_gir": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, C.POINTER(Stats)]),
+    "stml_corr_coeff": (C.c_int, [_vp, C.c_int, _dp]),
+    "stml_restrict": (C.c_int, [_fp, _fp, C.c_int, C.c_int, _ip, _vp]),
+    "stml_prolong": (C.c_int, [_fp, _fp, C.c_int, C.c_int, _ip, _vp]),
+    "stml_prolong_adjoint": (C.c_int, [_fp, _fp, C.c_int, C.c_int, _ip, _vp]),
+    "stml_predict_linear": (C.c_int, [_fp, _ip, C.c_int, _fp, _ip, C.c_int, C.c_size_t, _vp]),
+    "stml_predict_ls": (C.c_int, [_fp, _ip, C.c_int, _fp, _fp, C.c_int, C.c_double, C.c_size_t, _vp]),
+    "stml_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "stml_profile_read": (C.c_int, [_vp, C.POINTER(C.c_longlong), _dp, _dp, _dp]),
+    "stml_launch_count": (C.c_longlong, [_vp]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libstml.so (built in-tree by ``_build.build``); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2001_06613_gb300._build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> List[str]:
+    return list(_SIGS)
+
+
+# ------------------------------------------------------------------ helpers
+def _ints(seq: Sequence[int]):
+    arr = (C.c_int * len(seq))(*[int(v) for v in seq])
+    return arr
+
+
+def _dev(t) -> int:
+    """Device pointer of a CUDA tensor (float32, contiguous)."""
+    if t is None:
+        return None
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _ptr(x):
+    """(pointer, on_device) for a CUDA tensor or a host numpy array / CPU tensor."""
+    if hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), int(x.is_cuda)
+    if not isinstance(x, np.ndarray) or not x.flags["C_CONTIGUOUS"] or x.dtype != np.float32:
+        raise TypeError("host buffers must be C-contiguous float32 numpy arrays")
+    return x.ctypes.data, 0
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        raise StmlError(status, stml_last_error(ctx))
+
+
+# ------------------------------------------------------------------ API
+def stml_default_params(**overrides) -> Params:
+    p = Params()
+    load().stml_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k in ("lambda", "lam") else k, v)
+    return p
+
+
+def stml_create(params: Params, stream=None):
+    out = _vp()
+    _check(load().stml_create(C.byref(params), _stream(stream), C.byref(out)))
+    return out
+
+
+def stml_destroy(ctx):
+    if ctx:
+        load().stml_destroy(ctx)
+
+
+def stml_last_error(ctx=None) -> str:
+    s = load().stml_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def stml_set_params(ctx, params: Params):
+    _check(load().stml_set_params(ctx, C.byref(params)), ctx)
+
+
+def stml_load_sequence(ctx, frames, shape: Optional[Sequence[int]] = None):
+    """frames: (n, *shape) float32 CUDA tensor or host array."""
+    shape = list(frames.shape[1:]) if shape is None else list(shape)
+    if hasattr(frames, "dtype") and str(frames.dtype) not in ("float32", "torch.float32"):
+        raise TypeError("frames must be float32")
+    if not hasattr(frames, "is_cuda"):
+        frames = np.ascontiguousarray(frames, dtype=np.float32)
+    ptr, on_dev = _ptr(frames)
+    _check(load().stml_load_sequence(ctx, ptr, on_dev, int(frames.shape[0]), len(shape), _ints(shape)), ctx)
+
+
+def stml_build_pyramid(ctx):
+    _check(load().stml_build_pyramid(ctx), ctx)
+
+
+def stml_level_info(ctx, level: int):
+    sh = (C.c_int * 3)()
+    h = C.c_double()
+    _check(load().stml_level_info(ctx, level, sh, C.byref(h)), ctx)
+    return tuple(sh), h.value
+
+
+def stml_temporal_set(ctx, tlevel: int) -> List[int]:
+    cnt = C.c_int()
+    _check(load().stml_temporal_set(ctx, tlevel, None, 0, C.byref(cnt)), ctx)
+    buf = (C.c_int * cnt.value)()
+    _check(load().stml_temporal_set(ctx, tlevel, buf, cnt.value, C.byref(cnt)), ctx)
+    return list(buf)
+
+
+def stml_get_images(ctx, level: int, out):
+    ptr, on_dev = _ptr(out)
+    _check(load().stml_get_images(ctx, level, ptr, on_dev), ctx)
+    return out
+
+
+def stml_get_field(ctx, level: int, out):
+    ptr, on_dev = _ptr(out)
+    _check(load().stml_get_field(ctx, level, ptr, on_dev), ctx)
+    return out
+
+
+def stml_set_field(ctx, level: int, src):
+    ptr, on_dev = _ptr(src)
+    _check(load().stml_set_field(ctx, level, ptr, on_dev), ctx)
+
+
+def stml_register(ctx, mode: int = MODE_STML, cap: int = 512):
+    stats = (Stats * cap)()
+    n = C.c_int()
+    _check(load().stml_register(ctx, mode, stats, cap, C.byref(n)), ctx)
+    return [stats[i].as_dict() for i in range(min(n.value, cap))]
+
+
+def stml_predict(ctx, level: int, tlevel: int):
+    _check(load().stml_predict(ctx, level, tlevel), ctx)
+
+
+def stml_correct(ctx, level: int, tlevel: int):
+    st = Stats()
+    fin = C.c_int()
+    _check(load().stml_correct(ctx, level, tlevel, C.byref(st), C.byref(fin)), ctx)
+    return st.as_dict(), bool(fin.value)
+
+
+def stml_eval(ctx, level: int, frames: Sequence[int], u, g=None, dT=None) -> np.ndarray:
+    out = (C.c_double * 6)()
+    _check(load().stml_eval(ctx, level, _ints(frames), len(frames), _dev(u), out, _dev(g), _dev(dT)), ctx)
+    return np.array(out[:])
+
+
+def stml_hessvec(ctx, level: int, frames: Sequence[int], dT, v, Hv) -> float:
+    vhv = C.c_double()
+    _check(load().stml_hessvec(ctx, level, _ints(frames), len(frames), _dev(dT), _dev(v), _dev(Hv),
+                               C.byref(vhv)), ctx)
+    return vhv.value
+
+
+def stml_gir(ctx, level: int, frames: Sequence[int], u) -> dict:
+    st = Stats()
+    _check(load().stml_gir(ctx, level, _ints(frames), len(frames), _dev(u), C.byref(st)), ctx)
+    return st.as_dict()
+
+
+def stml_corr_coeff(ctx, level: int, n: int) -> np.ndarray:
+    rho = (C.c_double * max(1, n - 1))()
+    _check(load().stml_corr_coeff(ctx, level, rho), ctx)
+    return np.array(rho[:n - 1])
+
+
+def stml_restrict(fine, coarse, planes: int, fine_shape: Sequence[int], stream=None):
+    _check(load().stml_restrict(_dev(fine), _dev(coarse), planes, len(fine_shape), _ints(fine_shape),
+                                _stream(stream)))
+
+
+def stml_prolong(coarse, fine, planes: int, coarse_shape: Sequence[int], stream=None):
+    _check(load().stml_prolong(_dev(coarse), _dev(fine), planes, len(coarse_shape), _ints(coarse_shape),
+                               _stream(stream)))
+
+
+def stml_prolong_adjoint(fine, coarse, planes: int, coarse_shape: Sequence[int], stream=None):
+    _check(load().stml_prolong_adjoint(_dev(fine), _dev(coarse), planes, len(coarse_shape),
+                                       _ints(coarse_shape), _stream(stream)))
+
+
+def stml_predict_linear(yK, K: Sequence[int], z, targets: Sequence[int], plane_elems: int, stream=None):
+    _check(load().stml_predict_linear(_dev(yK), _ints(K), len(K), _dev(z), _ints(targets), len(targets),
+                                      plane_elems, _stream(stream)))
+
+
+def stml_predict_ls(eta, K: Sequence[int], omega, zeta, n: int, beta: float, n_comp: int, stream=None):
+    _check(load().stml_predict_ls(_dev(eta), _ints(K), len(K), _dev(omega), _dev(zeta), n, beta, n_comp,
+                                  _stream(stream)))
+
+
+def stml_profile_enable(ctx, enable: bool = True):
+    _check(load().stml_profile_enable(ctx, int(enable)), ctx)
+
+
+def stml_profile_read(ctx):
+    n = C.c_longlong()
+    ms, by, pf = C.c_double(), C.c_double(), C.c_double()
+    _check(load().stml_profile_read(ctx, C.byref(n), C.byref(ms), C.byref(by), C.byref(pf)), ctx)
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value, "pixel_frames": pf.value}
+
+
+def stml_launch_count(ctx=None) -> int:
+    return int(load().stml_launch_count(ctx))
+
+
+class Context:
+    """Owns one stml_ctx; destroys it on close()/garbage collection."""
+
+    def __init__(self, params: Params, stream=None):
+        self.params = params
+        self.ptr = stml_create(params, stream)
+
+    def close(self):
+        if self.ptr:
+            stml_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,266 @@
+// Shared device helpers of the STML library: level geometry, interpolation,
+// stencils and the deterministic two-stage FP64 reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stml {
+
+constexpr int kThreads = 256;          // threads per CTA of the elementwise kernels
+constexpr int kMaxRed = 8;             // values one reduction carries
+
+// One spatial level.  Axes are (z, y, x) with x fastest; a 2-D level has nz = 1.
+// Component c of a field moves along axis (3 - d) + c of (z, y, x).
+struct Geom {
+    int nx, ny, nz;
+    int d;
+    long long N;          // cells per frame
+    float h, inv_h, hd;   // cell width, its inverse (a power of two), cell volume h^d
+};
+
+// Device-resident scalars of one context.  The reducing kernels write their
+// totals here; the PCG kernels keep their coefficients here so that no value
+// has to travel to the host inside the conjugate-gradient loop.
+struct DevScalars {
+    double red[kMaxRed];      // totals of the last evaluation (J, D, S, P, |g|^2, |u|^2, ...)
+    double trial[kMaxRed];    // totals of the last objective-only evaluation
+    double dots[kMaxRed];     // totals of the last dot-product kernel
+    double rho, bnorm2, pq, alpha, beta, rnorm2;
+    int cg_active, cg_iter, cg_flag, cg_pad;
+    unsigned int ticket[8];   // arrival counters of the last-CTA reduction
+};
+
+enum CgFlag { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_ZERO = 4 };
+
+// Per-GIR description of the frame subset K in device memory.
+struct FrameSet {
+    const int* frames;      // frame numbers of K (index into the image array)
+    const float* w_next;    // 1/(k_{j+1} - k_j)^2, 0 for the last frame of K
+    int nK;
+};
+
+// Constant coefficients of one objective evaluation.
+struct Coef {
+    float alpha_hd;     // alpha * hd
+    float alphat_hd;    // alpha_t * hd
+    float pen_g;        // 2 lambda hd / |K|   (penalty gradient factor on ubar)
+    float pen_h;        // 2 lambda hd / |K|^2 (penalty Hessian factor on sum_j v_j)
+    float lam_hd;       // lambda * hd
+    float half_hd;      // hd / 2
+    float hd;
+    float inv_h2;       // 1 / h^2
+    float inv_nK;       // 1 / |K|
+    float diag_D;       // hd (1 - 1/|K|)
+};
+
+// ------------------------------------------------------------ coordinates
+__device__ __forceinline__ void unflatten(const Geom& g, long long p, int& x, int& y, int& z) {
+    x = (int)(p % g.nx);
+    long long r = p / g.nx;
+    y = (int)(r % g.ny);
+    z = (int)(r / g.ny);
+}
+
+// Stride of axis a (0 = z, 1 = y, 2 = x) in a plane.
+__device__ __forceinline__ long long axis_stride(const Geom& g, int a) {
+    return a == 2 ? 1LL : (a == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
+}
+
+// Number of neighbours inside the grid (all axes), i.e. h^2 * diag(B^T B).
+__device__ __forceinline__ int neighbour_count(const Geom& g, int x, int y, int z) {
+    int c = 0;
+    c += (x > 0) + (x < g.nx - 1);
+    c += (y > 0) + (y < g.ny - 1);
+    if (g.d == 3) c += (z > 0) + (z < g.nz - 1);
+    return c;
+}
+
+// (B^T B w)(p) * h^2 for one scalar plane w: sum over in-grid neighbours of
+// (w(p) - w(neighbour)); homogeneous Neumann boundary.
+__device__ __forceinline__ float neg_laplacian_h2(const float* __restrict__ w, const Geom& g,
+                                                  long long p, int x, int y, int z) {
+    const float c = w[p];
+    float acc = 0.f;
+    if (x > 0) acc += c - w[p - 1];
+    if (x < g.nx - 1) acc += c - w[p + 1];
+    if (y > 0) acc += c - w[p - g.nx];
+    if (y < g.ny - 1) acc += c - w[p + g.nx];
+    if (g.d == 3) {
+        const long long s = (long long)g.nx * g.ny;
+        if (z > 0) acc += c - w[p - s];
+        if (z < g.nz - 1) acc += c - w[p + s];
+    }
+    return acc;
+}
+
+// Sum of squared forward differences (times h^2) from p to its +x, +y (, +z)
+// neighbours, each interior edge counted once over the plane.
+__device__ __forceinline__ float forward_diff2_h2(const float* __restrict__ w, const Geom& g,
+                                                  long long p, int x, int y, int z) {
+    const float c = w[p];
+    float acc = 0.f;
+    if (x < g.nx - 1) { float t = w[p + 1] - c; acc += t * t; }
+    if (y < g.ny - 1) { float t = w[p + g.nx] - c; acc += t * t; }
+    if (g.d == 3 && z < g.nz - 1) { float t = w[p + (long long)g.nx * g.ny] - c; acc += t * t; }
+    return acc;
+}
+
+// ------------------------------------------------------------ interpolation
+// Index coordinate of a displaced cell centre along one axis, split exactly:
+// xi = i + u/h with u/h exact (h is a power of two), i0 = i + floor(u/h),
+// f = u/h - floor(u/h) exact in float32.
+__device__ __forceinline__ void split_coord(int i, float u, float inv_h, int& i0, float& f) {
+    float t = u * inv_h;
+    if (!(fabsf(t) < 1.0e7f)) {   // NaN, Inf or absurd: far outside the grid
+        i0 = -1000000000;
+        f = 0.f;
+        return;
+    }
+    float fl = floorf(t);
+    f = t - fl;
+    i0 = i + (int)fl;
+}
+
+__device__ __forceinline__ float fetch2(const float* __restrict__ T, int nx, int ny, int ix, int iy) {
+    return (ix >= 0 && ix < nx && iy >= 0 && iy < ny) ? __ldg(T + (long long)iy * nx + ix) : 0.f;
+}
+
+// Bilinear value and gradient (zero extension) of the level image T at the
+// cell centre (x, y) displaced by (uy, ux) physical units.
+__device__ __forceinline__ void interp2(const float* __restrict__ T, const Geom& g, int x, int y,
+                                        float uy, float ux, float& val, float& gy, float& gx) {
+    int iy, ix;
+    float fy, fx;
+    split_coord(y, uy, g.inv_h, iy, fy);
+    split_coord(x, ux, g.inv_h, ix, fx);
+    const float t00 = fetch2(T, g.nx, g.ny, ix, iy);
+    const float t01 = fetch2(T, g.nx, g.ny, ix + 1, iy);
+    const float t10 = fetch2(T, g.nx, g.ny, ix, iy + 1);
+    const float t11 = fetch2(T, g.nx, g.ny, ix + 1, iy + 1);
+    const float a0 = t00 + fx * (t01 - t00);
+    const float a1 = t10 + fx * (t11 - t10);
+    val = a0 + fy * (a1 - a0);
+    gx = g.inv_h * ((t01 - t00) + fy * ((t11 - t10) - (t01 - t00)));
+    gy = g.inv_h * (a1 - a0);
+}
+
+__device__ __forceinline__ float fetch3(const float* __restrict__ T, const Geom& g, int ix, int iy, int iz) {
+    return (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny && iz >= 0 && iz < g.nz)
+               ? __ldg(T + ((long long)iz * g.ny + iy) * g.nx + ix)
+               : 0.f;
+}
+
+// Trilinear value and gradient (zero extension), displacement (uz, uy, ux).
+__device__ __forceinline__ void interp3(const float* __restrict__ T, const Geom& g, int x, int y, int z,
+                                        float uz, float uy, float ux, float& val, float& gz,
+                                        float& gy, float& gx) {
+    int iz, iy, ix;
+    float fz, fy, fx;
+    split_coord(z, uz, g.inv_h, iz, fz);
+    split_coord(y, uy, g.inv_h, iy, fy);
+    split_coord(x, ux, g.inv_h, ix, fx);
+    float c[2][2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) c[a][b][e] = fetch3(T, g, ix + e, iy + b, iz + a);
+    // blend along x
+    float cx[2][2], dx[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            dx[a][b] = c[a][b][1] - c[a][b][0];
+            cx[a][b] = c[a][b][0] + fx * dx[a][b];
+        }
+    // along y
+    float cy[2], dy[2], dxy[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        dy[a] = cx[a][1] - cx[a][0];
+        cy[a] = cx[a][0] + fy * dy[a];
+        dxy[a] = dx[a][0] + fy * (dx[a][1] - dx[a][0]);
+    }
+    val = cy[0] + fz * (cy[1] - cy[0]);
+    gz = g.inv_h * (cy[1] - cy[0]);
+    gy = g.inv_h * (dy[0] + fz * (dy[1] - dy[0]));
+    gx = g.inv_h * (dxy[0] + fz * (dxy[1] - dxy[0]));
+}
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Two-stage deterministic reduction of NV values over the whole grid.
+//
+// Stage 1: every thread holds float partials over its few elements; a warp
+// sums them in float with a fixed butterfly, the warp totals are summed in
+// double in warp order and the CTA total goes to partials[cta * NV + i].
+// Stage 2: the CTA that arrives last (an integer ticket, no float atomics)
+// sums all CTA totals in double in a fixed order and writes out[0..NV).
+// The result depends only on the launch shape, never on scheduling.
+// Returns true in every thread of the last CTA (so it may finish the step).
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const float (&val)[NV], double* __restrict__ partials,
+                                            unsigned int* ticket, double* out) {
+    __shared__ double s_warp[kThreads / 32][NV];
+    __shared__ double s_fin[kThreads / 32][NV];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float w = warp_sum(val[i]);
+        if (lane == 0) s_warp[warp][i] = (double)w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += s_warp[w][i];
+            partials[(size_t)bid * NV + i] = s;
+        }
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) s += __ldcg(partials + (size_t)b * NV + i);
+        s = warp_sum_d(s);
+        if (lane == 0) s_fin[warp][i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += s_fin[w][i];
+            out[i] = s;
+        }
+        *ticket = 0u;
+    }
+    __syncthreads();
+    return true;
+}
+
+}  // namespace stml

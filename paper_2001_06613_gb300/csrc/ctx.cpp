@@ -1,0 +1,958 @@
+// Host runtime of the STML library: context and memory plan, the
+// Gauss-Newton/PCG/Armijo registration of a frame subset (the GIR of Sec. 2),
+// the spatio-temporal predictor-corrector sweep (Sec. 3, eqs. 2-3), the
+// spatial-only multilevel baseline and the C ABI of include/stml.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/stml.h"
+#include "kernels.h"
+
+using namespace stml;
+
+namespace {
+
+thread_local std::string g_free_error;   // error text of the context-free calls
+
+struct LevelBuf {
+    Geom g{};
+    int shape3[3] = {1, 1, 1};
+    float* img = nullptr;    // n * N
+    float* y = nullptr;      // n * d * N  (y_{l,all})
+};
+
+}  // namespace
+
+struct stml_ctx {
+    stml_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n = 0, d = 0;
+    int shape[3] = {1, 1, 1};            // finest level (z, y, x)
+    std::vector<LevelBuf> lv;
+    std::vector<std::vector<int>> sets;  // K_0 .. K_T
+    bool loaded = false, built = false;
+
+    // workspace, sized for the finest level and all frames
+    float *w_u = nullptr, *w_g = nullptr, *w_dT = nullptr, *w_x = nullptr, *w_r = nullptr,
+          *w_p = nullptr, *w_q = nullptr, *w_ut = nullptr;
+    float *w_a = nullptr, *w_m1 = nullptr, *w_m2 = nullptr;
+    float *w_z = nullptr, *w_z2 = nullptr;     // predictor state z_{l,q,all}
+    double* partials = nullptr;
+    size_t partials_cap = 0;                   // in doubles
+    DevScalars* S = nullptr;                   // device scalars
+    DevScalars* Sh = nullptr;                  // pinned host mirror
+    int* d_frames = nullptr;
+    float* d_wnext = nullptr;
+    int* d_idx = nullptr;
+    float* d_lsf = nullptr;                    // cp | inv_den | sub
+    int* d_kidx = nullptr;
+    LinTap* d_taps = nullptr;
+    double* d_rho = nullptr;
+
+    // STML sweep state
+    int cur_level = -1, last_q = -1;
+    double dhat_prev = 0.0;
+    bool level_done = false;
+
+    // profiling of the Hessian-product launches
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t ev_used = 0;
+    double prof_bytes = 0.0, prof_pf = 0.0;
+
+    std::string err;
+};
+
+namespace {
+
+stml_status fail(stml_ctx* c, stml_status s, const std::string& msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_free_error = msg;
+    return s;
+}
+
+stml_status cuda_fail(stml_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, STML_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+#define TRY(call)                           \
+    do {                                    \
+        stml_status s_ = (call);            \
+        if (s_ != STML_OK) return s_;       \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+bool valid_params(const stml_params* p, std::string& why) {
+    if (!p) { why = "params is NULL"; return false; }
+    if (p->n_levels < 1 || p->n_levels > 12) { why = "n_levels must be in 1..12"; return false; }
+    if (p->n_tlevels < 1 || p->n_tlevels > 20) { why = "n_tlevels must be in 1..20"; return false; }
+    if (!(p->alpha >= 0) || !(p->alpha_t >= 0) || !(p->lambda >= 0) || !(p->beta >= 0)) {
+        why = "alpha, alpha_t, lambda and beta must be >= 0";
+        return false;
+    }
+    if (p->max_gn < 0 || p->max_cg < 0 || p->max_ls < 1) { why = "iteration limits out of range"; return false; }
+    if (!(p->tol_cg > 0) || !(p->armijo_c > 0 && p->armijo_c < 1)) { why = "tol_cg > 0 and 0 < armijo_c < 1"; return false; }
+    return true;
+}
+
+Coef make_coef(const Geom& g, const stml_params& p, int nK) {
+    Coef c;
+    const double hd = g.hd;
+    c.alpha_hd = (float)(p.alpha * hd);
+    c.alphat_hd = (float)(p.alpha_t * hd);
+    c.pen_g = (float)(2.0 * p.lambda * hd / nK);
+    c.pen_h = (float)(2.0 * p.lambda * hd / ((double)nK * nK));
+    c.lam_hd = (float)(p.lambda * hd);
+    c.half_hd = (float)(0.5 * hd);
+    c.hd = (float)hd;
+    c.inv_h2 = (float)(1.0 / ((double)g.h * g.h));
+    c.inv_nK = (float)(1.0 / nK);
+    c.diag_D = (float)(hd * (1.0 - 1.0 / nK));
+    return c;
+}
+
+void free_buffers(stml_ctx* c) {
+    for (auto& L : c->lv) {
+        dfree(L.img);
+        dfree(L.y);
+    }
+    c->lv.clear();
+    dfree(c->w_u); dfree(c->w_g); dfree(c->w_dT); dfree(c->w_x); dfree(c->w_r);
+    dfree(c->w_p); dfree(c->w_q); dfree(c->w_ut); dfree(c->w_a); dfree(c->w_m1);
+    dfree(c->w_m2); dfree(c->w_z); dfree(c->w_z2); dfree(c->partials);
+    dfree(c->d_frames); dfree(c->d_wnext); dfree(c->d_idx); dfree(c->d_lsf);
+    dfree(c->d_kidx); dfree(c->d_taps); dfree(c->d_rho);
+    c->loaded = c->built = false;
+}
+
+std::vector<std::vector<int>> make_sets(int n, int Q) {
+    // K_q takes every 2^(T-q)-th frame; the last frame always belongs to K_q.
+    std::vector<std::vector<int>> sets;
+    const int T = Q - 1;
+    for (int q = 0; q < Q; ++q) {
+        const long long stride = 1LL << (T - q);
+        std::vector<int> K;
+        for (long long k = 0; k < n; k += stride) K.push_back((int)k);
+        if (K.back() != n - 1) K.push_back(n - 1);
+        sets.push_back(K);
+    }
+    return sets;
+}
+
+stml_status check_frames(stml_ctx* c, const int* frames, int nK) {
+    if (!frames || nK < 1 || nK > c->n) return fail(c, STML_EINVAL, "frame subset size out of range");
+    for (int j = 0; j < nK; ++j) {
+        if (frames[j] < 0 || frames[j] >= c->n) return fail(c, STML_EINVAL, "frame number out of range");
+        if (j > 0 && frames[j] <= frames[j - 1]) return fail(c, STML_EINVAL, "frames must increase strictly");
+    }
+    return STML_OK;
+}
+
+stml_status check_level(stml_ctx* c, int level) {
+    if (!c->built) return fail(c, STML_ESTATE, "no pyramid: call stml_load_sequence and stml_build_pyramid");
+    if (level < 0 || level >= (int)c->lv.size()) return fail(c, STML_EINVAL, "level out of range");
+    return STML_OK;
+}
+
+// Uploads K and the temporal weights 1/(k_{j+1} - k_j)^2.
+stml_status upload_frameset(stml_ctx* c, const std::vector<int>& K, FrameSet& fs) {
+    std::vector<float> w(K.size(), 0.f);
+    for (size_t j = 0; j + 1 < K.size(); ++j) {
+        const double dk = (double)(K[j + 1] - K[j]);
+        w[j] = (float)(1.0 / (dk * dk));
+    }
+    CK(c, cudaMemcpyAsync(c->d_frames, K.data(), K.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->d_wnext, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    fs.frames = c->d_frames;
+    fs.w_next = c->d_wnext;
+    fs.nK = (int)K.size();
+    return STML_OK;
+}
+
+stml_status read_scalars(stml_ctx* c) {
+    CK(c, cudaMemcpyAsync(c->Sh, c->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+stml_status hessvec_launch(stml_ctx* c, const Geom& g, const FrameSet& fs, const Coef& cf,
+                           const float* dT, const float* v, float* Hv, DevScalars* pcg) {
+    HessWork hw{c->w_m1, c->w_m2, c->partials, c->partials_cap};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+        if (c->ev_used == c->ev.size()) {
+            cudaEvent_t a, b;
+            CK(c, cudaEventCreate(&a));
+            CK(c, cudaEventCreate(&b));
+            c->ev.emplace_back(a, b);
+        }
+        e0 = c->ev[c->ev_used].first;
+        e1 = c->ev[c->ev_used].second;
+        c->ev_used++;
+        CK(c, cudaEventRecord(e0, c->stream));
+    }
+    CK(c, launch_hessvec(g, fs, cf, dT, v, Hv, hw, &c->S->ticket[1], c->S->dots + 4, pcg, c->stream));
+    if (c->prof) {
+        CK(c, cudaEventRecord(e1, c->stream));
+        const double pf = (double)fs.nK * (double)g.N;
+        c->prof_pf += pf;
+        c->prof_bytes += pf * 12.0 * g.d;
+    }
+    return STML_OK;
+}
+
+// ------------------------------------------------------------------ GIR
+// Gauss-Newton on the frames K of `level`, from and into u (nK * d * N floats).
+stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_io, stml_stats* st) {
+    const auto t_start = std::chrono::steady_clock::now();
+    LevelBuf& L = c->lv[level];
+    const Geom& g = L.g;
+    const int nK = (int)K.size();
+    const size_t M = (size_t)nK * g.d * g.N;
+    const stml_params& p = c->p;
+    FrameSet fs;
+    TRY(upload_frameset(c, K, fs));
+    const Coef cf = make_coef(g, p, nK);
+    EvalWork ew{c->w_a, c->w_m1, c->w_m2, c->partials, c->partials_cap};
+    float* u = u_io;
+    float* ut = c->w_ut;
+    DevScalars* S = c->S;
+    const PcgArgs pa{(float)p.tol_cg, p.max_cg};
+
+    stml_stats s{};
+    s.level = level;
+    s.n_frames = nK;
+    s.status = STML_OK;
+
+    auto eval_full = [&]() -> stml_status {
+        CK(c, launch_eval(L.img, g, fs, cf, u, nullptr, 0.f, c->w_dT, c->w_g, ew, &S->ticket[0], S->red, c->stream));
+        return read_scalars(c);
+    };
+
+    TRY(eval_full());
+    const double J0 = c->Sh->red[0];
+    double J = J0, D = c->Sh->red[1], Sv = c->Sh->red[2], Pv = c->Sh->red[3];
+    double gnorm2 = c->Sh->red[4], unorm2 = c->Sh->red[5];
+    s.J0 = J0;
+    double J_old = 0.0, step_norm = 0.0;
+    int it = 0;
+    for (;;) {
+        if (!std::isfinite(J) || !std::isfinite(gnorm2)) {
+            s.status = STML_ENONFINITE;
+            break;
+        }
+        const double gnorm = std::sqrt(gnorm2);
+        if (it > 0) {
+            const bool c1 = std::fabs(J_old - J) <= p.tol_J * (1.0 + std::fabs(J0));
+            const bool c2 = step_norm <= p.tol_Y * (1.0 + std::sqrt(unorm2));
+            const bool c3 = gnorm <= p.tol_G * (1.0 + std::fabs(J0));
+            if (c1 && c2 && c3) break;
+        }
+        if (gnorm <= p.g_abs * (1.0 + std::fabs(J0)) || it >= p.max_gn) break;
+
+        // --- PCG for H d = -g, all coefficients on the device
+        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, c->w_x, c->w_r, c->w_p, c->partials, S, pa, c->stream));
+        // iterations are launched in chunks; once the device clears
+        // cg_active the remaining launches of a chunk return at once
+        int launched = 0;
+        do {
+            const int chunk = std::min(4, p.max_cg - launched);
+            for (int i = 0; i < chunk; ++i) {
+                TRY(hessvec_launch(c, g, fs, cf, c->w_dT, c->w_p, c->w_q, S));
+                CK(c, launch_pcg_update(g, fs, cf, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->partials, S, pa, c->stream));
+                CK(c, launch_pcg_pupdate(g, fs, cf, c->w_dT, c->w_r, c->w_p, S, c->stream));
+            }
+            launched += chunk;
+            TRY(read_scalars(c));
+        } while (c->Sh->cg_active && launched < p.max_cg);
+        s.cg_iters += c->Sh->cg_iter;
+        if (c->Sh->cg_flag == CG_BREAKDOWN && c->Sh->cg_iter == 0)   // preconditioned gradient step
+            CK(c, cudaMemcpyAsync(c->w_x, c->w_p, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+
+        // --- directional derivative and Armijo back-tracking
+        CK(c, launch_dot2(c->w_g, c->w_x, M, c->partials, &S->ticket[3], S->dots, c->stream));
+        TRY(read_scalars(c));
+        const double gTd = c->Sh->dots[0], dnorm2 = c->Sh->dots[1];
+        if (!(gTd < 0.0)) {
+            s.status = STML_EBREAKDOWN;
+            break;
+        }
+        double t = 1.0;
+        bool accepted = false;
+        for (int ls = 0; ls < p.max_ls; ++ls) {
+            s.ls_trials++;
+            CK(c, launch_eval(L.img, g, fs, cf, u, c->w_x, (float)t, nullptr, nullptr, ew, &S->ticket[0], S->trial, c->stream));
+            TRY(read_scalars(c));
+            const double Jt = c->Sh->trial[0];
+            if (Jt <= J + p.armijo_c * t * gTd) {
+                accepted = true;
+                break;
+            }
+            t *= 0.5;
+        }
+        if (!accepted) {
+            s.status = STML_ELINESEARCH;
+            break;
+        }
+        CK(c, launch_axpy(u, c->w_x, (float)t, ut, M, c->stream));
+        std::swap(u, ut);
+        step_norm = t * std::sqrt(dnorm2);
+        J_old = J;
+        TRY(eval_full());
+        J = c->Sh->red[0];
+        D = c->Sh->red[1];
+        Sv = c->Sh->red[2];
+        Pv = c->Sh->red[3];
+        gnorm2 = c->Sh->red[4];
+        unorm2 = c->Sh->red[5];
+        ++it;
+    }
+    if (u != u_io) {
+        CK(c, cudaMemcpyAsync(u_io, u, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    s.gn_iters = it;
+    s.J = J;
+    s.D = D;
+    s.S = Sv;
+    s.P = Pv;
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (st) *st = s;
+    return STML_OK;
+}
+
+// ------------------------------------------------------------------ predictors
+stml_status upload_idx(stml_ctx* c, const std::vector<int>& K) {
+    CK(c, cudaMemcpyAsync(c->d_idx, K.data(), K.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    return STML_OK;
+}
+
+// Linear taps: target frame k gets the registered field if k is in K, else
+// the interpolation between its neighbours in K.  Indices src_* point into
+// the compact (K-ordered) array; dst is the frame number (or target index).
+std::vector<LinTap> linear_taps(const std::vector<int>& K, const std::vector<int>& targets, bool dst_is_frame) {
+    std::vector<LinTap> taps;
+    for (size_t t = 0; t < targets.size(); ++t) {
+        const int k = targets[t];
+        LinTap tp{};
+        tp.dst = dst_is_frame ? k : (int)t;
+        auto it = std::lower_bound(K.begin(), K.end(), k);
+        if (it != K.end() && *it == k) {
+            tp.src_l = tp.src_r = (int)(it - K.begin());
+            tp.wl = 1.f;
+            tp.wr = 0.f;
+        } else {
+            const int r = (int)(it - K.begin()), l = r - 1;
+            const double kl = K[l], kr = K[r];
+            tp.src_l = l;
+            tp.src_r = r;
+            tp.wl = (float)((kr - k) / (kr - kl));
+            tp.wr = (float)((k - kl) / (kr - kl));
+        }
+        taps.push_back(tp);
+    }
+    return taps;
+}
+
+// Factors of D_K + beta L for Thomas' algorithm, computed in double.
+void ls_factors(int n, const std::vector<int>& K, double beta, std::vector<float>& tab, std::vector<int>& kidx) {
+    std::vector<double> diag(n, 0.0), sub(n, 0.0), sup(n, 0.0);
+    kidx.assign(n, -1);
+    for (size_t i = 0; i < K.size(); ++i) {
+        diag[K[i]] += 1.0;
+        kidx[K[i]] = (int)i;
+    }
+    for (int k = 0; k + 1 < n; ++k) {
+        diag[k] += beta;
+        diag[k + 1] += beta;
+        sup[k] -= beta;
+        sub[k + 1] -= beta;
+    }
+    tab.assign(3 * (size_t)n, 0.f);
+    double cp_prev = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double den = k == 0 ? diag[0] : diag[k] - sub[k] * cp_prev;
+        const double cp = sup[k] / den;
+        tab[k] = (float)cp;
+        tab[n + k] = (float)(1.0 / den);
+        tab[2 * n + k] = (float)sub[k];
+        cp_prev = cp;
+    }
+}
+
+stml_status run_predict_ls(stml_ctx* c, const std::vector<int>& K, const float* eta, const float* omega,
+                           float* zeta, size_t ncomp) {
+    std::vector<float> tab;
+    std::vector<int> kidx;
+    ls_factors(c->n, K, c->p.beta, tab, kidx);
+    CK(c, cudaMemcpyAsync(c->d_lsf, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->d_kidx, kidx.data(), kidx.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, launch_predict_ls(eta, omega, zeta, c->d_lsf, c->d_lsf + c->n, c->d_lsf + 2 * c->n, c->d_kidx, c->n,
+                            ncomp, c->stream));
+    return STML_OK;
+}
+
+stml_status run_predict_linear(stml_ctx* c, const std::vector<int>& K, const std::vector<int>& targets,
+                               const float* in, float* out, size_t plane) {
+    std::vector<LinTap> taps = linear_taps(K, targets, true);
+    CK(c, cudaMemcpyAsync(c->d_taps, taps.data(), taps.size() * sizeof(LinTap), cudaMemcpyHostToDevice, c->stream));
+    CK(c, launch_predict_linear(in, out, c->d_taps, (int)taps.size(), plane, c->stream));
+    return STML_OK;
+}
+
+// ------------------------------------------------------------------ STML steps
+stml_status do_predict(stml_ctx* c, int level, int q) {
+    LevelBuf& L = c->lv[level];
+    const size_t plane = (size_t)L.g.d * L.g.N;    // one frame of a field
+    const size_t total = (size_t)c->n * plane;
+    if (q == 0) {
+        if (level == 0) {
+            CK(c, cudaMemsetAsync(c->w_z, 0, total * sizeof(float), c->stream));
+        } else {
+            const LevelBuf& C = c->lv[level - 1];
+            if (L.g.nx != 2 * C.g.nx) return fail(c, STML_EINVAL, "level shapes do not halve");
+            CK(c, launch_prolong(C.y, c->w_z, c->n * c->d, C.g, c->stream));
+        }
+        c->cur_level = level;
+        c->last_q = -1;
+        c->level_done = false;
+        c->dhat_prev = 0.0;
+        return STML_OK;
+    }
+    if (c->cur_level != level || c->last_q != q - 1 || c->level_done)
+        return fail(c, STML_ESTATE, "stml_predict(level, q) needs stml_correct(level, q-1) first");
+    const std::vector<int>& Kp = c->sets[q - 1];
+    if (level == 0) {
+        TRY(run_predict_linear(c, Kp, c->sets[q], c->w_u, c->w_z, plane));
+    } else {
+        TRY(run_predict_ls(c, Kp, c->w_u, c->w_z, c->w_z2, plane));
+        std::swap(c->w_z, c->w_z2);
+    }
+    return STML_OK;
+}
+
+stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finished) {
+    if (c->cur_level != level || c->last_q != q - 1 || c->level_done)
+        return fail(c, STML_ESTATE, "stml_correct(level, q) needs stml_predict(level, q) first");
+    LevelBuf& L = c->lv[level];
+    const size_t plane = (size_t)L.g.d * L.g.N;
+    const std::vector<int>& K = c->sets[q];
+    const int Q = (int)c->sets.size();
+    TRY(upload_idx(c, K));
+    CK(c, launch_gather_planes(c->w_z, c->w_u, c->d_idx, (int)K.size(), plane, c->stream));
+    stml_stats s{};
+    TRY(run_gir(c, level, K, c->w_u, &s));
+    s.tlevel = q;
+    const double dhat = s.D / (double)K.size();
+    const bool stop = q > 0 && c->p.stop_rule &&
+                      std::fabs(dhat - c->dhat_prev) <= c->p.eps_stop * std::fabs(c->dhat_prev);
+    s.stopped_early = stop ? 1 : 0;
+    c->last_q = q;
+    int done = 0;
+    if (q == Q - 1) {
+        TRY(upload_idx(c, K));
+        CK(c, launch_scatter_planes(c->w_u, L.y, c->d_idx, (int)K.size(), plane, c->stream));
+        done = 1;
+    } else if (stop) {
+        std::vector<int> all(c->n);
+        for (int k = 0; k < c->n; ++k) all[k] = k;
+        if (level == 0) {
+            TRY(run_predict_linear(c, K, all, c->w_u, L.y, plane));
+        } else {
+            TRY(run_predict_ls(c, K, c->w_u, c->w_z, L.y, plane));
+            TRY(upload_idx(c, K));
+            CK(c, launch_scatter_planes(c->w_u, L.y, c->d_idx, (int)K.size(), plane, c->stream));
+        }
+        done = 1;
+    }
+    c->dhat_prev = dhat;
+    c->level_done = done != 0;
+    if (st) *st = s;
+    if (finished) *finished = done;
+    return STML_OK;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+extern "C" {
+
+void stml_default_params(stml_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->alpha = 0.02;
+    p->alpha_t = 0.0;
+    p->lambda = 1.0;
+    p->beta = 1e-5;
+    p->eps_stop = 1e-3;
+    p->stop_rule = 1;
+    p->n_levels = 2;
+    p->n_tlevels = 2;
+    p->tol_J = 1e-3;
+    p->tol_Y = 1e-2;
+    p->tol_G = 5e-2;
+    p->g_abs = 1e-12;
+    p->max_gn = 10;
+    p->tol_cg = 1e-1;
+    p->max_cg = 20;
+    p->max_ls = 10;
+    p->armijo_c = 1e-4;
+}
+
+stml_status stml_create(const stml_params* p, void* cuda_stream, stml_ctx** out) {
+    if (!out) return fail(nullptr, STML_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (!valid_params(p, why)) return fail(nullptr, STML_EINVAL, why);
+    stml_ctx* c = new (std::nothrow) stml_ctx();
+    if (!c) return fail(nullptr, STML_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = dalloc(&c->S, 1);
+    if (e == cudaSuccess) e = cudaMemset(c->S, 0, sizeof(DevScalars));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->Sh, sizeof(DevScalars));
+    if (e != cudaSuccess) {
+        g_free_error = std::string("stml_create: ") + cudaGetErrorString(e);
+        dfree(c->S);
+        delete c;
+        return STML_ECUDA;
+    }
+    std::memset(c->Sh, 0, sizeof(DevScalars));
+    *out = c;
+    return STML_OK;
+}
+
+void stml_destroy(stml_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_buffers(c);
+    for (auto& pr : c->ev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    dfree(c->S);
+    if (c->Sh) cudaFreeHost(c->Sh);
+    delete c;
+}
+
+const char* stml_last_error(const stml_ctx* c) { return c ? c->err.c_str() : g_free_error.c_str(); }
+
+stml_status stml_set_params(stml_ctx* c, const stml_params* p) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    std::string why;
+    if (!valid_params(p, why)) return fail(c, STML_EINVAL, why);
+    if (c->loaded && (p->n_levels != c->p.n_levels || p->n_tlevels != c->p.n_tlevels))
+        return fail(c, STML_EINVAL, "level counts cannot change after stml_load_sequence");
+    c->p = *p;
+    return STML_OK;
+}
+
+stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, int n_frames, int dim,
+                               const int* shape) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (!frames || !shape || n_frames < 1 || (dim != 2 && dim != 3))
+        return fail(c, STML_EINVAL, "need frames, shape, n_frames >= 1 and dim 2 or 3");
+    cudaSetDevice(c->device);
+    const int L = c->p.n_levels;
+    const long long f = 1LL << (L - 1);
+    int sh3[3] = {1, 1, 1};
+    for (int i = 0; i < dim; ++i) {
+        if (shape[i] < 1 || shape[i] % f) return fail(c, STML_EINVAL, "every axis must be a positive multiple of 2^(n_levels-1)");
+        sh3[3 - dim + i] = shape[i];
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    free_buffers(c);
+    c->n = n_frames;
+    c->d = dim;
+    std::memcpy(c->shape, sh3, sizeof(sh3));
+    c->lv.resize(L);
+    for (int l = 0; l < L; ++l) {
+        const int div = 1 << (L - 1 - l);
+        LevelBuf& B = c->lv[l];
+        B.shape3[0] = dim == 3 ? sh3[0] / div : 1;
+        B.shape3[1] = sh3[1] / div;
+        B.shape3[2] = sh3[2] / div;
+        B.g = make_geom(B.shape3, dim, (float)div);
+        if (dalloc(&B.img, (size_t)n_frames * B.g.N) != cudaSuccess ||
+            dalloc(&B.y, (size_t)n_frames * dim * B.g.N) != cudaSuccess) {
+            free_buffers(c);
+            return fail(c, STML_ENOMEM, "device allocation of the level buffers failed");
+        }
+    }
+    const Geom& G = c->lv[L - 1].g;
+    const size_t fieldN = (size_t)n_frames * dim * G.N;
+    const size_t imgN = (size_t)n_frames * G.N;
+    size_t pcap = 0;
+    for (int l = 0; l < L; ++l) pcap = std::max(pcap, partials_needed(c->lv[l].g, n_frames));
+    c->partials_cap = pcap;
+    bool ok = true;
+    float** fields[] = {&c->w_u, &c->w_g, &c->w_dT, &c->w_x, &c->w_r, &c->w_p, &c->w_q, &c->w_ut, &c->w_z, &c->w_z2};
+    for (float** fp : fields) ok = ok && dalloc(fp, fieldN) == cudaSuccess;
+    ok = ok && dalloc(&c->w_a, imgN) == cudaSuccess;
+    ok = ok && dalloc(&c->w_m1, (size_t)G.N) == cudaSuccess;
+    ok = ok && dalloc(&c->w_m2, (size_t)dim * G.N) == cudaSuccess;
+    ok = ok && dalloc(&c->partials, pcap) == cudaSuccess;
+    ok = ok && dalloc(&c->d_frames, n_frames) == cudaSuccess;
+    ok = ok && dalloc(&c->d_wnext, n_frames) == cudaSuccess;
+    ok = ok && dalloc(&c->d_idx, n_frames) == cudaSuccess;
+    ok = ok && dalloc(&c->d_lsf, 3 * (size_t)n_frames) == cudaSuccess;
+    ok = ok && dalloc(&c->d_kidx, n_frames) == cudaSuccess;
+    ok = ok && dalloc(&c->d_taps, n_frames) == cudaSuccess;
+    ok = ok && dalloc(&c->d_rho, n_frames) == cudaSuccess;
+    if (!ok) {
+        free_buffers(c);
+        return fail(c, STML_ENOMEM, "device allocation of the solver workspace failed");
+    }
+    CK(c, cudaMemsetAsync(c->S, 0, sizeof(DevScalars), c->stream));
+    CK(c, cudaMemcpyAsync(c->lv[L - 1].img, frames, imgN * sizeof(float),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    for (int l = 0; l < L; ++l)
+        CK(c, cudaMemsetAsync(c->lv[l].y, 0, (size_t)n_frames * dim * c->lv[l].g.N * sizeof(float), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->loaded = true;
+    c->built = false;
+    return STML_OK;
+}
+
+stml_status stml_build_pyramid(stml_ctx* c) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (!c->loaded) return fail(c, STML_ESTATE, "no sequence loaded");
+    cudaSetDevice(c->device);
+    const int L = (int)c->lv.size();
+    for (int l = L - 1; l > 0; --l)
+        CK(c, launch_restrict(c->lv[l].img, c->lv[l - 1].img, c->n, c->lv[l - 1].g, c->stream));
+    c->sets = make_sets(c->n, c->p.n_tlevels);
+    c->built = true;
+    c->cur_level = -1;
+    return STML_OK;
+}
+
+stml_status stml_level_info(const stml_ctx* c, int level, int* shape3, double* h) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (!c->loaded || level < 0 || level >= (int)c->lv.size()) return STML_EINVAL;
+    if (shape3) std::memcpy(shape3, c->lv[level].shape3, 3 * sizeof(int));
+    if (h) *h = c->lv[level].g.h;
+    return STML_OK;
+}
+
+stml_status stml_temporal_set(const stml_ctx* c, int tlevel, int* frames, int cap, int* count) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (!c->built || tlevel < 0 || tlevel >= (int)c->sets.size()) return STML_EINVAL;
+    const std::vector<int>& K = c->sets[tlevel];
+    if (count) *count = (int)K.size();
+    if (frames)
+        for (int i = 0; i < cap && i < (int)K.size(); ++i) frames[i] = K[i];
+    return STML_OK;
+}
+
+stml_status stml_get_images(stml_ctx* c, int level, float* dst, int dst_on_device) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    cudaSetDevice(c->device);
+    const size_t cnt = (size_t)c->n * c->lv[level].g.N;
+    CK(c, cudaMemcpyAsync(dst, c->lv[level].img, cnt * sizeof(float),
+                          dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+stml_status stml_get_field(stml_ctx* c, int level, float* dst, int dst_on_device) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    cudaSetDevice(c->device);
+    const size_t cnt = (size_t)c->n * c->d * c->lv[level].g.N;
+    CK(c, cudaMemcpyAsync(dst, c->lv[level].y, cnt * sizeof(float),
+                          dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+stml_status stml_set_field(stml_ctx* c, int level, const float* src, int src_on_device) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    cudaSetDevice(c->device);
+    const size_t cnt = (size_t)c->n * c->d * c->lv[level].g.N;
+    CK(c, cudaMemcpyAsync(c->lv[level].y, src, cnt * sizeof(float),
+                          src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+stml_status stml_predict(stml_ctx* c, int level, int tlevel) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    if (tlevel < 0 || tlevel >= (int)c->sets.size()) return fail(c, STML_EINVAL, "tlevel out of range");
+    cudaSetDevice(c->device);
+    return do_predict(c, level, tlevel);
+}
+
+stml_status stml_correct(stml_ctx* c, int level, int tlevel, stml_stats* stats, int* finished) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    if (tlevel < 0 || tlevel >= (int)c->sets.size()) return fail(c, STML_EINVAL, "tlevel out of range");
+    cudaSetDevice(c->device);
+    return do_correct(c, level, tlevel, stats, finished);
+}
+
+stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int cap, int* n_written) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (!c->built) return fail(c, STML_ESTATE, "no pyramid: call stml_build_pyramid");
+    if (mode != STML_MODE_STML && mode != STML_MODE_SPML) return fail(c, STML_EINVAL, "unknown mode");
+    cudaSetDevice(c->device);
+    int written = 0;
+    auto record = [&](const stml_stats& s) {
+        if (stats && written < cap) stats[written] = s;
+        ++written;
+    };
+    const int L = (int)c->lv.size();
+    std::vector<int> all(c->n);
+    for (int k = 0; k < c->n; ++k) all[k] = k;
+    for (int l = 0; l < L; ++l) {
+        if (mode == STML_MODE_SPML) {
+            TRY(do_predict(c, l, 0));
+            LevelBuf& B = c->lv[l];
+            const size_t total = (size_t)c->n * c->d * B.g.N;
+            CK(c, cudaMemcpyAsync(B.y, c->w_z, total * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+            stml_stats s{};
+            TRY(run_gir(c, l, all, B.y, &s));
+            s.tlevel = (int)c->sets.size() - 1;
+            record(s);
+            c->level_done = true;
+        } else {
+            for (int q = 0; q < (int)c->sets.size(); ++q) {
+                TRY(do_predict(c, l, q));
+                stml_stats s{};
+                int fin = 0;
+                TRY(do_correct(c, l, q, &s, &fin));
+                record(s);
+                if (fin) break;
+            }
+        }
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (n_written) *n_written = written;
+    return STML_OK;
+}
+
+stml_status stml_eval(stml_ctx* c, int level, const int* frames, int nK, const float* u, double* out,
+                      float* g, float* dT) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!u || !out) return fail(c, STML_EINVAL, "u and out are required");
+    cudaSetDevice(c->device);
+    LevelBuf& L = c->lv[level];
+    std::vector<int> K(frames, frames + nK);
+    FrameSet fs;
+    TRY(upload_frameset(c, K, fs));
+    const Coef cf = make_coef(L.g, c->p, nK);
+    EvalWork ew{c->w_a, c->w_m1, c->w_m2, c->partials, c->partials_cap};
+    const bool full = g || dT;
+    if (full) {
+        CK(c, launch_eval(L.img, L.g, fs, cf, u, nullptr, 0.f, dT ? dT : c->w_dT, g ? g : c->w_g, ew,
+                          &c->S->ticket[0], c->S->red, c->stream));
+    } else {
+        CK(c, launch_eval(L.img, L.g, fs, cf, u, nullptr, 0.f, nullptr, nullptr, ew, &c->S->ticket[0],
+                          c->S->red, c->stream));
+    }
+    TRY(read_scalars(c));
+    for (int i = 0; i < 6; ++i) out[i] = c->Sh->red[i];
+    if (!full) out[4] = 0.0;
+    return STML_OK;
+}
+
+stml_status stml_hessvec(stml_ctx* c, int level, const int* frames, int nK, const float* dT, const float* v,
+                         float* Hv, double* vHv) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!dT || !v || !Hv) return fail(c, STML_EINVAL, "dT, v and Hv are required");
+    cudaSetDevice(c->device);
+    LevelBuf& L = c->lv[level];
+    std::vector<int> K(frames, frames + nK);
+    FrameSet fs;
+    TRY(upload_frameset(c, K, fs));
+    const Coef cf = make_coef(L.g, c->p, nK);
+    TRY(hessvec_launch(c, L.g, fs, cf, dT, v, Hv, nullptr));
+    TRY(read_scalars(c));
+    if (vHv) *vHv = c->Sh->dots[4];
+    return STML_OK;
+}
+
+stml_status stml_gir(stml_ctx* c, int level, const int* frames, int nK, float* u, stml_stats* stats) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!u) return fail(c, STML_EINVAL, "u is required");
+    cudaSetDevice(c->device);
+    std::vector<int> K(frames, frames + nK);
+    return run_gir(c, level, K, u, stats);
+}
+
+stml_status stml_corr_coeff(stml_ctx* c, int level, double* rho) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    if (!rho) return fail(c, STML_EINVAL, "rho is required");
+    cudaSetDevice(c->device);
+    if (c->n < 2) return STML_OK;
+    CK(c, launch_corr_coeff(c->lv[level].img, c->n, c->lv[level].g.N, c->d_rho, c->stream));
+    CK(c, cudaMemcpyAsync(rho, c->d_rho, (size_t)(c->n - 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+// ------------------------------------------------------ context-free operators
+static bool shape_ok(int dim, const int* shape, int sh3[3]) {
+    if ((dim != 2 && dim != 3) || !shape) return false;
+    sh3[0] = 1;
+    for (int i = 0; i < dim; ++i) {
+        if (shape[i] < 1) return false;
+        sh3[3 - dim + i] = shape[i];
+    }
+    return true;
+}
+
+stml_status stml_restrict(const float* fine, float* coarse, int planes, int dim, const int* fine_shape,
+                          void* cuda_stream) {
+    int sh3[3];
+    if (!fine || !coarse || planes < 0 || !shape_ok(dim, fine_shape, sh3))
+        return fail(nullptr, STML_EINVAL, "stml_restrict: bad arguments");
+    for (int i = 3 - dim; i < 3; ++i) {
+        if (sh3[i] % 2) return fail(nullptr, STML_EINVAL, "stml_restrict: odd axis");
+        sh3[i] /= 2;
+    }
+    const Geom gc = make_geom(sh3, dim, 2.f);
+    cudaError_t e = launch_restrict(fine, coarse, planes, gc, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_restrict");
+}
+
+stml_status stml_prolong(const float* coarse, float* fine, int planes, int dim, const int* coarse_shape,
+                         void* cuda_stream) {
+    int sh3[3];
+    if (!fine || !coarse || planes < 0 || !shape_ok(dim, coarse_shape, sh3))
+        return fail(nullptr, STML_EINVAL, "stml_prolong: bad arguments");
+    const Geom gc = make_geom(sh3, dim, 2.f);
+    cudaError_t e = launch_prolong(coarse, fine, planes, gc, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_prolong");
+}
+
+stml_status stml_prolong_adjoint(const float* fine, float* coarse, int planes, int dim, const int* coarse_shape,
+                                 void* cuda_stream) {
+    int sh3[3];
+    if (!fine || !coarse || planes < 0 || !shape_ok(dim, coarse_shape, sh3))
+        return fail(nullptr, STML_EINVAL, "stml_prolong_adjoint: bad arguments");
+    const Geom gc = make_geom(sh3, dim, 2.f);
+    cudaError_t e = launch_prolong_adjoint(fine, coarse, planes, gc, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_prolong_adjoint");
+}
+
+static bool increasing(const int* K, int nK) {
+    for (int i = 1; i < nK; ++i)
+        if (K[i] <= K[i - 1]) return false;
+    return true;
+}
+
+stml_status stml_predict_linear(const float* yK, const int* K, int nK, float* z, const int* targets, int nT,
+                                size_t plane_elems, void* cuda_stream) {
+    if (!yK || !K || !z || !targets || nK < 1 || nT < 0 || !increasing(K, nK))
+        return fail(nullptr, STML_EINVAL, "stml_predict_linear: bad arguments");
+    std::vector<int> Kv(K, K + nK), tv(targets, targets + nT);
+    for (int t : tv)
+        if (t < Kv.front() || t > Kv.back())
+            return fail(nullptr, STML_EINVAL, "stml_predict_linear: target outside the span of K");
+    std::vector<LinTap> taps = linear_taps(Kv, tv, false);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    LinTap* d_taps = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d_taps, std::max<size_t>(1, taps.size()) * sizeof(LinTap), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_taps, taps.data(), taps.size() * sizeof(LinTap), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_predict_linear(yK, z, d_taps, nT, plane_elems, s);
+    if (d_taps) cudaFreeAsync(d_taps, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_predict_linear");
+}
+
+stml_status stml_predict_ls(const float* eta, const int* K, int nK, const float* omega, float* zeta, int n,
+                            double beta, size_t n_comp, void* cuda_stream) {
+    if (!eta || !K || !omega || !zeta || n < 1 || nK < 1 || nK > n || !(beta >= 0) || !increasing(K, nK) ||
+        K[0] < 0 || K[nK - 1] >= n)
+        return fail(nullptr, STML_EINVAL, "stml_predict_ls: bad arguments");
+    if (omega == zeta) return fail(nullptr, STML_EINVAL, "stml_predict_ls: omega and zeta must differ");
+    std::vector<int> Kv(K, K + nK), kidx;
+    std::vector<float> tab;
+    ls_factors(n, Kv, beta, tab, kidx);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float* d_tab = nullptr;
+    int* d_k = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d_tab, tab.size() * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_k, kidx.size() * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_k, kidx.data(), kidx.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_predict_ls(eta, omega, zeta, d_tab, d_tab + n, d_tab + 2 * n, d_k, n, n_comp, s);
+    if (d_tab) cudaFreeAsync(d_tab, s);
+    if (d_k) cudaFreeAsync(d_k, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_predict_ls");
+}
+
+// ------------------------------------------------------------ profiling
+stml_status stml_profile_enable(stml_ctx* c, int enable) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    c->prof = enable != 0;
+    c->ev_used = 0;
+    c->prof_bytes = 0.0;
+    c->prof_pf = 0.0;
+    return STML_OK;
+}
+
+stml_status stml_profile_read(stml_ctx* c, long long* launches, double* ms, double* bytes, double* pixel_frames) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    cudaSetDevice(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    double tot = 0.0;
+    for (size_t i = 0; i < c->ev_used; ++i) {
+        float m = 0.f;
+        CK(c, cudaEventElapsedTime(&m, c->ev[i].first, c->ev[i].second));
+        tot += m;
+    }
+    if (launches) *launches = (long long)c->ev_used;
+    if (ms) *ms = tot;
+    if (bytes) *bytes = c->prof_bytes;
+    if (pixel_frames) *pixel_frames = c->prof_pf;
+    return STML_OK;
+}
+
+long long stml_launch_count(const stml_ctx* c) {
+    (void)c;
+    return launches_total();
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Host-side launchers of the STML kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace stml {
+
+// Every launcher adds the number of kernels it launched to this counter.
+long long launches_total();
+void count_launches(int k);
+
+// Geometry of a level from its shape (nz, ny, nx), dimension and cell width.
+Geom make_geom(const int shape3[3], int d, float h);
+
+// CTAs for n work items at `threads` per CTA, capped for grid-stride loops.
+inline unsigned blocks_for(long long n, int threads = kThreads, long long cap = 1 << 20) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+// Pixels per CTA of the kernels that loop over the frames of a pixel: one
+// warp-wide row of pixels, the frames split over the 8 warps of the CTA.
+constexpr int kPixPerCta = 32;
+constexpr int kFrameGroups = kThreads / kPixPerCta;
+
+// ---------------------------------------------------------- transfer ops
+cudaError_t launch_restrict(const float* fine, float* coarse, int planes, const Geom& gc,
+                            cudaStream_t s);
+cudaError_t launch_prolong(const float* coarse, float* fine, int planes, const Geom& gc,
+                           cudaStream_t s);
+cudaError_t launch_prolong_adjoint(const float* fine, float* coarse, int planes, const Geom& gc,
+                                   cudaStream_t s);
+
+// Linear temporal predictor: for every target t, out[dst_t] = wl_t * in[src_l] + wr_t * in[src_r].
+struct LinTap {
+    int dst, src_l, src_r, pad;
+    float wl, wr;
+};
+cudaError_t launch_predict_linear(const float* in, float* out, const LinTap* taps, int nT,
+                                  size_t plane_elems, cudaStream_t s);
+
+// Thomas sweep for eq. (2): factors cp, inv_den, sub (n floats each) and
+// kidx (n ints, index into eta or -1) in device memory.
+cudaError_t launch_predict_ls(const float* eta, const float* omega, float* zeta, const float* cp,
+                              const float* inv_den, const float* sub, const int* kidx, int n,
+                              size_t ncomp, cudaStream_t s);
+
+// Copies planes: dst[j] = src[idx[j]] (gather) for j < nK, each plane_elems floats.
+cudaError_t launch_gather_planes(const float* src, float* dst, const int* idx, int nK,
+                                 size_t plane_elems, cudaStream_t s);
+// dst[idx[j]] = src[j] (scatter).
+cudaError_t launch_scatter_planes(const float* src, float* dst, const int* idx, int nK,
+                                  size_t plane_elems, cudaStream_t s);
+
+cudaError_t launch_corr_coeff(const float* img, int n, long long N, double* rho_dev, cudaStream_t s);
+
+// ---------------------------------------------------------- objective
+// Evaluation workspace (device).
+struct EvalWork {
+    float* a;          // nK * N warped images
+    float* mean_a;     // N
+    float* mean_u;     // d * N
+    double* partials;  // >= blocks * kMaxRed
+    size_t partials_cap;
+};
+
+// J, D, S, P (and gradient) at u (or at u + t du when du != nullptr).
+// grad == nullptr selects the objective only; results go to out[0..6):
+// J, D, S, P, |g|^2, |u|^2 (in device memory, DevScalars::red or ::trial).
+cudaError_t launch_eval(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf,
+                        const float* u, const float* du, float t, float* dT, float* grad,
+                        EvalWork& w, unsigned int* ticket, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------- Hessian product
+struct HessWork {
+    float* mean_s;     // N
+    float* sum_v;      // d * N
+    double* partials;
+    size_t partials_cap;
+};
+
+// Hv and <v, Hv> (to out[0]).  With pcg != nullptr the launch is a step of
+// the device-side PCG: it does nothing once cg_active is 0, and its last CTA
+// sets alpha = rho / <p, Hp> (or flags a breakdown).
+cudaError_t launch_hessvec(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
+                           const float* v, float* Hv, HessWork& w, unsigned int* ticket,
+                           double* out, DevScalars* pcg, cudaStream_t s);
+
+// ---------------------------------------------------------- PCG vector ops
+struct PcgArgs {
+    float tol_cg;
+    int max_cg;
+};
+cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad,
+                            const float* dT, float* x, float* r, float* p, double* partials,
+                            DevScalars* S, PcgArgs a, cudaStream_t s);
+cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
+                              float* x, float* r, const float* p, const float* q,
+                              double* partials, DevScalars* S, PcgArgs a, cudaStream_t s);
+cudaError_t launch_pcg_pupdate(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
+                               const float* r, float* p, DevScalars* S, cudaStream_t s);
+// out[0] = <a, b>, out[1] = <b, b>
+cudaError_t launch_dot2(const float* a, const float* b, size_t n, double* partials,
+                        unsigned int* ticket, double* out, cudaStream_t s);
+// y = x + t d
+cudaError_t launch_axpy(const float* x, const float* d, float t, float* y, size_t n, cudaStream_t s);
+
+size_t partials_needed(const Geom& g, int nK);
+
+}  // namespace stml

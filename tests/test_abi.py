@@ -1,0 +1,46 @@
+"""The C ABI library builds, loads and exports every symbol of include/stml.h
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+
+import pytest
+
+from _util import header_functions
+from oracle import Params
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2001_06613_gb300 import _build
+    _build.build()
+    import paper_2001_06613_gb300 as S
+    return S
+
+
+def test_every_declared_function_is_exported(lib):
+    raw = ctypes.CDLL(lib.binding.LIB_PATH)
+    declared = header_functions()
+    assert len(declared) >= 25
+    for name in declared:
+        assert hasattr(raw, name), name
+    assert sorted(lib.exported_symbols()) == declared
+
+
+def test_default_params_match_the_oracle_defaults(lib):
+    p = lib.stml_default_params()
+    o = Params()
+    assert (p.alpha, p.alpha_t, p.lambda_, p.beta) == (o.alpha, o.alpha_t, o.lam, o.beta)
+    assert (p.eps_stop, bool(p.stop_rule)) == (o.eps_stop, o.stop_rule)
+    assert (p.tol_J, p.tol_Y, p.tol_G, p.g_abs) == (o.tol_J, o.tol_Y, o.tol_G, o.g_abs)
+    assert (p.max_gn, p.tol_cg, p.max_cg, p.max_ls, p.armijo_c) == (
+        o.max_gn, o.tol_cg, o.max_cg, o.max_ls, o.armijo_c)
+
+
+def test_invalid_parameters_are_rejected_before_any_device_work(lib):
+    bad = lib.stml_default_params(n_levels=0)
+    with pytest.raises(lib.StmlError) as e:
+        lib.stml_create(bad)
+    assert e.value.status == -1
+    assert "n_levels" in lib.stml_last_error(None)
+    bad = lib.stml_default_params(alpha=-1.0)
+    with pytest.raises(lib.StmlError):
+        lib.stml_create(bad)

@@ -1,0 +1,163 @@
+"""GPU parity of the Gauss-Newton registration (GIR) and of the STML / SpML
+multilevel drivers against the oracle.
+
+Registration is an iteration on a non-convex objective; FP32 device arithmetic
+and FP64 oracle arithmetic follow the same algorithm but not the same
+rounding, so end-to-end results are compared through the objective and the
+fields (with stated tolerances) rather than bit for bit."""
+import numpy as np
+import pytest
+
+from _util import assert_scalar, cuda_lib
+from oracle import Params, grid, multilevel, solver
+from paper_2001_06613_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    return cuda_lib()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _oparams(prm, **kw):
+    base = dict(alpha=prm.alpha, alpha_t=prm.alpha_t, lam=prm.lambda_, beta=prm.beta,
+                eps_stop=prm.eps_stop, stop_rule=bool(prm.stop_rule), n_levels=prm.n_levels,
+                n_tlevels=prm.n_tlevels, tol_J=prm.tol_J, tol_Y=prm.tol_Y, tol_G=prm.tol_G,
+                max_gn=prm.max_gn, tol_cg=prm.tol_cg, max_cg=prm.max_cg, max_ls=prm.max_ls,
+                armijo_c=prm.armijo_c, g_abs=prm.g_abs)
+    base.update(kw)
+    return Params(**base)
+
+
+def _ctx(S, R, **kw):
+    prm = S.stml_default_params(**kw)
+    ctx = S.Context(prm)
+    S.stml_load_sequence(ctx.ptr, _dev(R))
+    S.stml_build_pyramid(ctx.ptr)
+    return ctx
+
+
+@pytest.mark.parametrize("max_gn", [1, 3])
+def test_gir_matches_oracle_gauss_newton(S, max_gn):
+    R = synthetic.make_sequence(synthetic.spec_custom(5, (32, 40), seed=21, amp=1.5))
+    ctx = _ctx(S, R, n_levels=1, max_gn=max_gn)
+    try:
+        frames = [0, 1, 2, 3, 4]
+        u0 = np.zeros((5, 2, 32, 40), np.float32)
+        ud = _dev(u0)
+        st = S.stml_gir(ctx.ptr, 0, frames, ud)
+        uo, so = solver.gauss_newton(R.astype(np.float64), u0, frames, 1.0, _oparams(ctx.params))
+        assert st["gn_iters"] == so.gn_iters
+        assert st["ls_trials"] == so.ls_trials
+        assert abs(st["cg_iters"] - so.cg_iters) <= max_gn
+        assert_scalar(st["J0"], so.J0, 1e-5, "J0")
+        assert_scalar(st["J"], so.J, 1e-4 * max_gn, "J after GN")
+        diff = ud.cpu().numpy() - uo
+        assert np.sqrt(np.mean(diff ** 2)) <= 1e-3 * max(1.0, np.sqrt(np.mean(uo ** 2)))
+    finally:
+        ctx.close()
+
+
+def test_zero_motion_exits_at_iteration_zero(S):
+    base = synthetic.make_sequence(synthetic.spec_custom(1, (32, 32), seed=3))
+    R = np.repeat(base, 4, axis=0)
+    ctx = _ctx(S, R, n_levels=2)
+    try:
+        u = _dev(np.zeros((4, 2, 32, 32)))
+        st = S.stml_gir(ctx.ptr, 1, [0, 1, 2, 3], u)
+        assert st["gn_iters"] == 0 and st["cg_iters"] == 0
+        assert float(u.abs().max()) == 0.0
+    finally:
+        ctx.close()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    spec = synthetic.spec_tiny()
+    return spec, synthetic.make_sequence(spec)
+
+
+def _register(S, R, mode, **kw):
+    ctx = _ctx(S, R, **kw)
+    try:
+        stats = S.stml_register(ctx.ptr, mode)
+        L = ctx.params.n_levels
+        y = np.empty((R.shape[0], R.ndim - 1) + R.shape[1:], np.float32)
+        S.stml_get_field(ctx.ptr, L - 1, y)
+        return stats, y, ctx.params
+    finally:
+        ctx.close()
+
+
+def _centred_rms(y, truth):
+    a = y - y.mean(axis=0, keepdims=True)
+    b = truth - truth.mean(axis=0, keepdims=True)
+    e = (a - b)[..., 4:-4, 4:-4]
+    return float(np.sqrt((e ** 2).sum(axis=1).mean()))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_register_tiny_matches_oracle(S, tiny, mode):
+    """16 frames of 64x64, 2 spatial x 2 temporal levels (STML) or spatial only (SpML)."""
+    spec, R = tiny
+    stats, y, prm = _register(S, R, mode, n_levels=2, n_tlevels=2)
+    op = _oparams(prm)
+    res = multilevel.register(R.astype(np.float64), op, "stml" if mode == 0 else "spml")
+    assert [(s["level"], s["tlevel"], s["n_frames"]) for s in stats] == \
+        [(s.level, s.tlevel, s.n_frames) for s in res.stats]
+    Jg = multilevel.final_objective(R.astype(np.float64), y.astype(np.float64), op)["J"]
+    Jo = multilevel.final_objective(R.astype(np.float64), res.y, op)["J"]
+    assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
+    rms = float(np.sqrt(np.mean((y - res.y) ** 2)))
+    assert rms <= 0.05, rms
+    truth = synthetic.planted_registration(spec)
+    assert _centred_rms(y.astype(np.float64), truth) < 0.2
+
+
+def test_stepwise_api_equals_register(S, tiny):
+    spec, R = tiny
+    stats, y_reg, prm = _register(S, R, 0, n_levels=2, n_tlevels=2)
+    ctx = _ctx(S, R, n_levels=2, n_tlevels=2)
+    try:
+        for lvl in range(2):
+            for q in range(2):
+                S.stml_predict(ctx.ptr, lvl, q)
+                st, fin = S.stml_correct(ctx.ptr, lvl, q)
+                if fin:
+                    break
+        y = np.empty_like(y_reg)
+        S.stml_get_field(ctx.ptr, 1, y)
+        assert np.array_equal(y, y_reg)     # same launches, deterministic reductions
+    finally:
+        ctx.close()
+
+
+def test_stopping_rule_fills_from_predictor(S):
+    R = synthetic.make_sequence(synthetic.spec_custom(9, (32, 32), seed=3, amp=1.0))
+    stats, y, prm = _register(S, R, 0, n_levels=2, n_tlevels=3, eps_stop=10.0)
+    assert [(s["level"], s["tlevel"], s["stopped_early"]) for s in stats] == \
+        [(0, 0, 0), (0, 1, 1), (1, 0, 0), (1, 1, 1)]
+    op = _oparams(prm)
+    res = multilevel.register(R.astype(np.float64), op, "stml")
+    assert np.all(np.isfinite(y))
+    assert float(np.sqrt(np.mean((y - res.y) ** 2))) <= 0.05
+
+
+def test_single_frame_and_3d_sequence(S):
+    R1 = synthetic.make_sequence(synthetic.spec_custom(1, (16, 16), seed=2))
+    stats, y, _ = _register(S, R1, 0, n_levels=2, n_tlevels=2)
+    assert np.all(y == 0.0)                 # one frame: the penalty pins it to Id
+    spec = synthetic.spec_custom(5, (16, 16, 16), seed=4, amp=1.0)
+    R3 = synthetic.make_sequence(spec)
+    stats, y3, prm = _register(S, R3, 0, n_levels=2, n_tlevels=2)
+    op = _oparams(prm)
+    res = multilevel.register(R3.astype(np.float64), op, "stml")
+    Jg = multilevel.final_objective(R3.astype(np.float64), y3.astype(np.float64), op)["J"]
+    Jo = multilevel.final_objective(R3.astype(np.float64), res.y, op)["J"]
+    assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
