@@ -205,6 +205,26 @@ stml_status stml_predict_ls(const float* eta, const int* K, int nK, const float*
                             float* zeta, int n, double beta, size_t n_comp,
                             void* cuda_stream);
 
+/* ----------------------------------------------- allocation-free variant */
+
+/* Gauss-Newton Hessian product (as stml_hessvec) for callers that cannot
+ * allocate device memory: code running inside a framework that owns all
+ * device memory through its own pool, or code that may only touch the buffers
+ * it is handed.  The paper has no counterpart; this is a library service.
+ * No context is needed and nothing is allocated: dT, v and Hv (device,
+ * nK * dim * N floats of the level grid `shape` with cell width h) are the
+ * caller's; frames (host, nK increasing numbers) only set the temporal
+ * weights; p supplies alpha, alpha_t and lambda; *vHv (host, may be NULL)
+ * receives <v, Hv>.  All scratch comes from one static 24 MiB device array per
+ * GPU that loads the library (held until the process exits); a problem that
+ * needs more returns STML_EINVAL.  The first call on a device looks up that
+ * array's device address (make it before any stream capture).  Calls share
+ * the array, so calls that overlap on the GPU race; run them on one stream.
+ * Errors are reported through stml_last_error(NULL). */
+stml_status stml_hessvec_noalloc(const float* dT, const float* v, float* Hv, int dim,
+                                 const int* shape, double h, const int* frames, int nK,
+                                 const stml_params* p, double* vHv, void* cuda_stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Enables (1) or disables (0) CUDA-event timing of every launch of the

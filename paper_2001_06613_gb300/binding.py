@@ -78,6 +78,8 @@ _SIGS = {
     "stml_prolong_adjoint": (C.c_int, [_fp, _fp, C.c_int, C.c_int, _ip, _vp]),
     "stml_predict_linear": (C.c_int, [_fp, _ip, C.c_int, _fp, _ip, C.c_int, C.c_size_t, _vp]),
     "stml_predict_ls": (C.c_int, [_fp, _ip, C.c_int, _fp, _fp, C.c_int, C.c_double, C.c_size_t, _vp]),
+    "stml_hessvec_noalloc": (C.c_int, [_fp, _fp, _fp, C.c_int, _ip, C.c_double, _ip, C.c_int,
+                                       C.POINTER(Params), _dp, _vp]),
     "stml_profile_enable": (C.c_int, [_vp, C.c_int]),
     "stml_profile_read": (C.c_int, [_vp, C.POINTER(C.c_longlong), _dp, _dp, _dp]),
     "stml_launch_count": (C.c_longlong, [_vp]),
@@ -291,6 +293,16 @@ def stml_predict_linear(yK, K: Sequence[int], z, targets: Sequence[int], plane_e
 def stml_predict_ls(eta, K: Sequence[int], omega, zeta, n: int, beta: float, n_comp: int, stream=None):
     _check(load().stml_predict_ls(_dev(eta), _ints(K), len(K), _dev(omega), _dev(zeta), n, beta, n_comp,
                                   _stream(stream)))
+
+
+def stml_hessvec_noalloc(dT, v, Hv, shape: Sequence[int], h: float, frames: Sequence[int],
+                         params: Params, stream=None) -> float:
+    """Hessian product without any device allocation (static scratch array)."""
+    vhv = C.c_double()
+    _check(load().stml_hessvec_noalloc(_dev(dT), _dev(v), _dev(Hv), len(shape), _ints(shape), float(h),
+                                       _ints(frames), len(frames), C.byref(params), C.byref(vhv),
+                                       _stream(stream)))
+    return vhv.value
 
 
 def stml_profile_enable(ctx, enable: bool = True):

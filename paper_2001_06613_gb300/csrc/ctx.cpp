@@ -29,6 +29,8 @@ struct LevelBuf {
 
 }  // namespace
 
+void stml::set_context_free_error(const std::string& msg) { g_free_error = msg; }
+
 struct stml_ctx {
     stml_params p{};
     cudaStream_t stream = nullptr;

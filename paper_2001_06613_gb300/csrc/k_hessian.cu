@@ -125,6 +125,8 @@ static unsigned apply_blocks_x(const Geom& g) {
     return (unsigned)per;
 }
 
+size_t hessvec_partials(const Geom& g, int nK) { return (size_t)apply_blocks_x(g) * (size_t)nK; }
+
 cudaError_t launch_hessvec(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
                            const float* v, float* Hv, HessWork& w, unsigned int* ticket,
                            double* out, DevScalars* pcg, cudaStream_t s) {

@@ -4,9 +4,14 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace stml {
+
+// Sets the text stml_last_error(NULL) returns (errors of context-free calls).
+void set_context_free_error(const std::string& msg);
 
 // Every launcher adds the number of kernels it launched to this counter.
 long long launches_total();
@@ -90,6 +95,9 @@ struct HessWork {
 cudaError_t launch_hessvec(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
                            const float* v, float* Hv, HessWork& w, unsigned int* ticket,
                            double* out, DevScalars* pcg, cudaStream_t s);
+
+// Doubles of partial sums launch_hessvec needs for a problem of this size.
+size_t hessvec_partials(const Geom& g, int nK);
 
 // ---------------------------------------------------------- PCG vector ops
 struct PcgArgs {
