@@ -268,8 +268,9 @@ def run_native(args):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
-    launches = S.stml_launch_count() - launches0 - 0
+    launches = S.stml_launch_count() - launches0
     prof = S.stml_profile_read(ctx.ptr)
+    table = S.stml_profile_report(ctx.ptr)
     S.stml_profile_enable(ctx.ptr, False)
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms_total = max_over_ranks(sum(ms_steps), world, dev)
@@ -332,13 +333,29 @@ def run_native(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = prof["bytes"] / (prof["ms"] / 1e3) / 1e9 if prof["ms"] > 0 else None
     tpf = matvec_traffic_per_pixel_frame()
+    finest = [r for r in table if r["kernel"] == "gn_hessian_product" and r["level"] == L - 1]
+    fin = None
+    if finest and finest[0]["ms"] > 0:
+        fgbs = finest[0]["bytes"] / (finest[0]["ms"] / 1e3) / 1e9
+        fin = {"achieved": fgbs, "frac": fgbs / peak, "launches": finest[0]["launches"],
+               "avg_us": 1e3 * finest[0]["ms"] / finest[0]["launches"],
+               "bytes_per_launch": finest[0]["bytes"] / finest[0]["launches"]}
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": (tpf * prof["pixel_frames"] / prof["launches"]) if tpf and prof["launches"] else None,
-            "kernel": "GN Hessian product (hv_sums + hv_apply)",
+            "kernel": "GN Hessian product (apply_kernel: read v, grad T; write Hv; 24 B per pixel-frame)",
             "algorithmic_bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
-            "launches": prof["launches"], "ms_total": prof["ms"],
+            "launches": prof["launches"], "ms_total": prof["ms"], "finest_level": fin,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s (of fallback)"}
+    per_kernel = {}
+    for r in table:
+        k = per_kernel.setdefault(r["kernel"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
+        k["launches"] += int(r["launches"])
+        k["ms"] += r["ms"]
+        k["bytes"] += r["bytes"]
+    for k in per_kernel.values():
+        k["GB/s"] = k["bytes"] / (k["ms"] / 1e3) / 1e9 if k["ms"] > 0 else None
+        k["ms_per_step"] = k["ms"] / args.steps
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
@@ -353,7 +370,8 @@ def run_native(args):
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": "frames/s",
                         "h2d_bytes_per_step": int(R.nbytes), "d2h_bytes_per_step": int(y_host.numel() * 4)},
-                "roofline": roof, "cpu_baseline": cpu, "final_J": outJ[0],
+                "roofline": roof, "cpu_baseline": cpu, "final_J": outJ[0], "kernels": per_kernel,
+                "kernel_levels": table,
                 "per_step_ms": ms_steps,
                 "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
                                                  "ls_trials", "stopped_early")} for s in stats],

@@ -22,7 +22,10 @@
  *   0-based frame numbers.
  * - Pointers documented as "device" must point to device memory of the GPU
  *   that was current when the context was created; "host" pointers to host
- *   memory.  The library never takes ownership of caller memory.
+ *   memory.  Device field arrays passed to stml_eval, stml_hessvec, stml_gir
+ *   and stml_hessvec_noalloc must be 16-byte aligned (cudaMalloc and torch
+ *   allocations are); others return STML_EINVAL.  The library never takes
+ *   ownership of caller memory.
  * - All work is ordered on the CUDA stream given to stml_create (or passed to
  *   the context-free operators); calls that return host values synchronise
  *   that stream only.
@@ -227,9 +230,9 @@ stml_status stml_hessvec_noalloc(const float* dT, const float* v, float* Hv, int
 
 /* ------------------------------------------------------------ profiling */
 
-/* Enables (1) or disables (0) CUDA-event timing of every launch of the
- * Gauss-Newton Hessian-product kernel on the context's stream, and resets
- * the counters. */
+/* Enables (1) or disables (0) CUDA-event timing of every solver launch on the
+ * context's stream (grouped by kernel class and level), and resets the
+ * counters. */
 stml_status stml_profile_enable(stml_ctx* ctx, int enable);
 
 /* Reads the counters: launches, summed device milliseconds, summed
@@ -237,6 +240,13 @@ stml_status stml_profile_enable(stml_ctx* ctx, int enable);
  * pixel-frame) and summed pixel-frames.  Synchronises the stream. */
 stml_status stml_profile_read(stml_ctx* ctx, long long* launches, double* ms, double* bytes,
                               double* pixel_frames);
+
+/* Per kernel class and level: launches, summed device milliseconds, summed
+ * algorithmic bytes and pixel-frames of every launch since
+ * stml_profile_enable(ctx, 1), as a JSON array written to buf (host, cap
+ * bytes, NUL-terminated, truncated if short); *needed (may be NULL) receives
+ * the full length plus one.  Synchronises the stream. */
+stml_status stml_profile_report(stml_ctx* ctx, char* buf, size_t cap, size_t* needed);
 
 /* Number of this library's kernel launches since the context was created. */
 long long stml_launch_count(const stml_ctx* ctx);

@@ -82,6 +82,7 @@ _SIGS = {
                                        C.POINTER(Params), _dp, _vp]),
     "stml_profile_enable": (C.c_int, [_vp, C.c_int]),
     "stml_profile_read": (C.c_int, [_vp, C.POINTER(C.c_longlong), _dp, _dp, _dp]),
+    "stml_profile_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "stml_launch_count": (C.c_longlong, [_vp]),
 }
 
@@ -314,6 +315,15 @@ def stml_profile_read(ctx):
     ms, by, pf = C.c_double(), C.c_double(), C.c_double()
     _check(load().stml_profile_read(ctx, C.byref(n), C.byref(ms), C.byref(by), C.byref(pf)), ctx)
     return {"launches": n.value, "ms": ms.value, "bytes": by.value, "pixel_frames": pf.value}
+
+
+def stml_profile_report(ctx) -> list:
+    import json
+    need = C.c_size_t()
+    _check(load().stml_profile_report(ctx, None, 0, C.byref(need)), ctx)
+    buf = C.create_string_buffer(need.value)
+    _check(load().stml_profile_report(ctx, buf, need.value, C.byref(need)), ctx)
+    return json.loads(buf.value.decode())
 
 
 def stml_launch_count(ctx=None) -> int:

@@ -28,10 +28,35 @@ struct DevScalars {
     double dots[kMaxRed];     // totals of the last dot-product kernel
     double rho, bnorm2, pq, alpha, beta, rnorm2;
     int cg_active, cg_iter, cg_flag, cg_pad;
+    unsigned int err_flags;   // bit 0: a bounded device wait expired
+    unsigned int err_pad;
     unsigned int ticket[8];   // arrival counters of the last-CTA reduction
 };
 
 enum CgFlag { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_ZERO = 4 };
+
+// Division by a fixed divisor d < 2^31 with a multiply-high (round-up method):
+// q = (umulhi(n, m) + n) >> s, s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+    unsigned d, m, s;
+    static FastDiv make(unsigned dv) {
+        FastDiv f;
+        f.d = dv;
+        unsigned sh = 0;
+        while ((1ull << sh) < dv) ++sh;
+        f.s = sh;
+        f.m = (unsigned)((((1ull << sh) - dv) << 32) / dv + 1);
+        return f;
+    }
+    __device__ __forceinline__ unsigned div(unsigned n) const {
+        return (unsigned)(((unsigned long long)__umulhi(n, m) + n) >> s);
+    }
+};
+
+// Divisors that turn a pixel index into (x, y, z).
+struct PixIndex {
+    FastDiv nx, ny;
+};
 
 // Per-GIR description of the frame subset K in device memory.
 struct FrameSet {

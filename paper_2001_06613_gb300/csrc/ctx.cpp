@@ -7,6 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <initializer_list>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -44,7 +47,8 @@ struct stml_ctx {
     // workspace, sized for the finest level and all frames
     float *w_u = nullptr, *w_g = nullptr, *w_dT = nullptr, *w_x = nullptr, *w_r = nullptr,
           *w_p = nullptr, *w_q = nullptr, *w_ut = nullptr;
-    float *w_a = nullptr, *w_m1 = nullptr, *w_m2 = nullptr;
+    float *w_abar = nullptr, *w_ubar = nullptr;    // per-pixel frame means of the last objective pass
+    float *w_m1 = nullptr, *w_m2 = nullptr;        // per-pixel frame sums of the PCG direction
     float *w_z = nullptr, *w_z2 = nullptr;     // predictor state z_{l,q,all}
     double* partials = nullptr;
     size_t partials_cap = 0;                   // in doubles
@@ -63,11 +67,16 @@ struct stml_ctx {
     double dhat_prev = 0.0;
     bool level_done = false;
 
-    // profiling of the Hessian-product launches
+    // profiling: CUDA events around every launch of the solver, per kernel
+    // class and level (key = class * 64 + level), with algorithmic bytes
     bool prof = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    struct ProfEvent {
+        int key;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfEvent> ev;
     size_t ev_used = 0;
-    double prof_bytes = 0.0, prof_pf = 0.0;
+    std::map<int, std::array<double, 3>> pacc;   // key -> launches, bytes, pixel-frames
 
     std::string err;
 };
@@ -147,7 +156,7 @@ void free_buffers(stml_ctx* c) {
     }
     c->lv.clear();
     dfree(c->w_u); dfree(c->w_g); dfree(c->w_dT); dfree(c->w_x); dfree(c->w_r);
-    dfree(c->w_p); dfree(c->w_q); dfree(c->w_ut); dfree(c->w_a); dfree(c->w_m1);
+    dfree(c->w_p); dfree(c->w_q); dfree(c->w_ut); dfree(c->w_abar); dfree(c->w_ubar); dfree(c->w_m1);
     dfree(c->w_m2); dfree(c->w_z); dfree(c->w_z2); dfree(c->partials);
     dfree(c->d_frames); dfree(c->d_wnext); dfree(c->d_idx); dfree(c->d_lsf);
     dfree(c->d_kidx); dfree(c->d_taps); dfree(c->d_rho);
@@ -177,6 +186,14 @@ stml_status check_frames(stml_ctx* c, const int* frames, int nK) {
     return STML_OK;
 }
 
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+stml_status check_aligned(stml_ctx* c, std::initializer_list<const void*> ptrs) {
+    for (const void* p : ptrs)
+        if (p && !al16(p)) return fail(c, STML_EINVAL, "device arrays must be 16-byte aligned");
+    return STML_OK;
+}
+
 stml_status check_level(stml_ctx* c, int level) {
     if (!c->built) return fail(c, STML_ESTATE, "no pyramid: call stml_load_sequence and stml_build_pyramid");
     if (level < 0 || level >= (int)c->lv.size()) return fail(c, STML_EINVAL, "level out of range");
@@ -201,32 +218,49 @@ stml_status upload_frameset(stml_ctx* c, const std::vector<int>& K, FrameSet& fs
 stml_status read_scalars(stml_ctx* c) {
     CK(c, cudaMemcpyAsync(c->Sh, c->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (c->Sh->err_flags & 1u) return fail(c, STML_ETIMEOUT, "a bounded device wait expired (bulk copy not completed)");
     return STML_OK;
 }
 
-stml_status hessvec_launch(stml_ctx* c, const Geom& g, const FrameSet& fs, const Coef& cf,
+enum ProfClass {
+    PC_HESS = 0, PC_EVAL, PC_TRIAL, PC_PCG_INIT, PC_PCG_UPDATE, PC_PCG_P, PC_DOT,
+    PC_PRED_LS, PC_PRED_LIN, PC_PROLONG, PC_GATHER, PC_RESTRICT, PC_COUNT
+};
+const char* const kProfNames[PC_COUNT] = {
+    "gn_hessian_product", "gradient_pass", "objective_pass", "pcg_init", "pcg_update",
+    "pcg_direction", "dot_gd", "predict_ls_eq2", "predict_linear", "prolong", "gather_scatter",
+    "restrict"};
+
+// Starts an event pair (returns its index, or -1 when profiling is off).
+long prof_begin(stml_ctx* c, int cls, int level) {
+    if (!c->prof) return -1;
+    if (c->ev_used == c->ev.size()) {
+        stml_ctx::ProfEvent pe{0, nullptr, nullptr};
+        if (cudaEventCreate(&pe.a) != cudaSuccess || cudaEventCreate(&pe.b) != cudaSuccess) return -1;
+        c->ev.push_back(pe);
+    }
+    const long i = (long)c->ev_used++;
+    c->ev[i].key = cls * 64 + level;
+    cudaEventRecord(c->ev[i].a, c->stream);
+    return i;
+}
+
+void prof_end(stml_ctx* c, long i, double bytes, double pixel_frames) {
+    if (i < 0) return;
+    cudaEventRecord(c->ev[i].b, c->stream);
+    auto& acc = c->pacc[c->ev[i].key];
+    acc[0] += 1;
+    acc[1] += bytes;
+    acc[2] += pixel_frames;
+}
+
+stml_status hessvec_launch(stml_ctx* c, int level, const Geom& g, const FrameSet& fs, const Coef& cf,
                            const float* dT, const float* v, float* Hv, DevScalars* pcg) {
     HessWork hw{c->w_m1, c->w_m2, c->partials, c->partials_cap};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->prof) {
-        if (c->ev_used == c->ev.size()) {
-            cudaEvent_t a, b;
-            CK(c, cudaEventCreate(&a));
-            CK(c, cudaEventCreate(&b));
-            c->ev.emplace_back(a, b);
-        }
-        e0 = c->ev[c->ev_used].first;
-        e1 = c->ev[c->ev_used].second;
-        c->ev_used++;
-        CK(c, cudaEventRecord(e0, c->stream));
-    }
+    const long pe = prof_begin(c, PC_HESS, level);
     CK(c, launch_hessvec(g, fs, cf, dT, v, Hv, hw, &c->S->ticket[1], c->S->dots + 4, pcg, c->stream));
-    if (c->prof) {
-        CK(c, cudaEventRecord(e1, c->stream));
-        const double pf = (double)fs.nK * (double)g.N;
-        c->prof_pf += pf;
-        c->prof_bytes += pf * 12.0 * g.d;
-    }
+    const double pf = (double)fs.nK * (double)g.N;
+    prof_end(c, pe, pf * 12.0 * g.d, pf);
     return STML_OK;
 }
 
@@ -242,7 +276,6 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     FrameSet fs;
     TRY(upload_frameset(c, K, fs));
     const Coef cf = make_coef(g, p, nK);
-    EvalWork ew{c->w_a, c->w_m1, c->w_m2, c->partials, c->partials_cap};
     float* u = u_io;
     float* ut = c->w_ut;
     DevScalars* S = c->S;
@@ -253,8 +286,17 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     s.n_frames = nK;
     s.status = STML_OK;
 
+    const double pfK = (double)nK * (double)g.N;
+    // objective + gradient at u (start of the GIR)
     auto eval_full = [&]() -> stml_status {
-        CK(c, launch_eval(L.img, g, fs, cf, u, nullptr, 0.f, c->w_dT, c->w_g, ew, &S->ticket[0], S->red, c->stream));
+        long pe = prof_begin(c, PC_TRIAL, level);
+        CK(c, launch_objective(L.img, g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->partials, c->partials_cap,
+                               &S->ticket[0], S->red, c->stream));
+        prof_end(c, pe, pfK * (4.0 + 4.0 * g.d), pfK);
+        pe = prof_begin(c, PC_EVAL, level);
+        CK(c, launch_gradient(L.img, g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->w_g, c->w_dT, nullptr,
+                              c->partials, c->partials_cap, &S->ticket[4], S->red, c->stream));
+        prof_end(c, pe, pfK * (4.0 + 12.0 * g.d), pfK);
         return read_scalars(c);
     };
 
@@ -280,16 +322,27 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         if (gnorm <= p.g_abs * (1.0 + std::fabs(J0)) || it >= p.max_gn) break;
 
         // --- PCG for H d = -g, all coefficients on the device
-        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, c->w_x, c->w_r, c->w_p, c->partials, S, pa, c->stream));
+        long pe = prof_begin(c, PC_PCG_INIT, level);
+        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_m1, c->w_m2, c->partials,
+                              c->partials_cap, S, pa, c->stream));
+        prof_end(c, pe, pfK * 20.0 * g.d, pfK);
         // iterations are launched in chunks; once the device clears
         // cg_active the remaining launches of a chunk return at once
         int launched = 0;
         do {
             const int chunk = std::min(4, p.max_cg - launched);
             for (int i = 0; i < chunk; ++i) {
-                TRY(hessvec_launch(c, g, fs, cf, c->w_dT, c->w_p, c->w_q, S));
-                CK(c, launch_pcg_update(g, fs, cf, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->partials, S, pa, c->stream));
-                CK(c, launch_pcg_pupdate(g, fs, cf, c->w_dT, c->w_r, c->w_p, S, c->stream));
+                pe = prof_begin(c, PC_HESS, level);
+                CK(c, launch_hess_apply(g, fs, cf, c->w_dT, c->w_p, c->w_m1, c->w_m2, c->w_q, c->partials,
+                                        c->partials_cap, &S->ticket[1], S->dots + 4, S, c->stream));
+                prof_end(c, pe, pfK * 12.0 * g.d, pfK);
+                pe = prof_begin(c, PC_PCG_UPDATE, level);
+                CK(c, launch_pcg_update(g, fs, cf, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->partials,
+                                        c->partials_cap, S, pa, c->stream));
+                prof_end(c, pe, pfK * 28.0 * g.d, pfK);
+                pe = prof_begin(c, PC_PCG_P, level);
+                CK(c, launch_pcg_direction(g, fs, cf, c->w_dT, c->w_r, c->w_p, c->w_m1, c->w_m2, S, c->stream));
+                prof_end(c, pe, pfK * 16.0 * g.d, pfK);
             }
             launched += chunk;
             TRY(read_scalars(c));
@@ -299,7 +352,9 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
             CK(c, cudaMemcpyAsync(c->w_x, c->w_p, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
 
         // --- directional derivative and Armijo back-tracking
+        pe = prof_begin(c, PC_DOT, level);
         CK(c, launch_dot2(c->w_g, c->w_x, M, c->partials, &S->ticket[3], S->dots, c->stream));
+        prof_end(c, pe, pfK * 8.0 * g.d, pfK);
         TRY(read_scalars(c));
         const double gTd = c->Sh->dots[0], dnorm2 = c->Sh->dots[1];
         if (!(gTd < 0.0)) {
@@ -310,7 +365,10 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         bool accepted = false;
         for (int ls = 0; ls < p.max_ls; ++ls) {
             s.ls_trials++;
-            CK(c, launch_eval(L.img, g, fs, cf, u, c->w_x, (float)t, nullptr, nullptr, ew, &S->ticket[0], S->trial, c->stream));
+            pe = prof_begin(c, PC_TRIAL, level);
+            CK(c, launch_objective(L.img, g, fs, cf, u, c->w_x, (float)t, c->w_abar, c->w_ubar, c->partials,
+                                   c->partials_cap, &S->ticket[0], S->trial, c->stream));
+            prof_end(c, pe, pfK * (4.0 + 8.0 * g.d), pfK);
             TRY(read_scalars(c));
             const double Jt = c->Sh->trial[0];
             if (Jt <= J + p.armijo_c * t * gTd) {
@@ -323,15 +381,20 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
             s.status = STML_ELINESEARCH;
             break;
         }
-        CK(c, launch_axpy(u, c->w_x, (float)t, ut, M, c->stream));
+        // accepted: the step u + t d is written by the gradient pass, which
+        // reuses the frame means of the last (accepted) trial's objective pass
+        pe = prof_begin(c, PC_EVAL, level);
+        CK(c, launch_gradient(L.img, g, fs, cf, u, c->w_x, (float)t, c->w_abar, c->w_ubar, c->w_g, c->w_dT, ut,
+                              c->partials, c->partials_cap, &S->ticket[4], S->red, c->stream));
+        prof_end(c, pe, pfK * (4.0 + 20.0 * g.d), pfK);
+        TRY(read_scalars(c));
         std::swap(u, ut);
         step_norm = t * std::sqrt(dnorm2);
         J_old = J;
-        TRY(eval_full());
-        J = c->Sh->red[0];
-        D = c->Sh->red[1];
-        Sv = c->Sh->red[2];
-        Pv = c->Sh->red[3];
+        J = c->Sh->trial[0];
+        D = c->Sh->trial[1];
+        Sv = c->Sh->trial[2];
+        Pv = c->Sh->trial[3];
         gnorm2 = c->Sh->red[4];
         unorm2 = c->Sh->red[5];
         ++it;
@@ -416,8 +479,10 @@ stml_status run_predict_ls(stml_ctx* c, const std::vector<int>& K, const float* 
     ls_factors(c->n, K, c->p.beta, tab, kidx);
     CK(c, cudaMemcpyAsync(c->d_lsf, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaMemcpyAsync(c->d_kidx, kidx.data(), kidx.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    const long pe = prof_begin(c, PC_PRED_LS, c->cur_level < 0 ? 0 : c->cur_level);
     CK(c, launch_predict_ls(eta, omega, zeta, c->d_lsf, c->d_lsf + c->n, c->d_lsf + 2 * c->n, c->d_kidx, c->n,
                             ncomp, c->stream));
+    prof_end(c, pe, (double)ncomp * (16.0 * c->n + 8.0 * K.size()), (double)ncomp * c->n / c->d);
     return STML_OK;
 }
 
@@ -425,7 +490,9 @@ stml_status run_predict_linear(stml_ctx* c, const std::vector<int>& K, const std
                                const float* in, float* out, size_t plane) {
     std::vector<LinTap> taps = linear_taps(K, targets, true);
     CK(c, cudaMemcpyAsync(c->d_taps, taps.data(), taps.size() * sizeof(LinTap), cudaMemcpyHostToDevice, c->stream));
+    const long pe = prof_begin(c, PC_PRED_LIN, c->cur_level < 0 ? 0 : c->cur_level);
     CK(c, launch_predict_linear(in, out, c->d_taps, (int)taps.size(), plane, c->stream));
+    prof_end(c, pe, 12.0 * plane * taps.size(), (double)plane * taps.size() / c->d);
     return STML_OK;
 }
 
@@ -440,7 +507,9 @@ stml_status do_predict(stml_ctx* c, int level, int q) {
         } else {
             const LevelBuf& C = c->lv[level - 1];
             if (L.g.nx != 2 * C.g.nx) return fail(c, STML_EINVAL, "level shapes do not halve");
+            const long pe = prof_begin(c, PC_PROLONG, level);
             CK(c, launch_prolong(C.y, c->w_z, c->n * c->d, C.g, c->stream));
+            prof_end(c, pe, 4.0 * c->n * c->d * (double)(L.g.N + C.g.N), (double)c->n * L.g.N);
         }
         c->cur_level = level;
         c->last_q = -1;
@@ -468,7 +537,9 @@ stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finis
     const std::vector<int>& K = c->sets[q];
     const int Q = (int)c->sets.size();
     TRY(upload_idx(c, K));
+    long pe = prof_begin(c, PC_GATHER, level);
     CK(c, launch_gather_planes(c->w_z, c->w_u, c->d_idx, (int)K.size(), plane, c->stream));
+    prof_end(c, pe, 8.0 * plane * K.size(), (double)K.size() * L.g.N);
     stml_stats s{};
     TRY(run_gir(c, level, K, c->w_u, &s));
     s.tlevel = q;
@@ -558,8 +629,8 @@ void stml_destroy(stml_ctx* c) {
     cudaStreamSynchronize(c->stream);
     free_buffers(c);
     for (auto& pr : c->ev) {
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
+        cudaEventDestroy(pr.a);
+        cudaEventDestroy(pr.b);
     }
     dfree(c->S);
     if (c->Sh) cudaFreeHost(c->Sh);
@@ -614,12 +685,15 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
     const size_t fieldN = (size_t)n_frames * dim * G.N;
     const size_t imgN = (size_t)n_frames * G.N;
     size_t pcap = 0;
-    for (int l = 0; l < L; ++l) pcap = std::max(pcap, partials_needed(c->lv[l].g, n_frames));
+    for (int l = 0; l < L; ++l)
+        pcap = std::max(pcap, std::max(eval_partials(c->lv[l].g, n_frames), gn_partials(c->lv[l].g, n_frames)));
+    pcap += 1024 * kMaxRed;
     c->partials_cap = pcap;
     bool ok = true;
     float** fields[] = {&c->w_u, &c->w_g, &c->w_dT, &c->w_x, &c->w_r, &c->w_p, &c->w_q, &c->w_ut, &c->w_z, &c->w_z2};
     for (float** fp : fields) ok = ok && dalloc(fp, fieldN) == cudaSuccess;
-    ok = ok && dalloc(&c->w_a, imgN) == cudaSuccess;
+    ok = ok && dalloc(&c->w_abar, (size_t)G.N) == cudaSuccess;
+    ok = ok && dalloc(&c->w_ubar, (size_t)dim * G.N) == cudaSuccess;
     ok = ok && dalloc(&c->w_m1, (size_t)G.N) == cudaSuccess;
     ok = ok && dalloc(&c->w_m2, (size_t)dim * G.N) == cudaSuccess;
     ok = ok && dalloc(&c->partials, pcap) == cudaSuccess;
@@ -771,21 +845,20 @@ stml_status stml_eval(stml_ctx* c, int level, const int* frames, int nK, const f
     TRY(check_level(c, level));
     TRY(check_frames(c, frames, nK));
     if (!u || !out) return fail(c, STML_EINVAL, "u and out are required");
+    TRY(check_aligned(c, {u, g, dT}));
     cudaSetDevice(c->device);
     LevelBuf& L = c->lv[level];
     std::vector<int> K(frames, frames + nK);
     FrameSet fs;
     TRY(upload_frameset(c, K, fs));
     const Coef cf = make_coef(L.g, c->p, nK);
-    EvalWork ew{c->w_a, c->w_m1, c->w_m2, c->partials, c->partials_cap};
     const bool full = g || dT;
-    if (full) {
-        CK(c, launch_eval(L.img, L.g, fs, cf, u, nullptr, 0.f, dT ? dT : c->w_dT, g ? g : c->w_g, ew,
-                          &c->S->ticket[0], c->S->red, c->stream));
-    } else {
-        CK(c, launch_eval(L.img, L.g, fs, cf, u, nullptr, 0.f, nullptr, nullptr, ew, &c->S->ticket[0],
-                          c->S->red, c->stream));
-    }
+    CK(c, launch_objective(L.img, L.g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->partials, c->partials_cap,
+                           &c->S->ticket[0], c->S->red, c->stream));
+    if (full)
+        CK(c, launch_gradient(L.img, L.g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, g ? g : c->w_g,
+                              dT ? dT : c->w_dT, nullptr, c->partials, c->partials_cap, &c->S->ticket[4], c->S->red,
+                              c->stream));
     TRY(read_scalars(c));
     for (int i = 0; i < 6; ++i) out[i] = c->Sh->red[i];
     if (!full) out[4] = 0.0;
@@ -798,13 +871,14 @@ stml_status stml_hessvec(stml_ctx* c, int level, const int* frames, int nK, cons
     TRY(check_level(c, level));
     TRY(check_frames(c, frames, nK));
     if (!dT || !v || !Hv) return fail(c, STML_EINVAL, "dT, v and Hv are required");
+    TRY(check_aligned(c, {dT, v, Hv}));
     cudaSetDevice(c->device);
     LevelBuf& L = c->lv[level];
     std::vector<int> K(frames, frames + nK);
     FrameSet fs;
     TRY(upload_frameset(c, K, fs));
     const Coef cf = make_coef(L.g, c->p, nK);
-    TRY(hessvec_launch(c, L.g, fs, cf, dT, v, Hv, nullptr));
+    TRY(hessvec_launch(c, level, L.g, fs, cf, dT, v, Hv, nullptr));
     TRY(read_scalars(c));
     if (vHv) *vHv = c->Sh->dots[4];
     return STML_OK;
@@ -815,6 +889,7 @@ stml_status stml_gir(stml_ctx* c, int level, const int* frames, int nK, float* u
     TRY(check_level(c, level));
     TRY(check_frames(c, frames, nK));
     if (!u) return fail(c, STML_EINVAL, "u is required");
+    TRY(check_aligned(c, {u}));
     cudaSetDevice(c->device);
     std::vector<int> K(frames, frames + nK);
     return run_gir(c, level, K, u, stats);
@@ -930,8 +1005,7 @@ stml_status stml_profile_enable(stml_ctx* c, int enable) {
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
     c->prof = enable != 0;
     c->ev_used = 0;
-    c->prof_bytes = 0.0;
-    c->prof_pf = 0.0;
+    c->pacc.clear();
     return STML_OK;
 }
 
@@ -939,16 +1013,57 @@ stml_status stml_profile_read(stml_ctx* c, long long* launches, double* ms, doub
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
     cudaSetDevice(c->device);
     CK(c, cudaStreamSynchronize(c->stream));
-    double tot = 0.0;
+    double tot = 0.0, by = 0.0, pf = 0.0;
+    long long nl = 0;
+    for (size_t i = 0; i < c->ev_used; ++i) {
+        if (c->ev[i].key / 64 != PC_HESS) continue;
+        float m = 0.f;
+        CK(c, cudaEventElapsedTime(&m, c->ev[i].a, c->ev[i].b));
+        tot += m;
+        ++nl;
+    }
+    for (const auto& kv : c->pacc)
+        if (kv.first / 64 == PC_HESS) {
+            by += kv.second[1];
+            pf += kv.second[2];
+        }
+    if (launches) *launches = nl;
+    if (ms) *ms = tot;
+    if (bytes) *bytes = by;
+    if (pixel_frames) *pixel_frames = pf;
+    return STML_OK;
+}
+
+stml_status stml_profile_report(stml_ctx* c, char* buf, size_t cap, size_t* needed) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    cudaSetDevice(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::map<int, double> ms;
     for (size_t i = 0; i < c->ev_used; ++i) {
         float m = 0.f;
-        CK(c, cudaEventElapsedTime(&m, c->ev[i].first, c->ev[i].second));
-        tot += m;
+        CK(c, cudaEventElapsedTime(&m, c->ev[i].a, c->ev[i].b));
+        ms[c->ev[i].key] += m;
     }
-    if (launches) *launches = (long long)c->ev_used;
-    if (ms) *ms = tot;
-    if (bytes) *bytes = c->prof_bytes;
-    if (pixel_frames) *pixel_frames = c->prof_pf;
+    std::string out = "[";
+    bool first = true;
+    char line[256];
+    for (const auto& kv : c->pacc) {
+        const int cls = kv.first / 64, lvl = kv.first % 64;
+        std::snprintf(line, sizeof(line),
+                      "%s{\"kernel\": \"%s\", \"level\": %d, \"launches\": %.0f, \"ms\": %.6f, "
+                      "\"bytes\": %.6g, \"pixel_frames\": %.6g}",
+                      first ? "" : ", ", kProfNames[cls], lvl, kv.second[0], ms[kv.first], kv.second[1],
+                      kv.second[2]);
+        out += line;
+        first = false;
+    }
+    out += "]";
+    if (needed) *needed = out.size() + 1;
+    if (buf && cap > 0) {
+        const size_t n = std::min(cap - 1, out.size());
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
     return STML_OK;
 }
 

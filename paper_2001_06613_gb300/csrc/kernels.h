@@ -3,6 +3,9 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
+
+#include <initializer_list>
 
 #include <string>
 
@@ -64,22 +67,20 @@ cudaError_t launch_scatter_planes(const float* src, float* dst, const int* idx, 
 
 cudaError_t launch_corr_coeff(const float* img, int n, long long N, double* rho_dev, cudaStream_t s);
 
-// ---------------------------------------------------------- objective
-// Evaluation workspace (device).
-struct EvalWork {
-    float* a;          // nK * N warped images
-    float* mean_a;     // N
-    float* mean_u;     // d * N
-    double* partials;  // >= blocks * kMaxRed
-    size_t partials_cap;
-};
-
-// J, D, S, P (and gradient) at u (or at u + t du when du != nullptr).
-// grad == nullptr selects the objective only; results go to out[0..6):
-// J, D, S, P, |g|^2, |u|^2 (in device memory, DevScalars::red or ::trial).
-cudaError_t launch_eval(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf,
-                        const float* u, const float* du, float t, float* dT, float* grad,
-                        EvalWork& w, unsigned int* ticket, double* out, cudaStream_t s);
+// ---------------------------------------------------------- objective (k_eval.cu)
+// Objective pass at u (or u + t du): J, D, S, P, |u|^2 to out[0..3], out[5]
+// (out[4] = 0), and the per-pixel frame means abar (N) and ubar (d N).
+cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
+                             const float* du, float t, float* abar, float* ubar, double* partials,
+                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s);
+// Gradient pass at u (or u + t du) with abar, ubar of the same point: g and
+// grad T, optionally the point itself (unew); |g|^2 and |u|^2 to out[4], out[5].
+cudaError_t launch_gradient(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
+                            const float* du, float t, const float* abar, const float* ubar, float* grad, float* dT,
+                            float* unew, double* partials, size_t partials_cap, unsigned int* ticket, double* out,
+                            cudaStream_t s);
+// Doubles of partial sums the evaluation kernels need.
+size_t eval_partials(const Geom& g, int nK);
 
 // ---------------------------------------------------------- Hessian product
 struct HessWork {
@@ -89,35 +90,45 @@ struct HessWork {
     size_t partials_cap;
 };
 
-// Hv and <v, Hv> (to out[0]).  With pcg != nullptr the launch is a step of
-// the device-side PCG: it does nothing once cg_active is 0, and its last CTA
-// sets alpha = rho / <p, Hp> (or flags a breakdown).
+// Hv and <v, Hv> (to out[0]) for a given v: per-pixel frame sums, then the
+// stencil stream.  With pcg != nullptr the launch is a step of the device-side
+// PCG: it does nothing once cg_active is 0, and its last CTA sets
+// alpha = rho / <p, Hp> (or flags a breakdown).
 cudaError_t launch_hessvec(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
                            const float* v, float* Hv, HessWork& w, unsigned int* ticket,
                            double* out, DevScalars* pcg, cudaStream_t s);
 
-// Doubles of partial sums launch_hessvec needs for a problem of this size.
-size_t hessvec_partials(const Geom& g, int nK);
+// Doubles of partial sums the Gauss-Newton kernels need for a problem of this size.
+size_t gn_partials(const Geom& g, int nK);
+
+// The two halves of the Hessian product (k_gn.cu): per-pixel frame sums of v
+// (mean of grad T . v, sum of v) and the stencil stream that uses them.
+cudaError_t launch_hess_sums(const Geom& g, const FrameSet& fs, const float* dT, const float* v, float* mean_s,
+                             float* sum_v, cudaStream_t s);
+cudaError_t launch_hess_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const float* v,
+                              const float* mean_s, const float* sum_v, float* Hv, double* partials,
+                              size_t partials_cap, unsigned int* ticket, double* out, DevScalars* pcg,
+                              cudaStream_t s);
 
 // ---------------------------------------------------------- PCG vector ops
 struct PcgArgs {
     float tol_cg;
     int max_cg;
 };
-cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad,
-                            const float* dT, float* x, float* r, float* p, double* partials,
-                            DevScalars* S, PcgArgs a, cudaStream_t s);
-cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
-                              float* x, float* r, const float* p, const float* q,
-                              double* partials, DevScalars* S, PcgArgs a, cudaStream_t s);
-cudaError_t launch_pcg_pupdate(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
-                               const float* r, float* p, DevScalars* S, cudaStream_t s);
+// r = -g, p = M^-1 r, x = 0, rho = <r, M^-1 r>, |r|^2, and the frame sums of p.
+cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+                            float* x, float* r, float* p, float* mean_s, float* sum_v, double* partials,
+                            size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s);
+// x += alpha p, r -= alpha q; rho, convergence test, beta.
+cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, float* x, float* r,
+                              const float* p, const float* q, double* partials, size_t partials_cap, DevScalars* S,
+                              PcgArgs a, cudaStream_t s);
+// p = M^-1 r + beta p, and the frame sums of the new p.
+cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const float* r,
+                                 float* p, float* mean_s, float* sum_v, DevScalars* S, cudaStream_t s);
 // out[0] = <a, b>, out[1] = <b, b>
 cudaError_t launch_dot2(const float* a, const float* b, size_t n, double* partials,
                         unsigned int* ticket, double* out, cudaStream_t s);
-// y = x + t d
-cudaError_t launch_axpy(const float* x, const float* d, float t, float* y, size_t n, cudaStream_t s);
 
-size_t partials_needed(const Geom& g, int nK);
 
 }  // namespace stml

@@ -53,15 +53,17 @@ extern "C" stml_status stml_hessvec_noalloc(const float* dT, const float* v, flo
         if (shape[i] < 1) return err(STML_EINVAL, "stml_hessvec_noalloc: bad shape");
         sh3[3 - dim + i] = shape[i];
     }
+    if (((uintptr_t)dT | (uintptr_t)v | (uintptr_t)Hv) & 15u)
+        return err(STML_EINVAL, "stml_hessvec_noalloc: device arrays must be 16-byte aligned");
     for (int j = 1; j < nK; ++j)
         if (frames[j] <= frames[j - 1]) return err(STML_EINVAL, "stml_hessvec_noalloc: frames must increase");
     const Geom g = make_geom(sh3, dim, (float)h);
 
-    // scratch layout: ticket + result | frames | w_next | partials | mean_s | sum_v
+    // scratch layout: ticket (0), result (8) | frames | w_next | partials | mean_s | sum_v
     const size_t off_frames = 256;
     const size_t off_w = off_frames + align256((size_t)nK * sizeof(int));
     const size_t off_part = off_w + align256((size_t)nK * sizeof(float));
-    const size_t off_ms = off_part + align256(hessvec_partials(g, nK) * sizeof(double));
+    const size_t off_ms = off_part + align256(gn_partials(g, nK) * sizeof(double));
     const size_t off_sv = off_ms + align256((size_t)g.N * sizeof(float));
     const size_t need = off_sv + align256((size_t)dim * g.N * sizeof(float));
     if (need > kScratchBytes)
@@ -111,8 +113,7 @@ extern "C" stml_status stml_hessvec_noalloc(const float* dT, const float* v, flo
     cf.inv_h2 = (float)(1.0 / (h * h));
     cf.inv_nK = (float)(1.0 / nK);
     cf.diag_D = (float)(hd * (1.0 - 1.0 / nK));
-    HessWork hw{(float*)(base + off_ms), (float*)(base + off_sv), (double*)(base + off_part),
-                hessvec_partials(g, nK)};
+    HessWork hw{(float*)(base + off_ms), (float*)(base + off_sv), (double*)(base + off_part), gn_partials(g, nK)};
     e = launch_hessvec(g, fs, cf, dT, v, Hv, hw, ticket, out, nullptr, s);
     if (e != cudaSuccess) return err(STML_ECUDA, cudaGetErrorString(e));
     if (vHv) {

@@ -1,0 +1,109 @@
+"""Per-operation throughput of the library on one grid level (CUDA events).
+
+    python -m paper_2001_06613_gb300.opbench --op all --shape 256 256 --frames 200
+
+Each operation is timed through the C ABI on device-resident data and reported
+as achieved GB/s of its algorithmic bytes (every array it must read or write
+counted once, per pixel-frame, fp32; see the table in each result) against
+the measured HBM copy bandwidth.  Inputs are larger than L2 at the default
+size, and L2 is flushed before every timed call.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _peak():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        return 6800.0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="all",
+                    choices=["all", "hessvec", "eval", "objective", "trial", "pcg", "predict_ls"])
+    ap.add_argument("--shape", type=int, nargs="+", default=[256, 256])
+    ap.add_argument("--frames", type=int, default=200)
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    args = ap.parse_args(argv)
+
+    import torch
+    import paper_2001_06613_gb300 as S
+    from paper_2001_06613_gb300 import synthetic
+    S.load()
+    dev = torch.device("cuda", 0)
+    shape = tuple(args.shape)
+    d = len(shape)
+    n = args.frames
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(0)
+    R = torch.rand((n,) + shape, device=dev, dtype=torch.float32)
+    prm = S.stml_default_params(n_levels=1, n_tlevels=1)
+    ctx = S.Context(prm)
+    S.stml_load_sequence(ctx.ptr, R)
+    S.stml_build_pyramid(ctx.ptr)
+    frames = list(range(n))
+    u = torch.from_numpy(synthetic.random_field(rng, 1, d, shape, amp=2.0, rough=0.3)).to(dev)
+    u = u.expand(n, *u.shape[1:]).contiguous()
+    v = torch.randn((n, d) + shape, device=dev)
+    g = torch.empty_like(v)
+    dT = torch.empty_like(v)
+    Hv = torch.empty_like(v)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    peak = _peak()
+    pf = n * N
+    S.stml_eval(ctx.ptr, 0, frames, u, g, dT)
+
+    def timed(fn, nbytes, name, per_pf):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.iters):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        gbs = nbytes / (ms / 1e3) / 1e9
+        print(json.dumps({"op": name, "shape": list(shape), "frames": n, "ms": ms, "GB/s": gbs,
+                          "frac_of_measured_hbm": gbs / peak, "bytes_per_pixel_frame": per_pf}), flush=True)
+
+    ops = [args.op] if args.op != "all" else ["hessvec", "eval", "objective", "predict_ls"]
+    for op in ops:
+        if op == "hessvec":
+            b = 12 * d                     # read v, read grad T, write Hv
+            timed(lambda: S.stml_hessvec(ctx.ptr, 0, frames, dT, v, Hv), b * pf, op, b)
+        elif op == "eval":
+            b = 4 + 4 * d + 12 * d         # read T, read u; write grad T, g, M^-1
+            timed(lambda: S.stml_eval(ctx.ptr, 0, frames, u, g, dT), b * pf, op, b)
+        elif op == "objective":
+            b = 4 + 4 * d                  # read T, read u
+            timed(lambda: S.stml_eval(ctx.ptr, 0, frames, u), b * pf, op, b)
+        elif op == "predict_ls":
+            K = list(range(0, n, 4))
+            if K[-1] != n - 1:
+                K.append(n - 1)
+            eta = torch.randn((len(K), d) + shape, device=dev)
+            omega = torch.randn((n, d) + shape, device=dev)
+            zeta = torch.empty_like(omega)
+            b = 16 + 8 * len(K) / n        # omega (all + K), zeta x3 (in-place sweep), eta on K
+            timed(lambda: S.stml_predict_ls(eta, K, omega, zeta, n, 1e-5, d * N), b * d * pf, op, b * d)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

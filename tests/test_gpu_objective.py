@@ -166,3 +166,45 @@ def test_bad_frames_are_rejected(S):
         assert e.value.status == -8
     finally:
         ctx.close()
+
+
+def test_many_frames_use_the_two_pass_path(S):
+    """1000 frames exceed the shared memory of the single-pass cluster kernels
+    (their staged per-frame terms); the two-pass kernels take over."""
+    import torch
+    n, shape = 1000, (8, 64)
+    R = synthetic.make_sequence(synthetic.spec_custom(n, shape, seed=17, amp=1.0))
+    ctx = _ctx(S, R, 1)
+    try:
+        frames = list(range(n))
+        rng = np.random.default_rng(18)
+        u = synthetic.random_field(rng, n, 2, shape, amp=0.8, rough=0.2, modes=1)
+        g = torch.empty((n, 2) + shape, device="cuda")
+        dT = torch.empty_like(g)
+        out = S.stml_eval(ctx.ptr, 0, frames, _dev(u), g, dT)
+        p = _oracle_params(ctx.params)
+        ev = objective.evaluate(R.astype(np.float64), u.astype(np.float64), frames, 1.0, p)
+        assert_scalar(out[0], ev["J"], what="J")
+        assert_array(g.cpu().numpy(), ev["g"], what="gradient")
+        v = synthetic.random_field(rng, n, 2, shape, amp=1.0, rough=0.5, modes=1)
+        Hv = torch.empty_like(g)
+        vhv = S.stml_hessvec(ctx.ptr, 0, frames, dT, _dev(v), Hv)
+        ref = objective.hessvec(dT.cpu().numpy().astype(np.float64), v.astype(np.float64), frames, 1.0, p)
+        assert_array(Hv.cpu().numpy(), ref, what="Hv")
+        assert_scalar(vhv, float(np.sum(v.astype(np.float64) * ref)), what="<v,Hv>")
+    finally:
+        ctx.close()
+
+
+def test_misaligned_device_arrays_are_rejected(S):
+    import torch
+    R = synthetic.make_sequence(synthetic.spec_custom(3, (16, 16), seed=1))
+    ctx = _ctx(S, R, 1)
+    try:
+        buf = torch.zeros(3 * 2 * 16 * 16 + 1, device="cuda")
+        u = buf[1:]                                   # 4-byte offset
+        with pytest.raises(S.StmlError) as e:
+            S.stml_eval(ctx.ptr, 0, [0, 1, 2], u)
+        assert e.value.status == -1 and "aligned" in S.stml_last_error(ctx.ptr)
+    finally:
+        ctx.close()
