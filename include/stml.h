@@ -230,9 +230,9 @@ stml_status stml_hessvec_noalloc(const float* dT, const float* v, float* Hv, int
 
 /* ------------------------------------------------------------ profiling */
 
-/* Enables (1) or disables (0) CUDA-event timing of every solver launch on the
- * context's stream (grouped by kernel class and level), and resets the
- * counters. */
+/* CUDA-event timing of solver launches on the context's stream, grouped by
+ * kernel class and level: 1 times every launch, 2 only the Gauss-Newton
+ * Hessian-product launches, 0 none.  Resets the counters. */
 stml_status stml_profile_enable(stml_ctx* ctx, int enable);
 
 /* Reads the counters: launches, summed device milliseconds, summed

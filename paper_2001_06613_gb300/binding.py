@@ -306,8 +306,9 @@ def stml_hessvec_noalloc(dT, v, Hv, shape: Sequence[int], h: float, frames: Sequ
     return vhv.value
 
 
-def stml_profile_enable(ctx, enable: bool = True):
-    _check(load().stml_profile_enable(ctx, int(enable)), ctx)
+def stml_profile_enable(ctx, mode: int = 1):
+    """mode 1: time every solver launch; 2: only the Hessian product; 0: off."""
+    _check(load().stml_profile_enable(ctx, int(mode)), ctx)
 
 
 def stml_profile_read(ctx):

@@ -170,6 +170,22 @@ __device__ __forceinline__ void interp2(const float* __restrict__ T, const Geom&
     gy = g.inv_h * (a1 - a0);
 }
 
+// Bilinear value only (zero extension).
+__device__ __forceinline__ float interp2_val(const float* __restrict__ T, const Geom& g, int x, int y, float uy,
+                                             float ux) {
+    int iy, ix;
+    float fy, fx;
+    split_coord(y, uy, g.inv_h, iy, fy);
+    split_coord(x, ux, g.inv_h, ix, fx);
+    const float t00 = fetch2(T, g.nx, g.ny, ix, iy);
+    const float t01 = fetch2(T, g.nx, g.ny, ix + 1, iy);
+    const float t10 = fetch2(T, g.nx, g.ny, ix, iy + 1);
+    const float t11 = fetch2(T, g.nx, g.ny, ix + 1, iy + 1);
+    const float a0 = t00 + fx * (t01 - t00);
+    const float a1 = t10 + fx * (t11 - t10);
+    return a0 + fy * (a1 - a0);
+}
+
 __device__ __forceinline__ float fetch3(const float* __restrict__ T, const Geom& g, int ix, int iy, int iz) {
     return (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny && iz >= 0 && iz < g.nz)
                ? __ldg(T + ((long long)iz * g.ny + iy) * g.nx + ix)

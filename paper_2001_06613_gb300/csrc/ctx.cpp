@@ -70,6 +70,7 @@ struct stml_ctx {
     // profiling: CUDA events around every launch of the solver, per kernel
     // class and level (key = class * 64 + level), with algorithmic bytes
     bool prof = false;
+    bool prof_hess_only = false;
     struct ProfEvent {
         int key;
         cudaEvent_t a, b;
@@ -223,17 +224,17 @@ stml_status read_scalars(stml_ctx* c) {
 }
 
 enum ProfClass {
-    PC_HESS = 0, PC_EVAL, PC_TRIAL, PC_PCG_INIT, PC_PCG_UPDATE, PC_PCG_P, PC_DOT,
+    PC_HESS = 0, PC_EVAL, PC_TRIAL, PC_PCG_INIT, PC_PCG_UPDATE, PC_PCG_P, PC_PCG_COOP,
     PC_PRED_LS, PC_PRED_LIN, PC_PROLONG, PC_GATHER, PC_RESTRICT, PC_COUNT
 };
 const char* const kProfNames[PC_COUNT] = {
     "gn_hessian_product", "gradient_pass", "objective_pass", "pcg_init", "pcg_update",
-    "pcg_direction", "dot_gd", "predict_ls_eq2", "predict_linear", "prolong", "gather_scatter",
+    "pcg_direction", "pcg_solve_cooperative", "predict_ls_eq2", "predict_linear", "prolong", "gather_scatter",
     "restrict"};
 
 // Starts an event pair (returns its index, or -1 when profiling is off).
 long prof_begin(stml_ctx* c, int cls, int level) {
-    if (!c->prof) return -1;
+    if (!c->prof || (c->prof_hess_only && cls != PC_HESS)) return -1;
     if (c->ev_used == c->ev.size()) {
         stml_ctx::ProfEvent pe{0, nullptr, nullptr};
         if (cudaEventCreate(&pe.a) != cudaSuccess || cudaEventCreate(&pe.b) != cudaSuccess) return -1;
@@ -290,8 +291,8 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     // objective + gradient at u (start of the GIR)
     auto eval_full = [&]() -> stml_status {
         long pe = prof_begin(c, PC_TRIAL, level);
-        CK(c, launch_objective(L.img, g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->partials, c->partials_cap,
-                               &S->ticket[0], S->red, c->stream));
+        CK(c, launch_objective(L.img, g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
+                               c->partials_cap, &S->ticket[0], S->red, c->stream));
         prof_end(c, pe, pfK * (4.0 + 4.0 * g.d), pfK);
         pe = prof_begin(c, PC_EVAL, level);
         CK(c, launch_gradient(L.img, g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->w_g, c->w_dT, nullptr,
@@ -307,87 +308,119 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     s.J0 = J0;
     double J_old = 0.0, step_norm = 0.0;
     int it = 0;
-    for (;;) {
+    int predict_cg = 8;        // CG steps launched in the first chunk of a solve
+    int launched = 0;
+    long pe = -1;
+
+    // Stopping tests of the Gauss-Newton loop at the current iterate.
+    auto should_stop = [&]() -> bool {
         if (!std::isfinite(J) || !std::isfinite(gnorm2)) {
             s.status = STML_ENONFINITE;
-            break;
+            return true;
         }
         const double gnorm = std::sqrt(gnorm2);
         if (it > 0) {
             const bool c1 = std::fabs(J_old - J) <= p.tol_J * (1.0 + std::fabs(J0));
             const bool c2 = step_norm <= p.tol_Y * (1.0 + std::sqrt(unorm2));
             const bool c3 = gnorm <= p.tol_G * (1.0 + std::fabs(J0));
-            if (c1 && c2 && c3) break;
+            if (c1 && c2 && c3) return true;
         }
-        if (gnorm <= p.g_abs * (1.0 + std::fabs(J0)) || it >= p.max_gn) break;
-
-        // --- PCG for H d = -g, all coefficients on the device
-        long pe = prof_begin(c, PC_PCG_INIT, level);
+        return gnorm <= p.g_abs * (1.0 + std::fabs(J0)) || it >= p.max_gn;
+    };
+    // PCG steps (Hessian product, update, direction), `n` of them, queued.
+    auto launch_cg = [&](int n) -> stml_status {
+        for (int i = 0; i < n; ++i) {
+            pe = prof_begin(c, PC_HESS, level);
+            CK(c, launch_hess_apply(g, fs, cf, c->w_dT, c->w_p, c->w_m1, c->w_m2, c->w_q, c->partials,
+                                    c->partials_cap, &S->ticket[1], S->dots + 4, S, c->stream));
+            prof_end(c, pe, pfK * 12.0 * g.d, pfK);
+            pe = prof_begin(c, PC_PCG_UPDATE, level);
+            CK(c, launch_pcg_update(g, fs, cf, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->partials,
+                                    c->partials_cap, S, pa, c->stream));
+            prof_end(c, pe, pfK * 28.0 * g.d, pfK);
+            pe = prof_begin(c, PC_PCG_P, level);
+            CK(c, launch_pcg_direction(g, fs, cf, c->w_dT, c->w_r, c->w_p, c->w_m1, c->w_m2, S, c->stream));
+            prof_end(c, pe, pfK * 16.0 * g.d, pfK);
+        }
+        launched += n;
+        return STML_OK;
+    };
+    // Start of a PCG solve for H d = -g plus its first chunk of steps (small
+    // levels: the whole solve in one cooperative launch).
+    const bool coop = pcg_coop_preferred(g, nK);
+    auto start_cg = [&]() -> stml_status {
+        if (coop) {
+            pe = prof_begin(c, PC_PCG_COOP, level);
+            CK(c, launch_pcg_coop(g, fs, cf, c->w_g, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->w_m1, c->w_m2,
+                                  c->partials, c->partials_cap, S, pa, c->stream));
+            prof_end(c, pe, 0.0, pfK);
+            launched = p.max_cg;
+            return STML_OK;
+        }
+        pe = prof_begin(c, PC_PCG_INIT, level);
         CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_m1, c->w_m2, c->partials,
                               c->partials_cap, S, pa, c->stream));
         prof_end(c, pe, pfK * 20.0 * g.d, pfK);
-        // iterations are launched in chunks; once the device clears
-        // cg_active the remaining launches of a chunk return at once
-        int launched = 0;
-        do {
-            const int chunk = std::min(4, p.max_cg - launched);
-            for (int i = 0; i < chunk; ++i) {
-                pe = prof_begin(c, PC_HESS, level);
-                CK(c, launch_hess_apply(g, fs, cf, c->w_dT, c->w_p, c->w_m1, c->w_m2, c->w_q, c->partials,
-                                        c->partials_cap, &S->ticket[1], S->dots + 4, S, c->stream));
-                prof_end(c, pe, pfK * 12.0 * g.d, pfK);
-                pe = prof_begin(c, PC_PCG_UPDATE, level);
-                CK(c, launch_pcg_update(g, fs, cf, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->partials,
-                                        c->partials_cap, S, pa, c->stream));
-                prof_end(c, pe, pfK * 28.0 * g.d, pfK);
-                pe = prof_begin(c, PC_PCG_P, level);
-                CK(c, launch_pcg_direction(g, fs, cf, c->w_dT, c->w_r, c->w_p, c->w_m1, c->w_m2, S, c->stream));
-                prof_end(c, pe, pfK * 16.0 * g.d, pfK);
-            }
-            launched += chunk;
+        launched = 0;
+        return launch_cg(std::min(p.max_cg, std::max(2, predict_cg)));
+    };
+
+    bool started = false;     // a PCG solve (with its first chunk) is already queued and read
+    if (!should_stop()) {
+        TRY(start_cg());
+        TRY(read_scalars(c));
+        started = true;
+    }
+    while (started) {
+        // --- finish the PCG solve: all coefficients stay on the device; chunks of
+        // launches whose kernels return at once when the device cleared cg_active
+        while (c->Sh->cg_active && launched < p.max_cg) {
+            TRY(launch_cg(std::min(4, p.max_cg - launched)));
             TRY(read_scalars(c));
-        } while (c->Sh->cg_active && launched < p.max_cg);
+        }
         s.cg_iters += c->Sh->cg_iter;
+        predict_cg = c->Sh->cg_iter;
         if (c->Sh->cg_flag == CG_BREAKDOWN && c->Sh->cg_iter == 0)   // preconditioned gradient step
             CK(c, cudaMemcpyAsync(c->w_x, c->w_p, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
 
-        // --- directional derivative and Armijo back-tracking
-        pe = prof_begin(c, PC_DOT, level);
-        CK(c, launch_dot2(c->w_g, c->w_x, M, c->partials, &S->ticket[3], S->dots, c->stream));
-        prof_end(c, pe, pfK * 8.0 * g.d, pfK);
-        TRY(read_scalars(c));
-        const double gTd = c->Sh->dots[0], dnorm2 = c->Sh->dots[1];
-        if (!(gTd < 0.0)) {
-            s.status = STML_EBREAKDOWN;
-            break;
-        }
-        double t = 1.0;
-        bool accepted = false;
+        // --- Armijo back-tracking; the first trial also reduces <g, d> and |d|^2
+        double t = 1.0, gTd = 0.0, dnorm2 = 0.0;
+        bool accepted = false, descent = true;
         for (int ls = 0; ls < p.max_ls; ++ls) {
             s.ls_trials++;
             pe = prof_begin(c, PC_TRIAL, level);
-            CK(c, launch_objective(L.img, g, fs, cf, u, c->w_x, (float)t, c->w_abar, c->w_ubar, c->partials,
-                                   c->partials_cap, &S->ticket[0], S->trial, c->stream));
-            prof_end(c, pe, pfK * (4.0 + 8.0 * g.d), pfK);
+            CK(c, launch_objective(L.img, g, fs, cf, u, c->w_x, (float)t, ls == 0 ? c->w_g : nullptr, c->w_abar,
+                                   c->w_ubar, c->partials, c->partials_cap, &S->ticket[0], S->trial, c->stream));
+            prof_end(c, pe, pfK * (4.0 + (ls == 0 ? 16.0 : 8.0) * g.d), pfK);
             TRY(read_scalars(c));
-            const double Jt = c->Sh->trial[0];
-            if (Jt <= J + p.armijo_c * t * gTd) {
+            if (ls == 0) {
+                gTd = c->Sh->trial[6];
+                dnorm2 = c->Sh->trial[7];
+                if (!(gTd < 0.0)) {
+                    descent = false;
+                    break;
+                }
+            }
+            if (c->Sh->trial[0] <= J + p.armijo_c * t * gTd) {
                 accepted = true;
                 break;
             }
             t *= 0.5;
         }
+        if (!descent) {
+            s.status = STML_EBREAKDOWN;
+            break;
+        }
         if (!accepted) {
             s.status = STML_ELINESEARCH;
             break;
         }
-        // accepted: the step u + t d is written by the gradient pass, which
-        // reuses the frame means of the last (accepted) trial's objective pass
+        // --- accepted: the gradient pass writes u + t d, g and grad T there,
+        // reusing the frame means of the accepted trial's objective pass
         pe = prof_begin(c, PC_EVAL, level);
         CK(c, launch_gradient(L.img, g, fs, cf, u, c->w_x, (float)t, c->w_abar, c->w_ubar, c->w_g, c->w_dT, ut,
                               c->partials, c->partials_cap, &S->ticket[4], S->red, c->stream));
         prof_end(c, pe, pfK * (4.0 + 20.0 * g.d), pfK);
-        TRY(read_scalars(c));
         std::swap(u, ut);
         step_norm = t * std::sqrt(dnorm2);
         J_old = J;
@@ -395,9 +428,18 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         D = c->Sh->trial[1];
         Sv = c->Sh->trial[2];
         Pv = c->Sh->trial[3];
+        ++it;
+        // the next solve is queued before |g| of the new iterate is known; it is
+        // dropped if the stopping tests fire
+        started = false;
+        if (it < p.max_gn) {
+            TRY(start_cg());
+            started = true;
+        }
+        TRY(read_scalars(c));
         gnorm2 = c->Sh->red[4];
         unorm2 = c->Sh->red[5];
-        ++it;
+        if (should_stop()) started = false;
     }
     if (u != u_io) {
         CK(c, cudaMemcpyAsync(u_io, u, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
@@ -853,8 +895,8 @@ stml_status stml_eval(stml_ctx* c, int level, const int* frames, int nK, const f
     TRY(upload_frameset(c, K, fs));
     const Coef cf = make_coef(L.g, c->p, nK);
     const bool full = g || dT;
-    CK(c, launch_objective(L.img, L.g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->partials, c->partials_cap,
-                           &c->S->ticket[0], c->S->red, c->stream));
+    CK(c, launch_objective(L.img, L.g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
+                           c->partials_cap, &c->S->ticket[0], c->S->red, c->stream));
     if (full)
         CK(c, launch_gradient(L.img, L.g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, g ? g : c->w_g,
                               dT ? dT : c->w_dT, nullptr, c->partials, c->partials_cap, &c->S->ticket[4], c->S->red,
@@ -1004,6 +1046,7 @@ stml_status stml_predict_ls(const float* eta, const int* K, int nK, const float*
 stml_status stml_profile_enable(stml_ctx* c, int enable) {
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
     c->prof = enable != 0;
+    c->prof_hess_only = enable == 2;
     c->ev_used = 0;
     c->pacc.clear();
     return STML_OK;

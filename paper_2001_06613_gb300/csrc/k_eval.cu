@@ -72,12 +72,14 @@ __device__ __forceinline__ void interp(const float* __restrict__ Tk, const Geom&
 
 // ----------------------------------------------------------------- objective
 // Reduced values: 0 D, 1 S_x, 2 S_t, 3 P, 4 (unused), 5 |u|^2.
-template <int D, int VEC>
-__global__ void __launch_bounds__(kThreads)
+// With gdot != nullptr the pass also reduces <gdot, du> and |du|^2 (the
+// directional derivative of the Gauss-Newton step) into out[6], out[7].
+template <int D, int VEC, int TPR>
+__global__ void __launch_bounds__(kThreads, 3)
 obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, FView U,
-           float* __restrict__ abar, float* __restrict__ ubar, double* __restrict__ partials,
-           unsigned int* ticket, double* out) {
-    constexpr int TPR = VEC == 4 ? 16 : 32, SEG = TPR * VEC, FG = kThreads / TPR;
+           const float* __restrict__ gdot, float* __restrict__ abar, float* __restrict__ ubar,
+           double* __restrict__ partials, unsigned int* ticket, double* out) {
+    constexpr int SEG = TPR * VEC, FG = kThreads / TPR;
     __shared__ float sh_n[FG][SEG], sh_m[FG][SEG], sh_q[FG][SEG];
     __shared__ float sh_u[FG][D][SEG];
     const int lane = threadIdx.x % TPR, fg = threadIdx.x / TPR;
@@ -94,10 +96,26 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
 #pragma unroll
         for (int c = 0; c < D; ++c) su[c][e] = 0.f;
     }
-    float sx = 0.f, st = 0.f, u2 = 0.f;
+    float sx = 0.f, st = 0.f, u2 = 0.f, gd = 0.f, dd = 0.f;
     if (valid) {
+#pragma unroll 2
         for (int j = fg; j < fs.nK; j += FG) {
             const float* Tk = T + (size_t)__ldg(fs.frames + j) * N;
+            if (gdot) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    const size_t base = ((size_t)j * D + c) * N + p;
+                    float gv[VEC], dv[VEC];
+                    const FView G{gdot, nullptr, 0.f}, Dv{U.d, nullptr, 0.f};
+                    vload<VEC>(G, base, gv);
+                    vload<VEC>(Dv, base, dv);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        gd = fmaf(gv[e], dv[e], gd);
+                        dd = fmaf(dv[e], dv[e], dd);
+                    }
+                }
+            }
             const float w_next = (cf.alphat_hd != 0.f && j + 1 < fs.nK) ? __ldg(fs.w_next + j) : 0.f;
             float uc[D][VEC];
 #pragma unroll
@@ -145,10 +163,15 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
             const float rc = 1.0f / cnt;
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                float uu[D], a, gr[D];
+                float a;
+                if constexpr (D == 2) {
+                    a = interp2_val(Tk, g, x + e, y, uc[0][e], uc[1][e]);
+                } else {
+                    float uu[D], gr[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) uu[c] = uc[c][e];
-                interp<D>(Tk, g, x + e, y, z, uu, a, gr);
+                    for (int c = 0; c < D; ++c) uu[c] = uc[c][e];
+                    interp<D>(Tk, g, x + e, y, z, uu, a, gr);
+                }
                 const float dlt = a - mean[e];
                 mean[e] = fmaf(dlt, rc, mean[e]);
                 m2[e] = fmaf(dlt, a - mean[e], m2[e]);
@@ -194,8 +217,8 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
             }
         }
     }
-    float acc[6] = {dsum, sx, st, pen, 0.f, u2};
-    if (grid_reduce<6>(acc, partials, ticket, out) && threadIdx.x == 0) {
+    float acc[8] = {dsum, sx, st, pen, 0.f, u2, gd, dd};
+    if (grid_reduce<8>(acc, partials, ticket, out) && threadIdx.x == 0) {
         const double Dv = out[0], Sx = out[1], St = out[2], Pv = out[3];
         out[0] = Dv + Sx + St + Pv;
         out[1] = Dv;
@@ -354,27 +377,39 @@ bool v4ok(const Geom& g, std::initializer_list<const void*> ptrs) {
 }  // namespace
 
 size_t eval_partials(const Geom& g, int nK) {
-    const size_t obj = (size_t)((g.N + 31) / 32) * 6;
+    const size_t obj = (size_t)((g.N + 7) / 8) * 8;
     return obj > (size_t)kGridStride * 2 ? obj : (size_t)kGridStride * 2;
     (void)nK;
 }
 
+template <int D, int VEC, int TPR>
+static void obj_go(unsigned blocks, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
+                   const FrameSet& fs, const Coef& cf, const FView& U, const float* gdot, float* abar, float* ubar,
+                   double* partials, unsigned int* ticket, double* out) {
+    obj_kernel<D, VEC, TPR><<<blocks, kThreads, 0, s>>>(T, g, pi, fs, cf, U, gdot, abar, ubar, partials, ticket, out);
+}
+
 cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
-                             const float* du, float t, float* abar, float* ubar, double* partials,
+                             const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
                              size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s) {
     const PixIndex pi{FastDiv::make((unsigned)g.nx), FastDiv::make((unsigned)g.ny)};
-    const bool v4 = v4ok(g, {u, du, abar, ubar});
-    const int seg = v4 ? 64 : 32;
+    const bool v4 = v4ok(g, {u, du, gdot, abar, ubar});
+    // wide pixel tiles on large levels, narrow ones (more CTAs, more frame groups) on small levels
+    const bool narrow = g.N < 4LL * 152 * (v4 ? 64 : 32);
+    const int seg = v4 ? (narrow ? 16 : 64) : (narrow ? 8 : 32);
     const unsigned blocks = (unsigned)((g.N + seg - 1) / seg);
-    if ((size_t)blocks * 6 > partials_cap) return cudaErrorInvalidValue;
+    if ((size_t)blocks * 8 > partials_cap) return cudaErrorInvalidValue;
+    if (gdot && !du) return cudaErrorInvalidValue;
     const FView U{u, du, t};
+#define STML_OBJ(D_, V_, T_) obj_go<D_, V_, T_>(blocks, s, T, g, pi, fs, cf, U, gdot, abar, ubar, partials, ticket, out)
     if (g.d == 2) {
-        if (v4) obj_kernel<2, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, fs, cf, U, abar, ubar, partials, ticket, out);
-        else obj_kernel<2, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, fs, cf, U, abar, ubar, partials, ticket, out);
+        if (v4) { if (narrow) STML_OBJ(2, 4, 4); else STML_OBJ(2, 4, 16); }
+        else { if (narrow) STML_OBJ(2, 1, 8); else STML_OBJ(2, 1, 32); }
     } else {
-        if (v4) obj_kernel<3, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, fs, cf, U, abar, ubar, partials, ticket, out);
-        else obj_kernel<3, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, fs, cf, U, abar, ubar, partials, ticket, out);
+        if (v4) { if (narrow) STML_OBJ(3, 4, 4); else STML_OBJ(3, 4, 16); }
+        else { if (narrow) STML_OBJ(3, 1, 8); else STML_OBJ(3, 1, 32); }
     }
+#undef STML_OBJ
     count_launches(1);
     return cudaGetLastError();
 }

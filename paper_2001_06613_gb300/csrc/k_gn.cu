@@ -1,21 +1,29 @@
-// Gauss-Newton Hessian product and the PCG vector kernels around it.
+// Gauss-Newton Hessian product and the PCG solve around it.
 //
 //   (Hv)_k = hd grad T_k (s_k - sbar) + alpha hd B^T B v_k + alpha_t hd (L_t v)_k
 //            + 2 lambda hd / |K|^2 sum_j v_j,          s_k = grad T_k . v_k
 //
 // The Hessian product needs two per-pixel sums over all frames of K (sbar and
-// sum_j v_j).  They are produced by the kernel that writes v: in the PCG loop
-// the search direction p is written by `dir_kernel`, which visits all frames
-// of a pixel anyway (p = M^-1 r + beta p); it reduces sbar and sum_j p_j over
-// the frames in the same pass.  The Hessian product itself (`apply_kernel`) is
-// then an element-wise stencil stream: it reads v (and its stencil
-// neighbours, served from L1/L2), grad T and the sums, writes Hv and reduces
-// <v, Hv>.  Per PCG iteration and pixel-frame: apply 12d bytes, update 28d,
-// direction 16d -- every array read or written once.
+// sum_j v_j).  They are produced by the step that writes v: in the PCG loop the
+// search direction p is written by the direction step, which visits all frames
+// of a pixel anyway (p = M^-1 r + beta p) and reduces sbar and sum_j p_j over
+// the frames in the same pass.  The Hessian product itself is then an
+// element-wise stencil stream: it reads v (stencil neighbours come from L1/L2),
+// grad T and the sums, writes Hv and reduces <v, Hv>.  Per PCG iteration and
+// pixel-frame: Hessian product 12d bytes, update 28d, direction 16d -- every
+// array read or written once.
 //
-// The Jacobi preconditioner is computed from grad T where it is needed
-// (`jacobi_inv`, one rounding sequence everywhere), so no M^-1 array exists.
+// Two ways to run a solve: three stream kernels per iteration whose CG
+// coefficients stay in device memory (large levels), or one cooperative
+// kernel that runs the whole solve with grid-wide barriers between the steps
+// (small levels, where launch latency would dominate).  Both use the same
+// per-item code below.  The Jacobi preconditioner is computed from grad T
+// where it is needed (`jacobi_inv`, one rounding sequence everywhere).
+#include <cooperative_groups.h>
+
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace stml {
 
@@ -59,8 +67,6 @@ __device__ __forceinline__ void pix_pos(const PixIndex& pi, unsigned p, int& x, 
     z = (int)zz;
 }
 
-}  // namespace
-
 // Inverse of the Jacobi diagonal of the Gauss-Newton Hessian at one element:
 // hd (1 - 1/|K|) (d_c T_k)^2 + alpha hd nnb / h^2 + alpha_t hd (w_prev + w_next)
 // + 2 lambda hd / |K|^2 (explicit roundings: every kernel gets the same value).
@@ -72,27 +78,29 @@ __device__ __forceinline__ float jacobi_inv(float dt, int nnb, float tdiag, cons
     return dg > 0.f ? __frcp_rn(dg) : 1.0f;   // zero only when alpha = lambda = 0 and grad T = 0
 }
 
-// ----------------------------------------------------------------- direction
-// MODE 0: sums of a given v.  MODE 1: p = M^-1 r + beta p (PCG step), sums of
-// the new p.  MODE 2: r = -g, p = M^-1 r, x = 0, <r, M^-1 r>, |r|^2 (PCG start),
-// sums of p.  CTA = SEG consecutive pixels x FG frame groups; group f visits
-// the frames f, f + FG, ...; the per-pixel sums of the groups are combined in
-// group order.  Writes mean_s[p] = sum_k s_k / |K| and sum_v[c][p].
-template <int D, int VEC, int MODE>
-__global__ void __launch_bounds__(kThreads)
-dir_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ dT, float* __restrict__ v,
-           float* __restrict__ r, const float* __restrict__ grad, float* __restrict__ x,
-           float* __restrict__ mean_s, float* __restrict__ sum_v, double* __restrict__ partials,
-           DevScalars* S, PcgArgs a) {
-    if (MODE == 1 && !S->cg_active) return;
-    constexpr int TPR = VEC == 4 ? 16 : 32, SEG = TPR * VEC, FG = kThreads / TPR, NR = 1 + D;
-    __shared__ float sh[FG][NR][SEG];
+__device__ __forceinline__ float tdiag_of(const FrameSet& fs, int j) {
+    return (j + 1 < fs.nK ? __ldg(fs.w_next + j) : 0.f) + (j > 0 ? __ldg(fs.w_next + j - 1) : 0.f);
+}
+
+// ------------------------------------------------------------- per-item bodies
+// Direction step on one pixel tile (SEG pixels, all frames; CTA = SEG/VEC
+// threads per row x FG frame groups).  MODE 0: sums of a given v.  MODE 1:
+// p = M^-1 r + beta p and sums of the new p.  MODE 2: r = -g, p = M^-1 r,
+// x = 0, the sums, and rz += <r, M^-1 r>, rr += |r|^2.  Writes
+// mean_s = sum_k s_k / |K| and sum_v[c]; the frame groups are combined in
+// group order.  Every thread of the CTA must call it (it synchronises).
+template <int D, int VEC, int MODE, int TPR>
+__device__ __forceinline__ void dir_tile(const Geom& g, const PixIndex& pi, const FrameSet& fs, const Coef& cf,
+                                         const float* __restrict__ dT, float* __restrict__ v,
+                                         float* __restrict__ r, const float* __restrict__ grad,
+                                         float* __restrict__ x, float* __restrict__ mean_s,
+                                         float* __restrict__ sum_v, float beta, unsigned tile, float* sh,
+                                         float& rz, float& rr) {
+    constexpr int SEG = TPR * VEC, FG = kThreads / TPR, NR = 1 + D;
     const int lane = threadIdx.x % TPR, fg = threadIdx.x / TPR;
-    const unsigned p = blockIdx.x * SEG + lane * VEC;
+    const unsigned p = tile * SEG + lane * VEC;
     const bool valid = p < (unsigned)g.N;
     const size_t N = (size_t)g.N;
-    float beta = 0.f;
-    if constexpr (MODE == 1) beta = (float)S->beta;
     int nnb[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) nnb[e] = 0;
@@ -109,12 +117,9 @@ dir_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ 
 #pragma unroll
         for (int c = 0; c < D; ++c) av[c][e] = 0.f;
     }
-    float rz = 0.f, rr = 0.f;
     if (valid) {
         for (int j = fg; j < fs.nK; j += FG) {
-            float tdiag = 0.f;
-            if (MODE != 0)
-                tdiag = (j + 1 < fs.nK ? __ldg(fs.w_next + j) : 0.f) + (j > 0 ? __ldg(fs.w_next + j - 1) : 0.f);
+            const float tdiag = MODE != 0 ? tdiag_of(fs, j) : 0.f;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 const size_t e0 = ((size_t)j * D + c) * N + p;
@@ -155,61 +160,36 @@ dir_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ 
     }
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
-        sh[fg][0][lane * VEC + e] = as[e];
+        sh[(fg * NR + 0) * SEG + lane * VEC + e] = as[e];
 #pragma unroll
-        for (int c = 0; c < D; ++c) sh[fg][1 + c][lane * VEC + e] = av[c][e];
+        for (int c = 0; c < D; ++c) sh[(fg * NR + 1 + c) * SEG + lane * VEC + e] = av[c][e];
     }
     __syncthreads();
     const float invK = 1.0f / (float)fs.nK;
     for (int i = threadIdx.x; i < NR * SEG; i += blockDim.x) {
         const int q = i / SEG, k = i - q * SEG;
-        const unsigned pp = blockIdx.x * SEG + k;
+        const unsigned pp = tile * SEG + k;
         if (pp >= (unsigned)g.N) continue;
         float s = 0.f;
 #pragma unroll
-        for (int w = 0; w < FG; ++w) s += sh[w][q][k];
+        for (int w = 0; w < FG; ++w) s += sh[(w * NR + q) * SEG + k];
         if (q == 0)
             mean_s[pp] = s * invK;
         else
             sum_v[(size_t)(q - 1) * N + pp] = s;
     }
-    if constexpr (MODE == 2) {
-        float acc[2] = {rz, rr};
-        double tot[2];
-        if (grid_reduce<2>(acc, partials, &S->ticket[2], tot) && threadIdx.x == 0) {
-            S->rho = tot[0];
-            S->bnorm2 = tot[1];
-            S->rnorm2 = tot[1];
-            S->cg_iter = 0;
-            if (!(tot[1] > 0.0)) {
-                S->cg_flag = CG_ZERO;
-                S->cg_active = 0;
-            } else if (a.max_cg <= 0) {
-                S->cg_flag = CG_MAXIT;
-                S->cg_active = 0;
-            } else {
-                S->cg_flag = CG_RUNNING;
-                S->cg_active = 1;
-            }
-        }
-    }
+    __syncthreads();
 }
 
-// ----------------------------------------------------------------- apply
-// Element = (frame j = blockIdx.y, VEC pixels); all D components.
+// Hessian product on one item: frame j, pixels [ch * kThreads * VEC, +kThreads * VEC).
+// Every thread of the warp must call it (warp shuffles).  acc += <v, Hv>.
 template <int D, int VEC>
-__global__ void __launch_bounds__(kThreads)
-apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
-             const float* __restrict__ dT, const float* __restrict__ v, const float* __restrict__ mean_s,
-             const float* __restrict__ sum_v, float* __restrict__ Hv, double* __restrict__ partials,
-             unsigned int* ticket, double* out, DevScalars* pcg) {
-    if (pcg && !pcg->cg_active) return;
+__device__ __forceinline__ void apply_item(const Geom& g, const PixIndex& pi, const FrameSet& fs, const Coef& cf,
+                                           const float* __restrict__ dT, const float* __restrict__ v,
+                                           const float* __restrict__ mean_s, const float* __restrict__ sum_v,
+                                           float* __restrict__ Hv, int j, unsigned ch, float& acc) {
     const size_t N = (size_t)g.N;
     const int lane = threadIdx.x & 31;
-    float acc[1] = {0.f};
-    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-    const int j = (int)chunks.div((unsigned)it);
-    const unsigned ch = (unsigned)it - (unsigned)j * chunks.d;
     const unsigned p = (ch * kThreads + threadIdx.x) * VEC;
     const bool valid = p < (unsigned)g.N;
     const float w_next = (cf.alphat_hd != 0.f && j + 1 < fs.nK) ? __ldg(fs.w_next + j) : 0.f;
@@ -234,6 +214,12 @@ apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, 
         for (int e = 0; e < VEC; ++e) s[e] = fmaf(dt[c].a[e], vc[c].a[e], s[e]);
     }
     float ds[VEC], sv[D][VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        ds[e] = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) sv[c][e] = 0.f;
+    }
     if (valid) {
         V<VEC> ms;
         ms.load(mean_s + p);
@@ -294,7 +280,8 @@ apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, 
         }
         V<VEC> h;
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) h.a[e] = fmaf(ds[e], dt[c].a[e], fmaf(cf.alpha_hd * cf.inv_h2, lap[e], cf.pen_h * sv[c][e]));
+        for (int e = 0; e < VEC; ++e)
+            h.a[e] = fmaf(ds[e], dt[c].a[e], fmaf(cf.alpha_hd * cf.inv_h2, lap[e], cf.pen_h * sv[c][e]));
         if (w_next != 0.f) {
             nb.load(v + e0 + (size_t)D * N);
 #pragma unroll
@@ -307,24 +294,207 @@ apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, 
         }
         h.store(Hv + e0);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[0] = fmaf(vc[c].a[e], h.a[e], acc[0]);
+        for (int e = 0; e < VEC; ++e) acc = fmaf(vc[c].a[e], h.a[e], acc);
     }
+}
+
+// PCG update on one item: plane (frame j, component c), one chunk of pixels.
+// x += alpha p, r -= alpha q; rz += <r, M^-1 r>, rr += |r|^2.
+template <int D, int VEC>
+__device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, const FrameSet& fs, const Coef& cf,
+                                            const float* __restrict__ dT, float* __restrict__ x,
+                                            float* __restrict__ r, const float* __restrict__ p,
+                                            const float* __restrict__ q, int plane, unsigned ch, float al,
+                                            float& rz, float& rr) {
+    const unsigned px = (ch * kThreads + threadIdx.x) * VEC;
+    if (px >= (unsigned)g.N) return;
+    const float tdiag = tdiag_of(fs, plane / D);
+    int xx, yy, zz;
+    pix_pos(pi, px, xx, yy, zz);
+    const size_t e0 = (size_t)plane * g.N + px;
+    V<VEC> dt, pv, qv, xv, rv;
+    dt.load(dT + e0);
+    pv.load(p + e0);
+    qv.load(q + e0);
+    xv.load_rw(x + e0);
+    rv.load_rw(r + e0);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        xv.a[e] = fmaf(al, pv.a[e], xv.a[e]);
+        rv.a[e] = fmaf(-al, qv.a[e], rv.a[e]);
+        const float zv = jacobi_inv(dt.a[e], neighbour_count(g, xx + e, yy, zz), tdiag, cf) * rv.a[e];
+        rz = fmaf(rv.a[e], zv, rz);
+        rr = fmaf(rv.a[e], rv.a[e], rr);
     }
-    if (grid_reduce<1>(acc, partials, ticket, out) && threadIdx.x == 0 && pcg) {
-        const double pq = out[0];
-        pcg->pq = pq;
-        if (!(pq > 0.0)) {
-            pcg->cg_flag = CG_BREAKDOWN;
-            pcg->cg_active = 0;
-        } else {
-            pcg->alpha = pcg->rho / pq;
+    xv.store(x + e0);
+    rv.store(r + e0);
+}
+
+// CG decisions (shared by both solve paths).
+struct CgState {
+    double rho, bnorm2, rnorm2, pq, alpha, beta;
+    int iter, flag, active;
+};
+
+__device__ __forceinline__ void cg_after_init(CgState& s, double rz, double rr, int max_cg) {
+    s.rho = rz;
+    s.bnorm2 = rr;
+    s.rnorm2 = rr;
+    s.iter = 0;
+    if (!(rr > 0.0)) {
+        s.flag = CG_ZERO;
+        s.active = 0;
+    } else if (max_cg <= 0) {
+        s.flag = CG_MAXIT;
+        s.active = 0;
+    } else {
+        s.flag = CG_RUNNING;
+        s.active = 1;
+    }
+}
+
+__device__ __forceinline__ void cg_after_apply(CgState& s, double pq) {
+    s.pq = pq;
+    if (!(pq > 0.0)) {
+        s.flag = CG_BREAKDOWN;
+        s.active = 0;
+    } else {
+        s.alpha = s.rho / pq;
+    }
+}
+
+__device__ __forceinline__ void cg_after_update(CgState& s, double rz, double rr, float tol_cg, int max_cg) {
+    s.iter += 1;
+    s.rnorm2 = rr;
+    if (sqrt(rr) <= (double)tol_cg * sqrt(s.bnorm2)) {
+        s.flag = CG_CONVERGED;
+        s.active = 0;
+    } else if (s.iter >= max_cg) {
+        s.flag = CG_MAXIT;
+        s.active = 0;
+    } else {
+        s.beta = rz / s.rho;
+        s.rho = rz;
+    }
+}
+
+__device__ __forceinline__ CgState cg_load(const DevScalars* S) {
+    CgState s;
+    s.rho = S->rho;
+    s.bnorm2 = S->bnorm2;
+    s.rnorm2 = S->rnorm2;
+    s.pq = S->pq;
+    s.alpha = S->alpha;
+    s.beta = S->beta;
+    s.iter = S->cg_iter;
+    s.flag = S->cg_flag;
+    s.active = S->cg_active;
+    return s;
+}
+
+__device__ __forceinline__ void cg_store(DevScalars* S, const CgState& s) {
+    S->rho = s.rho;
+    S->bnorm2 = s.bnorm2;
+    S->rnorm2 = s.rnorm2;
+    S->pq = s.pq;
+    S->alpha = s.alpha;
+    S->beta = s.beta;
+    S->cg_iter = s.iter;
+    S->cg_flag = s.flag;
+    S->cg_active = s.active;
+}
+
+// Block sum of NV floats (fixed order) -> partials[block * NV + i] in double.
+template <int NV>
+__device__ __forceinline__ void block_partials(const float (&v)[NV], double* partials) {
+    __shared__ double s_w[kThreads / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float w = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) s_w[warp][i] = (double)w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) s += s_w[w][i];
+            partials[(size_t)blockIdx.x * NV + i] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Sum of the partials of all CTAs in a fixed order; every CTA gets the same value.
+template <int NV>
+__device__ __forceinline__ void grid_total(const double* partials, double (&tot)[NV]) {
+    __shared__ double s_t[kThreads / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(partials + (size_t)b * NV + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) s_t[warp][i] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += s_t[w][i];
+        tot[i] = s;
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- stream kernels
+template <int D, int VEC, int MODE, int TPR>
+__global__ void __launch_bounds__(kThreads)
+dir_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ dT, float* __restrict__ v,
+           float* __restrict__ r, const float* __restrict__ grad, float* __restrict__ x,
+           float* __restrict__ mean_s, float* __restrict__ sum_v, double* __restrict__ partials,
+           DevScalars* S, PcgArgs a) {
+    if (MODE == 1 && !S->cg_active) return;
+    __shared__ float sh[(kThreads / TPR) * (1 + D) * TPR * VEC];
+    const float beta = MODE == 1 ? (float)S->beta : 0.f;
+    float rz = 0.f, rr = 0.f;
+    dir_tile<D, VEC, MODE, TPR>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v, beta, blockIdx.x, sh, rz, rr);
+    if constexpr (MODE == 2) {
+        float acc[2] = {rz, rr};
+        double tot[2];
+        if (grid_reduce<2>(acc, partials, &S->ticket[2], tot) && threadIdx.x == 0) {
+            CgState st = cg_load(S);
+            cg_after_init(st, tot[0], tot[1], a.max_cg);
+            cg_store(S, st);
         }
     }
 }
 
-// ----------------------------------------------------------------- update
-// x += alpha p, r -= alpha q, z = M^-1 r; <r, z>, |r|^2 -> convergence, beta.
-// Element = (plane = blockIdx.y, VEC pixels).
+template <int D, int VEC>
+__global__ void __launch_bounds__(kThreads)
+apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
+             const float* __restrict__ dT, const float* __restrict__ v, const float* __restrict__ mean_s,
+             const float* __restrict__ sum_v, float* __restrict__ Hv, double* __restrict__ partials,
+             unsigned int* ticket, double* out, DevScalars* pcg) {
+    if (pcg && !pcg->cg_active) return;
+    float acc[1] = {0.f};
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int j = (int)chunks.div((unsigned)it);
+        apply_item<D, VEC>(g, pi, fs, cf, dT, v, mean_s, sum_v, Hv, j, (unsigned)it - (unsigned)j * chunks.d, acc[0]);
+    }
+    if (grid_reduce<1>(acc, partials, ticket, out) && threadIdx.x == 0 && pcg) {
+        CgState st = cg_load(pcg);
+        cg_after_apply(st, out[0]);
+        cg_store(pcg, st);
+    }
+}
+
 template <int D, int VEC>
 __global__ void __launch_bounds__(kThreads)
 update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
@@ -335,48 +505,91 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
     const float al = (float)S->alpha;
     float acc[2] = {0.f, 0.f};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-    const int plane = (int)chunks.div((unsigned)it);
-    const unsigned ch = (unsigned)it - (unsigned)plane * chunks.d;
-    const int j = plane / D;
-    const float tdiag = (j + 1 < fs.nK ? __ldg(fs.w_next + j) : 0.f) + (j > 0 ? __ldg(fs.w_next + j - 1) : 0.f);
-    const unsigned px = (ch * kThreads + threadIdx.x) * VEC;
-    if (px < (unsigned)g.N) {
-        int xx, yy, zz;
-        pix_pos(pi, px, xx, yy, zz);
-        const size_t e0 = (size_t)plane * g.N + px;
-        V<VEC> dt, pv, qv, xv, rv;
-        dt.load(dT + e0);
-        pv.load(p + e0);
-        qv.load(q + e0);
-        xv.load_rw(x + e0);
-        rv.load_rw(r + e0);
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            xv.a[e] = fmaf(al, pv.a[e], xv.a[e]);
-            rv.a[e] = fmaf(-al, qv.a[e], rv.a[e]);
-            const float zv = jacobi_inv(dt.a[e], neighbour_count(g, xx + e, yy, zz), tdiag, cf) * rv.a[e];
-            acc[0] = fmaf(rv.a[e], zv, acc[0]);
-            acc[1] = fmaf(rv.a[e], rv.a[e], acc[1]);
-        }
-        xv.store(x + e0);
-        rv.store(r + e0);
-    }
+        const int plane = (int)chunks.div((unsigned)it);
+        update_item<D, VEC>(g, pi, fs, cf, dT, x, r, p, q, plane, (unsigned)it - (unsigned)plane * chunks.d, al,
+                            acc[0], acc[1]);
     }
     double tot[2];
     if (grid_reduce<2>(acc, partials, &S->ticket[2], tot) && threadIdx.x == 0) {
-        S->cg_iter += 1;
-        S->rnorm2 = tot[1];
-        if (sqrt(tot[1]) <= (double)a.tol_cg * sqrt(S->bnorm2)) {
-            S->cg_flag = CG_CONVERGED;
-            S->cg_active = 0;
-        } else if (S->cg_iter >= a.max_cg) {
-            S->cg_flag = CG_MAXIT;
-            S->cg_active = 0;
-        } else {
-            S->beta = tot[0] / S->rho;
-            S->rho = tot[0];
-        }
+        CgState st = cg_load(S);
+        cg_after_update(st, tot[0], tot[1], a.tol_cg, a.max_cg);
+        cg_store(S, st);
     }
+}
+
+// ----------------------------------------------------------------- cooperative solve
+// The whole PCG solve in one cooperative launch: init, then per iteration the
+// Hessian product, the update and the direction step, separated by three
+// grid-wide barriers.  Every CTA evaluates the same CG decisions from the same
+// fixed-order totals, so all CTAs leave the loop together.
+template <int D, int VEC, int TPR>
+__global__ void __launch_bounds__(kThreads)
+pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, long long uitems, unsigned tiles,
+                FrameSet fs, Coef cf, const float* __restrict__ grad, const float* __restrict__ dT,
+                float* __restrict__ x, float* __restrict__ r, float* __restrict__ p, float* __restrict__ q,
+                float* __restrict__ mean_s, float* __restrict__ sum_v, double* __restrict__ partials,
+                DevScalars* S, PcgArgs a) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ float sh[(kThreads / TPR) * (1 + D) * TPR * VEC];
+    // two partial-sum buffers: A for <p, Hp>, B for the update's sums (and the
+    // start); a buffer is rewritten only after a barrier that follows every
+    // CTA's read of it, so three barriers per iteration suffice
+    double* partA = partials;
+    double* partB = partials + 2 * (size_t)gridDim.x;
+    CgState st{0, 0, 0, 0, 0, 0, 0, 0, 0};
+    {   // r = -g, p = M^-1 r, x = 0, frame sums of p
+        float rz = 0.f, rr = 0.f;
+        for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x)
+            dir_tile<D, VEC, 2, TPR>(g, pi, fs, cf, dT, p, r, grad, x, mean_s, sum_v, 0.f, t, sh, rz, rr);
+        const float v2[2] = {rz, rr};
+        block_partials<2>(v2, partB);
+        grid.sync();
+        double tot[2];
+        grid_total<2>(partB, tot);
+        cg_after_init(st, tot[0], tot[1], a.max_cg);
+    }
+    while (st.active) {
+        float pq = 0.f;
+        for (long long it = blockIdx.x; it < aitems; it += gridDim.x) {
+            const int j = (int)chunks.div((unsigned)it);
+            apply_item<D, VEC>(g, pi, fs, cf, dT, p, mean_s, sum_v, q, j, (unsigned)it - (unsigned)j * chunks.d, pq);
+        }
+        {
+            const float v1[1] = {pq};
+            block_partials<1>(v1, partA);
+        }
+        grid.sync();   // q and the <p, Hp> partials are complete
+        {
+            double tot[1];
+            grid_total<1>(partA, tot);
+            cg_after_apply(st, tot[0]);
+        }
+        if (!st.active) break;
+        const float al = (float)st.alpha;
+        float rz = 0.f, rr = 0.f;
+        for (long long it = blockIdx.x; it < uitems; it += gridDim.x) {
+            const int plane = (int)chunks.div((unsigned)it);
+            update_item<D, VEC>(g, pi, fs, cf, dT, x, r, p, q, plane, (unsigned)it - (unsigned)plane * chunks.d, al,
+                                rz, rr);
+        }
+        {
+            const float v2[2] = {rz, rr};
+            block_partials<2>(v2, partB);
+        }
+        grid.sync();   // r and the update partials are complete
+        {
+            double tot[2];
+            grid_total<2>(partB, tot);
+            cg_after_update(st, tot[0], tot[1], a.tol_cg, a.max_cg);
+        }
+        if (!st.active) break;
+        const float be = (float)st.beta;
+        float d0 = 0.f, d1 = 0.f;
+        for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x)
+            dir_tile<D, VEC, 1, TPR>(g, pi, fs, cf, dT, p, r, nullptr, nullptr, mean_s, sum_v, be, t, sh, d0, d1);
+        grid.sync();   // p and its frame sums are complete
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) cg_store(S, st);
 }
 
 // ----------------------------------------------------------------- launchers
@@ -387,12 +600,21 @@ PixIndex make_pix_index(const Geom& g) {
     return pi;
 }
 
-static bool vec4_ok(const Geom& g, std::initializer_list<const void*> ptrs) {
+namespace {
+
+constexpr int kGridStride = 152 * 8;   // CTAs of the grid-stride launches (8 per SM of a GB300)
+
+bool vec4_ok(const Geom& g, std::initializer_list<const void*> ptrs) {
     if (g.nx % 4) return false;
     for (const void* q : ptrs)
         if (q && ((uintptr_t)q & 15u)) return false;
     return true;
 }
+
+// Wide pixel tiles on large levels, narrow ones (more CTAs, more frame groups) on small levels.
+bool narrow_tiles(const Geom& g, bool v4) { return g.N < 4LL * 152 * (v4 ? 64 : 32); }
+
+}  // namespace
 
 template <int MODE>
 static cudaError_t dir_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, float* v, float* r,
@@ -400,27 +622,25 @@ static cudaError_t dir_launch(const Geom& g, const FrameSet& fs, const Coef& cf,
                               DevScalars* S, PcgArgs a, cudaStream_t s) {
     const PixIndex pi = make_pix_index(g);
     const bool v4 = vec4_ok(g, {dT, v, r, grad, x});
-    const int seg = v4 ? 64 : 32;
+    const bool narrow = narrow_tiles(g, v4);
+    const int seg = v4 ? (narrow ? 16 : 64) : (narrow ? 8 : 32);
     const unsigned blocks = (unsigned)((g.N + seg - 1) / seg);
+#define STML_DIR(D_, V_, T_) \
+    dir_kernel<D_, V_, MODE, T_><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v, partials, S, a)
     if (g.d == 2) {
-        if (v4)
-            dir_kernel<2, 4, MODE><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v, partials, S, a);
-        else
-            dir_kernel<2, 1, MODE><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v, partials, S, a);
+        if (v4) { if (narrow) STML_DIR(2, 4, 4); else STML_DIR(2, 4, 16); }
+        else { if (narrow) STML_DIR(2, 1, 8); else STML_DIR(2, 1, 32); }
     } else {
-        if (v4)
-            dir_kernel<3, 4, MODE><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v, partials, S, a);
-        else
-            dir_kernel<3, 1, MODE><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v, partials, S, a);
+        if (v4) { if (narrow) STML_DIR(3, 4, 4); else STML_DIR(3, 4, 16); }
+        else { if (narrow) STML_DIR(3, 1, 8); else STML_DIR(3, 1, 32); }
     }
+#undef STML_DIR
     count_launches(1);
     return cudaGetLastError();
 }
 
-constexpr int kGridStride = 152 * 8;   // CTAs of the grid-stride launches (8 per SM of a GB300)
-
 size_t gn_partials(const Geom& g, int nK) {
-    const size_t dir = (size_t)((g.N + 31) / 32) * 2;
+    const size_t dir = (size_t)((g.N + 7) / 8) * 2;
     const size_t gs = (size_t)kGridStride * 2;
     (void)nK;
     return dir > gs ? dir : gs;
@@ -463,7 +683,7 @@ cudaError_t launch_hess_apply(const Geom& g, const FrameSet& fs, const Coef& cf,
 cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
                             float* x, float* r, float* p, float* mean_s, float* sum_v, double* partials,
                             size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s) {
-    if ((size_t)((g.N + 31) / 32) * 2 > partials_cap) return cudaErrorInvalidValue;
+    if ((size_t)((g.N + 7) / 8) * 2 > partials_cap) return cudaErrorInvalidValue;
     return dir_launch<2>(g, fs, cf, dT, p, r, grad, x, mean_s, sum_v, partials, S, a, s);
 }
 
@@ -497,6 +717,56 @@ cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf,
     }
     count_launches(1);
     return cudaGetLastError();
+}
+
+namespace {
+
+template <int D, int VEC, int TPR>
+cudaError_t coop_go(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT, float* x,
+                    float* r, float* p, float* q, float* mean_s, float* sum_v, double* partials, size_t partials_cap,
+                    DevScalars* S, PcgArgs a, cudaStream_t s) {
+    const void* kern = (const void*)pcg_coop_kernel<D, VEC, TPR>;
+    int dev = 0, sms = 1, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    PixIndex pi = make_pix_index(g);
+    long long cpf = (g.N + (long long)kThreads * VEC - 1) / ((long long)kThreads * VEC);
+    long long aitems = cpf * fs.nK, uitems = cpf * fs.nK * D;
+    unsigned tiles = (unsigned)((g.N + TPR * VEC - 1) / (TPR * VEC));
+    const long long want = uitems > (long long)tiles ? uitems : (long long)tiles;
+    // one CTA per SM at most: the solve is small and grid barriers get dearer with more CTAs
+    const long long cap = (long long)sms;
+    unsigned blocks = (unsigned)(want < cap ? want : cap);
+    if (blocks < 1) blocks = 1;
+    if ((size_t)blocks * 4 > partials_cap) return cudaErrorInvalidValue;
+    FastDiv chunks = FastDiv::make((unsigned)cpf);
+    Geom gg = g;
+    FrameSet ff = fs;
+    Coef cc = cf;
+    PcgArgs aa = a;
+    void* args[] = {&gg, &pi, &chunks, &aitems, &uitems, &tiles, &ff, &cc, (void*)&grad, (void*)&dT, &x, &r, &p,
+                    &q, &mean_s, &sum_v, &partials, &S, &aa};
+    e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(kThreads), args, 0, s);
+    count_launches(1);
+    return e;
+}
+
+}  // namespace
+
+bool pcg_coop_preferred(const Geom& g, int nK) { return (long long)g.N * nK <= (1LL << 20); }
+
+cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+                            float* x, float* r, float* p, float* q, float* mean_s, float* sum_v, double* partials,
+                            size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s) {
+    const bool v4 = vec4_ok(g, {grad, dT, x, r, p, q, mean_s, sum_v});
+    if (g.d == 2)
+        return v4 ? coop_go<2, 4, 4>(g, fs, cf, grad, dT, x, r, p, q, mean_s, sum_v, partials, partials_cap, S, a, s)
+                  : coop_go<2, 1, 8>(g, fs, cf, grad, dT, x, r, p, q, mean_s, sum_v, partials, partials_cap, S, a, s);
+    return v4 ? coop_go<3, 4, 4>(g, fs, cf, grad, dT, x, r, p, q, mean_s, sum_v, partials, partials_cap, S, a, s)
+              : coop_go<3, 1, 8>(g, fs, cf, grad, dT, x, r, p, q, mean_s, sum_v, partials, partials_cap, S, a, s);
 }
 
 }  // namespace stml

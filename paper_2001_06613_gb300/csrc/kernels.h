@@ -70,8 +70,9 @@ cudaError_t launch_corr_coeff(const float* img, int n, long long N, double* rho_
 // ---------------------------------------------------------- objective (k_eval.cu)
 // Objective pass at u (or u + t du): J, D, S, P, |u|^2 to out[0..3], out[5]
 // (out[4] = 0), and the per-pixel frame means abar (N) and ubar (d N).
+// With gdot (requires du) the pass also reduces <gdot, du> and |du|^2 into out[6], out[7].
 cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
-                             const float* du, float t, float* abar, float* ubar, double* partials,
+                             const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
                              size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s);
 // Gradient pass at u (or u + t du) with abar, ubar of the same point: g and
 // grad T, optionally the point itself (unew); |g|^2 and |u|^2 to out[4], out[5].
@@ -123,12 +124,14 @@ cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, c
 cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, float* x, float* r,
                               const float* p, const float* q, double* partials, size_t partials_cap, DevScalars* S,
                               PcgArgs a, cudaStream_t s);
+// The whole PCG solve (start, iterations, exit) in one cooperative launch, for
+// small problems where launch latency dominates; the final CG state goes to S.
+bool pcg_coop_preferred(const Geom& g, int nK);
+cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+                            float* x, float* r, float* p, float* q, float* mean_s, float* sum_v, double* partials,
+                            size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s);
 // p = M^-1 r + beta p, and the frame sums of the new p.
 cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const float* r,
                                  float* p, float* mean_s, float* sum_v, DevScalars* S, cudaStream_t s);
-// out[0] = <a, b>, out[1] = <b, b>
-cudaError_t launch_dot2(const float* a, const float* b, size_t n, double* partials,
-                        unsigned int* ticket, double* out, cudaStream_t s);
-
 
 }  // namespace stml
