@@ -136,19 +136,31 @@ __device__ __forceinline__ float forward_diff2_h2(const float* __restrict__ w, c
 // xi = i + u/h with u/h exact (h is a power of two), i0 = i + floor(u/h),
 // f = u/h - floor(u/h) exact in float32.
 __device__ __forceinline__ void split_coord(int i, float u, float inv_h, int& i0, float& f) {
-    float t = u * inv_h;
-    if (!(fabsf(t) < 1.0e7f)) {   // NaN, Inf or absurd: far outside the grid
-        i0 = -1000000000;
-        f = 0.f;
-        return;
-    }
-    float fl = floorf(t);
-    f = t - fl;
-    i0 = i + (int)fl;
+    const float t = u * inv_h;
+    const bool ok = fabsf(t) < 1.0e7f;   // false for NaN, Inf and absurd: far outside the grid
+    const float fl = floorf(ok ? t : 0.f);
+    f = ok ? t - fl : 0.f;
+    i0 = ok ? i + (int)fl : -1000000000;
 }
 
-__device__ __forceinline__ float fetch2(const float* __restrict__ T, int nx, int ny, int ix, int iy) {
-    return (ix >= 0 && ix < nx && iy >= 0 && iy < ny) ? __ldg(T + (long long)iy * nx + ix) : 0.f;
+__device__ __forceinline__ int clampi(int v, int hi) { return min(max(v, 0), hi); }
+
+// The four corners (ix, iy) .. (ix + 1, iy + 1) of a bilinear stencil, zero
+// outside the grid.  Branch-free: every load reads a clamped (in-range)
+// address and outside corners are zeroed afterwards, so the loads of several
+// stencils can all be in flight together.
+__device__ __forceinline__ void corners2(const float* __restrict__ T, int nx, int ny, int ix, int iy, float& t00,
+                                         float& t01, float& t10, float& t11) {
+    const bool x0 = (unsigned)ix < (unsigned)nx, x1 = (unsigned)(ix + 1) < (unsigned)nx;
+    const bool y0 = (unsigned)iy < (unsigned)ny, y1 = (unsigned)(iy + 1) < (unsigned)ny;
+    const int cx0 = clampi(ix, nx - 1), cx1 = clampi(ix + 1, nx - 1);
+    const float* r0 = T + (long long)clampi(iy, ny - 1) * nx;
+    const float* r1 = T + (long long)clampi(iy + 1, ny - 1) * nx;
+    const float v00 = __ldg(r0 + cx0), v01 = __ldg(r0 + cx1), v10 = __ldg(r1 + cx0), v11 = __ldg(r1 + cx1);
+    t00 = (x0 && y0) ? v00 : 0.f;
+    t01 = (x1 && y0) ? v01 : 0.f;
+    t10 = (x0 && y1) ? v10 : 0.f;
+    t11 = (x1 && y1) ? v11 : 0.f;
 }
 
 // Bilinear value and gradient (zero extension) of the level image T at the
@@ -159,10 +171,8 @@ __device__ __forceinline__ void interp2(const float* __restrict__ T, const Geom&
     float fy, fx;
     split_coord(y, uy, g.inv_h, iy, fy);
     split_coord(x, ux, g.inv_h, ix, fx);
-    const float t00 = fetch2(T, g.nx, g.ny, ix, iy);
-    const float t01 = fetch2(T, g.nx, g.ny, ix + 1, iy);
-    const float t10 = fetch2(T, g.nx, g.ny, ix, iy + 1);
-    const float t11 = fetch2(T, g.nx, g.ny, ix + 1, iy + 1);
+    float t00, t01, t10, t11;
+    corners2(T, g.nx, g.ny, ix, iy, t00, t01, t10, t11);
     const float a0 = t00 + fx * (t01 - t00);
     const float a1 = t10 + fx * (t11 - t10);
     val = a0 + fy * (a1 - a0);
@@ -177,19 +187,60 @@ __device__ __forceinline__ float interp2_val(const float* __restrict__ T, const 
     float fy, fx;
     split_coord(y, uy, g.inv_h, iy, fy);
     split_coord(x, ux, g.inv_h, ix, fx);
-    const float t00 = fetch2(T, g.nx, g.ny, ix, iy);
-    const float t01 = fetch2(T, g.nx, g.ny, ix + 1, iy);
-    const float t10 = fetch2(T, g.nx, g.ny, ix, iy + 1);
-    const float t11 = fetch2(T, g.nx, g.ny, ix + 1, iy + 1);
+    float t00, t01, t10, t11;
+    corners2(T, g.nx, g.ny, ix, iy, t00, t01, t10, t11);
     const float a0 = t00 + fx * (t01 - t00);
     const float a1 = t10 + fx * (t11 - t10);
     return a0 + fy * (a1 - a0);
 }
 
-__device__ __forceinline__ float fetch3(const float* __restrict__ T, const Geom& g, int ix, int iy, int iz) {
-    return (ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny && iz >= 0 && iz < g.nz)
-               ? __ldg(T + ((long long)iz * g.ny + iy) * g.nx + ix)
-               : 0.f;
+// The eight corners c[dz][dy][dx] of a trilinear stencil, zero outside;
+// branch-free like corners2.
+__device__ __forceinline__ void corners3(const float* __restrict__ T, const Geom& g, int ix, int iy, int iz,
+                                         float (&c)[2][2][2]) {
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    int cx[2], cy[2], cz[2];
+    bool bx[2], by[2], bz[2];
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        bx[o] = (unsigned)(ix + o) < (unsigned)g.nx;
+        by[o] = (unsigned)(iy + o) < (unsigned)g.ny;
+        bz[o] = (unsigned)(iz + o) < (unsigned)g.nz;
+        cx[o] = clampi(ix + o, g.nx - 1);
+        cy[o] = clampi(iy + o, g.ny - 1);
+        cz[o] = clampi(iz + o, g.nz - 1);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float* r = T + cz[a] * sz + cy[q] * sy;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float v = __ldg(r + cx[e]);
+                c[a][q][e] = (bz[a] && by[q] && bx[e]) ? v : 0.f;
+            }
+        }
+}
+
+// Trilinear value only (zero extension), displacement (uz, uy, ux).
+__device__ __forceinline__ float interp3_val(const float* __restrict__ T, const Geom& g, int x, int y, int z,
+                                             float uz, float uy, float ux) {
+    int iz, iy, ix;
+    float fz, fy, fx;
+    split_coord(z, uz, g.inv_h, iz, fz);
+    split_coord(y, uy, g.inv_h, iy, fy);
+    split_coord(x, ux, g.inv_h, ix, fx);
+    float c[2][2][2];
+    corners3(T, g, ix, iy, iz, c);
+    float cy[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float c0 = c[a][0][0] + fx * (c[a][0][1] - c[a][0][0]);
+        const float c1 = c[a][1][0] + fx * (c[a][1][1] - c[a][1][0]);
+        cy[a] = c0 + fy * (c1 - c0);
+    }
+    return cy[0] + fz * (cy[1] - cy[0]);
 }
 
 // Trilinear value and gradient (zero extension), displacement (uz, uy, ux).
@@ -202,12 +253,7 @@ __device__ __forceinline__ void interp3(const float* __restrict__ T, const Geom&
     split_coord(y, uy, g.inv_h, iy, fy);
     split_coord(x, ux, g.inv_h, ix, fx);
     float c[2][2][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int e = 0; e < 2; ++e) c[a][b][e] = fetch3(T, g, ix + e, iy + b, iz + a);
+    corners3(T, g, ix, iy, iz, c);
     // blend along x
     float cx[2][2], dx[2][2];
 #pragma unroll

@@ -702,6 +702,7 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
     int sh3[3] = {1, 1, 1};
     for (int i = 0; i < dim; ++i) {
         if (shape[i] < 1 || shape[i] % f) return fail(c, STML_EINVAL, "every axis must be a positive multiple of 2^(n_levels-1)");
+        if (shape[i] > 65535) return fail(c, STML_EINVAL, "an axis has more than 65535 cells");
         sh3[3 - dim + i] = shape[i];
     }
     CK(c, cudaStreamSynchronize(c->stream));

@@ -14,7 +14,13 @@
 // Fields may be read as u + t du (an Armijo trial point); grad_kernel can also
 // write that point out (the accepted Gauss-Newton step), so the objective
 // pass of the trial supplies abar and ubar at the new iterate.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace stml {
 
@@ -71,44 +77,119 @@ __device__ __forceinline__ void interp(const float* __restrict__ Tk, const Geom&
 }  // namespace
 
 // ----------------------------------------------------------------- objective
-// Reduced values: 0 D, 1 S_x, 2 S_t, 3 P, 4 (unused), 5 |u|^2.
-// With gdot != nullptr the pass also reduces <gdot, du> and |du|^2 (the
-// directional derivative of the Gauss-Newton step) into out[6], out[7].
-template <int D, int VEC, int TPR>
-__global__ void __launch_bounds__(kThreads, 3)
-obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, FView U,
-           const float* __restrict__ gdot, float* __restrict__ abar, float* __restrict__ ubar,
-           double* __restrict__ partials, unsigned int* ticket, double* out) {
-    constexpr int SEG = TPR * VEC, FG = kThreads / TPR;
-    __shared__ float sh_n[FG][SEG], sh_m[FG][SEG], sh_q[FG][SEG];
+// Reduced values: 0 D, 1 S_x, 2 S_t, 3 P, 4 (unused), 5 |u|^2; with GDOT also
+// 6 <gdot, du> and 7 |du|^2 (the directional derivative of the Gauss-Newton
+// step).  Fields are read as u + t du when TRIAL.
+//
+// A CTA covers a run of SEG = 32 VEC pixels of one image row with FG warps;
+// lane l owns the VEC pixels p0 + VEC l ...  The frames are dealt to frame
+// groups: warp w of split r (blockIdx.y) takes j = r FG + w, j + FG S, ...,
+// with the field of its next frame loaded while the current one is used.
+// Per pixel a warp keeps shifted sums of a_k - s (s = its first a_k), which
+// give the mean and the sum of squared deviations at the end; the FG warps
+// of a CTA are merged in shared memory by a pairwise tree (Chan's update),
+// and the S splits of a run form one thread-block cluster whose rank 0
+// merges the others' results through distributed shared memory, in rank
+// order.
+namespace {
+
+// Resident CTAs per SM the objective kernel is compiled for (register cap).
+constexpr int obj_min_blocks(int d, int vec) { return vec == 4 || (d == 3 && vec == 2) ? 2 : 3; }
+
+template <int VEC>
+__device__ __forceinline__ void ldv(const float* __restrict__ q, size_t i, float (&o)[VEC]) {
+    if constexpr (VEC == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(q + i));
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else if constexpr (VEC == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(q + i));
+        o[0] = a.x; o[1] = a.y;
+    } else {
+        o[0] = __ldg(q + i);
+    }
+}
+
+// The field of one frame at a thread's pixels: the pixels, the next row, the
+// next plane (3-D) and, in lane 31, the first pixel of the next run.
+template <int D, int VEC, bool TRIAL>
+struct FrameU {
+    float c[D][VEC], ny[D][VEC], nz[D == 3 ? D : 1][VEC], tail[D];
+
+    __device__ __forceinline__ static void ld(const float* __restrict__ u, const float* __restrict__ du, float t,
+                                              size_t i, float (&o)[VEC]) {
+        ldv<VEC>(u, i, o);
+        if constexpr (TRIAL) {
+            float d[VEC];
+            ldv<VEC>(du, i, d);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) o[e] = fmaf(t, d[e], o[e]);
+        }
+    }
+    __device__ __forceinline__ void load(const float* __restrict__ u, const float* __restrict__ du, float t,
+                                         size_t b, size_t N, int nx, size_t sz, bool valid, bool has_y,
+                                         bool has_z, bool has_tail) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const size_t bk = b + (size_t)k * N;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) c[k][e] = ny[k][e] = 0.f;
+            if (valid) ld(u, du, t, bk, c[k]);
+            if (has_y) ld(u, du, t, bk + nx, ny[k]);
+            if constexpr (D == 3) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) nz[k][e] = 0.f;
+                if (has_z) ld(u, du, t, bk + sz, nz[k]);
+            }
+            tail[k] = has_tail ? (TRIAL ? fmaf(t, __ldg(du + bk + VEC), __ldg(u + bk + VEC)) : __ldg(u + bk + VEC))
+                               : 0.f;
+        }
+    }
+};
+
+}  // namespace
+
+template <int D, int VEC, bool TRIAL, bool GDOT>
+__global__ void __launch_bounds__(kThreads, obj_min_blocks(D, VEC))
+obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ u,
+           const float* __restrict__ du, float t, const float* __restrict__ gdot, float* __restrict__ abar,
+           float* __restrict__ ubar, double* __restrict__ partials, unsigned int* ticket, double* out) {
+    constexpr int FG = kThreads / 32, SEG = 32 * VEC;
+    __shared__ float sh_m[FG][SEG], sh_q[FG][SEG];
     __shared__ float sh_u[FG][D][SEG];
-    const int lane = threadIdx.x % TPR, fg = threadIdx.x / TPR;
-    const unsigned p = blockIdx.x * SEG + lane * VEC;
-    const bool valid = p < (unsigned)g.N;
+    __shared__ float sh_n[FG];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int S = (int)gridDim.y, TG = FG * S;
+    const unsigned p0 = blockIdx.x * SEG, p = p0 + (unsigned)lane * VEC;
     const size_t N = (size_t)g.N;
+    const size_t sz = (size_t)g.nx * g.ny;
+    const bool valid = p < (unsigned)g.N;
     int x = 0, y = 0, z = 0;
     if (valid) pos_of(pi, p, x, y, z);
-    float cnt = 0.f, mean[VEC], m2[VEC], su[D][VEC];
+    // rows hold a multiple of VEC pixels, so only the last pixel of a thread
+    // can have its x + 1 neighbour outside the row
+    const bool has_y = valid && y + 1 < g.ny, has_z = valid && D == 3 && z + 1 < g.nz;
+    const bool has_xl = valid && x + VEC < g.nx;
+    const bool has_tail = lane == 31 && has_xl;
+
+    float cnt = 0.f, sft[VEC], s1[VEC], s2[VEC], su[D][VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
-        mean[e] = 0.f;
-        m2[e] = 0.f;
+        sft[e] = s1[e] = s2[e] = 0.f;
 #pragma unroll
-        for (int c = 0; c < D; ++c) su[c][e] = 0.f;
+        for (int k = 0; k < D; ++k) su[k][e] = 0.f;
     }
     float sx = 0.f, st = 0.f, u2 = 0.f, gd = 0.f, dd = 0.f;
-    if (valid) {
-#pragma unroll 2
-        for (int j = fg; j < fs.nK; j += FG) {
-            const float* Tk = T + (size_t)__ldg(fs.frames + j) * N;
-            if (gdot) {
+    const float c_sx = 0.5f * cf.alpha_hd * cf.inv_h2;
+    const int j0 = (int)blockIdx.y * FG + w;
+    if constexpr (GDOT) {
+        if (valid) {
+            for (int j = j0; j < fs.nK; j += TG) {
 #pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const size_t base = ((size_t)j * D + c) * N + p;
+                for (int k = 0; k < D; ++k) {
+                    const size_t b = ((size_t)j * D + k) * N + p;
                     float gv[VEC], dv[VEC];
-                    const FView G{gdot, nullptr, 0.f}, Dv{U.d, nullptr, 0.f};
-                    vload<VEC>(G, base, gv);
-                    vload<VEC>(Dv, base, dv);
+                    ldv<VEC>(gdot, b, gv);
+                    ldv<VEC>(du, b, dv);
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) {
                         gd = fmaf(gv[e], dv[e], gd);
@@ -116,102 +197,147 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
                     }
                 }
             }
-            const float w_next = (cf.alphat_hd != 0.f && j + 1 < fs.nK) ? __ldg(fs.w_next + j) : 0.f;
-            float uc[D][VEC];
+        }
+    }
+    if (j0 < fs.nK) {
+        FrameU<D, VEC, TRIAL> cur;
+        cur.load(u, du, t, (size_t)j0 * D * N + p, N, g.nx, sz, valid, has_y, has_z, has_tail);
+        int fr = __ldg(fs.frames + j0);
+        for (int j = j0; j < fs.nK; j += TG) {
+            // warped image of frame j; every gather is unconditional (clamped
+            // addresses; invalid lanes sample pixel 0 with a zero field)
+            const float* Tk = T + (size_t)fr * N;
+            float a[VEC];
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const size_t base = ((size_t)j * D + c) * N + p;
-                vload<VEC>(U, base, uc[c]);
-                // forward differences to +x (inside the thread's run, then the next run), +y, +z
+            for (int e = 0; e < VEC; ++e) {
+                if constexpr (D == 2)
+                    a[e] = interp2_val(Tk, g, x + e, y, cur.c[0][e], cur.c[1][e]);
+                else
+                    a[e] = interp3_val(Tk, g, x + e, y, z, cur.c[0][e], cur.c[1][e], cur.c[2][e]);
+            }
+            // the field of this warp's next frame (the last frame again at the end)
+            const int jn = j + TG < fs.nK ? j + TG : j;
+            FrameU<D, VEC, TRIAL> nxt;
+            nxt.load(u, du, t, (size_t)jn * D * N + p, N, g.nx, sz, valid, has_y, has_z, has_tail);
+            const int fr_next = __ldg(fs.frames + jn);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float right = __shfl_down_sync(0xffffffffu, cur.c[k][0], 1);
+                const float xl = lane < 31 ? right : cur.tail[k];
                 float fw = 0.f;
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
-                    if (x + e < g.nx - 1) {
-                        const float nb = e + 1 < VEC ? uc[c][e + 1] : U.ld(base + VEC);
-                        fw = fmaf(nb - uc[c][e], nb - uc[c][e], fw);
+                    const float cc = cur.c[k][e];
+                    if (e + 1 < VEC || has_xl) {
+                        const float nb = e + 1 < VEC ? cur.c[k][(e + 1) % VEC] : xl;
+                        fw = fmaf(nb - cc, nb - cc, fw);
                     }
+                    if (has_y) fw = fmaf(cur.ny[k][e] - cc, cur.ny[k][e] - cc, fw);
+                    if constexpr (D == 3)
+                        if (has_z) fw = fmaf(cur.nz[k][e] - cc, cur.nz[k][e] - cc, fw);
+                    su[k][e] += cc;
+                    u2 = fmaf(cc, cc, u2);
                 }
-                if (y < g.ny - 1) {
-                    float nb[VEC];
-                    vload<VEC>(U, base + g.nx, nb);
+                sx = fmaf(c_sx, valid ? fw : 0.f, sx);
+                if (cf.alphat_hd != 0.f && j + 1 < fs.nK && valid) {
+                    const float cw = 0.5f * cf.alphat_hd * __ldg(fs.w_next + j);
+                    float nt[VEC];
+                    FrameU<D, VEC, TRIAL>::ld(u, du, t, ((size_t)(j + 1) * D + k) * N + p, nt);
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) fw = fmaf(nb[e] - uc[c][e], nb[e] - uc[c][e], fw);
-                }
-                if constexpr (D == 3) {
-                    if (z < g.nz - 1) {
-                        float nb[VEC];
-                        vload<VEC>(U, base + (size_t)g.nx * g.ny, nb);
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e) fw = fmaf(nb[e] - uc[c][e], nb[e] - uc[c][e], fw);
-                    }
-                }
-                sx = fmaf(0.5f * cf.alpha_hd * cf.inv_h2, fw, sx);
-                if (w_next != 0.f) {
-                    float nb[VEC];
-                    vload<VEC>(U, base + (size_t)D * N, nb);
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        st = fmaf(0.5f * cf.alphat_hd * w_next * (nb[e] - uc[c][e]), nb[e] - uc[c][e], st);
-                }
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    su[c][e] += uc[c][e];
-                    u2 = fmaf(uc[c][e], uc[c][e], u2);
+                    for (int e = 0; e < VEC; ++e) st = fmaf(cw * (nt[e] - cur.c[k][e]), nt[e] - cur.c[k][e], st);
                 }
             }
-            cnt += 1.f;
-            const float rc = 1.0f / cnt;
+            if (cnt == 0.f) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) sft[e] = a[e];
+            }
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                float a;
-                if constexpr (D == 2) {
-                    a = interp2_val(Tk, g, x + e, y, uc[0][e], uc[1][e]);
-                } else {
-                    float uu[D], gr[D];
-#pragma unroll
-                    for (int c = 0; c < D; ++c) uu[c] = uc[c][e];
-                    interp<D>(Tk, g, x + e, y, z, uu, a, gr);
-                }
-                const float dlt = a - mean[e];
-                mean[e] = fmaf(dlt, rc, mean[e]);
-                m2[e] = fmaf(dlt, a - mean[e], m2[e]);
+                const float dl = a[e] - sft[e];
+                s1[e] += dl;
+                s2[e] = fmaf(dl, dl, s2[e]);
             }
+            cnt += 1.f;
+            cur = nxt;
+            fr = fr_next;
         }
     }
+    // this warp's mean and sum of squared deviations per pixel
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
         const int k = lane * VEC + e;
-        sh_n[fg][k] = cnt;
-        sh_m[fg][k] = mean[e];
-        sh_q[fg][k] = m2[e];
+        const float mb = cnt > 0.f ? s1[e] / cnt : 0.f;
+        sh_m[w][k] = sft[e] + mb;
+        sh_q[w][k] = fmaxf(fmaf(-s1[e], mb, s2[e]), 0.f);
 #pragma unroll
-        for (int c = 0; c < D; ++c) sh_u[fg][c][k] = su[c][e];
+        for (int c = 0; c < D; ++c) sh_u[w][c][k] = su[c][e];
+    }
+    if (lane == 0) sh_n[w] = cnt;
+    // pairwise tree over the warps of this CTA: slot w absorbs slot w + s
+#pragma unroll
+    for (int s = FG / 2; s > 0; s >>= 1) {
+        __syncthreads();
+        if (w < s) {
+            const float na = sh_n[w], nb = sh_n[w + s];
+            if (nb > 0.f) {
+                const float n = na + nb, wb = nb / n, wab = na * nb / n;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const int k = lane * VEC + e;
+                    const float dl = sh_m[w + s][k] - sh_m[w][k];
+                    sh_m[w][k] = na > 0.f ? fmaf(dl, wb, sh_m[w][k]) : sh_m[w + s][k];
+                    sh_q[w][k] = sh_q[w][k] + sh_q[w + s][k] + dl * dl * wab;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) sh_u[w][c][k] += sh_u[w + s][c][k];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) sh_n[w] = na + nb;
+        }
     }
     __syncthreads();
-    // combine the frame groups of every pixel (Chan's update, group order)
-    float dsum = 0.f, pen = 0.f;
-    if (threadIdx.x < SEG) {
-        const int k = threadIdx.x;
-        const unsigned pp = blockIdx.x * SEG + k;
-        if (pp < (unsigned)g.N) {
-            float n = 0.f, m = 0.f, q = 0.f;
-            for (int w = 0; w < FG; ++w) {
-                const float nb = sh_n[w][k];
-                if (nb == 0.f) continue;
-                const float tot = n + nb;
-                const float dl = sh_m[w][k] - m;
-                m = fmaf(dl, nb / tot, m);
-                q = q + sh_q[w][k] + dl * dl * (n * nb / tot);
-                n = tot;
+    bool finisher = true;
+    if (S > 1) {
+        // merge the splits of this run: rank 0 reads ranks 1..S-1 in order
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        finisher = cl.block_rank() == 0;
+        if (finisher && threadIdx.x < SEG) {
+            const int k = threadIdx.x;
+            float n = sh_n[0], m = sh_m[0][k], q = sh_q[0][k], us[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) us[c] = sh_u[0][c][k];
+            for (int rr = 1; rr < S; ++rr) {
+                const float nb = *cl.map_shared_rank(&sh_n[0], rr);
+                if (nb > 0.f) {
+                    const float mb = *cl.map_shared_rank(&sh_m[0][k], rr);
+                    const float qb = *cl.map_shared_rank(&sh_q[0][k], rr);
+                    const float tot = n + nb, dl = mb - m;
+                    m = n > 0.f ? fmaf(dl, nb / tot, m) : mb;
+                    q = q + qb + dl * dl * (n * nb / tot);
+                    n = tot;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) us[c] += *cl.map_shared_rank(&sh_u[0][c][k], rr);
+                }
             }
-            abar[pp] = m;
-            dsum = cf.half_hd * q;
+            sh_m[0][k] = m;
+            sh_q[0][k] = q;
+#pragma unroll
+            for (int c = 0; c < D; ++c) sh_u[0][c][k] = us[c];
+        }
+        cl.sync();   // the other ranks' shared memory stays alive until rank 0 has read it
+    }
+    float dsum = 0.f, pen = 0.f;
+    if (finisher && threadIdx.x < SEG) {
+        const int k = threadIdx.x;
+        const unsigned pp = p0 + k;
+        if (pp < (unsigned)g.N) {
+            abar[pp] = sh_m[0][k];
+            dsum = cf.half_hd * sh_q[0][k];
             const float invK = 1.0f / (float)fs.nK;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                float s = 0.f;
-                for (int w = 0; w < FG; ++w) s += sh_u[w][c][k];
-                const float ub = s * invK;
+                const float ub = sh_u[0][c][k] * invK;
                 ubar[(size_t)c * N + pp] = ub;
                 pen = fmaf(cf.lam_hd * ub, ub, pen);
             }
@@ -376,41 +502,85 @@ bool v4ok(const Geom& g, std::initializer_list<const void*> ptrs) {
 
 }  // namespace
 
-size_t eval_partials(const Geom& g, int nK) {
-    const size_t obj = (size_t)((g.N + 7) / 8) * 8;
-    return obj > (size_t)kGridStride * 2 ? obj : (size_t)kGridStride * 2;
-    (void)nK;
+// Launch shape of the objective pass: pixels per lane and frame splits.
+struct ObjShape {
+    int vec, splits;
+    unsigned runs;
+};
+
+ObjShape obj_shape(const Geom& g, int nK, int vec_max) {
+    constexpr int FG = kThreads / 32;
+    ObjShape sh{1, 1, 0};
+    int slots = 0;
+    for (int v : {4, 2, 1}) {
+        if (v > vec_max || g.nx % v) continue;
+        slots = 152 * obj_min_blocks(g.d, v);   // resident CTAs of obj_kernel on a GB300
+        sh.vec = v;
+        sh.runs = (unsigned)((g.N + 32LL * v - 1) / (32LL * v));
+        if (sh.runs >= (unsigned)slots) break;
+    }
+    const int max_split = std::max(1, std::min(8, (nK + FG - 1) / FG));
+    sh.splits = (int)std::min<long long>(max_split, ((long long)slots + sh.runs - 1) / sh.runs);
+    return sh;
 }
 
-template <int D, int VEC, int TPR>
-static void obj_go(unsigned blocks, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
-                   const FrameSet& fs, const Coef& cf, const FView& U, const float* gdot, float* abar, float* ubar,
-                   double* partials, unsigned int* ticket, double* out) {
-    obj_kernel<D, VEC, TPR><<<blocks, kThreads, 0, s>>>(T, g, pi, fs, cf, U, gdot, abar, ubar, partials, ticket, out);
+size_t eval_partials(const Geom& g, int nK) {
+    const ObjShape sh = obj_shape(g, nK < 1 ? 1 : nK, 1);   // the most runs any launch uses
+    const size_t obj = (size_t)sh.runs * 8 * 8;              // every split count up to 8
+    return obj > (size_t)kGridStride * 2 ? obj : (size_t)kGridStride * 2;
+}
+
+template <int D, int VEC, bool TRIAL, bool GDOT>
+static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
+                          const FrameSet& fs, const Coef& cf, const float* u, const float* du, float t,
+                          const float* gdot, float* abar, float* ubar, double* partials, unsigned int* ticket,
+                          double* out) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(sh.runs, (unsigned)sh.splits, 1);
+    lc.blockDim = dim3(kThreads, 1, 1);
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)sh.splits;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = sh.splits > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, obj_kernel<D, VEC, TRIAL, GDOT>, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar,
+                              partials, ticket, out);
+}
+
+template <int D, int VEC>
+static cudaError_t obj_mode(const ObjShape& sh, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
+                            const FrameSet& fs, const Coef& cf, const float* u, const float* du, float t,
+                            const float* gdot, float* abar, float* ubar, double* partials, unsigned int* ticket,
+                            double* out) {
+    if (!du) return obj_go<D, VEC, false, false>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out);
+    if (!gdot) return obj_go<D, VEC, true, false>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out);
+    return obj_go<D, VEC, true, true>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out);
 }
 
 cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                              const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
                              size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s) {
     const PixIndex pi{FastDiv::make((unsigned)g.nx), FastDiv::make((unsigned)g.ny)};
-    const bool v4 = v4ok(g, {u, du, gdot, abar, ubar});
-    // wide pixel tiles on large levels, narrow ones (more CTAs, more frame groups) on small levels
-    const bool narrow = g.N < 4LL * 152 * (v4 ? 64 : 32);
-    const int seg = v4 ? (narrow ? 16 : 64) : (narrow ? 8 : 32);
-    const unsigned blocks = (unsigned)((g.N + seg - 1) / seg);
-    if ((size_t)blocks * 8 > partials_cap) return cudaErrorInvalidValue;
+    // pixels per lane: 4 (2 in 3-D) when rows and every array allow vector access
+    int vec_max = g.d == 3 ? 2 : 4;
+    for (const void* q : {(const void*)u, (const void*)du, (const void*)gdot})
+        if (q && ((uintptr_t)q & 15u)) vec_max = (uintptr_t)q & 7u ? 1 : std::min(vec_max, 2);
+    const ObjShape sh = obj_shape(g, fs.nK, vec_max);
+    if ((size_t)sh.runs * sh.splits * 8 > partials_cap) return cudaErrorInvalidValue;
     if (gdot && !du) return cudaErrorInvalidValue;
-    const FView U{u, du, t};
-#define STML_OBJ(D_, V_, T_) obj_go<D_, V_, T_>(blocks, s, T, g, pi, fs, cf, U, gdot, abar, ubar, partials, ticket, out)
+    cudaError_t e;
+#define STML_OBJ(D_, V_) e = obj_mode<D_, V_>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out)
     if (g.d == 2) {
-        if (v4) { if (narrow) STML_OBJ(2, 4, 4); else STML_OBJ(2, 4, 16); }
-        else { if (narrow) STML_OBJ(2, 1, 8); else STML_OBJ(2, 1, 32); }
+        if (sh.vec == 4) STML_OBJ(2, 4); else if (sh.vec == 2) STML_OBJ(2, 2); else STML_OBJ(2, 1);
     } else {
-        if (v4) { if (narrow) STML_OBJ(3, 4, 4); else STML_OBJ(3, 4, 16); }
-        else { if (narrow) STML_OBJ(3, 1, 8); else STML_OBJ(3, 1, 32); }
+        if (sh.vec == 2) STML_OBJ(3, 2); else STML_OBJ(3, 1);
     }
 #undef STML_OBJ
     count_launches(1);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
