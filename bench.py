@@ -147,7 +147,7 @@ def matvec_traffic_per_pixel_frame():
     """DRAM bytes per pixel-frame of the Hessian-product kernel from the
     committed ncu summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "gn_matvec_paper_scale.md")
-    src = os.path.join(ROOT, "paper_2001_06613_gb300", "csrc", "k_hessian.cu")
+    src = os.path.join(ROOT, "paper_2001_06613_gb300", "csrc", "k_gn.cu")
     try:
         txt = open(path).read()
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -156,7 +156,7 @@ def matvec_traffic_per_pixel_frame():
             if ":" in ln and ln.strip().startswith("- "):
                 k, v = ln.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("k_hessian.cu sha256[:16]") != digest:
+        if vals.get("k_gn.cu sha256[:16]") != digest:
             return None
         return float(vals["dram bytes per pixel-frame"])
     except Exception:

@@ -110,8 +110,9 @@ stml_status stml_set_params(stml_ctx* ctx, const stml_params* p);
 
 /* Copies n_frames images of `shape` (dim = 2 or 3) from `frames` (host, or
  * device when on_device != 0) into library memory.  Every axis must be
- * divisible by 2^(n_levels-1) and have at most 65535 cells.  Allocates all
- * level buffers. */
+ * divisible by 2^(n_levels-1) and have at most 65535 cells, and an image at
+ * most 2^31 - 1 cells (pixel indices are 32-bit).  Allocates all level
+ * buffers. */
 stml_status stml_load_sequence(stml_ctx* ctx, const float* frames, int on_device,
                                int n_frames, int dim, const int* shape);
 

@@ -26,7 +26,7 @@ struct DevScalars {
     double red[kMaxRed];      // totals of the last evaluation (J, D, S, P, |g|^2, |u|^2, ...)
     double trial[kMaxRed];    // totals of the last objective-only evaluation
     double dots[kMaxRed];     // totals of the last dot-product kernel
-    double rho, bnorm2, pq, alpha, beta, rnorm2;
+    float rho, bnorm2, pq, alpha, beta, rnorm2;   // CG coefficients (device only)
     int cg_active, cg_iter, cg_flag, cg_pad;
     unsigned int err_flags;   // bit 0: a bounded device wait expired
     unsigned int err_pad;
@@ -290,60 +290,126 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Double-float ("double-word") numbers hi + lo with |lo| <= ulp(hi) / 2 and
+// their accurate addition from error-free transformations (TwoSum, Knuth;
+// Fast2Sum, Dekker; the accurate double-word sum analysed by Joldes, Muller
+// and Popescu, 2017): about 44 significant bits from FP32 instructions only.
+// The reductions use it in place of FP64 arithmetic, whose instructions are
+// far slower than FP32 ones on this GPU.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float ap = s - b;
+    const float bp = s - ap;
+    return {s, (a - ap) + (b - bp)};
+}
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
+    const dfloat s = df_two_sum(x.hi, y.hi);
+    const dfloat t = df_two_sum(x.lo, y.lo);
+    const dfloat v = df_fast_two_sum(s.hi, s.lo + t.hi);
+    return df_fast_two_sum(v.hi, t.lo + v.lo);
+}
+
+__device__ __forceinline__ dfloat df_shfl_xor(dfloat v, int o) {
+    return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// Stage 1 of a grid reduction: the CTA total of each of NV float values
+// (fixed butterfly inside a warp, then warp order in double-float), stored as
+// (hi, lo) at part[block * NV + i].  Threads 0..NV-1 write; all threads of
+// the CTA must call it.
+template <int NV>
+__device__ __forceinline__ void cta_partials(const float (&val)[NV], float2* __restrict__ part, unsigned block) {
+    static_assert(NV <= 32, "at most 32 values");
+    __shared__ float s_warp[kThreads / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const float w = warp_sum(val[i]);
+        if (lane == 0) s_warp[warp][i] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int i = threadIdx.x;
+        dfloat s = {s_warp[0][i], 0.f};
+        for (int w = 1; w < nwarps; ++w) s = df_add(s, dfloat{s_warp[w][i], 0.f});
+        part[(size_t)block * NV + i] = make_float2(s.hi, s.lo);
+    }
+}
+
+// Stage 2: the sum over nblocks CTA totals in a fixed order (thread-strided
+// double-float sums, a fixed butterfly, then warp order); every thread gets
+// the totals.  All threads of the CTA must call it.
+template <int NV>
+__device__ __forceinline__ void cta_total(const float2* __restrict__ part, unsigned nblocks, dfloat (&tot)[NV]) {
+    __shared__ dfloat s_w2[kThreads / 32][NV];
+    __shared__ dfloat s_tot[NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        dfloat s = {0.f, 0.f};
+        for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+            const float2 q = __ldcg(part + (size_t)b * NV + i);
+            s = df_add(s, dfloat{q.x, q.y});
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o));
+        if (lane == 0) s_w2[warp][i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int i = threadIdx.x;
+        dfloat s = s_w2[0][i];
+        for (int w = 1; w < nwarps; ++w) s = df_add(s, s_w2[w][i]);
+        s_tot[i] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) tot[i] = s_tot[i];
+    __syncthreads();
+}
+
 // Two-stage deterministic reduction of NV values over the whole grid.
 //
 // Stage 1: every thread holds float partials over its few elements; a warp
 // sums them in float with a fixed butterfly, the warp totals are summed in
-// double in warp order and the CTA total goes to partials[cta * NV + i].
+// double-float in warp order and the CTA total goes to the partials buffer.
 // Stage 2: the CTA that arrives last (an integer ticket, no float atomics)
-// sums all CTA totals in double in a fixed order and writes out[0..NV).
-// The result depends only on the launch shape, never on scheduling.
-// Returns true in every thread of the last CTA (so it may finish the step).
+// sums all CTA totals in double-float in a fixed order and writes out[0..NV)
+// (as double, from thread 0).  The result depends only on the launch shape,
+// never on scheduling.  Returns true in every thread of the last CTA (so it
+// may finish the step).  `partials` holds one 8-byte slot per CTA and value.
 template <int NV>
 __device__ __forceinline__ bool grid_reduce(const float (&val)[NV], double* __restrict__ partials,
                                             unsigned int* ticket, double* out) {
-    __shared__ double s_warp[kThreads / 32][NV];
-    __shared__ double s_fin[kThreads / 32][NV];
     __shared__ bool s_last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    float2* part = reinterpret_cast<float2*>(partials);
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        float w = warp_sum(val[i]);
-        if (lane == 0) s_warp[warp][i] = (double)w;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += s_warp[w][i];
-            partials[(size_t)bid * NV + i] = s;
-        }
-        __threadfence();
-        unsigned t = atomicAdd(ticket, 1u);
-        s_last = (t == nblocks - 1);
+    cta_partials<NV>(val, part, bid);
+    if (threadIdx.x < 32) {
+        __threadfence();   // the CTA totals (written by lanes 0..NV-1) before the ticket
+        if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == nblocks - 1;
     }
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        double s = 0.0;
-        for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) s += __ldcg(partials + (size_t)b * NV + i);
-        s = warp_sum_d(s);
-        if (lane == 0) s_fin[warp][i] = s;
-    }
-    __syncthreads();
+    dfloat tot[NV];
+    cta_total<NV>(part, nblocks, tot);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += s_fin[w][i];
-            out[i] = s;
-        }
+        for (int i = 0; i < NV; ++i) out[i] = (double)tot[i].hi + (double)tot[i].lo;
         *ticket = 0u;
     }
     __syncthreads();

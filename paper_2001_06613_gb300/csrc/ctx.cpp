@@ -705,6 +705,8 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
         if (shape[i] > 65535) return fail(c, STML_EINVAL, "an axis has more than 65535 cells");
         sh3[3 - dim + i] = shape[i];
     }
+    if ((long long)sh3[0] * sh3[1] * sh3[2] > 0x7fffffffLL)
+        return fail(c, STML_EINVAL, "an image has more than 2^31 - 1 cells");
     CK(c, cudaStreamSynchronize(c->stream));
     free_buffers(c);
     c->n = n_frames;
@@ -896,12 +898,18 @@ stml_status stml_eval(stml_ctx* c, int level, const int* frames, int nK, const f
     TRY(upload_frameset(c, K, fs));
     const Coef cf = make_coef(L.g, c->p, nK);
     const bool full = g || dT;
+    const double pfK = (double)nK * L.g.N;
+    long pe = prof_begin(c, PC_TRIAL, level);
     CK(c, launch_objective(L.img, L.g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
                            c->partials_cap, &c->S->ticket[0], c->S->red, c->stream));
-    if (full)
+    prof_end(c, pe, pfK * (4.0 + 4.0 * L.g.d), pfK);
+    if (full) {
+        pe = prof_begin(c, PC_EVAL, level);
         CK(c, launch_gradient(L.img, L.g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, g ? g : c->w_g,
                               dT ? dT : c->w_dT, nullptr, c->partials, c->partials_cap, &c->S->ticket[4], c->S->red,
                               c->stream));
+        prof_end(c, pe, pfK * (4.0 + 20.0 * L.g.d), pfK);
+    }
     TRY(read_scalars(c));
     for (int i = 0; i < 6; ++i) out[i] = c->Sh->red[i];
     if (!full) out[4] = 0.0;
@@ -951,14 +959,18 @@ stml_status stml_corr_coeff(stml_ctx* c, int level, double* rho) {
 }
 
 // ------------------------------------------------------ context-free operators
+// A valid 2-D / 3-D shape whose image, and its 2x refinement, has at most
+// 2^31 - 1 cells (pixel indices are 32-bit).
 static bool shape_ok(int dim, const int* shape, int sh3[3]) {
     if ((dim != 2 && dim != 3) || !shape) return false;
     sh3[0] = 1;
+    long long cells = 1LL << dim;
     for (int i = 0; i < dim; ++i) {
-        if (shape[i] < 1) return false;
+        if (shape[i] < 1 || shape[i] > 65535) return false;
         sh3[3 - dim + i] = shape[i];
+        cells *= shape[i];
     }
-    return true;
+    return cells <= 0x7fffffffLL;
 }
 
 stml_status stml_restrict(const float* fine, float* coarse, int planes, int dim, const int* fine_shape,

@@ -330,18 +330,21 @@ __device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, c
     rv.store(r + e0);
 }
 
-// CG decisions (shared by both solve paths).
+// CG decisions (shared by both solve paths), in float: the step lengths are
+// applied in float anyway, and the totals they come from are double-float.
 struct CgState {
-    double rho, bnorm2, rnorm2, pq, alpha, beta;
+    float rho, bnorm2, rnorm2, pq, alpha, beta;
     int iter, flag, active;
 };
 
-__device__ __forceinline__ void cg_after_init(CgState& s, double rz, double rr, int max_cg) {
+__device__ __forceinline__ float df_val(const dfloat& v) { return v.hi + v.lo; }
+
+__device__ __forceinline__ void cg_after_init(CgState& s, float rz, float rr, int max_cg) {
     s.rho = rz;
     s.bnorm2 = rr;
     s.rnorm2 = rr;
     s.iter = 0;
-    if (!(rr > 0.0)) {
+    if (!(rr > 0.f)) {
         s.flag = CG_ZERO;
         s.active = 0;
     } else if (max_cg <= 0) {
@@ -353,9 +356,9 @@ __device__ __forceinline__ void cg_after_init(CgState& s, double rz, double rr, 
     }
 }
 
-__device__ __forceinline__ void cg_after_apply(CgState& s, double pq) {
+__device__ __forceinline__ void cg_after_apply(CgState& s, float pq) {
     s.pq = pq;
-    if (!(pq > 0.0)) {
+    if (!(pq > 0.f)) {
         s.flag = CG_BREAKDOWN;
         s.active = 0;
     } else {
@@ -363,10 +366,10 @@ __device__ __forceinline__ void cg_after_apply(CgState& s, double pq) {
     }
 }
 
-__device__ __forceinline__ void cg_after_update(CgState& s, double rz, double rr, float tol_cg, int max_cg) {
+__device__ __forceinline__ void cg_after_update(CgState& s, float rz, float rr, float tol_cg, int max_cg) {
     s.iter += 1;
     s.rnorm2 = rr;
-    if (sqrt(rr) <= (double)tol_cg * sqrt(s.bnorm2)) {
+    if (sqrtf(rr) <= tol_cg * sqrtf(s.bnorm2)) {
         s.flag = CG_CONVERGED;
         s.active = 0;
     } else if (s.iter >= max_cg) {
@@ -404,53 +407,6 @@ __device__ __forceinline__ void cg_store(DevScalars* S, const CgState& s) {
     S->cg_active = s.active;
 }
 
-// Block sum of NV floats (fixed order) -> partials[block * NV + i] in double.
-template <int NV>
-__device__ __forceinline__ void block_partials(const float (&v)[NV], double* partials) {
-    __shared__ double s_w[kThreads / 32][NV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        float w = v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if (lane == 0) s_w[warp][i] = (double)w;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            double s = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) s += s_w[w][i];
-            partials[(size_t)blockIdx.x * NV + i] = s;
-        }
-    }
-    __syncthreads();
-}
-
-// Sum of the partials of all CTAs in a fixed order; every CTA gets the same value.
-template <int NV>
-__device__ __forceinline__ void grid_total(const double* partials, double (&tot)[NV]) {
-    __shared__ double s_t[kThreads / 32][NV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        double s = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(partials + (size_t)b * NV + i);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) s_t[warp][i] = s;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += s_t[w][i];
-        tot[i] = s;
-    }
-    __syncthreads();
-}
-
 }  // namespace
 
 // ----------------------------------------------------------------- stream kernels
@@ -462,7 +418,7 @@ dir_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ 
            DevScalars* S, PcgArgs a) {
     if (MODE == 1 && !S->cg_active) return;
     __shared__ float sh[(kThreads / TPR) * (1 + D) * TPR * VEC];
-    const float beta = MODE == 1 ? (float)S->beta : 0.f;
+    const float beta = MODE == 1 ? S->beta : 0.f;
     float rz = 0.f, rr = 0.f;
     dir_tile<D, VEC, MODE, TPR>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v, beta, blockIdx.x, sh, rz, rr);
     if constexpr (MODE == 2) {
@@ -470,7 +426,7 @@ dir_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ 
         double tot[2];
         if (grid_reduce<2>(acc, partials, &S->ticket[2], tot) && threadIdx.x == 0) {
             CgState st = cg_load(S);
-            cg_after_init(st, tot[0], tot[1], a.max_cg);
+            cg_after_init(st, (float)tot[0], (float)tot[1], a.max_cg);
             cg_store(S, st);
         }
     }
@@ -490,7 +446,7 @@ apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, 
     }
     if (grid_reduce<1>(acc, partials, ticket, out) && threadIdx.x == 0 && pcg) {
         CgState st = cg_load(pcg);
-        cg_after_apply(st, out[0]);
+        cg_after_apply(st, (float)out[0]);
         cg_store(pcg, st);
     }
 }
@@ -502,7 +458,7 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
               const float* __restrict__ p, const float* __restrict__ q, double* __restrict__ partials,
               DevScalars* S, PcgArgs a) {
     if (!S->cg_active) return;
-    const float al = (float)S->alpha;
+    const float al = S->alpha;
     float acc[2] = {0.f, 0.f};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int plane = (int)chunks.div((unsigned)it);
@@ -512,7 +468,7 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
     double tot[2];
     if (grid_reduce<2>(acc, partials, &S->ticket[2], tot) && threadIdx.x == 0) {
         CgState st = cg_load(S);
-        cg_after_update(st, tot[0], tot[1], a.tol_cg, a.max_cg);
+        cg_after_update(st, (float)tot[0], (float)tot[1], a.tol_cg, a.max_cg);
         cg_store(S, st);
     }
 }
@@ -534,19 +490,19 @@ pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, long long
     // two partial-sum buffers: A for <p, Hp>, B for the update's sums (and the
     // start); a buffer is rewritten only after a barrier that follows every
     // CTA's read of it, so three barriers per iteration suffice
-    double* partA = partials;
-    double* partB = partials + 2 * (size_t)gridDim.x;
+    float2* partA = reinterpret_cast<float2*>(partials);
+    float2* partB = partA + 2 * (size_t)gridDim.x;
     CgState st{0, 0, 0, 0, 0, 0, 0, 0, 0};
     {   // r = -g, p = M^-1 r, x = 0, frame sums of p
         float rz = 0.f, rr = 0.f;
         for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x)
             dir_tile<D, VEC, 2, TPR>(g, pi, fs, cf, dT, p, r, grad, x, mean_s, sum_v, 0.f, t, sh, rz, rr);
         const float v2[2] = {rz, rr};
-        block_partials<2>(v2, partB);
+        cta_partials<2>(v2, partB, blockIdx.x);
         grid.sync();
-        double tot[2];
-        grid_total<2>(partB, tot);
-        cg_after_init(st, tot[0], tot[1], a.max_cg);
+        dfloat tot[2];
+        cta_total<2>(partB, gridDim.x, tot);
+        cg_after_init(st, df_val(tot[0]), df_val(tot[1]), a.max_cg);
     }
     while (st.active) {
         float pq = 0.f;
@@ -556,16 +512,16 @@ pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, long long
         }
         {
             const float v1[1] = {pq};
-            block_partials<1>(v1, partA);
+            cta_partials<1>(v1, partA, blockIdx.x);
         }
         grid.sync();   // q and the <p, Hp> partials are complete
         {
-            double tot[1];
-            grid_total<1>(partA, tot);
-            cg_after_apply(st, tot[0]);
+            dfloat tot[1];
+            cta_total<1>(partA, gridDim.x, tot);
+            cg_after_apply(st, df_val(tot[0]));
         }
         if (!st.active) break;
-        const float al = (float)st.alpha;
+        const float al = st.alpha;
         float rz = 0.f, rr = 0.f;
         for (long long it = blockIdx.x; it < uitems; it += gridDim.x) {
             const int plane = (int)chunks.div((unsigned)it);
@@ -574,16 +530,16 @@ pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, long long
         }
         {
             const float v2[2] = {rz, rr};
-            block_partials<2>(v2, partB);
+            cta_partials<2>(v2, partB, blockIdx.x);
         }
         grid.sync();   // r and the update partials are complete
         {
-            double tot[2];
-            grid_total<2>(partB, tot);
-            cg_after_update(st, tot[0], tot[1], a.tol_cg, a.max_cg);
+            dfloat tot[2];
+            cta_total<2>(partB, gridDim.x, tot);
+            cg_after_update(st, df_val(tot[0]), df_val(tot[1]), a.tol_cg, a.max_cg);
         }
         if (!st.active) break;
-        const float be = (float)st.beta;
+        const float be = st.beta;
         float d0 = 0.f, d1 = 0.f;
         for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x)
             dir_tile<D, VEC, 1, TPR>(g, pi, fs, cf, dT, p, r, nullptr, nullptr, mean_s, sum_v, be, t, sh, d0, d1);

@@ -2,11 +2,13 @@
 
     python -m paper_2001_06613_gb300.opbench --op all --shape 256 256 --frames 200
 
-Each operation is timed through the C ABI on device-resident data and reported
-as achieved GB/s of its algorithmic bytes (every array it must read or write
+Each operation is timed through the C ABI on device-resident data (the call,
+including its host work) and reported as achieved GB/s of its algorithmic bytes (every array it must read or write
 counted once, per pixel-frame, fp32; see the table in each result) against
-the measured HBM copy bandwidth.  Inputs are larger than L2 at the default
-size, and L2 is flushed before every timed call.
+the measured HBM copy bandwidth; "kernel_us_per_launch" gives the device
+time of each kernel class from the library's own CUDA-event profiling.
+Inputs are larger than L2 at the default size, and L2 is flushed before every
+timed call.
 """
 from __future__ import annotations
 
@@ -69,6 +71,7 @@ def main(argv=None):
             fn()
         torch.cuda.synchronize()
         ts = []
+        S.stml_profile_enable(ctx.ptr, 1)   # CUDA events around every library launch
         for _ in range(args.iters):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -77,10 +80,15 @@ def main(argv=None):
             b.record()
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
+        kernels = {}
+        for r in S.stml_profile_report(ctx.ptr):
+            kernels[r["kernel"]] = round(1e3 * r["ms"] / max(1, r["launches"]), 3)
+        S.stml_profile_enable(ctx.ptr, 0)
         ms = float(np.median(ts))
         gbs = nbytes / (ms / 1e3) / 1e9
         print(json.dumps({"op": name, "shape": list(shape), "frames": n, "ms": ms, "GB/s": gbs,
-                          "frac_of_measured_hbm": gbs / peak, "bytes_per_pixel_frame": per_pf}), flush=True)
+                          "frac_of_measured_hbm": gbs / peak, "bytes_per_pixel_frame": per_pf,
+                          "kernel_us_per_launch": kernels}), flush=True)
 
     ops = [args.op] if args.op != "all" else ["hessvec", "eval", "objective", "predict_ls"]
     for op in ops:
