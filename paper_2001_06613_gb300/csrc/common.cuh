@@ -194,6 +194,81 @@ __device__ __forceinline__ float interp2_val(const float* __restrict__ T, const 
     return a0 + fy * (a1 - a0);
 }
 
+// Bilinear values (zero extension) at the cells (x + e, y), e < VEC, of one
+// row, displaced by (uy[e], ux[e]).  When every stencil of the warp lies
+// inside the image (the common case), the corners are read from one base
+// address per value with no per-corner tests; otherwise each value takes the
+// general path.  Both paths give identical results.  All lanes of the warp
+// must call it.
+template <int VEC>
+__device__ __forceinline__ void interp2_row(const float* __restrict__ T, const Geom& g, int x, int y,
+                                            const float (&uy)[VEC], const float (&ux)[VEC], float (&a)[VEC]) {
+    int ix[VEC], iy[VEC];
+    float fx[VEC], fy[VEC];
+    bool inside = true;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        const float ty = uy[e] * g.inv_h, tx = ux[e] * g.inv_h;
+        const float fly = floorf(ty), flx = floorf(tx);
+        fy[e] = ty - fly;
+        fx[e] = tx - flx;
+        iy[e] = y + (int)fly;
+        ix[e] = x + e + (int)flx;
+        inside = inside && fabsf(ty) < 1.0e7f && fabsf(tx) < 1.0e7f && (unsigned)ix[e] < (unsigned)(g.nx - 1) &&
+                 (unsigned)iy[e] < (unsigned)(g.ny - 1);
+    }
+    if (__all_sync(0xffffffffu, inside)) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const float* b = T + (iy[e] * g.nx + ix[e]);
+            const float t00 = __ldg(b), t01 = __ldg(b + 1), t10 = __ldg(b + g.nx), t11 = __ldg(b + g.nx + 1);
+            const float a0 = t00 + fx[e] * (t01 - t00);
+            const float a1 = t10 + fx[e] * (t11 - t10);
+            a[e] = a0 + fy[e] * (a1 - a0);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) a[e] = interp2_val(T, g, x + e, y, uy[e], ux[e]);
+    }
+}
+
+// interp2_row with the image gradient (d/dy, d/dx) at the same points, as
+// interp2 computes it.
+template <int VEC>
+__device__ __forceinline__ void interp2_row_grad(const float* __restrict__ T, const Geom& g, int x, int y,
+                                                 const float (&uy)[VEC], const float (&ux)[VEC], float (&a)[VEC],
+                                                 float (&gy)[VEC], float (&gx)[VEC]) {
+    int ix[VEC], iy[VEC];
+    float fx[VEC], fy[VEC];
+    bool inside = true;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        const float ty = uy[e] * g.inv_h, tx = ux[e] * g.inv_h;
+        const float fly = floorf(ty), flx = floorf(tx);
+        fy[e] = ty - fly;
+        fx[e] = tx - flx;
+        iy[e] = y + (int)fly;
+        ix[e] = x + e + (int)flx;
+        inside = inside && fabsf(ty) < 1.0e7f && fabsf(tx) < 1.0e7f && (unsigned)ix[e] < (unsigned)(g.nx - 1) &&
+                 (unsigned)iy[e] < (unsigned)(g.ny - 1);
+    }
+    if (__all_sync(0xffffffffu, inside)) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const float* b = T + (iy[e] * g.nx + ix[e]);
+            const float t00 = __ldg(b), t01 = __ldg(b + 1), t10 = __ldg(b + g.nx), t11 = __ldg(b + g.nx + 1);
+            const float a0 = t00 + fx[e] * (t01 - t00);
+            const float a1 = t10 + fx[e] * (t11 - t10);
+            a[e] = a0 + fy[e] * (a1 - a0);
+            gx[e] = g.inv_h * ((t01 - t00) + fy[e] * ((t11 - t10) - (t01 - t00)));
+            gy[e] = g.inv_h * (a1 - a0);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) interp2(T, g, x + e, y, uy[e], ux[e], a[e], gy[e], gx[e]);
+    }
+}
+
 // The eight corners c[dz][dy][dx] of a trilinear stencil, zero outside;
 // branch-free like corners2.
 __device__ __forceinline__ void corners3(const float* __restrict__ T, const Geom& g, int ix, int iy, int iz,

@@ -208,11 +208,11 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
             // addresses; invalid lanes sample pixel 0 with a zero field)
             const float* Tk = T + (size_t)fr * N;
             float a[VEC];
+            if constexpr (D == 2) {
+                interp2_row<VEC>(Tk, g, x, y, cur.c[0], cur.c[1], a);
+            } else {
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                if constexpr (D == 2)
-                    a[e] = interp2_val(Tk, g, x + e, y, cur.c[0][e], cur.c[1][e]);
-                else
+                for (int e = 0; e < VEC; ++e)
                     a[e] = interp3_val(Tk, g, x + e, y, z, cur.c[0][e], cur.c[1][e], cur.c[2][e]);
             }
             // the field of this warp's next frame (the last frame again at the end)
@@ -385,7 +385,22 @@ grad_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, lo
                 for (int e = 0; e < VEC; ++e) uc[c][e] = 0.f;
         }
         float r[VEC], dt[D][VEC];
-        if (valid) {
+        if constexpr (D == 2) {
+            // every lane takes part (invalid lanes sample pixel 0 with a zero field)
+            float a[VEC];
+            interp2_row_grad<VEC>(Tk, g, x, y, uc[0], uc[1], a, dt[0], dt[1]);
+            if (valid) {
+                float ab[VEC];
+                if constexpr (VEC == 4) {
+                    const float4 q = __ldg(reinterpret_cast<const float4*>(abar + p));
+                    ab[0] = q.x; ab[1] = q.y; ab[2] = q.z; ab[3] = q.w;
+                } else {
+                    ab[0] = __ldg(abar + p);
+                }
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) r[e] = a[e] - ab[e];
+            }
+        } else if (valid) {
             float ab[VEC];
             if constexpr (VEC == 4) {
                 const float4 q = __ldg(reinterpret_cast<const float4*>(abar + p));
