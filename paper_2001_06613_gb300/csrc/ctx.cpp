@@ -48,7 +48,9 @@ struct stml_ctx {
     float *w_u = nullptr, *w_g = nullptr, *w_dT = nullptr, *w_x = nullptr, *w_r = nullptr,
           *w_p = nullptr, *w_q = nullptr, *w_ut = nullptr;
     float *w_abar = nullptr, *w_ubar = nullptr;    // per-pixel frame means of the last objective pass
-    float *w_m1 = nullptr, *w_m2 = nullptr;        // per-pixel frame sums of the PCG direction
+    float *w_m1 = nullptr, *w_m2 = nullptr;        // per-pixel frame sums of a Hessian-product field / of z
+    float *w_p2 = nullptr, *w_cz = nullptr;        // second PCG direction buffer, PCG z = M^-1 r
+    float *w_sp0 = nullptr, *w_sp1 = nullptr;      // frame sums of the PCG direction ((1 + d) N each)
     float *w_z = nullptr, *w_z2 = nullptr;     // predictor state z_{l,q,all}
     double* partials = nullptr;
     size_t partials_cap = 0;                   // in doubles
@@ -159,6 +161,7 @@ void free_buffers(stml_ctx* c) {
     dfree(c->w_u); dfree(c->w_g); dfree(c->w_dT); dfree(c->w_x); dfree(c->w_r);
     dfree(c->w_p); dfree(c->w_q); dfree(c->w_ut); dfree(c->w_abar); dfree(c->w_ubar); dfree(c->w_m1);
     dfree(c->w_m2); dfree(c->w_z); dfree(c->w_z2); dfree(c->partials);
+    dfree(c->w_p2); dfree(c->w_cz); dfree(c->w_sp0); dfree(c->w_sp1);
     dfree(c->d_frames); dfree(c->d_wnext); dfree(c->d_idx); dfree(c->d_lsf);
     dfree(c->d_kidx); dfree(c->d_taps); dfree(c->d_rho);
     c->loaded = c->built = false;
@@ -327,19 +330,21 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         }
         return gnorm <= p.g_abs * (1.0 + std::fabs(J0)) || it >= p.max_gn;
     };
-    // PCG steps (Hessian product, update, direction), `n` of them, queued.
+    // PCG vectors of this level: the direction sums live at [0, N) (mean of
+    // grad T . p) and [N, (1 + d) N) (sum of p) of w_sp0 / w_sp1
+    const PcgBufs pb{c->w_x, c->w_r, c->w_cz, c->w_q, {c->w_p, c->w_p2}, c->w_m1, c->w_m2,
+                     {c->w_sp0, c->w_sp1}, {c->w_sp0 + g.N, c->w_sp1 + g.N}};
+    // PCG iterations (Hessian product, update, direction), `n` of them, queued.
     auto launch_cg = [&](int n) -> stml_status {
         for (int i = 0; i < n; ++i) {
             pe = prof_begin(c, PC_HESS, level);
-            CK(c, launch_hess_apply(g, fs, cf, c->w_dT, c->w_p, c->w_m1, c->w_m2, c->w_q, c->partials,
-                                    c->partials_cap, &S->ticket[1], S->dots + 4, S, c->stream));
+            CK(c, launch_pcg_apply(g, fs, cf, c->w_dT, pb, c->partials, c->partials_cap, S, c->stream));
             prof_end(c, pe, pfK * 12.0 * g.d, pfK);
             pe = prof_begin(c, PC_PCG_UPDATE, level);
-            CK(c, launch_pcg_update(g, fs, cf, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->partials,
-                                    c->partials_cap, S, pa, c->stream));
+            CK(c, launch_pcg_update(g, fs, cf, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream));
             prof_end(c, pe, pfK * 28.0 * g.d, pfK);
             pe = prof_begin(c, PC_PCG_P, level);
-            CK(c, launch_pcg_direction(g, fs, cf, c->w_dT, c->w_r, c->w_p, c->w_m1, c->w_m2, S, c->stream));
+            CK(c, launch_pcg_direction(g, fs, cf, c->w_dT, pb, S, c->stream));
             prof_end(c, pe, pfK * 16.0 * g.d, pfK);
         }
         launched += n;
@@ -351,15 +356,13 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     auto start_cg = [&]() -> stml_status {
         if (coop) {
             pe = prof_begin(c, PC_PCG_COOP, level);
-            CK(c, launch_pcg_coop(g, fs, cf, c->w_g, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_q, c->w_m1, c->w_m2,
-                                  c->partials, c->partials_cap, S, pa, c->stream));
+            CK(c, launch_pcg_coop(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream));
             prof_end(c, pe, 0.0, pfK);
             launched = p.max_cg;
             return STML_OK;
         }
         pe = prof_begin(c, PC_PCG_INIT, level);
-        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, c->w_x, c->w_r, c->w_p, c->w_m1, c->w_m2, c->partials,
-                              c->partials_cap, S, pa, c->stream));
+        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream));
         prof_end(c, pe, pfK * 20.0 * g.d, pfK);
         launched = 0;
         return launch_cg(std::min(p.max_cg, std::max(2, predict_cg)));
@@ -380,7 +383,7 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         }
         s.cg_iters += c->Sh->cg_iter;
         predict_cg = c->Sh->cg_iter;
-        if (c->Sh->cg_flag == CG_BREAKDOWN && c->Sh->cg_iter == 0)   // preconditioned gradient step
+        if (c->Sh->cg_flag == CG_BREAKDOWN && c->Sh->cg_iter == 0)   // preconditioned gradient step p_0
             CK(c, cudaMemcpyAsync(c->w_x, c->w_p, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
 
         // --- Armijo back-tracking; the first trial also reduces <g, d> and |d|^2
@@ -735,12 +738,15 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
     pcap += 1024 * kMaxRed;
     c->partials_cap = pcap;
     bool ok = true;
-    float** fields[] = {&c->w_u, &c->w_g, &c->w_dT, &c->w_x, &c->w_r, &c->w_p, &c->w_q, &c->w_ut, &c->w_z, &c->w_z2};
+    float** fields[] = {&c->w_u, &c->w_g, &c->w_dT, &c->w_x, &c->w_r, &c->w_p, &c->w_q, &c->w_ut, &c->w_z, &c->w_z2,
+                        &c->w_p2, &c->w_cz};
     for (float** fp : fields) ok = ok && dalloc(fp, fieldN) == cudaSuccess;
     ok = ok && dalloc(&c->w_abar, (size_t)G.N) == cudaSuccess;
     ok = ok && dalloc(&c->w_ubar, (size_t)dim * G.N) == cudaSuccess;
     ok = ok && dalloc(&c->w_m1, (size_t)G.N) == cudaSuccess;
     ok = ok && dalloc(&c->w_m2, (size_t)dim * G.N) == cudaSuccess;
+    ok = ok && dalloc(&c->w_sp0, (size_t)(1 + dim) * G.N) == cudaSuccess;
+    ok = ok && dalloc(&c->w_sp1, (size_t)(1 + dim) * G.N) == cudaSuccess;
     ok = ok && dalloc(&c->partials, pcap) == cudaSuccess;
     ok = ok && dalloc(&c->d_frames, n_frames) == cudaSuccess;
     ok = ok && dalloc(&c->d_wnext, n_frames) == cudaSuccess;

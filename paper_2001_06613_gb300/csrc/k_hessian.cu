@@ -1,8 +1,8 @@
 // Gauss-Newton Hessian product for a given v (the stml_hessvec building block):
-// the per-pixel frame sums of v (dir_kernel, mode 0) followed by the stencil
-// stream (apply_kernel), both in k_gn.cu.  Inside the PCG loop the sums come
-// from the direction update instead (launch_pcg_direction), so only the
-// stencil stream runs there.
+// the per-pixel frame sums of v (tile_kernel, TILE_SUMS) followed by the
+// stencil stream (apply_kernel), both in k_gn.cu.  Inside the PCG loop the
+// sums come from the update pass (those of z) and the previous direction, so
+// only the stencil stream runs there (launch_pcg_apply).
 #include "kernels.h"
 
 namespace stml {

@@ -116,22 +116,40 @@ struct PcgArgs {
     float tol_cg;
     int max_cg;
 };
-// r = -g, p = M^-1 r, x = 0, rho = <r, M^-1 r>, |r|^2, and the frame sums of p.
+// Vectors of one PCG solve (all n d N floats unless noted).  The streaming
+// solve keeps its direction in p[0] and the direction's frame sums in
+// ms_z / sv_z.  The cooperative solve keeps z = M^-1 r in z and its sums in
+// ms_z / sv_z, and double-buffers the direction and its sums: iteration k
+// writes p[k & 1] from p[(k + 1) & 1]; p_0 = z_0 lands in p[0] either way.
+struct PcgBufs {
+    float* x;
+    float* r;
+    float* z;                      // M^-1 r (cooperative solve)
+    float* q;                      // H p
+    float* p[2];
+    float* ms_z;                   // frame sums: mean of grad T . w (N) ...
+    float* sv_z;                   // ... and sum of w (d N)
+    float* ms_p[2];                // frame sums of p (cooperative solve)
+    float* sv_p[2];
+};
+// r = -g, p = M^-1 r, x = 0, the frame sums of p; rho = <r, M^-1 r>, |r|^2.
 cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
-                            float* x, float* r, float* p, float* mean_s, float* sum_v, double* partials,
-                            size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s);
-// x += alpha p, r -= alpha q; rho, convergence test, beta.
-cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, float* x, float* r,
-                              const float* p, const float* q, double* partials, size_t partials_cap, DevScalars* S,
-                              PcgArgs a, cudaStream_t s);
+                            const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
+                            cudaStream_t s);
+// q = H p (from p and its frame sums); alpha = rho / <p, q>.
+cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
+                             double* partials, size_t partials_cap, DevScalars* S, cudaStream_t s);
+// x += alpha p, r -= alpha q; rho, the convergence test and beta.
+cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
+                              double* partials, size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s);
+// p = M^-1 r + beta p and the frame sums of the new p.
+cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
+                                 const PcgBufs& b, DevScalars* S, cudaStream_t s);
 // The whole PCG solve (start, iterations, exit) in one cooperative launch, for
 // small problems where launch latency dominates; the final CG state goes to S.
 bool pcg_coop_preferred(const Geom& g, int nK);
 cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
-                            float* x, float* r, float* p, float* q, float* mean_s, float* sum_v, double* partials,
-                            size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s);
-// p = M^-1 r + beta p, and the frame sums of the new p.
-cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const float* r,
-                                 float* p, float* mean_s, float* sum_v, DevScalars* S, cudaStream_t s);
+                            const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
+                            cudaStream_t s);
 
 }  // namespace stml
