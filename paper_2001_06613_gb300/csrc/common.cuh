@@ -28,6 +28,12 @@ struct DevScalars {
     double dots[kMaxRed];     // totals of the last dot-product kernel
     float rho, bnorm2, pq, alpha, beta, rnorm2;   // CG coefficients (device only)
     int cg_active, cg_iter, cg_flag, cg_pad;
+    // Armijo line search decided on the device (trial k has t = 2^-k)
+    double ls_gTd, ls_dnorm2;  // <g, d> and |d|^2 from trial 0
+    float ls_t;                // the accepted step
+    int ls_accepted;           // a trial met the Armijo test
+    int ls_nodescent;          // trial 0 found <g, d> >= 0
+    int ls_trials;             // trials that ran
     unsigned int err_flags;   // bit 0: a bounded device wait expired
     unsigned int err_pad;
     unsigned int ticket[8];   // arrival counters of the last-CTA reduction

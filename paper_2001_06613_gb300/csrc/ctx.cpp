@@ -352,17 +352,20 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     };
     // Start of a PCG solve for H d = -g plus its first chunk of steps (small
     // levels: the whole solve in one cooperative launch).
+    // With gate != nullptr the solve starts only if the device accepted a step.
     const bool coop = pcg_coop_preferred(g, nK);
-    auto start_cg = [&]() -> stml_status {
+    auto start_cg = [&](const int* gate = nullptr) -> stml_status {
         if (coop) {
             pe = prof_begin(c, PC_PCG_COOP, level);
-            CK(c, launch_pcg_coop(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream));
+            CK(c, launch_pcg_coop(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream,
+                                  gate));
             prof_end(c, pe, 0.0, pfK);
             launched = p.max_cg;
             return STML_OK;
         }
         pe = prof_begin(c, PC_PCG_INIT, level);
-        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream));
+        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream,
+                              gate));
         prof_end(c, pe, pfK * 20.0 * g.d, pfK);
         launched = 0;
         return launch_cg(std::min(p.max_cg, std::max(2, predict_cg)));
@@ -386,30 +389,44 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         if (c->Sh->cg_flag == CG_BREAKDOWN && c->Sh->cg_iter == 0)   // preconditioned gradient step p_0
             CK(c, cudaMemcpyAsync(c->w_x, c->w_p, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
 
-        // --- Armijo back-tracking; the first trial also reduces <g, d> and |d|^2
-        double t = 1.0, gTd = 0.0, dnorm2 = 0.0;
+        // --- Armijo back-tracking, decided on the device.  Trials t = 1 and
+        // t = 1/2 are queued together (the second returns at once if the first
+        // is accepted), then the gradient pass at the accepted point and the
+        // next PCG start, both gated on acceptance: one host wait per
+        // Gauss-Newton step unless both trials fail.
         bool accepted = false, descent = true;
-        for (int ls = 0; ls < p.max_ls; ++ls) {
-            s.ls_trials++;
+        int ls_next = 0;              // next trial to queue
+        auto queue_trial = [&](int k) -> stml_status {
+            const double t = std::ldexp(1.0, -k);
+            const LineSearchArgs la{S, k, J, p.armijo_c};
             pe = prof_begin(c, PC_TRIAL, level);
-            CK(c, launch_objective(L.img, g, fs, cf, u, c->w_x, (float)t, ls == 0 ? c->w_g : nullptr, c->w_abar,
-                                   c->w_ubar, c->partials, c->partials_cap, &S->ticket[0], S->trial, c->stream));
-            prof_end(c, pe, pfK * (4.0 + (ls == 0 ? 16.0 : 8.0) * g.d), pfK);
+            CK(c, launch_objective(L.img, g, fs, cf, u, c->w_x, (float)t, k == 0 ? c->w_g : nullptr, c->w_abar,
+                                   c->w_ubar, c->partials, c->partials_cap, &S->ticket[0], S->trial, c->stream, &la));
+            prof_end(c, pe, pfK * (4.0 + (k == 0 ? 16.0 : 8.0) * g.d), pfK);
+            return STML_OK;
+        };
+        // gradient pass at the accepted point (writes u + t d to ut, g, grad T)
+        // and the speculative start of the next solve
+        const bool next_solve = it + 1 < p.max_gn;
+        auto queue_accept = [&]() -> stml_status {
+            pe = prof_begin(c, PC_EVAL, level);
+            CK(c, launch_gradient(L.img, g, fs, cf, u, c->w_x, 1.0f, c->w_abar, c->w_ubar, c->w_g, c->w_dT, ut,
+                                  c->partials, c->partials_cap, &S->ticket[4], S->red, c->stream, S));
+            prof_end(c, pe, pfK * (4.0 + 20.0 * g.d), pfK);
+            if (next_solve) TRY(start_cg(&S->ls_accepted));
+            return STML_OK;
+        };
+        for (; ls_next < std::min(2, p.max_ls); ++ls_next) TRY(queue_trial(ls_next));
+        TRY(queue_accept());
+        TRY(read_scalars(c));
+        while (!c->Sh->ls_nodescent && !c->Sh->ls_accepted && ls_next < p.max_ls) {
+            TRY(queue_trial(ls_next++));
+            TRY(queue_accept());
             TRY(read_scalars(c));
-            if (ls == 0) {
-                gTd = c->Sh->trial[6];
-                dnorm2 = c->Sh->trial[7];
-                if (!(gTd < 0.0)) {
-                    descent = false;
-                    break;
-                }
-            }
-            if (c->Sh->trial[0] <= J + p.armijo_c * t * gTd) {
-                accepted = true;
-                break;
-            }
-            t *= 0.5;
         }
+        s.ls_trials += c->Sh->ls_trials;
+        descent = !c->Sh->ls_nodescent;
+        accepted = c->Sh->ls_accepted != 0;
         if (!descent) {
             s.status = STML_EBREAKDOWN;
             break;
@@ -418,28 +435,17 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
             s.status = STML_ELINESEARCH;
             break;
         }
-        // --- accepted: the gradient pass writes u + t d, g and grad T there,
-        // reusing the frame means of the accepted trial's objective pass
-        pe = prof_begin(c, PC_EVAL, level);
-        CK(c, launch_gradient(L.img, g, fs, cf, u, c->w_x, (float)t, c->w_abar, c->w_ubar, c->w_g, c->w_dT, ut,
-                              c->partials, c->partials_cap, &S->ticket[4], S->red, c->stream));
-        prof_end(c, pe, pfK * (4.0 + 20.0 * g.d), pfK);
         std::swap(u, ut);
-        step_norm = t * std::sqrt(dnorm2);
+        step_norm = (double)c->Sh->ls_t * std::sqrt(c->Sh->ls_dnorm2);
         J_old = J;
         J = c->Sh->trial[0];
         D = c->Sh->trial[1];
         Sv = c->Sh->trial[2];
         Pv = c->Sh->trial[3];
         ++it;
-        // the next solve is queued before |g| of the new iterate is known; it is
-        // dropped if the stopping tests fire
-        started = false;
-        if (it < p.max_gn) {
-            TRY(start_cg());
-            started = true;
-        }
-        TRY(read_scalars(c));
+        // the next solve was queued before |g| of the new iterate was known; it
+        // is dropped if the stopping tests fire
+        started = next_solve;
         gnorm2 = c->Sh->red[4];
         unorm2 = c->Sh->red[5];
         if (should_stop()) started = false;

@@ -152,7 +152,10 @@ template <int D, int VEC, bool TRIAL, bool GDOT>
 __global__ void __launch_bounds__(kThreads, obj_min_blocks(D, VEC))
 obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ u,
            const float* __restrict__ du, float t, const float* __restrict__ gdot, float* __restrict__ abar,
-           float* __restrict__ ubar, double* __restrict__ partials, unsigned int* ticket, double* out) {
+           float* __restrict__ ubar, double* __restrict__ partials, unsigned int* ticket, double* out,
+           LineSearchArgs ls) {
+    // a later Armijo trial has nothing to do once an earlier one decided
+    if (ls.S && ls.k > 0 && (ls.S->ls_accepted || ls.S->ls_nodescent)) return;
     constexpr int FG = kThreads / 32, SEG = 32 * VEC;
     __shared__ float sh_m[FG][SEG], sh_q[FG][SEG];
     __shared__ float sh_u[FG][D][SEG];
@@ -350,6 +353,20 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
         out[1] = Dv;
         out[2] = Sx + St;
         out[3] = Pv;
+        if (ls.S) {   // Armijo decision of trial k
+            DevScalars* L = ls.S;
+            if (ls.k == 0) {
+                L->ls_gTd = out[6];
+                L->ls_dnorm2 = out[7];
+                L->ls_accepted = 0;
+                L->ls_nodescent = !(out[6] < 0.0);
+            }
+            L->ls_trials = ls.k + 1;
+            if (!L->ls_nodescent && out[0] <= ls.J + ls.c * (double)t * L->ls_gTd) {
+                L->ls_accepted = 1;
+                L->ls_t = t;
+            }
+        }
     }
 }
 
@@ -361,7 +378,11 @@ __global__ void __launch_bounds__(kThreads)
 grad_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
             Coef cf, FView U, const float* __restrict__ abar, const float* __restrict__ ubar,
             float* __restrict__ grad, float* __restrict__ dTout, float* __restrict__ unew,
-            double* __restrict__ partials, unsigned int* ticket, double* out) {
+            double* __restrict__ partials, unsigned int* ticket, double* out, const DevScalars* gate) {
+    if (gate) {   // the accepted step of a line search decided on the device
+        if (!gate->ls_accepted) return;
+        U.t = gate->ls_t;
+    }
     const size_t N = (size_t)g.N;
     const int lane = threadIdx.x & 31;
     float g2 = 0.f, u2 = 0.f;
@@ -549,7 +570,7 @@ template <int D, int VEC, bool TRIAL, bool GDOT>
 static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
                           const FrameSet& fs, const Coef& cf, const float* u, const float* du, float t,
                           const float* gdot, float* abar, float* ubar, double* partials, unsigned int* ticket,
-                          double* out) {
+                          double* out, const LineSearchArgs& ls) {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(sh.runs, (unsigned)sh.splits, 1);
     lc.blockDim = dim3(kThreads, 1, 1);
@@ -562,23 +583,26 @@ static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const float* T, co
     lc.attrs = at;
     lc.numAttrs = sh.splits > 1 ? 1 : 0;
     return cudaLaunchKernelEx(&lc, obj_kernel<D, VEC, TRIAL, GDOT>, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar,
-                              partials, ticket, out);
+                              partials, ticket, out, ls);
 }
 
 template <int D, int VEC>
 static cudaError_t obj_mode(const ObjShape& sh, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
                             const FrameSet& fs, const Coef& cf, const float* u, const float* du, float t,
                             const float* gdot, float* abar, float* ubar, double* partials, unsigned int* ticket,
-                            double* out) {
-    if (!du) return obj_go<D, VEC, false, false>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out);
-    if (!gdot) return obj_go<D, VEC, true, false>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out);
-    return obj_go<D, VEC, true, true>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out);
+                            double* out, const LineSearchArgs& ls) {
+    if (!du) return obj_go<D, VEC, false, false>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out, ls);
+    if (!gdot) return obj_go<D, VEC, true, false>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out, ls);
+    return obj_go<D, VEC, true, true>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out, ls);
 }
 
 cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                              const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
-                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s) {
+                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s,
+                             const LineSearchArgs* lsp) {
     const PixIndex pi{FastDiv::make((unsigned)g.nx), FastDiv::make((unsigned)g.ny)};
+    const LineSearchArgs ls = lsp ? *lsp : LineSearchArgs{nullptr, 0, 0.0, 0.0};
+    if (ls.S && ls.k == 0 && !gdot) return cudaErrorInvalidValue;
     // pixels per lane: 4 (2 in 3-D) when rows and every array allow vector access
     int vec_max = g.d == 3 ? 2 : 4;
     for (const void* q : {(const void*)u, (const void*)du, (const void*)gdot})
@@ -587,7 +611,7 @@ cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, 
     if ((size_t)sh.runs * sh.splits * 8 > partials_cap) return cudaErrorInvalidValue;
     if (gdot && !du) return cudaErrorInvalidValue;
     cudaError_t e;
-#define STML_OBJ(D_, V_) e = obj_mode<D_, V_>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out)
+#define STML_OBJ(D_, V_) e = obj_mode<D_, V_>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out, ls)
     if (g.d == 2) {
         if (sh.vec == 4) STML_OBJ(2, 4); else if (sh.vec == 2) STML_OBJ(2, 2); else STML_OBJ(2, 1);
     } else {
@@ -602,7 +626,7 @@ cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, 
 cudaError_t launch_gradient(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                             const float* du, float t, const float* abar, const float* ubar, float* grad, float* dT,
                             float* unew, double* partials, size_t partials_cap, unsigned int* ticket, double* out,
-                            cudaStream_t s) {
+                            cudaStream_t s, const DevScalars* gate) {
     const PixIndex pi{FastDiv::make((unsigned)g.nx), FastDiv::make((unsigned)g.ny)};
     const bool v4 = v4ok(g, {u, du, abar, ubar, grad, dT, unew});
     const int vec = v4 ? 4 : 1;
@@ -613,11 +637,11 @@ cudaError_t launch_gradient(const float* T, const Geom& g, const FrameSet& fs, c
     const FastDiv chunks = FastDiv::make((unsigned)cpf);
     const FView U{u, du, t};
     if (g.d == 2) {
-        if (v4) grad_kernel<2, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out);
-        else grad_kernel<2, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out);
+        if (v4) grad_kernel<2, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
+        else grad_kernel<2, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
     } else {
-        if (v4) grad_kernel<3, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out);
-        else grad_kernel<3, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out);
+        if (v4) grad_kernel<3, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
+        else grad_kernel<3, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
     }
     count_launches(1);
     return cudaGetLastError();

@@ -464,9 +464,10 @@ __global__ void __launch_bounds__(kThreads)
 tile_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ dT, float* __restrict__ v,
             float* __restrict__ r, const float* __restrict__ grad, float* __restrict__ x,
             float* __restrict__ mean_s, float* __restrict__ sum_v, double* __restrict__ partials, DevScalars* S,
-            PcgArgs a) {
+            PcgArgs a, const int* gate) {
     static_assert(MODE != TILE_UPDATE, "the update runs as a grid-stride stream");
     if (MODE == TILE_DIR && !S->cg_active) return;
+    if (gate && !*gate) return;
     __shared__ float sh[(kThreads / TPR) * (1 + D) * TPR * VEC];
     const float beta = MODE == TILE_DIR ? S->beta : 0.f;
     float rz = 0.f, rr = 0.f;
@@ -569,7 +570,8 @@ template <int D, int VEC, int TPR>
 __global__ void __launch_bounds__(kThreads)
 pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, unsigned tiles, FrameSet fs, Coef cf,
                 const float* __restrict__ grad, const float* __restrict__ dT, PcgBufs b,
-                double* __restrict__ partials, DevScalars* S, PcgArgs a) {
+                double* __restrict__ partials, DevScalars* S, PcgArgs a, const int* gate) {
+    if (gate && !*gate) return;   // every CTA leaves before the first barrier
     cg::grid_group grid = cg::this_grid();
     __shared__ float sh[(kThreads / TPR) * (1 + D) * TPR * VEC];
     // two partial-sum buffers: A for <p, Hp>, B for the start and the
@@ -653,7 +655,7 @@ bool narrow_tiles(const Geom& g, bool v4) { return g.N < 4LL * 152 * (v4 ? 64 : 
 template <int MODE>
 cudaError_t tile_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, float* v, float* r,
                         const float* grad, float* x, float* mean_s, float* sum_v, double* partials, DevScalars* S,
-                        PcgArgs a, cudaStream_t s) {
+                        PcgArgs a, cudaStream_t s, const int* gate = nullptr) {
     const PixIndex pi = make_pix_index(g);
     const bool v4 = vec4_ok(g, {dT, v, r, grad, x});
     const bool narrow = narrow_tiles(g, v4);
@@ -661,7 +663,7 @@ cudaError_t tile_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const
     const unsigned blocks = (unsigned)((g.N + seg - 1) / seg);
 #define STML_TILE(D_, V_, T_)                                                                                      \
     tile_kernel<D_, V_, MODE, T_><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v,      \
-                                                              partials, S, a)
+                                                              partials, S, a, gate)
     if (g.d == 2) {
         if (v4) { if (narrow) STML_TILE(2, 4, 4); else STML_TILE(2, 4, 16); }
         else { if (narrow) STML_TILE(2, 1, 8); else STML_TILE(2, 1, 32); }
@@ -725,9 +727,9 @@ cudaError_t launch_hess_apply(const Geom& g, const FrameSet& fs, const Coef& cf,
 
 cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* gate) {
     if ((size_t)((g.N + 7) / 8) * 2 > partials_cap) return cudaErrorInvalidValue;
-    return tile_launch<TILE_INIT>(g, fs, cf, dT, b.p[0], b.r, grad, b.x, b.ms_z, b.sv_z, partials, S, a, s);
+    return tile_launch<TILE_INIT>(g, fs, cf, dT, b.p[0], b.r, grad, b.x, b.ms_z, b.sv_z, partials, S, a, s, gate);
 }
 
 cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
@@ -769,7 +771,7 @@ namespace {
 template <int D, int VEC, int TPR>
 cudaError_t coop_go(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
                     const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int* gate) {
     const void* kern = (const void*)pcg_coop_kernel<D, VEC, TPR>;
     int dev = 0, sms = 1, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -794,7 +796,8 @@ cudaError_t coop_go(const Geom& g, const FrameSet& fs, const Coef& cf, const flo
     Coef cc = cf;
     PcgBufs bb = b;
     PcgArgs aa = a;
-    void* args[] = {&gg, &pi, &chunks, &aitems, &tiles, &ff, &cc, (void*)&grad, (void*)&dT, &bb, &partials, &S, &aa};
+    void* args[] = {&gg, &pi, &chunks, &aitems, &tiles, &ff, &cc, (void*)&grad, (void*)&dT, &bb, &partials, &S, &aa,
+                    (void*)&gate};
     e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(kThreads), args, 0, s);
     count_launches(1);
     return e;
@@ -806,14 +809,14 @@ bool pcg_coop_preferred(const Geom& g, int nK) { return (long long)g.N * nK <= (
 
 cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* gate) {
     const bool v4 = vec4_ok(g, {grad, dT, b.x, b.r, b.z, b.q, b.p[0], b.p[1], b.ms_z, b.sv_z, b.ms_p[0], b.sv_p[0],
                                 b.ms_p[1], b.sv_p[1]});
     if (g.d == 2)
-        return v4 ? coop_go<2, 4, 4>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s)
-                  : coop_go<2, 1, 8>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s);
-    return v4 ? coop_go<3, 4, 4>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s)
-              : coop_go<3, 1, 8>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s);
+        return v4 ? coop_go<2, 4, 4>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate)
+                  : coop_go<2, 1, 8>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate);
+    return v4 ? coop_go<3, 4, 4>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate)
+              : coop_go<3, 1, 8>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate);
 }
 
 }  // namespace stml

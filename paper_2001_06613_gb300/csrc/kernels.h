@@ -71,15 +71,27 @@ cudaError_t launch_corr_coeff(const float* img, int n, long long N, double* rho_
 // Objective pass at u (or u + t du): J, D, S, P, |u|^2 to out[0..3], out[5]
 // (out[4] = 0), and the per-pixel frame means abar (N) and ubar (d N).
 // With gdot (requires du) the pass also reduces <gdot, du> and |du|^2 into out[6], out[7].
+// Armijo trial k (t = 2^-k) of a line search decided on the device: the
+// trial does nothing once an earlier one was accepted (or trial 0 found no
+// descent); its last CTA applies J(u + t d) <= J + c t <g, d> and records the
+// outcome in S (ls_*).  Trial 0 must carry gdot.
+struct LineSearchArgs {
+    DevScalars* S;
+    int k;
+    double J;
+    double c;
+};
 cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                              const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
-                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s);
+                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s,
+                             const LineSearchArgs* ls = nullptr);
 // Gradient pass at u (or u + t du) with abar, ubar of the same point: g and
 // grad T, optionally the point itself (unew); |g|^2 and |u|^2 to out[4], out[5].
+// With gate != nullptr it runs only if gate->ls_accepted, with t = gate->ls_t.
 cudaError_t launch_gradient(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                             const float* du, float t, const float* abar, const float* ubar, float* grad, float* dT,
                             float* unew, double* partials, size_t partials_cap, unsigned int* ticket, double* out,
-                            cudaStream_t s);
+                            cudaStream_t s, const DevScalars* gate = nullptr);
 // Doubles of partial sums the evaluation kernels need.
 size_t eval_partials(const Geom& g, int nK);
 
@@ -133,9 +145,11 @@ struct PcgBufs {
     float* sv_p[2];
 };
 // r = -g, p = M^-1 r, x = 0, the frame sums of p; rho = <r, M^-1 r>, |r|^2.
+// With gate != nullptr the start runs only if *gate is nonzero (otherwise
+// cg_active keeps its value, 0 after any finished solve).
 cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* gate = nullptr);
 // q = H p (from p and its frame sums); alpha = rho / <p, q>.
 cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
                              double* partials, size_t partials_cap, DevScalars* S, cudaStream_t s);
@@ -150,6 +164,6 @@ cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& 
 bool pcg_coop_preferred(const Geom& g, int nK);
 cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* gate = nullptr);
 
 }  // namespace stml
