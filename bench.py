@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--mode", default="stml", choices=["stml", "spml"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spml", action="store_true")
-    ap.add_argument("--cpu-sample-frames", type=int, default=9)
+    ap.add_argument("--cpu-sample-frames", type=int, default=25)
     return ap.parse_args()
 
 

@@ -258,6 +258,18 @@ void prof_end(stml_ctx* c, long i, double bytes, double pixel_frames) {
     acc[2] += pixel_frames;
 }
 
+// Removes `n` launches of a class that returned at once (a stopped PCG solve,
+// a line-search trial or step that was not needed) from the byte and launch
+// counts; their (short) event time stays in the class total.
+void prof_discount(stml_ctx* c, int cls, int level, double n, double bytes_each, double pf_each) {
+    if (!c->prof || (c->prof_hess_only && cls != PC_HESS) || n <= 0) return;
+    auto it = c->pacc.find(cls * 64 + level);
+    if (it == c->pacc.end()) return;
+    it->second[0] -= n;
+    it->second[1] -= n * bytes_each;
+    it->second[2] -= n * pf_each;
+}
+
 stml_status hessvec_launch(stml_ctx* c, int level, const Geom& g, const FrameSet& fs, const Coef& cf,
                            const float* dT, const float* v, float* Hv, DevScalars* pcg) {
     HessWork hw{c->w_m1, c->w_m2, c->partials, c->partials_cap};
@@ -352,6 +364,14 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     };
     // Start of a PCG solve for H d = -g plus its first chunk of steps (small
     // levels: the whole solve in one cooperative launch).
+    // Launches of a streaming solve that returned at once (after the solve
+    // stopped, or because its gated start did not run) leave the profile.
+    auto discount_cg = [&](int queued, int ran_apply, int ran_update, int ran_dir, bool init_ran) {
+        prof_discount(c, PC_HESS, level, queued - ran_apply, pfK * 12.0 * g.d, pfK);
+        prof_discount(c, PC_PCG_UPDATE, level, queued - ran_update, pfK * 28.0 * g.d, pfK);
+        prof_discount(c, PC_PCG_P, level, queued - ran_dir, pfK * 16.0 * g.d, pfK);
+        if (!init_ran) prof_discount(c, PC_PCG_INIT, level, 1, pfK * 20.0 * g.d, pfK);
+    };
     // With gate != nullptr the solve starts only if the device accepted a step.
     const bool coop = pcg_coop_preferred(g, nK);
     auto start_cg = [&](const int* gate = nullptr) -> stml_status {
@@ -386,6 +406,13 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         }
         s.cg_iters += c->Sh->cg_iter;
         predict_cg = c->Sh->cg_iter;
+        if (!coop) {   // launches of this solve that did work
+            const int n_it = c->Sh->cg_iter, fl = c->Sh->cg_flag;
+            const bool brk = fl == CG_BREAKDOWN;
+            const int ran_apply = fl == CG_ZERO ? 0 : n_it + (brk ? 1 : 0);
+            const int ran_dir = brk ? n_it : std::max(n_it - 1, 0);
+            discount_cg(launched, ran_apply, n_it, ran_dir, true);
+        }
         if (c->Sh->cg_flag == CG_BREAKDOWN && c->Sh->cg_iter == 0)   // preconditioned gradient step p_0
             CK(c, cudaMemcpyAsync(c->w_x, c->w_p, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
 
@@ -408,6 +435,11 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         // gradient pass at the accepted point (writes u + t d to ut, g, grad T)
         // and the speculative start of the next solve
         const bool next_solve = it + 1 < p.max_gn;
+        auto drop_accept = [&]() {   // a queued gated step and start that did not run
+            prof_discount(c, PC_EVAL, level, 1, pfK * (4.0 + 20.0 * g.d), pfK);
+            if (next_solve && !coop) discount_cg(launched, 0, 0, 0, false);
+            if (next_solve && coop) prof_discount(c, PC_PCG_COOP, level, 1, 0.0, pfK);
+        };
         auto queue_accept = [&]() -> stml_status {
             pe = prof_begin(c, PC_EVAL, level);
             CK(c, launch_gradient(L.img, g, fs, cf, u, c->w_x, 1.0f, c->w_abar, c->w_ubar, c->w_g, c->w_dT, ut,
@@ -420,10 +452,14 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         TRY(queue_accept());
         TRY(read_scalars(c));
         while (!c->Sh->ls_nodescent && !c->Sh->ls_accepted && ls_next < p.max_ls) {
+            drop_accept();
             TRY(queue_trial(ls_next++));
             TRY(queue_accept());
             TRY(read_scalars(c));
         }
+        if (!c->Sh->ls_accepted) drop_accept();
+        // queued trials that returned at once
+        prof_discount(c, PC_TRIAL, level, ls_next - c->Sh->ls_trials, pfK * (4.0 + 8.0 * g.d), pfK);
         s.ls_trials += c->Sh->ls_trials;
         descent = !c->Sh->ls_nodescent;
         accepted = c->Sh->ls_accepted != 0;
