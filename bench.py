@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spml", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=25)
+    ap.add_argument("--image-dtype", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage of the image pyramid and of the solver's grad T (arithmetic stays FP32)")
     return ap.parse_args()
 
 
@@ -237,7 +239,8 @@ def run_native(args):
     n, shape, L, Q, _ = WORKLOADS[args.workload]
     R, spec = make_sequence(args.workload, seed_offset=rank)
     mode = S.MODE_STML if args.mode == "stml" else S.MODE_SPML
-    prm = S.stml_default_params(n_levels=L, n_tlevels=Q)
+    prm = S.stml_default_params(n_levels=L, n_tlevels=Q,
+                                image_dtype={"f32": 0, "f16": 1, "bf16": 2}[args.image_dtype])
     stream = torch.cuda.current_stream(dev)
     ctx = S.Context(prm, stream.cuda_stream)
     R_dev = torch.from_numpy(R).to(dev)
@@ -368,7 +371,8 @@ def run_native(args):
                 "config": {"workload": f"{args.workload}: {n} frames {shape[0]}x{shape[1]} fp32, "
                                        f"{L} spatial x {Q} temporal levels, {args.mode.upper()}",
                            "n_frames": n, "shape": list(shape), "levels": L, "tlevels": Q,
-                           "mode": args.mode, "l2": "flushed (256 MB write) before every timed step",
+                           "mode": args.mode, "image_storage": args.image_dtype,
+                           "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": "frames/s",

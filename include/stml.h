@@ -58,6 +58,12 @@ typedef enum {
 
 typedef enum { STML_MODE_STML = 0, STML_MODE_SPML = 1 } stml_mode;
 
+/* Storage of the image pyramid and of the solver's image gradient grad T
+ * (mixed precision): every value is computed in FP32 and rounded to nearest
+ * even when stored; objective terms, PCG coefficients and the Armijo test keep
+ * their double-float / FP64 reductions.  Fields are always FP32. */
+typedef enum { STML_DTYPE_F32 = 0, STML_DTYPE_F16 = 1, STML_DTYPE_BF16 = 2 } stml_dtype;
+
 /* Solver parameters.  Objective terms (Sec. 2, eq. 1):
  *   J = hd/2 sum_k ||a_k - mean_j a_j||^2                       (distance, a_k = R_k o y_k)
  *     + alpha/2 hd sum_k sum_c sum_i ||d_i u_{k,c}||^2           (spatial diffusion S)
@@ -78,6 +84,7 @@ typedef struct {
     int max_cg;
     int max_ls;              /* Armijo trials */
     double armijo_c;
+    int image_dtype;         /* stml_dtype; fixed for a sequence when it is loaded */
 } stml_params;
 
 typedef struct {

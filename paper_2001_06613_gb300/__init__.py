@@ -8,4 +8,5 @@ from .binding import *  # noqa: F401,F403
 from .binding import Context, Params, Stats, StmlError, load, exported_symbols  # noqa: F401
 
 __all__ = [n for n in dir() if n.startswith("stml_")] + [
-    "Context", "Params", "Stats", "StmlError", "load", "exported_symbols", "MODE_STML", "MODE_SPML"]
+    "Context", "Params", "Stats", "StmlError", "load", "exported_symbols", "MODE_STML", "MODE_SPML",
+    "DTYPE_F32", "DTYPE_F16", "DTYPE_BF16"]

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libstml.so")
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EBREAKDOWN",
           -6: "ELINESEARCH", -7: "ETIMEOUT", -8: "ESTATE"}
 MODE_STML, MODE_SPML = 0, 1
+DTYPE_F32, DTYPE_F16, DTYPE_BF16 = 0, 1, 2     # stml_dtype: image / grad T storage
 
 
 class StmlError(RuntimeError):
@@ -33,7 +34,8 @@ class Params(C.Structure):
                 ("n_levels", C.c_int), ("n_tlevels", C.c_int),
                 ("tol_J", C.c_double), ("tol_Y", C.c_double), ("tol_G", C.c_double),
                 ("g_abs", C.c_double), ("max_gn", C.c_int), ("tol_cg", C.c_double),
-                ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double)]
+                ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double),
+                ("image_dtype", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

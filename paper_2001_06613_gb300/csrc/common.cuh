@@ -2,10 +2,61 @@
 // stencils and the deterministic two-stage FP64 reduction.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace stml {
+
+// Storage types of the image pyramid and of grad T (the arithmetic is FP32).
+enum StoreType { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+
+inline size_t store_bytes(int st) { return st == ST_F32 ? 4 : 2; }
+
+// One value of a stored array, as float (read-only path), and its store
+// (round to nearest even).
+__device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldf(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stf(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// Four consecutive stored values (address aligned to four elements), as float.
+__device__ __forceinline__ void ld4f(const float* p, float (&o)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+}
+__device__ __forceinline__ void ld4f(const __half* p, float (&o)[4]) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4f(const __nv_bfloat16* p, float (&o)[4]) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4f(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4f(__half* p, const float (&v)[4]) {
+    const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    uint2 q;
+    q.x = *reinterpret_cast<const unsigned*>(&a);
+    q.y = *reinterpret_cast<const unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = q;
+}
+__device__ __forceinline__ void st4f(__nv_bfloat16* p, const float (&v)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 q;
+    q.x = *reinterpret_cast<const unsigned*>(&a);
+    q.y = *reinterpret_cast<const unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = q;
+}
 
 constexpr int kThreads = 256;          // threads per CTA of the elementwise kernels
 constexpr int kMaxRed = 8;             // values one reduction carries
@@ -155,14 +206,15 @@ __device__ __forceinline__ int clampi(int v, int hi) { return min(max(v, 0), hi)
 // outside the grid.  Branch-free: every load reads a clamped (in-range)
 // address and outside corners are zeroed afterwards, so the loads of several
 // stencils can all be in flight together.
-__device__ __forceinline__ void corners2(const float* __restrict__ T, int nx, int ny, int ix, int iy, float& t00,
+template <typename TI>
+__device__ __forceinline__ void corners2(const TI* __restrict__ T, int nx, int ny, int ix, int iy, float& t00,
                                          float& t01, float& t10, float& t11) {
     const bool x0 = (unsigned)ix < (unsigned)nx, x1 = (unsigned)(ix + 1) < (unsigned)nx;
     const bool y0 = (unsigned)iy < (unsigned)ny, y1 = (unsigned)(iy + 1) < (unsigned)ny;
     const int cx0 = clampi(ix, nx - 1), cx1 = clampi(ix + 1, nx - 1);
-    const float* r0 = T + (long long)clampi(iy, ny - 1) * nx;
-    const float* r1 = T + (long long)clampi(iy + 1, ny - 1) * nx;
-    const float v00 = __ldg(r0 + cx0), v01 = __ldg(r0 + cx1), v10 = __ldg(r1 + cx0), v11 = __ldg(r1 + cx1);
+    const TI* r0 = T + (long long)clampi(iy, ny - 1) * nx;
+    const TI* r1 = T + (long long)clampi(iy + 1, ny - 1) * nx;
+    const float v00 = ldf(r0 + cx0), v01 = ldf(r0 + cx1), v10 = ldf(r1 + cx0), v11 = ldf(r1 + cx1);
     t00 = (x0 && y0) ? v00 : 0.f;
     t01 = (x1 && y0) ? v01 : 0.f;
     t10 = (x0 && y1) ? v10 : 0.f;
@@ -171,7 +223,8 @@ __device__ __forceinline__ void corners2(const float* __restrict__ T, int nx, in
 
 // Bilinear value and gradient (zero extension) of the level image T at the
 // cell centre (x, y) displaced by (uy, ux) physical units.
-__device__ __forceinline__ void interp2(const float* __restrict__ T, const Geom& g, int x, int y,
+template <typename TI>
+__device__ __forceinline__ void interp2(const TI* __restrict__ T, const Geom& g, int x, int y,
                                         float uy, float ux, float& val, float& gy, float& gx) {
     int iy, ix;
     float fy, fx;
@@ -187,7 +240,8 @@ __device__ __forceinline__ void interp2(const float* __restrict__ T, const Geom&
 }
 
 // Bilinear value only (zero extension).
-__device__ __forceinline__ float interp2_val(const float* __restrict__ T, const Geom& g, int x, int y, float uy,
+template <typename TI>
+__device__ __forceinline__ float interp2_val(const TI* __restrict__ T, const Geom& g, int x, int y, float uy,
                                              float ux) {
     int iy, ix;
     float fy, fx;
@@ -206,8 +260,8 @@ __device__ __forceinline__ float interp2_val(const float* __restrict__ T, const 
 // address per value with no per-corner tests; otherwise each value takes the
 // general path.  Both paths give identical results.  All lanes of the warp
 // must call it.
-template <int VEC>
-__device__ __forceinline__ void interp2_row(const float* __restrict__ T, const Geom& g, int x, int y,
+template <int VEC, typename TI>
+__device__ __forceinline__ void interp2_row(const TI* __restrict__ T, const Geom& g, int x, int y,
                                             const float (&uy)[VEC], const float (&ux)[VEC], float (&a)[VEC]) {
     int ix[VEC], iy[VEC];
     float fx[VEC], fy[VEC];
@@ -226,8 +280,8 @@ __device__ __forceinline__ void interp2_row(const float* __restrict__ T, const G
     if (__all_sync(0xffffffffu, inside)) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-            const float* b = T + (iy[e] * g.nx + ix[e]);
-            const float t00 = __ldg(b), t01 = __ldg(b + 1), t10 = __ldg(b + g.nx), t11 = __ldg(b + g.nx + 1);
+            const TI* b = T + (iy[e] * g.nx + ix[e]);
+            const float t00 = ldf(b), t01 = ldf(b + 1), t10 = ldf(b + g.nx), t11 = ldf(b + g.nx + 1);
             const float a0 = t00 + fx[e] * (t01 - t00);
             const float a1 = t10 + fx[e] * (t11 - t10);
             a[e] = a0 + fy[e] * (a1 - a0);
@@ -240,8 +294,8 @@ __device__ __forceinline__ void interp2_row(const float* __restrict__ T, const G
 
 // interp2_row with the image gradient (d/dy, d/dx) at the same points, as
 // interp2 computes it.
-template <int VEC>
-__device__ __forceinline__ void interp2_row_grad(const float* __restrict__ T, const Geom& g, int x, int y,
+template <int VEC, typename TI>
+__device__ __forceinline__ void interp2_row_grad(const TI* __restrict__ T, const Geom& g, int x, int y,
                                                  const float (&uy)[VEC], const float (&ux)[VEC], float (&a)[VEC],
                                                  float (&gy)[VEC], float (&gx)[VEC]) {
     int ix[VEC], iy[VEC];
@@ -261,8 +315,8 @@ __device__ __forceinline__ void interp2_row_grad(const float* __restrict__ T, co
     if (__all_sync(0xffffffffu, inside)) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-            const float* b = T + (iy[e] * g.nx + ix[e]);
-            const float t00 = __ldg(b), t01 = __ldg(b + 1), t10 = __ldg(b + g.nx), t11 = __ldg(b + g.nx + 1);
+            const TI* b = T + (iy[e] * g.nx + ix[e]);
+            const float t00 = ldf(b), t01 = ldf(b + 1), t10 = ldf(b + g.nx), t11 = ldf(b + g.nx + 1);
             const float a0 = t00 + fx[e] * (t01 - t00);
             const float a1 = t10 + fx[e] * (t11 - t10);
             a[e] = a0 + fy[e] * (a1 - a0);
@@ -277,7 +331,8 @@ __device__ __forceinline__ void interp2_row_grad(const float* __restrict__ T, co
 
 // The eight corners c[dz][dy][dx] of a trilinear stencil, zero outside;
 // branch-free like corners2.
-__device__ __forceinline__ void corners3(const float* __restrict__ T, const Geom& g, int ix, int iy, int iz,
+template <typename TI>
+__device__ __forceinline__ void corners3(const TI* __restrict__ T, const Geom& g, int ix, int iy, int iz,
                                          float (&c)[2][2][2]) {
     const long long sy = g.nx, sz = (long long)g.nx * g.ny;
     int cx[2], cy[2], cz[2];
@@ -295,17 +350,18 @@ __device__ __forceinline__ void corners3(const float* __restrict__ T, const Geom
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const float* r = T + cz[a] * sz + cy[q] * sy;
+            const TI* r = T + cz[a] * sz + cy[q] * sy;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const float v = __ldg(r + cx[e]);
+                const float v = ldf(r + cx[e]);
                 c[a][q][e] = (bz[a] && by[q] && bx[e]) ? v : 0.f;
             }
         }
 }
 
 // Trilinear value only (zero extension), displacement (uz, uy, ux).
-__device__ __forceinline__ float interp3_val(const float* __restrict__ T, const Geom& g, int x, int y, int z,
+template <typename TI>
+__device__ __forceinline__ float interp3_val(const TI* __restrict__ T, const Geom& g, int x, int y, int z,
                                              float uz, float uy, float ux) {
     int iz, iy, ix;
     float fz, fy, fx;
@@ -325,7 +381,8 @@ __device__ __forceinline__ float interp3_val(const float* __restrict__ T, const 
 }
 
 // Trilinear value and gradient (zero extension), displacement (uz, uy, ux).
-__device__ __forceinline__ void interp3(const float* __restrict__ T, const Geom& g, int x, int y, int z,
+template <typename TI>
+__device__ __forceinline__ void interp3(const TI* __restrict__ T, const Geom& g, int x, int y, int z,
                                         float uz, float uy, float ux, float& val, float& gz,
                                         float& gy, float& gx) {
     int iz, iy, ix;

@@ -26,7 +26,7 @@ thread_local std::string g_free_error;   // error text of the context-free calls
 struct LevelBuf {
     Geom g{};
     int shape3[3] = {1, 1, 1};
-    float* img = nullptr;    // n * N
+    void* img = nullptr;     // n * N values of the context's image storage type
     float* y = nullptr;      // n * d * N  (y_{l,all})
 };
 
@@ -39,6 +39,7 @@ struct stml_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int n = 0, d = 0;
+    int img_type = ST_F32;               // storage of the image pyramid and of the solver's grad T
     int shape[3] = {1, 1, 1};            // finest level (z, y, x)
     std::vector<LevelBuf> lv;
     std::vector<std::vector<int>> sets;  // K_0 .. K_T
@@ -133,6 +134,10 @@ bool valid_params(const stml_params* p, std::string& why) {
     }
     if (p->max_gn < 0 || p->max_cg < 0 || p->max_ls < 1) { why = "iteration limits out of range"; return false; }
     if (!(p->tol_cg > 0) || !(p->armijo_c > 0 && p->armijo_c < 1)) { why = "tol_cg > 0 and 0 < armijo_c < 1"; return false; }
+    if (p->image_dtype < STML_DTYPE_F32 || p->image_dtype > STML_DTYPE_BF16) {
+        why = "image_dtype must be STML_DTYPE_F32, _F16 or _BF16";
+        return false;
+    }
     return true;
 }
 
@@ -303,16 +308,28 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     s.status = STML_OK;
 
     const double pfK = (double)nK * (double)g.N;
+    // Algorithmic bytes per pixel-frame of each pass (every array read or
+    // written once; images and grad T in their storage type of bS bytes).
+    const double bS = (double)store_bytes(c->img_type), d = g.d;
+    const double B_obj = bS + 4.0 * d;                        // T, u
+    const double B_trial0 = bS + 16.0 * d, B_trial = bS + 8.0 * d;   // T, u, d (, g and d again)
+    const double B_grad0 = bS + (8.0 + bS) * d;               // T, u; g, grad T
+    const double B_grad = bS + (16.0 + bS) * d;               // T, u, d; g, grad T, u + t d
+    const double B_apply = (8.0 + bS) * d;                    // p, grad T; Hp
+    const double B_update = (24.0 + bS) * d;                  // x, p, r, q, grad T; x, r
+    const double B_dir = (12.0 + bS) * d;                     // r, grad T, p; p
+    const double B_init = (16.0 + bS) * d;                    // g, grad T; r, p, x
     // objective + gradient at u (start of the GIR)
     auto eval_full = [&]() -> stml_status {
         long pe = prof_begin(c, PC_TRIAL, level);
-        CK(c, launch_objective(L.img, g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
+        CK(c, launch_objective(Stored{L.img, c->img_type}, g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
                                c->partials_cap, &S->ticket[0], S->red, c->stream));
-        prof_end(c, pe, pfK * (4.0 + 4.0 * g.d), pfK);
+        prof_end(c, pe, pfK * B_obj, pfK);
         pe = prof_begin(c, PC_EVAL, level);
-        CK(c, launch_gradient(L.img, g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->w_g, c->w_dT, nullptr,
-                              c->partials, c->partials_cap, &S->ticket[4], S->red, c->stream));
-        prof_end(c, pe, pfK * (4.0 + 12.0 * g.d), pfK);
+        CK(c, launch_gradient(Stored{L.img, c->img_type}, g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->w_g,
+                              c->w_dT, c->img_type, nullptr, c->partials, c->partials_cap, &S->ticket[4], S->red,
+                              c->stream));
+        prof_end(c, pe, pfK * B_grad0, pfK);
         return read_scalars(c);
     };
 
@@ -344,20 +361,21 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     };
     // PCG vectors of this level: the direction sums live at [0, N) (mean of
     // grad T . p) and [N, (1 + d) N) (sum of p) of w_sp0 / w_sp1
+    const Stored dTs{c->w_dT, c->img_type};   // the solver's grad T, in the image storage type
     const PcgBufs pb{c->w_x, c->w_r, c->w_cz, c->w_q, {c->w_p, c->w_p2}, c->w_m1, c->w_m2,
                      {c->w_sp0, c->w_sp1}, {c->w_sp0 + g.N, c->w_sp1 + g.N}};
     // PCG iterations (Hessian product, update, direction), `n` of them, queued.
     auto launch_cg = [&](int n) -> stml_status {
         for (int i = 0; i < n; ++i) {
             pe = prof_begin(c, PC_HESS, level);
-            CK(c, launch_pcg_apply(g, fs, cf, c->w_dT, pb, c->partials, c->partials_cap, S, c->stream));
-            prof_end(c, pe, pfK * 12.0 * g.d, pfK);
+            CK(c, launch_pcg_apply(g, fs, cf, dTs, pb, c->partials, c->partials_cap, S, c->stream));
+            prof_end(c, pe, pfK * B_apply, pfK);
             pe = prof_begin(c, PC_PCG_UPDATE, level);
-            CK(c, launch_pcg_update(g, fs, cf, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream));
-            prof_end(c, pe, pfK * 28.0 * g.d, pfK);
+            CK(c, launch_pcg_update(g, fs, cf, dTs, pb, c->partials, c->partials_cap, S, pa, c->stream));
+            prof_end(c, pe, pfK * B_update, pfK);
             pe = prof_begin(c, PC_PCG_P, level);
-            CK(c, launch_pcg_direction(g, fs, cf, c->w_dT, pb, S, c->stream));
-            prof_end(c, pe, pfK * 16.0 * g.d, pfK);
+            CK(c, launch_pcg_direction(g, fs, cf, dTs, pb, S, c->stream));
+            prof_end(c, pe, pfK * B_dir, pfK);
         }
         launched += n;
         return STML_OK;
@@ -367,26 +385,26 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     // Launches of a streaming solve that returned at once (after the solve
     // stopped, or because its gated start did not run) leave the profile.
     auto discount_cg = [&](int queued, int ran_apply, int ran_update, int ran_dir, bool init_ran) {
-        prof_discount(c, PC_HESS, level, queued - ran_apply, pfK * 12.0 * g.d, pfK);
-        prof_discount(c, PC_PCG_UPDATE, level, queued - ran_update, pfK * 28.0 * g.d, pfK);
-        prof_discount(c, PC_PCG_P, level, queued - ran_dir, pfK * 16.0 * g.d, pfK);
-        if (!init_ran) prof_discount(c, PC_PCG_INIT, level, 1, pfK * 20.0 * g.d, pfK);
+        prof_discount(c, PC_HESS, level, queued - ran_apply, pfK * B_apply, pfK);
+        prof_discount(c, PC_PCG_UPDATE, level, queued - ran_update, pfK * B_update, pfK);
+        prof_discount(c, PC_PCG_P, level, queued - ran_dir, pfK * B_dir, pfK);
+        if (!init_ran) prof_discount(c, PC_PCG_INIT, level, 1, pfK * B_init, pfK);
     };
     // With gate != nullptr the solve starts only if the device accepted a step.
     const bool coop = pcg_coop_preferred(g, nK);
     auto start_cg = [&](const int* gate = nullptr) -> stml_status {
         if (coop) {
             pe = prof_begin(c, PC_PCG_COOP, level);
-            CK(c, launch_pcg_coop(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream,
+            CK(c, launch_pcg_coop(g, fs, cf, c->w_g, dTs, pb, c->partials, c->partials_cap, S, pa, c->stream,
                                   gate));
             prof_end(c, pe, 0.0, pfK);
             launched = p.max_cg;
             return STML_OK;
         }
         pe = prof_begin(c, PC_PCG_INIT, level);
-        CK(c, launch_pcg_init(g, fs, cf, c->w_g, c->w_dT, pb, c->partials, c->partials_cap, S, pa, c->stream,
+        CK(c, launch_pcg_init(g, fs, cf, c->w_g, dTs, pb, c->partials, c->partials_cap, S, pa, c->stream,
                               gate));
-        prof_end(c, pe, pfK * 20.0 * g.d, pfK);
+        prof_end(c, pe, pfK * B_init, pfK);
         launched = 0;
         return launch_cg(std::min(p.max_cg, std::max(2, predict_cg)));
     };
@@ -427,24 +445,25 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
             const double t = std::ldexp(1.0, -k);
             const LineSearchArgs la{S, k, J, p.armijo_c};
             pe = prof_begin(c, PC_TRIAL, level);
-            CK(c, launch_objective(L.img, g, fs, cf, u, c->w_x, (float)t, k == 0 ? c->w_g : nullptr, c->w_abar,
+            CK(c, launch_objective(Stored{L.img, c->img_type}, g, fs, cf, u, c->w_x, (float)t, k == 0 ? c->w_g : nullptr, c->w_abar,
                                    c->w_ubar, c->partials, c->partials_cap, &S->ticket[0], S->trial, c->stream, &la));
-            prof_end(c, pe, pfK * (4.0 + (k == 0 ? 16.0 : 8.0) * g.d), pfK);
+            prof_end(c, pe, pfK * (k == 0 ? B_trial0 : B_trial), pfK);
             return STML_OK;
         };
         // gradient pass at the accepted point (writes u + t d to ut, g, grad T)
         // and the speculative start of the next solve
         const bool next_solve = it + 1 < p.max_gn;
         auto drop_accept = [&]() {   // a queued gated step and start that did not run
-            prof_discount(c, PC_EVAL, level, 1, pfK * (4.0 + 20.0 * g.d), pfK);
+            prof_discount(c, PC_EVAL, level, 1, pfK * B_grad, pfK);
             if (next_solve && !coop) discount_cg(launched, 0, 0, 0, false);
             if (next_solve && coop) prof_discount(c, PC_PCG_COOP, level, 1, 0.0, pfK);
         };
         auto queue_accept = [&]() -> stml_status {
             pe = prof_begin(c, PC_EVAL, level);
-            CK(c, launch_gradient(L.img, g, fs, cf, u, c->w_x, 1.0f, c->w_abar, c->w_ubar, c->w_g, c->w_dT, ut,
-                                  c->partials, c->partials_cap, &S->ticket[4], S->red, c->stream, S));
-            prof_end(c, pe, pfK * (4.0 + 20.0 * g.d), pfK);
+            CK(c, launch_gradient(Stored{L.img, c->img_type}, g, fs, cf, u, c->w_x, 1.0f, c->w_abar, c->w_ubar,
+                                  c->w_g, c->w_dT, c->img_type, ut, c->partials, c->partials_cap, &S->ticket[4],
+                                  S->red, c->stream, S));
+            prof_end(c, pe, pfK * B_grad, pfK);
             if (next_solve) TRY(start_cg(&S->ls_accepted));
             return STML_OK;
         };
@@ -459,7 +478,7 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         }
         if (!c->Sh->ls_accepted) drop_accept();
         // queued trials that returned at once
-        prof_discount(c, PC_TRIAL, level, ls_next - c->Sh->ls_trials, pfK * (4.0 + 8.0 * g.d), pfK);
+        prof_discount(c, PC_TRIAL, level, ls_next - c->Sh->ls_trials, pfK * B_trial, pfK);
         s.ls_trials += c->Sh->ls_trials;
         descent = !c->Sh->ls_nodescent;
         accepted = c->Sh->ls_accepted != 0;
@@ -756,6 +775,7 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
     free_buffers(c);
     c->n = n_frames;
     c->d = dim;
+    c->img_type = c->p.image_dtype;
     std::memcpy(c->shape, sh3, sizeof(sh3));
     c->lv.resize(L);
     for (int l = 0; l < L; ++l) {
@@ -765,7 +785,7 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
         B.shape3[1] = sh3[1] / div;
         B.shape3[2] = sh3[2] / div;
         B.g = make_geom(B.shape3, dim, (float)div);
-        if (dalloc(&B.img, (size_t)n_frames * B.g.N) != cudaSuccess ||
+        if (cudaMalloc(&B.img, (size_t)n_frames * B.g.N * store_bytes(c->img_type)) != cudaSuccess ||
             dalloc(&B.y, (size_t)n_frames * dim * B.g.N) != cudaSuccess) {
             free_buffers(c);
             return fail(c, STML_ENOMEM, "device allocation of the level buffers failed");
@@ -802,8 +822,17 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
         return fail(c, STML_ENOMEM, "device allocation of the solver workspace failed");
     }
     CK(c, cudaMemsetAsync(c->S, 0, sizeof(DevScalars), c->stream));
-    CK(c, cudaMemcpyAsync(c->lv[L - 1].img, frames, imgN * sizeof(float),
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (c->img_type == ST_F32) {
+        CK(c, cudaMemcpyAsync(c->lv[L - 1].img, frames, imgN * sizeof(float),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    } else {   // 16-bit storage: round the float frames (host frames pass through the workspace)
+        const float* src = frames;
+        if (!on_device) {
+            CK(c, cudaMemcpyAsync(c->w_g, frames, imgN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            src = c->w_g;
+        }
+        CK(c, launch_to_store(src, c->lv[L - 1].img, c->img_type, (long long)imgN, c->stream));
+    }
     for (int l = 0; l < L; ++l)
         CK(c, cudaMemsetAsync(c->lv[l].y, 0, (size_t)n_frames * dim * c->lv[l].g.N * sizeof(float), c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -818,7 +847,7 @@ stml_status stml_build_pyramid(stml_ctx* c) {
     cudaSetDevice(c->device);
     const int L = (int)c->lv.size();
     for (int l = L - 1; l > 0; --l)
-        CK(c, launch_restrict(c->lv[l].img, c->lv[l - 1].img, c->n, c->lv[l - 1].g, c->stream));
+        CK(c, launch_restrict(c->lv[l].img, c->lv[l - 1].img, c->img_type, c->n, c->lv[l - 1].g, c->stream));
     c->sets = make_sets(c->n, c->p.n_tlevels);
     c->built = true;
     c->cur_level = -1;
@@ -848,8 +877,15 @@ stml_status stml_get_images(stml_ctx* c, int level, float* dst, int dst_on_devic
     TRY(check_level(c, level));
     cudaSetDevice(c->device);
     const size_t cnt = (size_t)c->n * c->lv[level].g.N;
-    CK(c, cudaMemcpyAsync(dst, c->lv[level].img, cnt * sizeof(float),
-                          dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (c->img_type == ST_F32) {
+        CK(c, cudaMemcpyAsync(dst, c->lv[level].img, cnt * sizeof(float),
+                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    } else if (dst_on_device) {
+        CK(c, launch_from_store(c->lv[level].img, c->img_type, dst, (long long)cnt, c->stream));
+    } else {
+        CK(c, launch_from_store(c->lv[level].img, c->img_type, c->w_g, (long long)cnt, c->stream));
+        CK(c, cudaMemcpyAsync(dst, c->w_g, cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     return STML_OK;
 }
@@ -948,15 +984,16 @@ stml_status stml_eval(stml_ctx* c, int level, const int* frames, int nK, const f
     const bool full = g || dT;
     const double pfK = (double)nK * L.g.N;
     long pe = prof_begin(c, PC_TRIAL, level);
-    CK(c, launch_objective(L.img, L.g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
+    CK(c, launch_objective(Stored{L.img, c->img_type}, L.g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
                            c->partials_cap, &c->S->ticket[0], c->S->red, c->stream));
-    prof_end(c, pe, pfK * (4.0 + 4.0 * L.g.d), pfK);
+    const double bS = (double)store_bytes(c->img_type);
+    prof_end(c, pe, pfK * (bS + 4.0 * L.g.d), pfK);
     if (full) {
         pe = prof_begin(c, PC_EVAL, level);
-        CK(c, launch_gradient(L.img, L.g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, g ? g : c->w_g,
-                              dT ? dT : c->w_dT, nullptr, c->partials, c->partials_cap, &c->S->ticket[4], c->S->red,
+        CK(c, launch_gradient(Stored{L.img, c->img_type}, L.g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar,
+                              g ? g : c->w_g, dT ? dT : c->w_dT, ST_F32, nullptr, c->partials, c->partials_cap, &c->S->ticket[4], c->S->red,
                               c->stream));
-        prof_end(c, pe, pfK * (4.0 + 20.0 * L.g.d), pfK);
+        prof_end(c, pe, pfK * (bS + 20.0 * L.g.d), pfK);
     }
     TRY(read_scalars(c));
     for (int i = 0; i < 6; ++i) out[i] = c->Sh->red[i];
@@ -1000,7 +1037,7 @@ stml_status stml_corr_coeff(stml_ctx* c, int level, double* rho) {
     if (!rho) return fail(c, STML_EINVAL, "rho is required");
     cudaSetDevice(c->device);
     if (c->n < 2) return STML_OK;
-    CK(c, launch_corr_coeff(c->lv[level].img, c->n, c->lv[level].g.N, c->d_rho, c->stream));
+    CK(c, launch_corr_coeff(c->lv[level].img, c->img_type, c->n, c->lv[level].g.N, c->d_rho, c->stream));
     CK(c, cudaMemcpyAsync(rho, c->d_rho, (size_t)(c->n - 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return STML_OK;
@@ -1031,7 +1068,7 @@ stml_status stml_restrict(const float* fine, float* coarse, int planes, int dim,
         sh3[i] /= 2;
     }
     const Geom gc = make_geom(sh3, dim, 2.f);
-    cudaError_t e = launch_restrict(fine, coarse, planes, gc, (cudaStream_t)cuda_stream);
+    cudaError_t e = launch_restrict(fine, coarse, ST_F32, planes, gc, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_restrict");
 }
 

@@ -65,8 +65,8 @@ __device__ __forceinline__ void pos_of(const PixIndex& pi, unsigned p, int& x, i
     z = (int)zz;
 }
 
-template <int D>
-__device__ __forceinline__ void interp(const float* __restrict__ Tk, const Geom& g, int x, int y, int z,
+template <int D, typename TI>
+__device__ __forceinline__ void interp(const TI* __restrict__ Tk, const Geom& g, int x, int y, int z,
                                        const float (&u)[D], float& a, float (&gr)[D]) {
     if constexpr (D == 2)
         interp2(Tk, g, x, y, u[0], u[1], a, gr[0], gr[1]);
@@ -148,9 +148,9 @@ struct FrameU {
 
 }  // namespace
 
-template <int D, int VEC, bool TRIAL, bool GDOT>
+template <int D, int VEC, bool TRIAL, bool GDOT, typename TI>
 __global__ void __launch_bounds__(kThreads, obj_min_blocks(D, VEC))
-obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ u,
+obj_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ u,
            const float* __restrict__ du, float t, const float* __restrict__ gdot, float* __restrict__ abar,
            float* __restrict__ ubar, double* __restrict__ partials, unsigned int* ticket, double* out,
            LineSearchArgs ls) {
@@ -209,7 +209,7 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
         for (int j = j0; j < fs.nK; j += TG) {
             // warped image of frame j; every gather is unconditional (clamped
             // addresses; invalid lanes sample pixel 0 with a zero field)
-            const float* Tk = T + (size_t)fr * N;
+            const TI* Tk = T + (size_t)fr * N;
             float a[VEC];
             if constexpr (D == 2) {
                 interp2_row<VEC>(Tk, g, x, y, cur.c[0], cur.c[1], a);
@@ -373,11 +373,11 @@ obj_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef c
 // ----------------------------------------------------------------- gradient
 // Grid-stride over items (frame j, chunk of kThreads * VEC pixels).  Reduced:
 // out[4] = |g|^2 (added to the objective pass's totals), out[5] = |u|^2.
-template <int D, int VEC>
+template <int D, int VEC, typename TI, typename TD>
 __global__ void __launch_bounds__(kThreads)
-grad_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
+grad_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
             Coef cf, FView U, const float* __restrict__ abar, const float* __restrict__ ubar,
-            float* __restrict__ grad, float* __restrict__ dTout, float* __restrict__ unew,
+            float* __restrict__ grad, TD* __restrict__ dTout, float* __restrict__ unew,
             double* __restrict__ partials, unsigned int* ticket, double* out, const DevScalars* gate) {
     if (gate) {   // the accepted step of a line search decided on the device
         if (!gate->ls_accepted) return;
@@ -393,7 +393,7 @@ grad_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, lo
         const bool valid = p < (unsigned)g.N;
         int x = 0, y = 0, z = 0;
         if (valid) pos_of(pi, p, x, y, z);
-        const float* Tk = T + (size_t)__ldg(fs.frames + j) * N;
+        const TI* Tk = T + (size_t)__ldg(fs.frames + j) * N;
         const float w_next = (cf.alphat_hd != 0.f && j + 1 < (unsigned)fs.nK) ? __ldg(fs.w_next + j) : 0.f;
         const float w_prev = (cf.alphat_hd != 0.f && j > 0) ? __ldg(fs.w_next + j - 1) : 0.f;
         float uc[D][VEC];
@@ -512,7 +512,10 @@ grad_kernel(const float* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, lo
                 u2 = fmaf(uc[c][e], uc[c][e], u2);
             }
             vstore<VEC>(grad, base, gv);
-            vstore<VEC>(dTout, base, dt[c]);
+            if constexpr (VEC == 4)
+                st4f(dTout + base, dt[c]);
+            else
+                stf(dTout + base, dt[c][0]);
             if (unew) vstore<VEC>(unew, base, uc[c]);
         }
     }
@@ -566,8 +569,8 @@ size_t eval_partials(const Geom& g, int nK) {
     return obj > (size_t)kGridStride * 2 ? obj : (size_t)kGridStride * 2;
 }
 
-template <int D, int VEC, bool TRIAL, bool GDOT>
-static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
+template <int D, int VEC, bool TRIAL, bool GDOT, typename TI>
+static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const TI* T, const Geom& g, const PixIndex& pi,
                           const FrameSet& fs, const Coef& cf, const float* u, const float* du, float t,
                           const float* gdot, float* abar, float* ubar, double* partials, unsigned int* ticket,
                           double* out, const LineSearchArgs& ls) {
@@ -582,12 +585,12 @@ static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const float* T, co
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = sh.splits > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&lc, obj_kernel<D, VEC, TRIAL, GDOT>, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar,
+    return cudaLaunchKernelEx(&lc, obj_kernel<D, VEC, TRIAL, GDOT, TI>, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar,
                               partials, ticket, out, ls);
 }
 
-template <int D, int VEC>
-static cudaError_t obj_mode(const ObjShape& sh, cudaStream_t s, const float* T, const Geom& g, const PixIndex& pi,
+template <int D, int VEC, typename TI>
+static cudaError_t obj_mode(const ObjShape& sh, cudaStream_t s, const TI* T, const Geom& g, const PixIndex& pi,
                             const FrameSet& fs, const Coef& cf, const float* u, const float* du, float t,
                             const float* gdot, float* abar, float* ubar, double* partials, unsigned int* ticket,
                             double* out, const LineSearchArgs& ls) {
@@ -596,7 +599,7 @@ static cudaError_t obj_mode(const ObjShape& sh, cudaStream_t s, const float* T, 
     return obj_go<D, VEC, true, true>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out, ls);
 }
 
-cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
+cudaError_t launch_objective(const Stored& T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                              const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
                              size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s,
                              const LineSearchArgs* lsp) {
@@ -610,23 +613,30 @@ cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, 
     const ObjShape sh = obj_shape(g, fs.nK, vec_max);
     if ((size_t)sh.runs * sh.splits * 8 > partials_cap) return cudaErrorInvalidValue;
     if (gdot && !du) return cudaErrorInvalidValue;
-    cudaError_t e;
-#define STML_OBJ(D_, V_) e = obj_mode<D_, V_>(sh, s, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out, ls)
-    if (g.d == 2) {
-        if (sh.vec == 4) STML_OBJ(2, 4); else if (sh.vec == 2) STML_OBJ(2, 2); else STML_OBJ(2, 1);
-    } else {
-        if (sh.vec == 2) STML_OBJ(3, 2); else STML_OBJ(3, 1);
-    }
+    cudaError_t e = with_store_type(T.type, [&](auto tag) {
+        using TI = decltype(tag);
+        const TI* Ti = static_cast<const TI*>(T.p);
+        cudaError_t r;
+#define STML_OBJ(D_, V_) r = obj_mode<D_, V_>(sh, s, Ti, g, pi, fs, cf, u, du, t, gdot, abar, ubar, partials, ticket, out, ls)
+        if (g.d == 2) {
+            if (sh.vec == 4) STML_OBJ(2, 4); else if (sh.vec == 2) STML_OBJ(2, 2); else STML_OBJ(2, 1);
+        } else {
+            if (sh.vec == 2) STML_OBJ(3, 2); else STML_OBJ(3, 1);
+        }
 #undef STML_OBJ
+        return r;
+    });
     count_launches(1);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-cudaError_t launch_gradient(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
-                            const float* du, float t, const float* abar, const float* ubar, float* grad, float* dT,
-                            float* unew, double* partials, size_t partials_cap, unsigned int* ticket, double* out,
-                            cudaStream_t s, const DevScalars* gate) {
+cudaError_t launch_gradient(const Stored& T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
+                            const float* du, float t, const float* abar, const float* ubar, float* grad, void* dT,
+                            int dT_type, float* unew, double* partials, size_t partials_cap, unsigned int* ticket,
+                            double* out, cudaStream_t s, const DevScalars* gate) {
+    // grad T is stored as float or in the image's own 16-bit type
+    if (dT_type != ST_F32 && dT_type != T.type) return cudaErrorInvalidValue;
     const PixIndex pi{FastDiv::make((unsigned)g.nx), FastDiv::make((unsigned)g.ny)};
     const bool v4 = v4ok(g, {u, du, abar, ubar, grad, dT, unew});
     const int vec = v4 ? 4 : 1;
@@ -636,15 +646,27 @@ cudaError_t launch_gradient(const float* T, const Geom& g, const FrameSet& fs, c
     if ((size_t)blocks * 2 > partials_cap) return cudaErrorInvalidValue;
     const FastDiv chunks = FastDiv::make((unsigned)cpf);
     const FView U{u, du, t};
-    if (g.d == 2) {
-        if (v4) grad_kernel<2, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
-        else grad_kernel<2, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
-    } else {
-        if (v4) grad_kernel<3, 4><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
-        else grad_kernel<3, 1><<<blocks, kThreads, 0, s>>>(T, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, dT, unew, partials, ticket, out, gate);
-    }
+    auto go = [&](auto ti_tag, auto td_tag) {
+        using TI = decltype(ti_tag);
+        using TD = decltype(td_tag);
+        const TI* Ti = static_cast<const TI*>(T.p);
+        TD* Td = static_cast<TD*>(dT);
+#define STML_GRAD(D_, V_) \
+    grad_kernel<D_, V_, TI, TD><<<blocks, kThreads, 0, s>>>(Ti, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, Td, unew, partials, ticket, out, gate)
+        if (g.d == 2) {
+            if (v4) STML_GRAD(2, 4); else STML_GRAD(2, 1);
+        } else {
+            if (v4) STML_GRAD(3, 4); else STML_GRAD(3, 1);
+        }
+#undef STML_GRAD
+        return cudaGetLastError();
+    };
+    cudaError_t e = with_store_type(T.type, [&](auto ti_tag) {
+        using TI = decltype(ti_tag);
+        return dT_type == ST_F32 ? go(ti_tag, float{}) : go(ti_tag, TI{});
+    });
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace stml

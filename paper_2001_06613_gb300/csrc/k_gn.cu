@@ -27,6 +27,8 @@
 // where it is needed (`jacobi_inv`, one rounding sequence everywhere).
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace cg = cooperative_groups;
@@ -54,6 +56,8 @@ struct V<4> {
     }
     __device__ __forceinline__ void store(float* p) const { st4(p, make_float4(a[0], a[1], a[2], a[3])); }
     __device__ __forceinline__ void zero() { a[0] = a[1] = a[2] = a[3] = 0.f; }
+    template <typename T>
+    __device__ __forceinline__ void load_t(const T* p) { ld4f(p, a); }   // stored type -> float
 };
 template <>
 struct V<1> {
@@ -62,6 +66,8 @@ struct V<1> {
     __device__ __forceinline__ void load_rw(const float* p) { a[0] = *p; }
     __device__ __forceinline__ void store(float* p) const { *p = a[0]; }
     __device__ __forceinline__ void zero() { a[0] = 0.f; }
+    template <typename T>
+    __device__ __forceinline__ void load_t(const T* p) { a[0] = ldf(p); }
 };
 
 // Position of pixel p: x, y, z via multiply-high division.
@@ -102,9 +108,9 @@ enum TileMode { TILE_SUMS = 0, TILE_DIR = 1, TILE_INIT = 2, TILE_UPDATE = 3 };
 //                rz += <r, z>, rr += |r|^2.
 // The frame groups are combined in group order.  Every thread of the CTA
 // must call it (it synchronises).
-template <int D, int VEC, int MODE, int TPR>
+template <int D, int VEC, int MODE, int TPR, typename TD>
 __device__ __forceinline__ void tile_pass(const Geom& g, const PixIndex& pi, const FrameSet& fs, const Coef& cf,
-                                          const float* __restrict__ dT, float* __restrict__ v,
+                                          const TD* __restrict__ dT, float* __restrict__ v,
                                           float* __restrict__ r, const float* __restrict__ grad,
                                           float* __restrict__ x, const float* __restrict__ p,
                                           const float* __restrict__ q, float al, float beta,
@@ -139,7 +145,7 @@ __device__ __forceinline__ void tile_pass(const Geom& g, const PixIndex& pi, con
             for (int c = 0; c < D; ++c) {
                 const size_t e0 = ((size_t)j * D + c) * N + px;
                 V<VEC> dt, wv;
-                dt.load(dT + e0);
+                dt.load_t(dT + e0);
                 if constexpr (MODE == TILE_SUMS) {
                     wv.load(v + e0);
                 } else if constexpr (MODE == TILE_DIR) {
@@ -232,9 +238,9 @@ struct DirSrc {
 
 // Hessian product on one item: frame j, pixels [ch * kThreads * VEC, +kThreads * VEC).
 // Every thread of the warp must call it (warp shuffles).  acc += <w, Hw>.
-template <int D, int VEC, bool FUSED>
+template <int D, int VEC, bool FUSED, typename TD>
 __device__ __forceinline__ void apply_item(const Geom& g, const PixIndex& pi, const FrameSet& fs, const Coef& cf,
-                                           const float* __restrict__ dT, const DirSrc& src,
+                                           const TD* __restrict__ dT, const DirSrc& src,
                                            float* __restrict__ Hv, int j, unsigned ch, float& acc) {
     const size_t N = (size_t)g.N;
     const int lane = threadIdx.x & 31;
@@ -268,7 +274,7 @@ __device__ __forceinline__ void apply_item(const Geom& g, const PixIndex& pi, co
         const size_t e0 = ((size_t)j * D + c) * N + p;
         if (valid) {
             ldw(e0, vc[c]);
-            dt[c].load(dT + e0);
+            dt[c].load_t(dT + e0);
             if (FUSED) vc[c].store(src.pout + e0);
         } else {
             vc[c].zero();
@@ -459,9 +465,9 @@ __device__ __forceinline__ void cg_store(DevScalars* S, const CgState& s) {
 // ----------------------------------------------------------------- stream kernels
 // Pixel-tiled pass (frame sums, PCG start, PCG direction); the PCG start ends
 // with the CG decisions of its step in the last CTA.
-template <int D, int VEC, int MODE, int TPR>
+template <int D, int VEC, int MODE, int TPR, typename TD>
 __global__ void __launch_bounds__(kThreads)
-tile_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__ dT, float* __restrict__ v,
+tile_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const TD* __restrict__ dT, float* __restrict__ v,
             float* __restrict__ r, const float* __restrict__ grad, float* __restrict__ x,
             float* __restrict__ mean_s, float* __restrict__ sum_v, double* __restrict__ partials, DevScalars* S,
             PcgArgs a, const int* gate) {
@@ -471,7 +477,7 @@ tile_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__
     __shared__ float sh[(kThreads / TPR) * (1 + D) * TPR * VEC];
     const float beta = MODE == TILE_DIR ? S->beta : 0.f;
     float rz = 0.f, rr = 0.f;
-    tile_pass<D, VEC, MODE, TPR>(g, pi, fs, cf, dT, v, r, grad, x, nullptr, nullptr, 0.f, beta, mean_s, sum_v,
+    tile_pass<D, VEC, MODE, TPR, TD>(g, pi, fs, cf, dT, v, r, grad, x, nullptr, nullptr, 0.f, beta, mean_s, sum_v,
                                  blockIdx.x, sh, rz, rr);
     if constexpr (MODE == TILE_INIT) {
         float acc[2] = {rz, rr};
@@ -486,9 +492,9 @@ tile_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const float* __restrict__
 
 // PCG update on one item: plane (frame j, component c), one chunk of pixels.
 // x += alpha p, r -= alpha q; rz += <r, M^-1 r>, rr += |r|^2.
-template <int D, int VEC>
+template <int D, int VEC, typename TD>
 __device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, const FrameSet& fs, const Coef& cf,
-                                            const float* __restrict__ dT, float* __restrict__ x,
+                                            const TD* __restrict__ dT, float* __restrict__ x,
                                             float* __restrict__ r, const float* __restrict__ p,
                                             const float* __restrict__ q, int plane, unsigned ch, float al,
                                             float& rz, float& rr) {
@@ -499,7 +505,7 @@ __device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, c
     pix_pos(pi, px, xx, yy, zz);
     const size_t e0 = (size_t)plane * g.N + px;
     V<VEC> dt, pv, qv, xv, rv;
-    dt.load(dT + e0);
+    dt.load_t(dT + e0);
     pv.load(p + e0);
     qv.load(q + e0);
     xv.load_rw(x + e0);
@@ -516,10 +522,10 @@ __device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, c
     rv.store(r + e0);
 }
 
-template <int D, int VEC>
+template <int D, int VEC, typename TD>
 __global__ void __launch_bounds__(kThreads)
 update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
-              const float* __restrict__ dT, float* __restrict__ x, float* __restrict__ r,
+              const TD* __restrict__ dT, float* __restrict__ x, float* __restrict__ r,
               const float* __restrict__ p, const float* __restrict__ q, double* __restrict__ partials,
               DevScalars* S, PcgArgs a) {
     if (!S->cg_active) return;
@@ -527,7 +533,7 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
     float acc[2] = {0.f, 0.f};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int plane = (int)chunks.div((unsigned)it);
-        update_item<D, VEC>(g, pi, fs, cf, dT, x, r, p, q, plane, (unsigned)it - (unsigned)plane * chunks.d, al,
+        update_item<D, VEC, TD>(g, pi, fs, cf, dT, x, r, p, q, plane, (unsigned)it - (unsigned)plane * chunks.d, al,
                             acc[0], acc[1]);
     }
     double tot[2];
@@ -542,17 +548,17 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
 // pcg != nullptr the launch is a PCG step: it does nothing once cg_active is
 // 0, FUSED forms the direction on the fly with beta from the device, and the
 // last CTA sets alpha = rho / <p, Hp> (or flags a breakdown).
-template <int D, int VEC, bool FUSED>
+template <int D, int VEC, bool FUSED, typename TD>
 __global__ void __launch_bounds__(kThreads)
 apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
-             const float* __restrict__ dT, DirSrc src, float* __restrict__ Hv, double* __restrict__ partials,
+             const TD* __restrict__ dT, DirSrc src, float* __restrict__ Hv, double* __restrict__ partials,
              unsigned int* ticket, double* out, DevScalars* pcg) {
     if (pcg && !pcg->cg_active) return;
     if (FUSED) src.beta = src.pold ? pcg->beta : 0.f;
     float acc[1] = {0.f};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int j = (int)chunks.div((unsigned)it);
-        apply_item<D, VEC, FUSED>(g, pi, fs, cf, dT, src, Hv, j, (unsigned)it - (unsigned)j * chunks.d, acc[0]);
+        apply_item<D, VEC, FUSED, TD>(g, pi, fs, cf, dT, src, Hv, j, (unsigned)it - (unsigned)j * chunks.d, acc[0]);
     }
     if (grid_reduce<1>(acc, partials, ticket, out) && threadIdx.x == 0 && pcg) {
         CgState st = cg_load(pcg);
@@ -566,10 +572,10 @@ apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, 
 // iteration the fused direction + Hessian product and the update, separated
 // by two grid-wide barriers.  Every CTA evaluates the same CG decisions from
 // the same fixed-order totals, so all CTAs leave the loop together.
-template <int D, int VEC, int TPR>
+template <int D, int VEC, int TPR, typename TD>
 __global__ void __launch_bounds__(kThreads)
 pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, unsigned tiles, FrameSet fs, Coef cf,
-                const float* __restrict__ grad, const float* __restrict__ dT, PcgBufs b,
+                const float* __restrict__ grad, const TD* __restrict__ dT, PcgBufs b,
                 double* __restrict__ partials, DevScalars* S, PcgArgs a, const int* gate) {
     if (gate && !*gate) return;   // every CTA leaves before the first barrier
     cg::grid_group grid = cg::this_grid();
@@ -583,7 +589,7 @@ pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, unsigned 
     {   // r = -g, z = M^-1 r, x = 0, frame sums of z
         float rz = 0.f, rr = 0.f;
         for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x)
-            tile_pass<D, VEC, TILE_INIT, TPR>(g, pi, fs, cf, dT, b.z, b.r, grad, b.x, nullptr, nullptr, 0.f, 0.f,
+            tile_pass<D, VEC, TILE_INIT, TPR, TD>(g, pi, fs, cf, dT, b.z, b.r, grad, b.x, nullptr, nullptr, 0.f, 0.f,
                                               b.ms_z, b.sv_z, t, sh, rz, rr);
         const float v2[2] = {rz, rr};
         cta_partials<2>(v2, partB, blockIdx.x);
@@ -599,7 +605,7 @@ pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, unsigned 
         float pq = 0.f;
         for (long long it = blockIdx.x; it < aitems; it += gridDim.x) {
             const int j = (int)chunks.div((unsigned)it);
-            apply_item<D, VEC, true>(g, pi, fs, cf, dT, src, b.q, j, (unsigned)it - (unsigned)j * chunks.d, pq);
+            apply_item<D, VEC, true, TD>(g, pi, fs, cf, dT, src, b.q, j, (unsigned)it - (unsigned)j * chunks.d, pq);
         }
         {
             const float v1[1] = {pq};
@@ -614,7 +620,7 @@ pcg_coop_kernel(Geom g, PixIndex pi, FastDiv chunks, long long aitems, unsigned 
         if (!st.active) break;
         float rz = 0.f, rr = 0.f;
         for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x)
-            tile_pass<D, VEC, TILE_UPDATE, TPR>(g, pi, fs, cf, dT, b.z, b.r, nullptr, b.x, b.p[cur], b.q, st.alpha,
+            tile_pass<D, VEC, TILE_UPDATE, TPR, TD>(g, pi, fs, cf, dT, b.z, b.r, nullptr, b.x, b.p[cur], b.q, st.alpha,
                                                 0.f, b.ms_z, b.sv_z, t, sh, rz, rr);
         {
             const float v2[2] = {rz, rr};
@@ -653,35 +659,41 @@ bool vec4_ok(const Geom& g, std::initializer_list<const void*> ptrs) {
 bool narrow_tiles(const Geom& g, bool v4) { return g.N < 4LL * 152 * (v4 ? 64 : 32); }
 
 template <int MODE>
-cudaError_t tile_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, float* v, float* r,
+cudaError_t tile_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, float* v, float* r,
                         const float* grad, float* x, float* mean_s, float* sum_v, double* partials, DevScalars* S,
                         PcgArgs a, cudaStream_t s, const int* gate = nullptr) {
     const PixIndex pi = make_pix_index(g);
-    const bool v4 = vec4_ok(g, {dT, v, r, grad, x});
+    const bool v4 = vec4_ok(g, {dT.p, v, r, grad, x});
     const bool narrow = narrow_tiles(g, v4);
     const int seg = v4 ? (narrow ? 16 : 64) : (narrow ? 8 : 32);
     const unsigned blocks = (unsigned)((g.N + seg - 1) / seg);
 #define STML_TILE(D_, V_, T_)                                                                                      \
-    tile_kernel<D_, V_, MODE, T_><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, dT, v, r, grad, x, mean_s, sum_v,      \
-                                                              partials, S, a, gate)
-    if (g.d == 2) {
-        if (v4) { if (narrow) STML_TILE(2, 4, 4); else STML_TILE(2, 4, 16); }
-        else { if (narrow) STML_TILE(2, 1, 8); else STML_TILE(2, 1, 32); }
-    } else {
-        if (v4) { if (narrow) STML_TILE(3, 4, 4); else STML_TILE(3, 4, 16); }
-        else { if (narrow) STML_TILE(3, 1, 8); else STML_TILE(3, 1, 32); }
-    }
+    tile_kernel<D_, V_, MODE, T_, TD><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, Td, v, r, grad, x, mean_s, sum_v, \
+                                                                  partials, S, a, gate)
+    with_store_type(dT.type, [&](auto tag) {
+        using TD = decltype(tag);
+        const TD* Td = static_cast<const TD*>(dT.p);
+        if constexpr (MODE == TILE_SUMS && !std::is_same<TD, float>::value) return 0;   // float grad T only
+        if (g.d == 2) {
+            if (v4) { if (narrow) STML_TILE(2, 4, 4); else STML_TILE(2, 4, 16); }
+            else { if (narrow) STML_TILE(2, 1, 8); else STML_TILE(2, 1, 32); }
+        } else {
+            if (v4) { if (narrow) STML_TILE(3, 4, 4); else STML_TILE(3, 4, 16); }
+            else { if (narrow) STML_TILE(3, 1, 8); else STML_TILE(3, 1, 32); }
+        }
+        return 0;
+    });
 #undef STML_TILE
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <bool FUSED>
-cudaError_t apply_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const DirSrc& src,
+cudaError_t apply_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const DirSrc& src,
                          float* Hv, double* partials, size_t partials_cap, unsigned int* ticket, double* out,
                          DevScalars* pcg, cudaStream_t s) {
     const PixIndex pi = make_pix_index(g);
-    const bool v4 = vec4_ok(g, {dT, src.z, src.pold, src.pout, Hv, src.ms_z, src.sv_z, src.ms_p, src.sv_p,
+    const bool v4 = vec4_ok(g, {dT.p, src.z, src.pold, src.pout, Hv, src.ms_z, src.sv_z, src.ms_p, src.sv_p,
                                 src.ms_out, src.sv_out});
     const int vec = v4 ? 4 : 1;
     const long long cpf = (g.N + (long long)kThreads * vec - 1) / ((long long)kThreads * vec);
@@ -690,12 +702,17 @@ cudaError_t apply_launch(const Geom& g, const FrameSet& fs, const Coef& cf, cons
     if ((size_t)grid > partials_cap) return cudaErrorInvalidValue;
     const FastDiv chunks = FastDiv::make((unsigned)cpf);
 #define STML_APPLY(D_, V_) \
-    apply_kernel<D_, V_, FUSED><<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, dT, src, Hv, partials, ticket, out, pcg)
-    if (g.d == 2) {
-        if (v4) STML_APPLY(2, 4); else STML_APPLY(2, 1);
-    } else {
-        if (v4) STML_APPLY(3, 4); else STML_APPLY(3, 1);
-    }
+    apply_kernel<D_, V_, FUSED, TD><<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, src, Hv, partials, ticket, out, pcg)
+    with_store_type(dT.type, [&](auto tag) {
+        using TD = decltype(tag);
+        const TD* Td = static_cast<const TD*>(dT.p);
+        if (g.d == 2) {
+            if (v4) STML_APPLY(2, 4); else STML_APPLY(2, 1);
+        } else {
+            if (v4) STML_APPLY(3, 4); else STML_APPLY(3, 1);
+        }
+        return 0;
+    });
 #undef STML_APPLY
     count_launches(1);
     return cudaGetLastError();
@@ -713,7 +730,7 @@ size_t gn_partials(const Geom& g, int nK) {
 cudaError_t launch_hess_sums(const Geom& g, const FrameSet& fs, const float* dT, const float* v, float* mean_s,
                              float* sum_v, cudaStream_t s) {
     Coef cf{};
-    return tile_launch<TILE_SUMS>(g, fs, cf, dT, const_cast<float*>(v), nullptr, nullptr, nullptr, mean_s, sum_v,
+    return tile_launch<TILE_SUMS>(g, fs, cf, Stored{dT, ST_F32}, const_cast<float*>(v), nullptr, nullptr, nullptr, mean_s, sum_v,
                                   nullptr, nullptr, PcgArgs{0.f, 0}, s);
 }
 
@@ -722,26 +739,26 @@ cudaError_t launch_hess_apply(const Geom& g, const FrameSet& fs, const Coef& cf,
                               size_t partials_cap, unsigned int* ticket, double* out, DevScalars* pcg,
                               cudaStream_t s) {
     const DirSrc src{v, nullptr, 0.f, nullptr, mean_s, sum_v, nullptr, nullptr, nullptr, nullptr};
-    return apply_launch<false>(g, fs, cf, dT, src, Hv, partials, partials_cap, ticket, out, pcg, s);
+    return apply_launch<false>(g, fs, cf, Stored{dT, ST_F32}, src, Hv, partials, partials_cap, ticket, out, pcg, s);
 }
 
-cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const Stored& dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
                             cudaStream_t s, const int* gate) {
     if ((size_t)((g.N + 7) / 8) * 2 > partials_cap) return cudaErrorInvalidValue;
     return tile_launch<TILE_INIT>(g, fs, cf, dT, b.p[0], b.r, grad, b.x, b.ms_z, b.sv_z, partials, S, a, s, gate);
 }
 
-cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
+cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
                              double* partials, size_t partials_cap, DevScalars* S, cudaStream_t s) {
-    return launch_hess_apply(g, fs, cf, dT, b.p[0], b.ms_z, b.sv_z, b.q, partials, partials_cap, &S->ticket[1],
-                             S->dots + 4, S, s);
+    const DirSrc src{b.p[0], nullptr, 0.f, nullptr, b.ms_z, b.sv_z, nullptr, nullptr, nullptr, nullptr};
+    return apply_launch<false>(g, fs, cf, dT, src, b.q, partials, partials_cap, &S->ticket[1], S->dots + 4, S, s);
 }
 
-cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
+cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
                               double* partials, size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s) {
     const PixIndex pi = make_pix_index(g);
-    const bool v4 = vec4_ok(g, {dT, b.x, b.r, b.p[0], b.q});
+    const bool v4 = vec4_ok(g, {dT.p, b.x, b.r, b.p[0], b.q});
     const int vec = v4 ? 4 : 1;
     const long long cpf = (g.N + (long long)kThreads * vec - 1) / ((long long)kThreads * vec);
     const long long items = cpf * fs.nK * g.d;
@@ -749,18 +766,23 @@ cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf,
     if ((size_t)grid * 2 > partials_cap) return cudaErrorInvalidValue;
     const FastDiv chunks = FastDiv::make((unsigned)cpf);
 #define STML_UPD(D_, V_) \
-    update_kernel<D_, V_><<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, dT, b.x, b.r, b.p[0], b.q, partials, S, a)
-    if (g.d == 2) {
-        if (v4) STML_UPD(2, 4); else STML_UPD(2, 1);
-    } else {
-        if (v4) STML_UPD(3, 4); else STML_UPD(3, 1);
-    }
+    update_kernel<D_, V_, TD><<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, b.x, b.r, b.p[0], b.q, partials, S, a)
+    with_store_type(dT.type, [&](auto tag) {
+        using TD = decltype(tag);
+        const TD* Td = static_cast<const TD*>(dT.p);
+        if (g.d == 2) {
+            if (v4) STML_UPD(2, 4); else STML_UPD(2, 1);
+        } else {
+            if (v4) STML_UPD(3, 4); else STML_UPD(3, 1);
+        }
+        return 0;
+    });
 #undef STML_UPD
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
+cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT,
                                  const PcgBufs& b, DevScalars* S, cudaStream_t s) {
     return tile_launch<TILE_DIR>(g, fs, cf, dT, b.p[0], b.r, nullptr, nullptr, b.ms_z, b.sv_z, nullptr, S,
                                  PcgArgs{0.f, 0}, s);
@@ -768,11 +790,11 @@ cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& 
 
 namespace {
 
-template <int D, int VEC, int TPR>
-cudaError_t coop_go(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+template <int D, int VEC, int TPR, typename TD>
+cudaError_t coop_go(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const TD* dT,
                     const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
                     cudaStream_t s, const int* gate) {
-    const void* kern = (const void*)pcg_coop_kernel<D, VEC, TPR>;
+    const void* kern = (const void*)pcg_coop_kernel<D, VEC, TPR, TD>;
     int dev = 0, sms = 1, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -807,16 +829,20 @@ cudaError_t coop_go(const Geom& g, const FrameSet& fs, const Coef& cf, const flo
 
 bool pcg_coop_preferred(const Geom& g, int nK) { return (long long)g.N * nK <= (1LL << 20); }
 
-cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const Stored& dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
                             cudaStream_t s, const int* gate) {
-    const bool v4 = vec4_ok(g, {grad, dT, b.x, b.r, b.z, b.q, b.p[0], b.p[1], b.ms_z, b.sv_z, b.ms_p[0], b.sv_p[0],
-                                b.ms_p[1], b.sv_p[1]});
-    if (g.d == 2)
-        return v4 ? coop_go<2, 4, 4>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate)
-                  : coop_go<2, 1, 8>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate);
-    return v4 ? coop_go<3, 4, 4>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate)
-              : coop_go<3, 1, 8>(g, fs, cf, grad, dT, b, partials, partials_cap, S, a, s, gate);
+    const bool v4 = vec4_ok(g, {grad, dT.p, b.x, b.r, b.z, b.q, b.p[0], b.p[1], b.ms_z, b.sv_z, b.ms_p[0],
+                                b.sv_p[0], b.ms_p[1], b.sv_p[1]});
+    return with_store_type(dT.type, [&](auto tag) {
+        using TD = decltype(tag);
+        const TD* Td = static_cast<const TD*>(dT.p);
+        if (g.d == 2)
+            return v4 ? coop_go<2, 4, 4>(g, fs, cf, grad, Td, b, partials, partials_cap, S, a, s, gate)
+                      : coop_go<2, 1, 8>(g, fs, cf, grad, Td, b, partials, partials_cap, S, a, s, gate);
+        return v4 ? coop_go<3, 4, 4>(g, fs, cf, grad, Td, b, partials, partials_cap, S, a, s, gate)
+                  : coop_go<3, 1, 8>(g, fs, cf, grad, Td, b, partials, partials_cap, S, a, s, gate);
+    });
 }
 
 }  // namespace stml

@@ -34,7 +34,10 @@ static inline unsigned grid1d(long long n, int threads, long long cap = 1 << 20)
 }
 
 // ---------------------------------------------------------------- restriction
-__global__ void restrict_kernel(const float* __restrict__ fine, float* __restrict__ coarse,
+// 2^d block mean in float of stored values; the result is stored in the same
+// type (rounded to nearest even for 16-bit storage).
+template <typename TI>
+__global__ void restrict_kernel(const TI* __restrict__ fine, TI* __restrict__ coarse,
                                 long long total, Geom gc) {
     const int fx = 2 * gc.nx, fy = 2 * gc.ny;
     const long long Nf = gc.N * (gc.d == 3 ? 8 : 4);
@@ -44,28 +47,68 @@ __global__ void restrict_kernel(const float* __restrict__ fine, float* __restric
         const long long pc = e - plane * gc.N;
         int x, y, z;
         unflatten(gc, pc, x, y, z);
-        const float* F = fine + plane * Nf;
+        const TI* F = fine + plane * Nf;
         float s;
         if (gc.d == 2) {
             const long long b = (long long)(2 * y) * fx + 2 * x;
-            s = (F[b] + F[b + 1]) + (F[b + fx] + F[b + fx + 1]);
+            s = (ldf(F + b) + ldf(F + b + 1)) + (ldf(F + b + fx) + ldf(F + b + fx + 1));
             s *= 0.25f;
         } else {
             const long long b = ((long long)(2 * z) * fy + 2 * y) * fx + 2 * x;
             const long long sz = (long long)fx * fy;
-            s = ((F[b] + F[b + 1]) + (F[b + fx] + F[b + fx + 1])) +
-                ((F[b + sz] + F[b + sz + 1]) + (F[b + sz + fx] + F[b + sz + fx + 1]));
+            s = ((ldf(F + b) + ldf(F + b + 1)) + (ldf(F + b + fx) + ldf(F + b + fx + 1))) +
+                ((ldf(F + b + sz) + ldf(F + b + sz + 1)) + (ldf(F + b + sz + fx) + ldf(F + b + sz + fx + 1)));
             s *= 0.125f;
         }
-        coarse[e] = s;
+        stf(coarse + e, s);
     }
 }
 
-cudaError_t launch_restrict(const float* fine, float* coarse, int planes, const Geom& gc,
+cudaError_t launch_restrict(const void* fine, void* coarse, int type, int planes, const Geom& gc,
                             cudaStream_t s) {
     const long long total = (long long)planes * gc.N;
     if (total == 0) return cudaSuccess;
-    restrict_kernel<<<grid1d(total, kThreads), kThreads, 0, s>>>(fine, coarse, total, gc);
+    with_store_type(type, [&](auto tag) {
+        using TI = decltype(tag);
+        restrict_kernel<TI><<<grid1d(total, kThreads), kThreads, 0, s>>>(static_cast<const TI*>(fine),
+                                                                          static_cast<TI*>(coarse), total, gc);
+        return 0;
+    });
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- storage conversion
+template <typename TI>
+__global__ void to_store_kernel(const float* __restrict__ src, TI* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        stf(dst + i, src[i]);
+}
+
+template <typename TI>
+__global__ void from_store_kernel(const TI* __restrict__ src, float* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = ldf(src + i);
+}
+
+cudaError_t launch_to_store(const float* src, void* dst, int type, long long n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    with_store_type(type, [&](auto tag) {
+        using TI = decltype(tag);
+        to_store_kernel<TI><<<grid1d(n, kThreads), kThreads, 0, s>>>(src, static_cast<TI*>(dst), n);
+        return 0;
+    });
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_store(const void* src, int type, float* dst, long long n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    with_store_type(type, [&](auto tag) {
+        using TI = decltype(tag);
+        from_store_kernel<TI><<<grid1d(n, kThreads), kThreads, 0, s>>>(static_cast<const TI*>(src), dst, n);
+        return 0;
+    });
     count_launches(1);
     return cudaGetLastError();
 }
@@ -302,13 +345,14 @@ cudaError_t launch_scatter_planes(const float* src, float* dst, const int* idx, 
 
 // ---------------------------------------------------------------- correlation
 // One CTA per consecutive pair (k, k+1); sums in double, fixed order.
-__global__ void corr_kernel(const float* __restrict__ img, long long N, double* __restrict__ rho) {
+template <typename TI>
+__global__ void corr_kernel(const TI* __restrict__ img, long long N, double* __restrict__ rho) {
     const int k = blockIdx.x;
-    const float* A = img + (size_t)k * N;
-    const float* B = A + N;
+    const TI* A = img + (size_t)k * N;
+    const TI* B = A + N;
     double s[5] = {0, 0, 0, 0, 0};
     for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-        const double a = A[i], b = B[i];
+        const double a = ldf(A + i), b = ldf(B + i);
         s[0] += a;
         s[1] += b;
         s[2] += a * a;
@@ -335,9 +379,13 @@ __global__ void corr_kernel(const float* __restrict__ img, long long N, double* 
     }
 }
 
-cudaError_t launch_corr_coeff(const float* img, int n, long long N, double* rho_dev, cudaStream_t s) {
+cudaError_t launch_corr_coeff(const void* img, int type, int n, long long N, double* rho_dev, cudaStream_t s) {
     if (n < 2) return cudaSuccess;
-    corr_kernel<<<n - 1, kThreads, 0, s>>>(img, N, rho_dev);
+    with_store_type(type, [&](auto tag) {
+        using TI = decltype(tag);
+        corr_kernel<TI><<<n - 1, kThreads, 0, s>>>(static_cast<const TI*>(img), N, rho_dev);
+        return 0;
+    });
     count_launches(1);
     return cudaGetLastError();
 }

@@ -13,6 +13,20 @@
 
 namespace stml {
 
+// A stored array and its element type (StoreType).
+struct Stored {
+    const void* p;
+    int type;
+};
+
+// Calls f with a value of the element type named by a StoreType.
+template <typename F>
+auto with_store_type(int st, F&& f) {
+    if (st == ST_F16) return f(__half{});
+    if (st == ST_BF16) return f(__nv_bfloat16{});
+    return f(float{});
+}
+
 // Sets the text stml_last_error(NULL) returns (errors of context-free calls).
 void set_context_free_error(const std::string& msg);
 
@@ -37,8 +51,12 @@ constexpr int kPixPerCta = 32;
 constexpr int kFrameGroups = kThreads / kPixPerCta;
 
 // ---------------------------------------------------------- transfer ops
-cudaError_t launch_restrict(const float* fine, float* coarse, int planes, const Geom& gc,
+// 2^d block mean of `planes` stored arrays of 2 gc (type: StoreType).
+cudaError_t launch_restrict(const void* fine, void* coarse, int type, int planes, const Geom& gc,
                             cudaStream_t s);
+// float <-> stored type, n values.
+cudaError_t launch_to_store(const float* src, void* dst, int type, long long n, cudaStream_t s);
+cudaError_t launch_from_store(const void* src, int type, float* dst, long long n, cudaStream_t s);
 cudaError_t launch_prolong(const float* coarse, float* fine, int planes, const Geom& gc,
                            cudaStream_t s);
 cudaError_t launch_prolong_adjoint(const float* fine, float* coarse, int planes, const Geom& gc,
@@ -65,7 +83,7 @@ cudaError_t launch_gather_planes(const float* src, float* dst, const int* idx, i
 cudaError_t launch_scatter_planes(const float* src, float* dst, const int* idx, int nK,
                                   size_t plane_elems, cudaStream_t s);
 
-cudaError_t launch_corr_coeff(const float* img, int n, long long N, double* rho_dev, cudaStream_t s);
+cudaError_t launch_corr_coeff(const void* img, int type, int n, long long N, double* rho_dev, cudaStream_t s);
 
 // ---------------------------------------------------------- objective (k_eval.cu)
 // Objective pass at u (or u + t du): J, D, S, P, |u|^2 to out[0..3], out[5]
@@ -81,17 +99,18 @@ struct LineSearchArgs {
     double J;
     double c;
 };
-cudaError_t launch_objective(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
+cudaError_t launch_objective(const Stored& T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                              const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
                              size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s,
                              const LineSearchArgs* ls = nullptr);
 // Gradient pass at u (or u + t du) with abar, ubar of the same point: g and
 // grad T, optionally the point itself (unew); |g|^2 and |u|^2 to out[4], out[5].
 // With gate != nullptr it runs only if gate->ls_accepted, with t = gate->ls_t.
-cudaError_t launch_gradient(const float* T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
-                            const float* du, float t, const float* abar, const float* ubar, float* grad, float* dT,
-                            float* unew, double* partials, size_t partials_cap, unsigned int* ticket, double* out,
-                            cudaStream_t s, const DevScalars* gate = nullptr);
+// grad T is written as float (dT_type ST_F32) or in the image's storage type.
+cudaError_t launch_gradient(const Stored& T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
+                            const float* du, float t, const float* abar, const float* ubar, float* grad, void* dT,
+                            int dT_type, float* unew, double* partials, size_t partials_cap, unsigned int* ticket,
+                            double* out, cudaStream_t s, const DevScalars* gate = nullptr);
 // Doubles of partial sums the evaluation kernels need.
 size_t eval_partials(const Geom& g, int nK);
 
@@ -147,22 +166,22 @@ struct PcgBufs {
 // r = -g, p = M^-1 r, x = 0, the frame sums of p; rho = <r, M^-1 r>, |r|^2.
 // With gate != nullptr the start runs only if *gate is nonzero (otherwise
 // cg_active keeps its value, 0 after any finished solve).
-cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const Stored& dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
                             cudaStream_t s, const int* gate = nullptr);
 // q = H p (from p and its frame sums); alpha = rho / <p, q>.
-cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
+cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
                              double* partials, size_t partials_cap, DevScalars* S, cudaStream_t s);
 // x += alpha p, r -= alpha q; rho, the convergence test and beta.
-cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const PcgBufs& b,
+cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
                               double* partials, size_t partials_cap, DevScalars* S, PcgArgs a, cudaStream_t s);
 // p = M^-1 r + beta p and the frame sums of the new p.
-cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT,
+cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT,
                                  const PcgBufs& b, DevScalars* S, cudaStream_t s);
 // The whole PCG solve (start, iterations, exit) in one cooperative launch, for
 // small problems where launch latency dominates; the final CG state goes to S.
 bool pcg_coop_preferred(const Geom& g, int nK);
-cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const float* dT,
+cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const Stored& dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
                             cudaStream_t s, const int* gate = nullptr);
 
