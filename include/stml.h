@@ -170,6 +170,15 @@ stml_status stml_correct(stml_ctx* ctx, int level, int tlevel, stml_stats* stats
 stml_status stml_eval(stml_ctx* ctx, int level, const int* frames, int nK, const float* u,
                       double* out, float* g, float* dT);
 
+/* Objective at the trial point u + t d of an Armijo line search (the
+ * objective of eq. (1) plus S and P as in stml_eval, no array formed), in the
+ * launch the solver uses.  out (host, 8 doubles): J, D, S, P, 0, |u + t d|^2,
+ * <gd, d>, |d|^2; the last two only when gd (the gradient at u, device,
+ * same layout as u) is given, else 0.  u, d, gd are device arrays of
+ * nK * d * N floats, 16-byte aligned. */
+stml_status stml_eval_trial(stml_ctx* ctx, int level, const int* frames, int nK, const float* u,
+                            const float* d, double t, const float* gd, double* out);
+
 /* Gauss-Newton Hessian product Hv = J^T J v + alpha hd B^T B v + alpha_t hd L_t v
  * + 2 lambda hd / |K|^2 sum_j v_j (device arrays of nK * d * N floats, dT as
  * returned by stml_eval).  *vHv (host, may be NULL) receives <v, Hv>. */

@@ -72,6 +72,7 @@ _SIGS = {
     "stml_predict": (C.c_int, [_vp, C.c_int, C.c_int]),
     "stml_correct": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(Stats), _ip]),
     "stml_eval": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, _dp, _fp, _fp]),
+    "stml_eval_trial": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, _fp, C.c_double, _fp, _dp]),
     "stml_hessvec": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, _fp, _fp, _dp]),
     "stml_gir": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, C.POINTER(Stats)]),
     "stml_corr_coeff": (C.c_int, [_vp, C.c_int, _dp]),
@@ -251,6 +252,13 @@ def stml_correct(ctx, level: int, tlevel: int):
 def stml_eval(ctx, level: int, frames: Sequence[int], u, g=None, dT=None) -> np.ndarray:
     out = (C.c_double * 6)()
     _check(load().stml_eval(ctx, level, _ints(frames), len(frames), _dev(u), out, _dev(g), _dev(dT)), ctx)
+    return np.array(out[:])
+
+
+def stml_eval_trial(ctx, level: int, frames: Sequence[int], u, d, t: float, gd=None) -> np.ndarray:
+    out = (C.c_double * 8)()
+    _check(load().stml_eval_trial(ctx, level, _ints(frames), len(frames), _dev(u), _dev(d), C.c_double(t),
+                                  _dev(gd), out), ctx)
     return np.array(out[:])
 
 

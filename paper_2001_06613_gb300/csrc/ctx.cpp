@@ -1001,6 +1001,32 @@ stml_status stml_eval(stml_ctx* c, int level, const int* frames, int nK, const f
     return STML_OK;
 }
 
+stml_status stml_eval_trial(stml_ctx* c, int level, const int* frames, int nK, const float* u, const float* d,
+                            double t, const float* gd, double* out) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!u || !d || !out) return fail(c, STML_EINVAL, "u, d and out are required");
+    TRY(check_aligned(c, {u, d, gd}));
+    cudaSetDevice(c->device);
+    LevelBuf& L = c->lv[level];
+    std::vector<int> K(frames, frames + nK);
+    FrameSet fs;
+    TRY(upload_frameset(c, K, fs));
+    const Coef cf = make_coef(L.g, c->p, nK);
+    const double pfK = (double)nK * L.g.N;
+    const double bS = (double)store_bytes(c->img_type);
+    const long pe = prof_begin(c, PC_TRIAL, level);
+    CK(c, launch_objective(Stored{L.img, c->img_type}, L.g, fs, cf, u, d, (float)t, gd, c->w_abar, c->w_ubar,
+                           c->partials, c->partials_cap, &c->S->ticket[0], c->S->trial, c->stream));
+    prof_end(c, pe, pfK * (bS + (gd ? 16.0 : 8.0) * L.g.d), pfK);
+    TRY(read_scalars(c));
+    for (int i = 0; i < 8; ++i) out[i] = c->Sh->trial[i];
+    if (!gd) out[6] = out[7] = 0.0;
+    out[4] = 0.0;
+    return STML_OK;
+}
+
 stml_status stml_hessvec(stml_ctx* c, int level, const int* frames, int nK, const float* dT, const float* v,
                          float* Hv, double* vHv) {
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");

@@ -146,6 +146,19 @@ struct FrameU {
     }
 };
 
+// One stage of the 2-D objective pass's copy ring (floats, per warp): for u
+// (and du in a trial) and each component, the run of 32 VEC pixels and the
+// run one row below; then the first pixel of the next run (lane 31).
+constexpr int kObjStages = 3;
+template <int D, int VEC, bool TRIAL>
+struct ObjStage {
+    static constexpr int kSrc = TRIAL ? 2 : 1;
+    static constexpr int kRow = 32 * VEC;
+    static constexpr int kRows = kSrc * D * 2 * kRow;
+    static constexpr int floats = kRows + ((kSrc * D + 3) / 4) * 4;
+    static constexpr size_t ring_bytes = (size_t)(kThreads / 32) * kObjStages * floats * sizeof(float);
+};
+
 }  // namespace
 
 template <int D, int VEC, bool TRIAL, bool GDOT, typename TI>
@@ -202,65 +215,135 @@ obj_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, 
             }
         }
     }
-    if (j0 < fs.nK) {
+    // the work on frame j (field `cur`, image number fr): warped image,
+    // forward-difference energy, temporal term, sums
+    auto consume = [&](const FrameU<D, VEC, TRIAL>& cur, int j, int fr) {
+        // every gather is unconditional (clamped addresses; invalid lanes
+        // sample pixel 0 with a zero field)
+        const TI* Tk = T + (size_t)fr * N;
+        float a[VEC];
+        if constexpr (D == 2) {
+            interp2_row<VEC>(Tk, g, x, y, cur.c[0], cur.c[1], a);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                a[e] = interp3_val(Tk, g, x + e, y, z, cur.c[0][e], cur.c[1][e], cur.c[2][e]);
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float right = __shfl_down_sync(0xffffffffu, cur.c[k][0], 1);
+            const float xl = lane < 31 ? right : cur.tail[k];
+            float fw = 0.f;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const float cc = cur.c[k][e];
+                if (e + 1 < VEC || has_xl) {
+                    const float nb = e + 1 < VEC ? cur.c[k][(e + 1) % VEC] : xl;
+                    fw = fmaf(nb - cc, nb - cc, fw);
+                }
+                if (has_y) fw = fmaf(cur.ny[k][e] - cc, cur.ny[k][e] - cc, fw);
+                if constexpr (D == 3)
+                    if (has_z) fw = fmaf(cur.nz[k][e] - cc, cur.nz[k][e] - cc, fw);
+                su[k][e] += cc;
+                u2 = fmaf(cc, cc, u2);
+            }
+            sx = fmaf(c_sx, valid ? fw : 0.f, sx);
+            if (cf.alphat_hd != 0.f && j + 1 < fs.nK && valid) {
+                const float cw = 0.5f * cf.alphat_hd * __ldg(fs.w_next + j);
+                float nt[VEC];
+                FrameU<D, VEC, TRIAL>::ld(u, du, t, ((size_t)(j + 1) * D + k) * N + p, nt);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) st = fmaf(cw * (nt[e] - cur.c[k][e]), nt[e] - cur.c[k][e], st);
+            }
+        }
+        if (cnt == 0.f) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) sft[e] = a[e];
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const float dl = a[e] - sft[e];
+            s1[e] += dl;
+            s2[e] = fmaf(dl, dl, s2[e]);
+        }
+        cnt += 1.f;
+    };
+    if constexpr (D == 2) {
+        // Each lane copies its own pieces of the fields of its next frames
+        // into this warp's ring of kObjStages stages with cp.async (one commit
+        // group per frame) and reads back only what it copied, so many loads
+        // are in flight without holding registers and no barrier is needed.
+        using STG = ObjStage<D, VEC, TRIAL>;
+        extern __shared__ float4 obj_ring4[];
+        float* ring = reinterpret_cast<float*>(obj_ring4) + (size_t)w * kObjStages * STG::floats;
+        auto issue = [&](int jj, int stage) {
+            float* b = ring + stage * STG::floats;
+#pragma unroll
+            for (int src = 0; src < STG::kSrc; ++src) {
+                const float* arr = src ? du : u;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float* gk = arr + ((size_t)jj * D + k) * N + p;
+                    float* rk = b + ((src * D + k) * 2) * STG::kRow + lane * VEC;
+                    if (valid) cp_async<4 * VEC>(rk, gk);
+                    if (has_y) cp_async<4 * VEC>(rk + STG::kRow, gk + g.nx);
+                    if (has_tail) cp_async<4>(b + STG::kRows + src * D + k, gk + VEC);
+                }
+            }
+        };
+        auto read = [&](int stage, FrameU<D, VEC, TRIAL>& cur) {
+            const float* b = ring + stage * STG::floats;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float* r0 = b + (k * 2) * STG::kRow + lane * VEC;
+                const float* r1 = b + ((STG::kSrc - 1) * D + k) * 2 * STG::kRow + lane * VEC;   // du rows
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    float cv = valid ? r0[e] : 0.f, nv = has_y ? r0[STG::kRow + e] : 0.f;
+                    if constexpr (TRIAL) {
+                        if (valid) cv = fmaf(t, r1[e], cv);
+                        if (has_y) nv = fmaf(t, r1[STG::kRow + e], nv);
+                    }
+                    cur.c[k][e] = cv;
+                    cur.ny[k][e] = nv;
+                }
+                float tl = has_tail ? b[STG::kRows + k] : 0.f;
+                if constexpr (TRIAL)
+                    if (has_tail) tl = fmaf(t, b[STG::kRows + (STG::kSrc - 1) * D + k], tl);
+                cur.tail[k] = tl;
+            }
+        };
+#pragma unroll
+        for (int s0 = 0; s0 < kObjStages - 1; ++s0) {
+            const int jj = j0 + s0 * TG;
+            if (jj < fs.nK) issue(jj, s0);
+            cp_async_commit();
+        }
+        int stage = 0;
+        for (int j = j0; j < fs.nK; j += TG) {
+            const int jf = j + (kObjStages - 1) * TG;
+            if (jf < fs.nK) issue(jf, (stage + kObjStages - 1) % kObjStages);
+            cp_async_commit();
+            const int fr = __ldg(fs.frames + j);
+            cp_async_wait<kObjStages - 1>();
+            FrameU<D, VEC, TRIAL> cur;
+            read(stage, cur);
+            consume(cur, j, fr);
+            stage = stage + 1 == kObjStages ? 0 : stage + 1;
+        }
+        cp_async_wait<0>();
+    } else if (j0 < fs.nK) {
+        // 3-D: the field of the next frame is loaded into registers while the
+        // current one is used
         FrameU<D, VEC, TRIAL> cur;
         cur.load(u, du, t, (size_t)j0 * D * N + p, N, g.nx, sz, valid, has_y, has_z, has_tail);
         int fr = __ldg(fs.frames + j0);
         for (int j = j0; j < fs.nK; j += TG) {
-            // warped image of frame j; every gather is unconditional (clamped
-            // addresses; invalid lanes sample pixel 0 with a zero field)
-            const TI* Tk = T + (size_t)fr * N;
-            float a[VEC];
-            if constexpr (D == 2) {
-                interp2_row<VEC>(Tk, g, x, y, cur.c[0], cur.c[1], a);
-            } else {
-#pragma unroll
-                for (int e = 0; e < VEC; ++e)
-                    a[e] = interp3_val(Tk, g, x + e, y, z, cur.c[0][e], cur.c[1][e], cur.c[2][e]);
-            }
-            // the field of this warp's next frame (the last frame again at the end)
             const int jn = j + TG < fs.nK ? j + TG : j;
             FrameU<D, VEC, TRIAL> nxt;
             nxt.load(u, du, t, (size_t)jn * D * N + p, N, g.nx, sz, valid, has_y, has_z, has_tail);
             const int fr_next = __ldg(fs.frames + jn);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const float right = __shfl_down_sync(0xffffffffu, cur.c[k][0], 1);
-                const float xl = lane < 31 ? right : cur.tail[k];
-                float fw = 0.f;
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const float cc = cur.c[k][e];
-                    if (e + 1 < VEC || has_xl) {
-                        const float nb = e + 1 < VEC ? cur.c[k][(e + 1) % VEC] : xl;
-                        fw = fmaf(nb - cc, nb - cc, fw);
-                    }
-                    if (has_y) fw = fmaf(cur.ny[k][e] - cc, cur.ny[k][e] - cc, fw);
-                    if constexpr (D == 3)
-                        if (has_z) fw = fmaf(cur.nz[k][e] - cc, cur.nz[k][e] - cc, fw);
-                    su[k][e] += cc;
-                    u2 = fmaf(cc, cc, u2);
-                }
-                sx = fmaf(c_sx, valid ? fw : 0.f, sx);
-                if (cf.alphat_hd != 0.f && j + 1 < fs.nK && valid) {
-                    const float cw = 0.5f * cf.alphat_hd * __ldg(fs.w_next + j);
-                    float nt[VEC];
-                    FrameU<D, VEC, TRIAL>::ld(u, du, t, ((size_t)(j + 1) * D + k) * N + p, nt);
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) st = fmaf(cw * (nt[e] - cur.c[k][e]), nt[e] - cur.c[k][e], st);
-                }
-            }
-            if (cnt == 0.f) {
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) sft[e] = a[e];
-            }
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                const float dl = a[e] - sft[e];
-                s1[e] += dl;
-                s2[e] = fmaf(dl, dl, s2[e]);
-            }
-            cnt += 1.f;
+            consume(cur, j, fr);
             cur = nxt;
             fr = fr_next;
         }
@@ -578,6 +661,17 @@ static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const TI* T, const
     lc.gridDim = dim3(sh.runs, (unsigned)sh.splits, 1);
     lc.blockDim = dim3(kThreads, 1, 1);
     lc.stream = s;
+    if constexpr (D == 2) {   // the copy ring of the staged 2-D pass
+        static bool attr_set = false;
+        const size_t ring = ObjStage<D, VEC, TRIAL>::ring_bytes;
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(obj_kernel<D, VEC, TRIAL, GDOT, TI>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        lc.dynamicSmemBytes = ring;
+    }
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 1;

@@ -32,7 +32,7 @@ def _peak():
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="all",
-                    choices=["all", "hessvec", "eval", "objective", "trial", "pcg", "predict_ls"])
+                    choices=["all", "hessvec", "eval", "objective", "trial", "predict_ls"])
     ap.add_argument("--shape", type=int, nargs="+", default=[256, 256])
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--iters", type=int, default=20)
@@ -59,6 +59,9 @@ def main(argv=None):
     u = u.expand(n, *u.shape[1:]).contiguous()
     v = torch.randn((n, d) + shape, device=dev)
     g = torch.empty_like(v)
+    # a smooth search direction for the trial objective (like a Gauss-Newton step)
+    dirn = torch.from_numpy(synthetic.random_field(rng, 1, d, shape, amp=0.7, rough=0.3)).to(dev)
+    dirn = dirn.expand(n, *dirn.shape[1:]).contiguous()
     dT = torch.empty_like(v)
     Hv = torch.empty_like(v)
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
@@ -90,7 +93,7 @@ def main(argv=None):
                           "frac_of_measured_hbm": gbs / peak, "bytes_per_pixel_frame": per_pf,
                           "kernel_us_per_launch": kernels}), flush=True)
 
-    ops = [args.op] if args.op != "all" else ["hessvec", "eval", "objective", "predict_ls"]
+    ops = [args.op] if args.op != "all" else ["hessvec", "eval", "objective", "trial", "predict_ls"]
     for op in ops:
         if op == "hessvec":
             b = 12 * d                     # read v, read grad T, write Hv
@@ -101,6 +104,11 @@ def main(argv=None):
         elif op == "objective":
             b = 4 + 4 * d                  # read T, read u
             timed(lambda: S.stml_eval(ctx.ptr, 0, frames, u), b * pf, op, b)
+        elif op == "trial":
+            b = 4 + 8 * d                  # read T, u, d
+            timed(lambda: S.stml_eval_trial(ctx.ptr, 0, frames, u, dirn, 0.5), b * pf, op, b)
+            b = 4 + 16 * d                 # and g, d for <g, d> (first Armijo trial)
+            timed(lambda: S.stml_eval_trial(ctx.ptr, 0, frames, u, dirn, 1.0, g), b * pf, "trial_gd", b)
         elif op == "predict_ls":
             K = list(range(0, n, 4))
             if K[-1] != n - 1:

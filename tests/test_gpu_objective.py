@@ -74,6 +74,38 @@ def test_eval_parity(S, shape, n, levels, level, frames, extra):
         ctx.close()
 
 
+@pytest.mark.parametrize("with_gd", [True, False])
+@pytest.mark.parametrize("shape,n,levels,level,frames,extra", CASES)
+def test_eval_trial_parity(S, shape, n, levels, level, frames, extra, with_gd):
+    """Armijo trial objective at u + t d in the solver's launch (no array formed),
+    with and without <g, d> and |d|^2."""
+    spec = synthetic.spec_custom(n, shape, seed=11, amp=1.5)
+    R = synthetic.make_sequence(spec)
+    ctx = _ctx(S, R, levels, **extra)
+    try:
+        T = multilevel.pyramid(R.astype(np.float64), levels)[level]
+        h = grid.level_h(levels, level)
+        m = T.shape[1:]
+        rng = np.random.default_rng(12)
+        u = synthetic.random_field(rng, len(frames), len(m), m, amp=1.0 * h, rough=0.3 * h)
+        d = synthetic.random_field(rng, len(frames), len(m), m, amp=0.5 * h, rough=0.3 * h)
+        gd = rng.normal(size=u.shape).astype(np.float32)
+        t = 0.5
+        out = S.stml_eval_trial(ctx.ptr, level, frames, _dev(u), _dev(d), t, _dev(gd) if with_gd else None)
+        ut = u.astype(np.float64) + t * d.astype(np.float64)
+        ev = objective.evaluate(T[frames], ut, frames, h, _oracle_params(ctx.params))
+        for i, k in enumerate(("J", "D", "S", "P")):
+            assert_scalar(out[i], ev[k], what=f"trial {k}")
+        assert_scalar(out[5], float(np.sum(ut ** 2)), what="|u + t d|^2")
+        if with_gd:
+            assert_scalar(out[6], float(np.sum(gd.astype(np.float64) * d)), what="<g, d>")
+            assert_scalar(out[7], float(np.sum(d.astype(np.float64) ** 2)), what="|d|^2")
+        else:
+            assert out[6] == 0.0 and out[7] == 0.0
+    finally:
+        ctx.close()
+
+
 @pytest.mark.parametrize("shape,n,levels,level,frames,extra", CASES)
 def test_hessvec_parity(S, shape, n, levels, level, frames, extra):
     import torch
