@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--mode", default="stml", choices=["stml", "spml"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spml", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=25)
     ap.add_argument("--image-dtype", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of the image pyramid and of the solver's grad T (arithmetic stays FP32)")
@@ -224,6 +225,59 @@ def run_reference(args):
         dist.barrier()
 
 
+# ----------------------------------------------------------------- batched serving
+BATCH_SEQUENCES = 16
+
+
+def run_batch(S, torch, dev, mode):
+    """Many sequences of uneven length and size (seeded, 20-120 frames of 128^2,
+    192^2 or 256^2, 3 spatial x 3 temporal levels): registered one after the
+    other with the default parameters, then all at once with
+    stml_register_batch (one stream per sequence, streaming PCG)."""
+    from paper_2001_06613_gb300 import synthetic
+    rng = np.random.default_rng(1000)
+    seqs = []
+    for i in range(BATCH_SEQUENCES):
+        n = int(rng.integers(20, 121))
+        m = int(rng.choice([128, 192, 256]))
+        seqs.append(torch.from_numpy(synthetic.make_sequence(
+            synthetic.spec_custom(n, (m, m), seed=1000 + i, amp=3.0))).to(dev))
+    frames = sum(int(r.shape[0]) for r in seqs)
+
+    def prep(ctx, R):
+        S.stml_load_sequence(ctx.ptr, R)
+        S.stml_build_pyramid(ctx.ptr)
+
+    seq_ctx = S.Context(S.stml_default_params(n_levels=3, n_tlevels=3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for R in seqs:
+        prep(seq_ctx, R)
+        S.stml_register(seq_ctx.ptr, mode)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    seq_ctx.close()
+
+    streams = [torch.cuda.Stream(dev) for _ in seqs]
+    prm = S.stml_default_params(n_levels=3, n_tlevels=3, pcg_cooperative=0)
+    ctxs = [S.Context(prm, st.cuda_stream) for st in streams]
+    for c, R in zip(ctxs, seqs):   # first round allocates the workspaces
+        prep(c, R)
+    S.stml_register_batch(ctxs, mode)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, R in zip(ctxs, seqs):
+        prep(c, R)
+    S.stml_register_batch(ctxs, mode)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    return {"sequences": len(seqs), "frames": frames, "sizes": "20-120 frames of 128^2/192^2/256^2",
+            "sequential_frames_per_s": frames / t_seq, "batched_frames_per_s": frames / t_bat,
+            "speedup": t_seq / t_bat, "timing": "host wall clock around the whole batch, device-resident inputs"}
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_native(args):
     import torch
@@ -327,6 +381,10 @@ def run_native(args):
                 "stml_over_spml_speedup": (value / world) / spml_fps if world else None,
                 "paper_speedup": "2.5x average (Sec. 4, Table 1; hardware not stated)"}
 
+    batch = None
+    if not args.no_batch and rank == 0 and world == 1:
+        batch = run_batch(S, torch, dev, mode)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         frames = min(args.cpu_sample_frames, n)
@@ -383,7 +441,7 @@ def run_native(args):
                 "per_step_ms": ms_steps,
                 "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
                                                  "ls_trials", "stopped_early")} for s in stats],
-                "spml": spml}
+                "spml": spml, "batch": batch}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

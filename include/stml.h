@@ -85,6 +85,9 @@ typedef struct {
     int max_ls;              /* Armijo trials */
     double armijo_c;
     int image_dtype;         /* stml_dtype; fixed for a sequence when it is loaded */
+    int pcg_cooperative;     /* 1: small levels solve PCG in one cooperative launch;
+                              * 0: always the streaming kernels (required by
+                              * stml_register_batch) */
 } stml_params;
 
 typedef struct {
@@ -149,6 +152,19 @@ stml_status stml_set_field(stml_ctx* ctx, int level, const float* src, int src_o
  * (either may be NULL).  The result is available via stml_get_field. */
 stml_status stml_register(stml_ctx* ctx, stml_mode mode, stml_stats* stats, int cap,
                           int* n_written);
+
+/* Registers the sequences of n_ctx contexts concurrently (batched serving of
+ * many sequences of uneven length and size): up to max_threads host threads
+ * (<= 0: one per context) each run stml_register on one context, whose work
+ * goes to that context's own stream, so small sequences share the GPU.
+ * Every context must hold a built pyramid and have pcg_cooperative = 0
+ * (a cooperative launch needs the whole GPU), else STML_EINVAL before any
+ * work starts; contexts must not share a stream.  status (host, n_ctx
+ * entries, may be NULL) receives each context's result; the return value is
+ * STML_OK or the first failure in context order.  Results equal those of
+ * stml_register on each context alone. */
+stml_status stml_register_batch(stml_ctx* const* ctxs, int n_ctx, stml_mode mode, int max_threads,
+                                stml_status* status);
 
 /* One predictor step of the STML sweep (Sec. 3): start values z_{l,q} on all
  * frames -- Id (level 0, q = 0), the prolongated y_{l-1,all} (q = 0), the

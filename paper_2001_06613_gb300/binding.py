@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("tol_J", C.c_double), ("tol_Y", C.c_double), ("tol_G", C.c_double),
                 ("g_abs", C.c_double), ("max_gn", C.c_int), ("tol_cg", C.c_double),
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double),
-                ("image_dtype", C.c_int)]
+                ("image_dtype", C.c_int), ("pcg_cooperative", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +69,7 @@ _SIGS = {
     "stml_get_field": (C.c_int, [_vp, C.c_int, _fp, C.c_int]),
     "stml_set_field": (C.c_int, [_vp, C.c_int, _fp, C.c_int]),
     "stml_register": (C.c_int, [_vp, C.c_int, C.POINTER(Stats), C.c_int, _ip]),
+    "stml_register_batch": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _ip]),
     "stml_predict": (C.c_int, [_vp, C.c_int, C.c_int]),
     "stml_correct": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(Stats), _ip]),
     "stml_eval": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, _dp, _fp, _fp]),
@@ -236,6 +237,17 @@ def stml_register(ctx, mode: int = MODE_STML, cap: int = 512):
     n = C.c_int()
     _check(load().stml_register(ctx, mode, stats, cap, C.byref(n)), ctx)
     return [stats[i].as_dict() for i in range(min(n.value, cap))]
+
+
+def stml_register_batch(ctxs: Sequence, mode: int = MODE_STML, max_threads: int = 0) -> List[int]:
+    """Registers several contexts concurrently; returns each context's status."""
+    arr = (_vp * len(ctxs))(*[c.ptr if hasattr(c, "ptr") else c for c in ctxs])
+    st = (C.c_int * len(ctxs))()
+    status = load().stml_register_batch(arr, len(ctxs), mode, max_threads, st)
+    if status != 0:
+        raise StmlError(status, stml_last_error(None) or "; ".join(
+            stml_last_error(c.ptr if hasattr(c, "ptr") else c) for c in ctxs))
+    return list(st)
 
 
 def stml_predict(ctx, level: int, tlevel: int):

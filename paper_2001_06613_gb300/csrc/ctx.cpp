@@ -11,6 +11,8 @@
 #include <initializer_list>
 #include <map>
 #include <string>
+#include <thread>
+#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -134,6 +136,7 @@ bool valid_params(const stml_params* p, std::string& why) {
     }
     if (p->max_gn < 0 || p->max_cg < 0 || p->max_ls < 1) { why = "iteration limits out of range"; return false; }
     if (!(p->tol_cg > 0) || !(p->armijo_c > 0 && p->armijo_c < 1)) { why = "tol_cg > 0 and 0 < armijo_c < 1"; return false; }
+    if (p->pcg_cooperative != 0 && p->pcg_cooperative != 1) { why = "pcg_cooperative must be 0 or 1"; return false; }
     if (p->image_dtype < STML_DTYPE_F32 || p->image_dtype > STML_DTYPE_BF16) {
         why = "image_dtype must be STML_DTYPE_F32, _F16 or _BF16";
         return false;
@@ -391,7 +394,7 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         if (!init_ran) prof_discount(c, PC_PCG_INIT, level, 1, pfK * B_init, pfK);
     };
     // With gate != nullptr the solve starts only if the device accepted a step.
-    const bool coop = pcg_coop_preferred(g, nK);
+    const bool coop = p.pcg_cooperative && pcg_coop_preferred(g, nK);
     auto start_cg = [&](const int* gate = nullptr) -> stml_status {
         if (coop) {
             pe = prof_begin(c, PC_PCG_COOP, level);
@@ -703,6 +706,8 @@ void stml_default_params(stml_params* p) {
     p->max_cg = 20;
     p->max_ls = 10;
     p->armijo_c = 1e-4;
+    p->image_dtype = STML_DTYPE_F32;
+    p->pcg_cooperative = 1;
 }
 
 stml_status stml_create(const stml_params* p, void* cuda_stream, stml_ctx** out) {
@@ -755,6 +760,32 @@ stml_status stml_set_params(stml_ctx* c, const stml_params* p) {
     return STML_OK;
 }
 
+// Copies the frames of a loaded layout into the finest level (rounding them
+// to the storage type), clears the fields and the device scalars.
+static stml_status load_frames(stml_ctx* c, const float* frames, int on_device) {
+    const int L = (int)c->lv.size();
+    const int n_frames = c->n, dim = c->d;
+    const size_t imgN = (size_t)n_frames * c->lv[L - 1].g.N;
+    CK(c, cudaMemsetAsync(c->S, 0, sizeof(DevScalars), c->stream));
+    if (c->img_type == ST_F32) {
+        CK(c, cudaMemcpyAsync(c->lv[L - 1].img, frames, imgN * sizeof(float),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    } else {   // 16-bit storage: round the float frames (host frames pass through the workspace)
+        const float* src = frames;
+        if (!on_device) {
+            CK(c, cudaMemcpyAsync(c->w_g, frames, imgN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            src = c->w_g;
+        }
+        CK(c, launch_to_store(src, c->lv[L - 1].img, c->img_type, (long long)imgN, c->stream));
+    }
+    for (int l = 0; l < L; ++l)
+        CK(c, cudaMemsetAsync(c->lv[l].y, 0, (size_t)n_frames * dim * c->lv[l].g.N * sizeof(float), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->loaded = true;
+    c->built = false;
+    return STML_OK;
+}
+
 stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, int n_frames, int dim,
                                const int* shape) {
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
@@ -771,6 +802,11 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
     }
     if ((long long)sh3[0] * sh3[1] * sh3[2] > 0x7fffffffLL)
         return fail(c, STML_EINVAL, "an image has more than 2^31 - 1 cells");
+    // a sequence of the same size, storage and level count reuses the buffers
+    // (no device-wide synchronising free / allocation between sequences)
+    const bool reuse = c->loaded && c->n == n_frames && c->d == dim && c->img_type == c->p.image_dtype &&
+                       (int)c->lv.size() == L && std::memcmp(c->shape, sh3, sizeof(sh3)) == 0;
+    if (reuse) return load_frames(c, frames, on_device);
     CK(c, cudaStreamSynchronize(c->stream));
     free_buffers(c);
     c->n = n_frames;
@@ -821,24 +857,7 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
         free_buffers(c);
         return fail(c, STML_ENOMEM, "device allocation of the solver workspace failed");
     }
-    CK(c, cudaMemsetAsync(c->S, 0, sizeof(DevScalars), c->stream));
-    if (c->img_type == ST_F32) {
-        CK(c, cudaMemcpyAsync(c->lv[L - 1].img, frames, imgN * sizeof(float),
-                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    } else {   // 16-bit storage: round the float frames (host frames pass through the workspace)
-        const float* src = frames;
-        if (!on_device) {
-            CK(c, cudaMemcpyAsync(c->w_g, frames, imgN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-            src = c->w_g;
-        }
-        CK(c, launch_to_store(src, c->lv[L - 1].img, c->img_type, (long long)imgN, c->stream));
-    }
-    for (int l = 0; l < L; ++l)
-        CK(c, cudaMemsetAsync(c->lv[l].y, 0, (size_t)n_frames * dim * c->lv[l].g.N * sizeof(float), c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    c->loaded = true;
-    c->built = false;
-    return STML_OK;
+    return load_frames(c, frames, on_device);
 }
 
 stml_status stml_build_pyramid(stml_ctx* c) {
@@ -966,6 +985,39 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
     CK(c, cudaStreamSynchronize(c->stream));
     if (n_written) *n_written = written;
     return STML_OK;
+}
+
+stml_status stml_register_batch(stml_ctx* const* ctxs, int n_ctx, stml_mode mode, int max_threads,
+                                stml_status* status) {
+    if (!ctxs || n_ctx < 1) return fail(nullptr, STML_EINVAL, "stml_register_batch: need contexts");
+    for (int i = 0; i < n_ctx; ++i) {
+        const stml_ctx* c = ctxs[i];
+        if (!c) return fail(nullptr, STML_EINVAL, "stml_register_batch: a context is NULL");
+        if (!c->built) return fail(nullptr, STML_ESTATE, "stml_register_batch: a context has no pyramid");
+        if (c->p.pcg_cooperative)
+            return fail(nullptr, STML_EINVAL, "stml_register_batch: contexts need pcg_cooperative = 0");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == c || (c->stream && ctxs[k]->stream == c->stream))
+                return fail(nullptr, STML_EINVAL, "stml_register_batch: contexts share a stream");
+    }
+    if (mode != STML_MODE_STML && mode != STML_MODE_SPML) return fail(nullptr, STML_EINVAL, "unknown mode");
+    const int nt = std::max(1, std::min(n_ctx, max_threads > 0 ? max_threads : n_ctx));
+    std::vector<stml_status> st(n_ctx, STML_OK);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (int i = next.fetch_add(1); i < n_ctx; i = next.fetch_add(1))
+            st[i] = stml_register(ctxs[i], mode, nullptr, 0, nullptr);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    stml_status first = STML_OK;
+    for (int i = 0; i < n_ctx; ++i) {
+        if (status) status[i] = st[i];
+        if (first == STML_OK && st[i] != STML_OK) first = st[i];
+    }
+    return first;
 }
 
 stml_status stml_eval(stml_ctx* c, int level, const int* frames, int nK, const float* u, double* out,

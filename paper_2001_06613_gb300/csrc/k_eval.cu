@@ -17,6 +17,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "kernels.h"
 
@@ -662,13 +663,13 @@ static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const TI* T, const
     lc.blockDim = dim3(kThreads, 1, 1);
     lc.stream = s;
     if constexpr (D == 2) {   // the copy ring of the staged 2-D pass
-        static bool attr_set = false;
+        static std::atomic<bool> attr_set{false};   // per instantiation; setting it twice is harmless
         const size_t ring = ObjStage<D, VEC, TRIAL>::ring_bytes;
-        if (!attr_set) {
+        if (!attr_set.load()) {
             const cudaError_t e = cudaFuncSetAttribute(obj_kernel<D, VEC, TRIAL, GDOT, TI>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
             if (e != cudaSuccess) return e;
-            attr_set = true;
+            attr_set.store(true);
         }
         lc.dynamicSmemBytes = ring;
     }
