@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spml", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the library time launch shapes and PCG paths on first use (warm-up steps)")
     ap.add_argument("--cpu-sample-frames", type=int, default=25)
     ap.add_argument("--image-dtype", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of the image pyramid and of the solver's grad T (arithmetic stays FP32)")
@@ -294,7 +296,8 @@ def run_native(args):
     R, spec = make_sequence(args.workload, seed_offset=rank)
     mode = S.MODE_STML if args.mode == "stml" else S.MODE_SPML
     prm = S.stml_default_params(n_levels=L, n_tlevels=Q,
-                                image_dtype={"f32": 0, "f16": 1, "bf16": 2}[args.image_dtype])
+                                image_dtype={"f32": 0, "f16": 1, "bf16": 2}[args.image_dtype],
+                                autotune=int(args.autotune))
     stream = torch.cuda.current_stream(dev)
     ctx = S.Context(prm, stream.cuda_stream)
     R_dev = torch.from_numpy(R).to(dev)
@@ -332,6 +335,7 @@ def run_native(args):
     step()
     table = S.stml_profile_report(ctx.ptr)
     S.stml_profile_enable(ctx.ptr, 0)
+    tuning = S.stml_tuning_report(ctx.ptr) if args.autotune else None
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms_total = max_over_ranks(sum(ms_steps), world, dev)
     frames_all = sum_over_ranks(float(n * args.steps), world, dev)
@@ -429,7 +433,7 @@ def run_native(args):
                 "config": {"workload": f"{args.workload}: {n} frames {shape[0]}x{shape[1]} fp32, "
                                        f"{L} spatial x {Q} temporal levels, {args.mode.upper()}",
                            "n_frames": n, "shape": list(shape), "levels": L, "tlevels": Q,
-                           "mode": args.mode, "image_storage": args.image_dtype,
+                           "mode": args.mode, "image_storage": args.image_dtype, "autotune": bool(args.autotune),
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "clocks": clk.summary(), "gpu_launches": launches,
@@ -441,7 +445,7 @@ def run_native(args):
                 "per_step_ms": ms_steps,
                 "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
                                                  "ls_trials", "stopped_early")} for s in stats],
-                "spml": spml, "batch": batch}
+                "spml": spml, "batch": batch, "tuning": tuning}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -88,6 +88,13 @@ typedef struct {
     int pcg_cooperative;     /* 1: small levels solve PCG in one cooperative launch;
                               * 0: always the streaming kernels (required by
                               * stml_register_batch) */
+    int autotune;            /* 1: the first call of each (level, frame count)
+                              * times the objective pass's launch shapes and,
+                              * for levels up to 2^23 pixel-frames, a
+                              * cooperative against a
+                              * streaming PCG solve, and keeps the fastest for
+                              * the context (reproducible within a context);
+                              * 0: built-in choices (default) */
 } stml_params;
 
 typedef struct {
@@ -281,6 +288,13 @@ stml_status stml_profile_read(stml_ctx* ctx, long long* launches, double* ms, do
  * bytes, NUL-terminated, truncated if short); *needed (may be NULL) receives
  * the full length plus one.  Synchronises the stream. */
 stml_status stml_profile_report(stml_ctx* ctx, char* buf, size_t cap, size_t* needed);
+
+/* The choices params.autotune made so far in this context, as JSON text:
+ * [{"what": "objective_shape", "level": l, "frames": n, "variant": v,
+ *   "vec": w, "splits": s}, {"what": "pcg_path", "level": l, "frames": n,
+ * "cooperative": 0|1}, ...] (variant 0 objective, 1 Armijo trial, 2 trial
+ * with <g, d>).  Same buffer protocol as stml_profile_report. */
+stml_status stml_tuning_report(const stml_ctx* ctx, char* buf, size_t cap, size_t* needed);
 
 /* Number of this library's kernel launches since the context was created. */
 long long stml_launch_count(const stml_ctx* ctx);

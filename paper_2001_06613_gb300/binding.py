@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("tol_J", C.c_double), ("tol_Y", C.c_double), ("tol_G", C.c_double),
                 ("g_abs", C.c_double), ("max_gn", C.c_int), ("tol_cg", C.c_double),
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double),
-                ("image_dtype", C.c_int), ("pcg_cooperative", C.c_int)]
+                ("image_dtype", C.c_int), ("pcg_cooperative", C.c_int), ("autotune", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,6 +88,7 @@ _SIGS = {
     "stml_profile_read": (C.c_int, [_vp, C.POINTER(C.c_longlong), _dp, _dp, _dp]),
     "stml_profile_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "stml_launch_count": (C.c_longlong, [_vp]),
+    "stml_tuning_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
 }
 
 
@@ -346,6 +347,15 @@ def stml_profile_report(ctx) -> list:
     _check(load().stml_profile_report(ctx, None, 0, C.byref(need)), ctx)
     buf = C.create_string_buffer(need.value)
     _check(load().stml_profile_report(ctx, buf, need.value, C.byref(need)), ctx)
+    return json.loads(buf.value.decode())
+
+
+def stml_tuning_report(ctx) -> list:
+    import json
+    need = C.c_size_t()
+    _check(load().stml_tuning_report(ctx, None, 0, C.byref(need)), ctx)
+    buf = C.create_string_buffer(need.value)
+    _check(load().stml_tuning_report(ctx, buf, need.value, C.byref(need)), ctx)
     return json.loads(buf.value.decode())
 
 

@@ -83,6 +83,10 @@ struct stml_ctx {
     std::vector<ProfEvent> ev;
     size_t ev_used = 0;
     std::map<int, std::array<double, 3>> pacc;   // key -> launches, bytes, pixel-frames
+    // autotuned choices (params.autotune): objective-pass launch shape per
+    // (level, nK, variant) and cooperative (1) or streaming (0) PCG per (level, nK)
+    std::map<std::array<int, 3>, ObjShapeChoice> obj_tuned;
+    std::map<std::array<int, 2>, int> coop_tuned;
 
     std::string err;
 };
@@ -137,6 +141,7 @@ bool valid_params(const stml_params* p, std::string& why) {
     if (p->max_gn < 0 || p->max_cg < 0 || p->max_ls < 1) { why = "iteration limits out of range"; return false; }
     if (!(p->tol_cg > 0) || !(p->armijo_c > 0 && p->armijo_c < 1)) { why = "tol_cg > 0 and 0 < armijo_c < 1"; return false; }
     if (p->pcg_cooperative != 0 && p->pcg_cooperative != 1) { why = "pcg_cooperative must be 0 or 1"; return false; }
+    if (p->autotune != 0 && p->autotune != 1) { why = "autotune must be 0 or 1"; return false; }
     if (p->image_dtype < STML_DTYPE_F32 || p->image_dtype > STML_DTYPE_BF16) {
         why = "image_dtype must be STML_DTYPE_F32, _F16 or _BF16";
         return false;
@@ -288,6 +293,56 @@ stml_status hessvec_launch(stml_ctx* c, int level, const Geom& g, const FrameSet
     return STML_OK;
 }
 
+// ------------------------------------------------------------------ autotuning
+// Launch shape of the objective pass for (level, nK, variant: 0 plain, 1
+// trial, 2 trial with <g, d>): nullptr (the built-in choice) unless
+// params.autotune.  The first call of a key times every candidate shape on
+// these very arguments (one warm-up and two timed launches each, CUDA events
+// on the context's stream) and keeps the fastest for the context's lifetime,
+// so results stay reproducible within a context.
+const ObjShapeChoice* obj_choice(stml_ctx* c, int level, const Geom& g, const FrameSet& fs, const Coef& cf,
+                                 const Stored& T, const float* u, const float* du, float t, const float* gdot,
+                                 int variant) {
+    if (!c->p.autotune) return nullptr;
+    const std::array<int, 3> key{level, fs.nK, variant};
+    auto it = c->obj_tuned.find(key);
+    if (it != c->obj_tuned.end()) return &it->second;
+    ObjShapeChoice cand[16];
+    const int nc = obj_shape_candidates(g, fs.nK, cand, 16);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return nullptr;
+    float best = 1e30f;
+    ObjShapeChoice pick{0, 0};
+    for (int i = 0; i < nc; ++i) {
+        // scratch outputs: the frame means and totals of queued launches stay
+        // untouched (w_m1 / w_m2 are rewritten by every PCG start)
+        auto go = [&]() {
+            return launch_objective(T, g, fs, cf, u, du, t, gdot, c->w_m1, c->w_m2, c->partials, c->partials_cap,
+                                    &c->S->ticket[0], c->S->dots, c->stream, nullptr, &cand[i]);
+        };
+        if (go() != cudaSuccess) {   // a shape these arrays do not allow
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(a, c->stream);
+        const bool ok = go() == cudaSuccess && go() == cudaSuccess;
+        cudaEventRecord(b, c->stream);
+        float ms = 0.f;
+        if (!ok || cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (ms < best) {
+            best = ms;
+            pick = cand[i];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (pick.vec == 0) return nullptr;
+    return &(c->obj_tuned[key] = pick);
+}
+
 // ------------------------------------------------------------------ GIR
 // Gauss-Newton on the frames K of `level`, from and into u (nK * d * N floats).
 stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_io, stml_stats* st) {
@@ -325,8 +380,10 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     // objective + gradient at u (start of the GIR)
     auto eval_full = [&]() -> stml_status {
         long pe = prof_begin(c, PC_TRIAL, level);
-        CK(c, launch_objective(Stored{L.img, c->img_type}, g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
-                               c->partials_cap, &S->ticket[0], S->red, c->stream));
+        const ObjShapeChoice* sh0 = obj_choice(c, level, g, fs, cf, Stored{L.img, c->img_type}, u, nullptr, 0.f,
+                                               nullptr, 0);
+        CK(c, launch_objective(Stored{L.img, c->img_type}, g, fs, cf, u, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar,
+                               c->partials, c->partials_cap, &S->ticket[0], S->red, c->stream, nullptr, sh0));
         prof_end(c, pe, pfK * B_obj, pfK);
         pe = prof_begin(c, PC_EVAL, level);
         CK(c, launch_gradient(Stored{L.img, c->img_type}, g, fs, cf, u, nullptr, 0.f, c->w_abar, c->w_ubar, c->w_g,
@@ -394,7 +451,7 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         if (!init_ran) prof_discount(c, PC_PCG_INIT, level, 1, pfK * B_init, pfK);
     };
     // With gate != nullptr the solve starts only if the device accepted a step.
-    const bool coop = p.pcg_cooperative && pcg_coop_preferred(g, nK);
+    bool coop = p.pcg_cooperative && pcg_coop_preferred(g, nK);
     auto start_cg = [&](const int* gate = nullptr) -> stml_status {
         if (coop) {
             pe = prof_begin(c, PC_PCG_COOP, level);
@@ -412,8 +469,51 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         return launch_cg(std::min(p.max_cg, std::max(2, predict_cg)));
     };
 
+    // params.autotune: time a cooperative and a streaming solve of the first
+    // system of this (level, nK) and keep the faster path for the context
+    auto tune_coop = [&]() -> stml_status {
+        const std::array<int, 2> key{level, nK};
+        const auto it = c->coop_tuned.find(key);
+        if (it != c->coop_tuned.end()) {
+            coop = it->second != 0;
+            return STML_OK;
+        }
+        cudaEvent_t a = nullptr, b = nullptr;
+        CK(c, cudaEventCreate(&a));
+        CK(c, cudaEventCreate(&b));
+        float t_coop = 1e30f, t_str = 1e30f;
+        CK(c, cudaEventRecord(a, c->stream));
+        CK(c, launch_pcg_coop(g, fs, cf, c->w_g, dTs, pb, c->partials, c->partials_cap, S, pa, c->stream));
+        CK(c, cudaEventRecord(b, c->stream));
+        CK(c, cudaEventSynchronize(b));
+        CK(c, cudaEventElapsedTime(&t_coop, a, b));
+        CK(c, cudaEventRecord(a, c->stream));
+        CK(c, launch_pcg_init(g, fs, cf, c->w_g, dTs, pb, c->partials, c->partials_cap, S, pa, c->stream));
+        int done = 0;
+        for (int chunk = std::min(p.max_cg, std::max(2, predict_cg)); done < p.max_cg;
+             chunk = std::min(4, p.max_cg - done)) {
+            for (int i = 0; i < chunk; ++i) {
+                CK(c, launch_pcg_apply(g, fs, cf, dTs, pb, c->partials, c->partials_cap, S, c->stream));
+                CK(c, launch_pcg_update(g, fs, cf, dTs, pb, c->partials, c->partials_cap, S, pa, c->stream));
+                CK(c, launch_pcg_direction(g, fs, cf, dTs, pb, S, c->stream));
+            }
+            done += chunk;
+            TRY(read_scalars(c));
+            if (!c->Sh->cg_active) break;
+        }
+        CK(c, cudaEventRecord(b, c->stream));
+        CK(c, cudaEventSynchronize(b));
+        CK(c, cudaEventElapsedTime(&t_str, a, b));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        coop = t_coop <= t_str;
+        c->coop_tuned[key] = coop ? 1 : 0;
+        return STML_OK;
+    };
+
     bool started = false;     // a PCG solve (with its first chunk) is already queued and read
     if (!should_stop()) {
+        if (p.autotune && p.pcg_cooperative && (long long)g.N * nK <= (1LL << 23)) TRY(tune_coop());
         TRY(start_cg());
         TRY(read_scalars(c));
         started = true;
@@ -447,9 +547,12 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         auto queue_trial = [&](int k) -> stml_status {
             const double t = std::ldexp(1.0, -k);
             const LineSearchArgs la{S, k, J, p.armijo_c};
+            const ObjShapeChoice* sh = obj_choice(c, level, g, fs, cf, Stored{L.img, c->img_type}, u, c->w_x,
+                                                  (float)t, k == 0 ? c->w_g : nullptr, k == 0 ? 2 : 1);
             pe = prof_begin(c, PC_TRIAL, level);
-            CK(c, launch_objective(Stored{L.img, c->img_type}, g, fs, cf, u, c->w_x, (float)t, k == 0 ? c->w_g : nullptr, c->w_abar,
-                                   c->w_ubar, c->partials, c->partials_cap, &S->ticket[0], S->trial, c->stream, &la));
+            CK(c, launch_objective(Stored{L.img, c->img_type}, g, fs, cf, u, c->w_x, (float)t, k == 0 ? c->w_g : nullptr,
+                                   c->w_abar, c->w_ubar, c->partials, c->partials_cap, &S->ticket[0], S->trial,
+                                   c->stream, &la, sh));
             prof_end(c, pe, pfK * (k == 0 ? B_trial0 : B_trial), pfK);
             return STML_OK;
         };
@@ -708,6 +811,7 @@ void stml_default_params(stml_params* p) {
     p->armijo_c = 1e-4;
     p->image_dtype = STML_DTYPE_F32;
     p->pcg_cooperative = 1;
+    p->autotune = 0;
 }
 
 stml_status stml_create(const stml_params* p, void* cuda_stream, stml_ctx** out) {
@@ -1069,8 +1173,10 @@ stml_status stml_eval_trial(stml_ctx* c, int level, const int* frames, int nK, c
     const double pfK = (double)nK * L.g.N;
     const double bS = (double)store_bytes(c->img_type);
     const long pe = prof_begin(c, PC_TRIAL, level);
+    const ObjShapeChoice* sh = obj_choice(c, level, L.g, fs, cf, Stored{L.img, c->img_type}, u, d, (float)t, gd,
+                                          gd ? 2 : 1);
     CK(c, launch_objective(Stored{L.img, c->img_type}, L.g, fs, cf, u, d, (float)t, gd, c->w_abar, c->w_ubar,
-                           c->partials, c->partials_cap, &c->S->ticket[0], c->S->trial, c->stream));
+                           c->partials, c->partials_cap, &c->S->ticket[0], c->S->trial, c->stream, nullptr, sh));
     prof_end(c, pe, pfK * (bS + (gd ? 16.0 : 8.0) * L.g.d), pfK);
     TRY(read_scalars(c));
     for (int i = 0; i < 8; ++i) out[i] = c->Sh->trial[i];
@@ -1282,6 +1388,35 @@ stml_status stml_profile_report(stml_ctx* c, char* buf, size_t cap, size_t* need
         const size_t n = std::min(cap - 1, out.size());
         std::memcpy(buf, out.data(), n);
         buf[n] = 0;
+    }
+    return STML_OK;
+}
+
+stml_status stml_tuning_report(const stml_ctx* c, char* buf, size_t cap, size_t* needed) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    std::string out = "[";
+    char line[256];
+    bool first = true;
+    for (const auto& kv : c->obj_tuned) {
+        std::snprintf(line, sizeof(line),
+                      "%s{\"what\": \"objective_shape\", \"level\": %d, \"frames\": %d, \"variant\": %d, "
+                      "\"vec\": %d, \"splits\": %d}",
+                      first ? "" : ", ", kv.first[0], kv.first[1], kv.first[2], kv.second.vec, kv.second.splits);
+        out += line;
+        first = false;
+    }
+    for (const auto& kv : c->coop_tuned) {
+        std::snprintf(line, sizeof(line), "%s{\"what\": \"pcg_path\", \"level\": %d, \"frames\": %d, \"cooperative\": %d}",
+                      first ? "" : ", ", kv.first[0], kv.first[1], kv.second);
+        out += line;
+        first = false;
+    }
+    out += "]";
+    if (needed) *needed = out.size() + 1;
+    if (buf && cap > 0) {
+        const size_t k = std::min(cap - 1, out.size());
+        std::memcpy(buf, out.data(), k);
+        buf[k] = 0;
     }
     return STML_OK;
 }

@@ -631,25 +631,40 @@ struct ObjShape {
     unsigned runs;
 };
 
-ObjShape obj_shape(const Geom& g, int nK, int vec_max) {
-    constexpr int FG = kThreads / 32;
+// Built-in launch shape (measured with the autotuner on 32^2 .. 256^2 levels
+// of 51 .. 200 frames): about 256 CTAs, from the widest pixel runs that reach
+// it with at most 4 frame splits; Armijo trials (field and step staged, twice
+// the ring) at most 2 pixels per lane in 2-D.
+ObjShape obj_shape(const Geom& g, int nK, int vec_max, bool trial) {
+    constexpr int FG = kThreads / 32, kTarget = 256, kMaxSplit = 4;
+    if (g.d == 2 && trial) vec_max = std::min(vec_max, 2);
+    const int max_split = std::max(1, std::min(kMaxSplit, (nK + FG - 1) / FG));
     ObjShape sh{1, 1, 0};
-    int slots = 0;
     for (int v : {4, 2, 1}) {
-        if (v > vec_max || g.nx % v) continue;
-        slots = 152 * obj_min_blocks(g.d, v);   // resident CTAs of obj_kernel on a GB300
+        if (v > vec_max || g.nx % v || (g.d == 3 && v == 4)) continue;
         sh.vec = v;
         sh.runs = (unsigned)((g.N + 32LL * v - 1) / (32LL * v));
-        if (sh.runs >= (unsigned)slots) break;
+        if ((long long)sh.runs * max_split >= kTarget) break;
     }
-    const int max_split = std::max(1, std::min(8, (nK + FG - 1) / FG));
-    sh.splits = (int)std::min<long long>(max_split, ((long long)slots + sh.runs - 1) / sh.runs);
+    sh.splits = (int)std::min<long long>(max_split, ((long long)kTarget + sh.runs - 1) / sh.runs);
     return sh;
 }
 
+int obj_shape_candidates(const Geom& g, int nK, ObjShapeChoice* out, int cap) {
+    constexpr int FG = kThreads / 32;
+    const int max_split = std::max(1, std::min(8, (nK + FG - 1) / FG));
+    int n = 0;
+    for (int v : {4, 2, 1}) {
+        if (g.nx % v || (g.d == 3 && v == 4)) continue;
+        for (int sp : {1, 2, 4, 8})
+            if (sp <= max_split && n < cap) out[n++] = ObjShapeChoice{v, sp};
+    }
+    return n;
+}
+
 size_t eval_partials(const Geom& g, int nK) {
-    const ObjShape sh = obj_shape(g, nK < 1 ? 1 : nK, 1);   // the most runs any launch uses
-    const size_t obj = (size_t)sh.runs * 8 * 8;              // every split count up to 8
+    const ObjShape sh = obj_shape(g, nK < 1 ? 1 : nK, 1, false);   // the most runs any launch uses
+    const size_t obj = (size_t)sh.runs * 8 * 8;                     // every split count up to 8
     return obj > (size_t)kGridStride * 2 ? obj : (size_t)kGridStride * 2;
 }
 
@@ -697,7 +712,7 @@ static cudaError_t obj_mode(const ObjShape& sh, cudaStream_t s, const TI* T, con
 cudaError_t launch_objective(const Stored& T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                              const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
                              size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s,
-                             const LineSearchArgs* lsp) {
+                             const LineSearchArgs* lsp, const ObjShapeChoice* force) {
     const PixIndex pi{FastDiv::make((unsigned)g.nx), FastDiv::make((unsigned)g.ny)};
     const LineSearchArgs ls = lsp ? *lsp : LineSearchArgs{nullptr, 0, 0.0, 0.0};
     if (ls.S && ls.k == 0 && !gdot) return cudaErrorInvalidValue;
@@ -705,7 +720,15 @@ cudaError_t launch_objective(const Stored& T, const Geom& g, const FrameSet& fs,
     int vec_max = g.d == 3 ? 2 : 4;
     for (const void* q : {(const void*)u, (const void*)du, (const void*)gdot})
         if (q && ((uintptr_t)q & 15u)) vec_max = (uintptr_t)q & 7u ? 1 : std::min(vec_max, 2);
-    const ObjShape sh = obj_shape(g, fs.nK, vec_max);
+    ObjShape sh = obj_shape(g, fs.nK, vec_max, du != nullptr);
+    if (force) {   // a tuned shape: valid for these arrays and this level, else refused
+        if (force->vec > vec_max || g.nx % force->vec || force->splits < 1 || force->splits > 8 ||
+            (g.d == 3 && force->vec == 4))
+            return cudaErrorInvalidValue;
+        sh.vec = force->vec;
+        sh.splits = force->splits;
+        sh.runs = (unsigned)((g.N + 32LL * sh.vec - 1) / (32LL * sh.vec));
+    }
     if ((size_t)sh.runs * sh.splits * 8 > partials_cap) return cudaErrorInvalidValue;
     if (gdot && !du) return cudaErrorInvalidValue;
     cudaError_t e = with_store_type(T.type, [&](auto tag) {

@@ -827,7 +827,9 @@ cudaError_t coop_go(const Geom& g, const FrameSet& fs, const Coef& cf, const flo
 
 }  // namespace
 
-bool pcg_coop_preferred(const Geom& g, int nK) { return (long long)g.N * nK <= (1LL << 20); }
+// Cooperative solves win up to about 2^21 pixel-frames (measured with the
+// autotuner on the paper-scale sequence).
+bool pcg_coop_preferred(const Geom& g, int nK) { return (long long)g.N * nK <= (1LL << 21); }
 
 cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const Stored& dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,

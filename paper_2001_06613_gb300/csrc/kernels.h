@@ -99,10 +99,18 @@ struct LineSearchArgs {
     double J;
     double c;
 };
+// Launch shape of the objective pass: pixels per lane (4, 2 or 1; 1 or 2 in
+// 3-D) and frame splits (1..8, one thread-block cluster per pixel run).
+struct ObjShapeChoice {
+    int vec;
+    int splits;
+};
+// The shapes an autotuner may try for this level and frame count.
+int obj_shape_candidates(const Geom& g, int nK, ObjShapeChoice* out, int cap);
 cudaError_t launch_objective(const Stored& T, const Geom& g, const FrameSet& fs, const Coef& cf, const float* u,
                              const float* du, float t, const float* gdot, float* abar, float* ubar, double* partials,
                              size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s,
-                             const LineSearchArgs* ls = nullptr);
+                             const LineSearchArgs* ls = nullptr, const ObjShapeChoice* shape = nullptr);
 // Gradient pass at u (or u + t du) with abar, ubar of the same point: g and
 // grad T, optionally the point itself (unew); |g|^2 and |u|^2 to out[4], out[5].
 // With gate != nullptr it runs only if gate->ls_accepted, with t = gate->ls_t.

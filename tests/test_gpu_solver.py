@@ -161,3 +161,33 @@ def test_single_frame_and_3d_sequence(S):
     Jg = multilevel.final_objective(R3.astype(np.float64), y3.astype(np.float64), op)["J"]
     Jo = multilevel.final_objective(R3.astype(np.float64), res.y, op)["J"]
     assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
+
+
+def test_autotune_is_reproducible_and_close(S, tiny):
+    """params.autotune: the tuned launch shapes and PCG path are kept for the
+    context (a second registration is bit-identical) and the result stays
+    within the end-to-end tolerance of the built-in choices."""
+    import torch
+    spec, R = tiny
+    _, y_ref, prm = _register(S, R, 0, n_levels=2, n_tlevels=2)
+    ctx = _ctx(S, R, n_levels=2, n_tlevels=2, autotune=1)
+    try:
+        ys = []
+        for _ in range(2):
+            S.stml_load_sequence(ctx.ptr, torch.from_numpy(R).cuda())
+            S.stml_build_pyramid(ctx.ptr)
+            S.stml_register(ctx.ptr, 0)
+            y = np.empty_like(y_ref)
+            S.stml_get_field(ctx.ptr, 1, y)
+            ys.append(y)
+        assert np.array_equal(ys[0], ys[1])
+        table = S.stml_tuning_report(ctx.ptr)
+        assert any(e["what"] == "objective_shape" for e in table)
+        assert all(e["vec"] in (1, 2, 4) and 1 <= e["splits"] <= 8 for e in table if e["what"] == "objective_shape")
+        op = _oparams(prm)
+        J_ref = multilevel.final_objective(R.astype(np.float64), y_ref.astype(np.float64), op)["J"]
+        J_tun = multilevel.final_objective(R.astype(np.float64), ys[0].astype(np.float64), op)["J"]
+        assert abs(J_tun - J_ref) <= 1e-2 * J_ref, (J_tun, J_ref)
+        assert float(np.sqrt(np.mean((ys[0] - y_ref) ** 2))) <= 0.05
+    finally:
+        ctx.close()
