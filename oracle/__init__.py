@@ -21,9 +21,15 @@ Layout of the oracle:
                     by a dense solve.
 * ``multilevel`` -- image pyramid, STML predictor-corrector driver with the
                     stopping rule of eq. (3), and the spatial-only (SpML) driver.
+* ``net``        -- the learned temporal predictor: a convolutional
+                    encoder-decoder proposing a skipped frame's field from its
+                    two registered neighbours and three images (in place of
+                    the predictors of Sec. 3 where the objective says it is
+                    better), its MSE loss, gradient and Adam update, with an
+                    optional BF16 rounding of the convolution operands.
 
 Every function works in float64 on numpy arrays.  Where the paper is silent the
 oracle follows one stated reading, documented on the function.
 """
 from .params import Params  # noqa: F401
-from . import grid, objective, solver, predictor, multilevel  # noqa: F401
+from . import grid, objective, solver, predictor, multilevel, net  # noqa: F401

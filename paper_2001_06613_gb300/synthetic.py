@@ -259,3 +259,25 @@ def random_field(rng: np.random.Generator, n: int, d: int, shape: Sequence[int],
     if rough > 0:
         out += rough * rng.normal(size=out.shape)
     return out.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# initial weights of the learned predictor's network (drawn here, passed in)
+# ---------------------------------------------------------------------------
+NET_CONVS = [(7, 32), (32, 32), (32, 64), (64, 64), (64, 96), (96, 96), (96, 128), (128, 128),
+             (224, 96), (96, 96), (160, 64), (64, 64), (96, 32), (32, 32)]
+
+
+def net_init_params(seed: int, head_scale: float = 0.0) -> np.ndarray:
+    """Flat float32 parameter vector of the predictor network: He-normal conv
+    weights W[ky][kx][ci][co] (sd sqrt(2 / (9 ci))), zero biases, and a head
+    (W[32][2], b[2]) of normal(0, head_scale / sqrt(32)) weights -- zero by
+    default, so that the untrained network reproduces linear interpolation."""
+    g = philox(seed, 7)
+    parts = []
+    for ci, co in NET_CONVS:
+        parts.append(g.normal(scale=math.sqrt(2.0 / (9 * ci)), size=9 * ci * co))
+        parts.append(np.zeros(co))
+    parts.append(g.normal(scale=head_scale / math.sqrt(32.0), size=64))
+    parts.append(np.zeros(2))
+    return np.concatenate(parts).astype(np.float32)
