@@ -104,6 +104,13 @@ typedef struct {
     int status;              /* stml_status of the GIR (0, ELINESEARCH, EBREAKDOWN ...) */
     double J0, J, D, S, P;   /* objective at start and end of the GIR */
     double seconds;          /* wall time of the GIR on the stream */
+    /* learned predictor (stml_net.h): -1 no learned proposal was made, 0 the
+     * classical proposal was kept, 1 the learned one (lower objective) */
+    int pred_learned;        /* for the start of this GIR */
+    int fill_learned;        /* for the fill after eq. (3) ended the level here */
+    double J0_classic;       /* objective at the classical start (pred_learned >= 0) */
+    double J_fill_classic;   /* objective over all frames at the classical fill */
+    double J_fill;           /* ... and at the kept fill (fill_learned >= 0) */
 } stml_stats;
 
 /* Fills *p with the library defaults (alpha 0.02, lambda 1, beta 1e-5, ...). */

@@ -46,10 +46,24 @@ class Stats(C.Structure):
                 ("gn_iters", C.c_int), ("cg_iters", C.c_int), ("ls_trials", C.c_int),
                 ("stopped_early", C.c_int), ("status", C.c_int),
                 ("J0", C.c_double), ("J", C.c_double), ("D", C.c_double), ("S", C.c_double),
-                ("P", C.c_double), ("seconds", C.c_double)]
+                ("P", C.c_double), ("seconds", C.c_double),
+                ("pred_learned", C.c_int), ("fill_learned", C.c_int), ("J0_classic", C.c_double),
+                ("J_fill_classic", C.c_double), ("J_fill", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class NetSample(C.Structure):
+    """stml_net_sample (include/stml_net.h): device pointers of one sample."""
+    _fields_ = [("y_l", C.c_void_p), ("y_r", C.c_void_p), ("T_l", C.c_void_p), ("T_k", C.c_void_p),
+                ("T_r", C.c_void_p), ("target", C.c_void_p), ("out", C.c_void_p),
+                ("plane", C.c_longlong), ("ld", C.c_int), ("ld_img", C.c_int),
+                ("w_l", C.c_float), ("h", C.c_float)]
+
+
+class Adam(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double)]
 
 
 _lib = None
@@ -89,6 +103,20 @@ _SIGS = {
     "stml_profile_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "stml_launch_count": (C.c_longlong, [_vp]),
     "stml_tuning_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    # learned temporal predictor (include/stml_net.h)
+    "stml_net_param_count": (C.c_size_t, []),
+    "stml_net_create": (C.c_int, [_fp, C.c_size_t, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
+    "stml_net_destroy": (None, [_vp]),
+    "stml_net_last_error": (C.c_char_p, [_vp]),
+    "stml_net_set_params": (C.c_int, [_vp, _fp, C.c_size_t]),
+    "stml_net_get_params": (C.c_int, [_vp, _fp, C.c_size_t]),
+    "stml_net_forward": (C.c_int, [_vp, C.POINTER(NetSample), C.c_int, C.c_int, C.c_int]),
+    "stml_net_loss_grad": (C.c_int, [_vp, C.POINTER(NetSample), C.c_int, C.c_int, C.c_int, _dp, _fp]),
+    "stml_net_train_step": (C.c_int, [_vp, C.POINTER(NetSample), C.c_int, C.c_int, C.c_int,
+                                      C.POINTER(Adam), _dp]),
+    "stml_set_predictor_net": (C.c_int, [_vp, _vp]),
+    "stml_net_conv3_block": (C.c_int, [C.c_int, _fp, _fp, _fp, _fp, _fp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.c_int, _vp]),
 }
 
 
@@ -380,3 +408,111 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------- learned temporal predictor
+def stml_net_param_count() -> int:
+    return int(load().stml_net_param_count())
+
+
+def _net_check(status: int, net=None):
+    if status != 0:
+        msg = load().stml_net_last_error(net).decode() if net else stml_last_error(None)
+        raise StmlError(status, msg)
+
+
+def _f32_host(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"expected {n} parameters, got {a.size}")
+    return a
+
+
+def net_samples(y_l, y_r, T_l, T_k, T_r, h, w_l, target=None, out=None):
+    """NetSample array for a batch of contiguous CUDA tensors: fields (B, 2, H, W),
+    images (B, H, W), h and w_l per sample (sequences or scalars).  The tensors
+    must stay alive while the samples are used."""
+    B, _, H, W = y_l.shape
+    h = np.broadcast_to(np.asarray(h, dtype=np.float64), (B,))
+    w_l = np.broadcast_to(np.asarray(w_l, dtype=np.float64), (B,))
+    arr = (NetSample * B)()
+    fb, ib = 2 * H * W * 4, H * W * 4
+    ptrs = [_dev(t) if t is not None else None for t in (y_l, y_r, T_l, T_k, T_r, target, out)]
+    for b in range(B):
+        s = arr[b]
+        s.y_l, s.y_r = ptrs[0] + b * fb, ptrs[1] + b * fb
+        s.T_l, s.T_k, s.T_r = ptrs[2] + b * ib, ptrs[3] + b * ib, ptrs[4] + b * ib
+        s.target = ptrs[5] + b * fb if ptrs[5] else None
+        s.out = ptrs[6] + b * fb if ptrs[6] else None
+        s.plane, s.ld, s.ld_img = H * W, W, W
+        s.w_l, s.h = float(w_l[b]), float(h[b])
+    return arr
+
+
+class Net:
+    """A learned-predictor network (stml_net) with host parameters ``params``."""
+
+    def __init__(self, params, max_batch: int, max_h: int, max_w: int, stream=None):
+        n = stml_net_param_count()
+        out = _vp()
+        _net_check(load().stml_net_create(_f32_host(params, n).ctypes.data, n, int(max_batch), int(max_h),
+                                          int(max_w), _stream(stream), C.byref(out)))
+        self.ptr = out
+
+    def close(self):
+        if self.ptr:
+            load().stml_net_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stml_net_set_params(net: Net, params):
+    n = stml_net_param_count()
+    _net_check(load().stml_net_set_params(net.ptr, _f32_host(params, n).ctypes.data, n), net.ptr)
+
+
+def stml_net_get_params(net: Net) -> np.ndarray:
+    n = stml_net_param_count()
+    out = np.empty(n, np.float32)
+    _net_check(load().stml_net_get_params(net.ptr, out.ctypes.data, n), net.ptr)
+    return out
+
+
+def stml_net_forward(net: Net, samples, H: int, W: int):
+    _net_check(load().stml_net_forward(net.ptr, samples, len(samples), int(H), int(W)), net.ptr)
+
+
+def stml_net_loss_grad(net: Net, samples, H: int, W: int, want_grad: bool = True):
+    loss = C.c_double()
+    g = np.empty(stml_net_param_count(), np.float32) if want_grad else None
+    _net_check(load().stml_net_loss_grad(net.ptr, samples, len(samples), int(H), int(W), C.byref(loss),
+                                         g.ctypes.data if want_grad else None), net.ptr)
+    return loss.value, g
+
+
+def stml_net_train_step(net: Net, samples, H: int, W: int, lr: float = 1e-3, beta1: float = 0.9,
+                        beta2: float = 0.999, eps: float = 1e-8, want_loss: bool = True):
+    opt = Adam(lr, beta1, beta2, eps)
+    loss = C.c_double()
+    _net_check(load().stml_net_train_step(net.ptr, samples, len(samples), int(H), int(W), C.byref(opt),
+                                          C.byref(loss) if want_loss else None), net.ptr)
+    return loss.value if want_loss else None
+
+
+def stml_set_predictor_net(ctx, net: Optional[Net]):
+    ptr = ctx.ptr if hasattr(ctx, "ptr") else ctx
+    _check(load().stml_set_predictor_net(ptr, net.ptr if net is not None else None), ptr)
+
+
+def stml_net_conv3_block(mode: int, x, a, W, b, y, stream=None):
+    """One convolution of the network on channels-last CUDA tensors (see stml_net.h):
+    x (B, H, W, C), W (3, 3, Cin, Cout), b (Cout,)."""
+    Bn, H, Wd = x.shape[:3]
+    Cin, Cout = W.shape[2], W.shape[3]
+    _check(load().stml_net_conv3_block(int(mode), _dev(x), _dev(a), _dev(W), _dev(b), _dev(y), Bn, H, Wd,
+                                       Cin, Cout, _stream(stream)))

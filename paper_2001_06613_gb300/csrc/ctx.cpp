@@ -17,7 +17,9 @@
 #include <vector>
 
 #include "../../include/stml.h"
+#include "../../include/stml_net.h"
 #include "kernels.h"
+#include "net.h"
 
 using namespace stml;
 
@@ -87,6 +89,11 @@ struct stml_ctx {
     // (level, nK, variant) and cooperative (1) or streaming (0) PCG per (level, nK)
     std::map<std::array<int, 3>, ObjShapeChoice> obj_tuned;
     std::map<std::array<int, 2>, int> coop_tuned;
+
+    // learned temporal predictor (stml_set_predictor_net) and its last decisions
+    ::stml_net* net = nullptr;
+    int pred_learned = -1;
+    double J0_classic = 0.0;
 
     std::string err;
 };
@@ -241,12 +248,12 @@ stml_status read_scalars(stml_ctx* c) {
 
 enum ProfClass {
     PC_HESS = 0, PC_EVAL, PC_TRIAL, PC_PCG_INIT, PC_PCG_UPDATE, PC_PCG_P, PC_PCG_COOP,
-    PC_PRED_LS, PC_PRED_LIN, PC_PROLONG, PC_GATHER, PC_RESTRICT, PC_COUNT
+    PC_PRED_LS, PC_PRED_LIN, PC_PROLONG, PC_GATHER, PC_RESTRICT, PC_PRED_NET, PC_COUNT
 };
 const char* const kProfNames[PC_COUNT] = {
     "gn_hessian_product", "gradient_pass", "objective_pass", "pcg_init", "pcg_update",
     "pcg_direction", "pcg_solve_cooperative", "predict_ls_eq2", "predict_linear", "prolong", "gather_scatter",
-    "restrict"};
+    "restrict", "predict_learned"};
 
 // Starts an event pair (returns its index, or -1 when profiling is off).
 long prof_begin(stml_ctx* c, int cls, int level) {
@@ -708,6 +715,78 @@ stml_status run_predict_linear(stml_ctx* c, const std::vector<int>& K, const std
     return STML_OK;
 }
 
+// ----------------------------------------------------------- learned predictor
+// Objective of eq. (1) over the frames K of `full` (fields of all frames).
+stml_status objective_of(stml_ctx* c, int level, const std::vector<int>& K, const float* full, double* J) {
+    LevelBuf& L = c->lv[level];
+    const size_t plane = (size_t)L.g.d * L.g.N;
+    TRY(upload_idx(c, K));
+    CK(c, launch_gather_planes(full, c->w_ut, c->d_idx, (int)K.size(), plane, c->stream));
+    FrameSet fs;
+    TRY(upload_frameset(c, K, fs));
+    const Coef cf = make_coef(L.g, c->p, (int)K.size());
+    CK(c, launch_objective(Stored{L.img, c->img_type}, L.g, fs, cf, c->w_ut, nullptr, 0.f, nullptr, c->w_abar,
+                           c->w_ubar, c->partials, c->partials_cap, &c->S->ticket[0], c->S->red, c->stream));
+    TRY(read_scalars(c));
+    *J = c->Sh->red[0];
+    return STML_OK;
+}
+
+// With a network attached: proposes the fields of `targets` (frames outside
+// Kp) from their registered neighbours in Kp (fields in K order in yK) and the
+// images, and keeps them in `dst` (fields of all frames, holding the classical
+// proposals) only if the objective over the frames Kj is lower with them.
+// *decision: -1 no proposal (no network, a 3-D sequence, a level larger than
+// the network's canvas, no target between two frames of Kp), 0 classical
+// kept, 1 learned kept; *J_classic and *J_kept the two objectives.
+stml_status learned_fill(stml_ctx* c, int level, const std::vector<int>& Kp, const float* yK,
+                         const std::vector<int>& targets, float* dst, const std::vector<int>& Kj, int* decision,
+                         double* J_classic, double* J_kept) {
+    *decision = -1;
+    LevelBuf& L = c->lv[level];
+    if (!c->net || c->d != 2 || targets.empty() || !net::fits(c->net, L.g.ny, L.g.nx)) return STML_OK;
+    const size_t plane = (size_t)L.g.d * L.g.N;
+    const size_t img_frame = (size_t)L.g.N * store_bytes(c->img_type);
+    const char* img = static_cast<const char*>(L.img);
+    std::vector<net::Sample> smp;
+    std::vector<int> used;
+    for (int k : targets) {
+        auto it = std::upper_bound(Kp.begin(), Kp.end(), k);
+        if (it == Kp.begin() || it == Kp.end() || *(it - 1) == k) continue;
+        const int r = *it, l = *(it - 1);
+        const size_t il = (size_t)(it - 1 - Kp.begin()), ir = (size_t)(it - Kp.begin());
+        smp.push_back(net::Sample{yK + il * plane, yK + ir * plane, img + (size_t)l * img_frame,
+                                  img + (size_t)k * img_frame, img + (size_t)r * img_frame, nullptr,
+                                  c->w_z2 + (size_t)k * plane, (long long)L.g.N, L.g.nx, L.g.nx, c->img_type,
+                                  (float)(r - k) / (float)(r - l), (float)L.g.h});
+        used.push_back(k);
+    }
+    if (smp.empty()) return STML_OK;
+    const long pe = prof_begin(c, PC_PRED_NET, level);
+    CK(c, cudaMemcpyAsync(c->w_z2, dst, (size_t)c->n * plane * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    const int mb = net::max_batch(c->net);
+    for (size_t b = 0; b < smp.size(); b += mb) {
+        const int nb = (int)std::min(smp.size() - b, (size_t)mb);
+        CK(c, net::forward_on(c->net, smp.data() + b, nb, L.g.ny, L.g.nx, c->stream));
+    }
+    prof_end(c, pe, 0.0, (double)smp.size() * L.g.N);
+    double Jc = 0.0, Jn = 0.0;
+    TRY(objective_of(c, level, Kj, dst, &Jc));
+    TRY(objective_of(c, level, Kj, c->w_z2, &Jn));
+    *J_classic = Jc;
+    if (std::isfinite(Jn) && Jn < Jc) {
+        for (int k : used)
+            CK(c, cudaMemcpyAsync(dst + (size_t)k * plane, c->w_z2 + (size_t)k * plane, plane * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+        *decision = 1;
+        *J_kept = Jn;
+    } else {
+        *decision = 0;
+        *J_kept = Jc;
+    }
+    return STML_OK;
+}
+
 // ------------------------------------------------------------------ STML steps
 stml_status do_predict(stml_ctx* c, int level, int q) {
     LevelBuf& L = c->lv[level];
@@ -738,6 +817,12 @@ stml_status do_predict(stml_ctx* c, int level, int q) {
         TRY(run_predict_ls(c, Kp, c->w_u, c->w_z, c->w_z2, plane));
         std::swap(c->w_z, c->w_z2);
     }
+    if (c->net) {
+        std::vector<int> fresh;
+        std::set_difference(c->sets[q].begin(), c->sets[q].end(), Kp.begin(), Kp.end(), std::back_inserter(fresh));
+        double Jk = 0.0;
+        TRY(learned_fill(c, level, Kp, c->w_u, fresh, c->w_z, c->sets[q], &c->pred_learned, &c->J0_classic, &Jk));
+    }
     return STML_OK;
 }
 
@@ -755,6 +840,10 @@ stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finis
     stml_stats s{};
     TRY(run_gir(c, level, K, c->w_u, &s));
     s.tlevel = q;
+    s.pred_learned = c->pred_learned;
+    s.J0_classic = s.pred_learned >= 0 ? c->J0_classic : s.J0;
+    s.fill_learned = -1;
+    c->pred_learned = -1;
     const double dhat = s.D / (double)K.size();
     const bool stop = q > 0 && c->p.stop_rule &&
                       std::fabs(dhat - c->dhat_prev) <= c->p.eps_stop * std::fabs(c->dhat_prev);
@@ -774,6 +863,11 @@ stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finis
             TRY(run_predict_ls(c, K, c->w_u, c->w_z, L.y, plane));
             TRY(upload_idx(c, K));
             CK(c, launch_scatter_planes(c->w_u, L.y, c->d_idx, (int)K.size(), plane, c->stream));
+        }
+        if (c->net) {
+            std::vector<int> rest;
+            std::set_difference(all.begin(), all.end(), K.begin(), K.end(), std::back_inserter(rest));
+            TRY(learned_fill(c, level, K, c->w_u, rest, L.y, all, &s.fill_learned, &s.J_fill_classic, &s.J_fill));
         }
         done = 1;
     }
@@ -1091,6 +1185,13 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
     return STML_OK;
 }
 
+stml_status stml_set_predictor_net(stml_ctx* c, stml_net* net) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    c->net = net;
+    c->pred_learned = -1;
+    return STML_OK;
+}
+
 stml_status stml_register_batch(stml_ctx* const* ctxs, int n_ctx, stml_mode mode, int max_threads,
                                 stml_status* status) {
     if (!ctxs || n_ctx < 1) return fail(nullptr, STML_EINVAL, "stml_register_batch: need contexts");
@@ -1100,9 +1201,12 @@ stml_status stml_register_batch(stml_ctx* const* ctxs, int n_ctx, stml_mode mode
         if (!c->built) return fail(nullptr, STML_ESTATE, "stml_register_batch: a context has no pyramid");
         if (c->p.pcg_cooperative)
             return fail(nullptr, STML_EINVAL, "stml_register_batch: contexts need pcg_cooperative = 0");
-        for (int k = 0; k < i; ++k)
+        for (int k = 0; k < i; ++k) {
             if (ctxs[k] == c || (c->stream && ctxs[k]->stream == c->stream))
                 return fail(nullptr, STML_EINVAL, "stml_register_batch: contexts share a stream");
+            if (c->net && ctxs[k]->net == c->net)
+                return fail(nullptr, STML_EINVAL, "stml_register_batch: contexts share a predictor network");
+        }
     }
     if (mode != STML_MODE_STML && mode != STML_MODE_SPML) return fail(nullptr, STML_EINVAL, "unknown mode");
     const int nt = std::max(1, std::min(n_ctx, max_threads > 0 ? max_threads : n_ctx));

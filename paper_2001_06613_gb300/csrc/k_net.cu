@@ -1,0 +1,872 @@
+// Learned temporal predictor: kernels of the convolutional encoder-decoder
+// (forward, backward, Adam, weight packing).  The network proposes the field
+// of a frame that the next temporal level adds (Sec. 3) from its two
+// registered neighbours and three images; the registration keeps a proposal
+// only where the objective of eq. (1) is lower there than at the classical
+// predictor's.
+//
+// Convolutions are implicit GEMMs on the tensor cores: BF16 operands staged
+// into shared memory by cp.async (zero-filled at the image border), loaded
+// with ldmatrix, multiplied by mma.sync m16n8k16 with FP32 accumulators.
+//   forward:        Y[p][co]  = sum_{tap, ci} X[p + off(tap)][ci] W[tap][ci][co]
+//   input gradient: dX[p][ci] = sum_{tap, co} G[p + off(tap)][co] W[8 - tap][ci][co]
+//                   (the same kernel with the flipped, transposed weights)
+//   weight grad.:   dW[tap][ci][co] = sum_p X[p + off(tap)][ci] G[p][co]
+//                   (split over pixel slices, slices summed in a fixed order)
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "net.h"
+
+namespace stml {
+namespace net {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 16-byte global -> shared copy; src_bytes = 0 writes zeros (src unread).
+__device__ __forceinline__ void cp16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// XOR swizzles of 16-byte segments: rows of 64 bytes (4 segments) and of
+// 128 bytes (8 segments); eight consecutive rows at one logical segment land
+// on 32 distinct banks, so ldmatrix phases are conflict-free.
+__device__ __forceinline__ int swz4(int row, int seg) { return seg ^ ((row >> 1) & 3); }
+__device__ __forceinline__ int swz8(int row, int seg) { return seg ^ (row & 7); }
+template <int BN>
+__device__ __forceinline__ int swzB(int row, int seg) {
+    return BN == 64 ? swz8(row, seg) : swz4(row, seg);
+}
+
+__device__ __forceinline__ float slope(float y) { return y > 0.f ? 1.f : kSlope; }
+__device__ __forceinline__ float leaky(float z) { return z > 0.f ? z : kSlope * z; }
+
+// Address of 8 input channels [ci, ci + 8) at pixel (n, yy, xx) of the
+// stacked sources, or nullptr outside the image.
+__device__ __forceinline__ const bf16* in_at(const ConvIn& in, int n, int yy, int xx, int H, int W,
+                                             int ci) {
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) return nullptr;
+    if (ci < in.ca) {
+        if (in.up)
+            return in.a + (((long long)n * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1)) * in.ca + ci;
+        return in.a + (((long long)n * H + yy) * W + xx) * in.ca + ci;
+    }
+    return in.b + (((long long)n * H + yy) * W + xx) * in.cb + (ci - in.ca);
+}
+
+// Unpacks 8 BF16 values.
+__device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float2 t = __bfloat1622float2(h[i]);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    return u;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ convolution
+template <int BN>
+struct ConvCfg {
+    static constexpr int BM = 128, BK = 32, STAGES = 3, THREADS = 128;
+    static constexpr int WARPS_N = BN / 32, WARPS_M = 4 / WARPS_N;
+    static constexpr int WM = BM / WARPS_M;
+    static constexpr int MI = WM / 16, NI = 4;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __restrict__ Wt, int Cin,
+                                                    int N, int B, int H, int W, ConvOut out) {
+    using C = ConvCfg<BN>;
+    __shared__ __align__(128) bf16 sA[C::STAGES][C::BM * C::BK];
+    __shared__ __align__(128) bf16 sB[C::STAGES][C::BK * BN];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp / C::WARPS_N, wn = warp % C::WARPS_N;
+    const long long HW = (long long)H * W;
+    const long long M = (long long)B * HW;
+    const long long m0 = (long long)blockIdx.x * C::BM;
+    const int n0 = blockIdx.y * BN;
+    const int cpt = Cin / 32, nchunks = 9 * cpt;
+
+    // the 4 rows (pixels) of the A tile this thread copies, one 8-channel segment each
+    const int aseg = tid & 3;
+    int an[4], ay[4], ax[4];
+    bool av[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long m = m0 + (tid >> 2) + 32 * i;
+        av[i] = m < M;
+        const long long mm = av[i] ? m : 0;
+        an[i] = (int)(mm / HW);
+        const int rem = (int)(mm - (long long)an[i] * HW);
+        ay[i] = rem / W;
+        ax[i] = rem - ay[i] * W;
+    }
+
+    auto load_stage = [&](int st, int j) {
+        const int tap = j / cpt;
+        const int ci = (j - tap * cpt) * 32 + aseg * 8;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = (tid >> 2) + 32 * i;
+            const bf16* src = av[i] ? in_at(in, an[i], ay[i] + dy, ax[i] + dx, H, W, ci) : nullptr;
+            cp16(&sA[st][r * 32 + (swz4(r, aseg) << 3)], src ? src : in.a, src ? 16 : 0);
+        }
+        constexpr int SEGS = BN / 8;
+#pragma unroll
+        for (int s = tid; s < 32 * SEGS; s += C::THREADS) {
+            const int row = s / SEGS, seg = s - row * SEGS;
+            cp16(&sB[st][row * BN + (swzB<BN>(row, seg) << 3)],
+                 Wt + (long long)(j * 32 + row) * N + n0 + seg * 8, 16);
+        }
+    };
+
+    float acc[C::MI][C::NI][4];
+#pragma unroll
+    for (int a = 0; a < C::MI; ++a)
+#pragma unroll
+        for (int b = 0; b < C::NI; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < C::STAGES - 1; ++s) {
+        if (s < nchunks) load_stage(s, s);
+        cp_commit();
+    }
+    for (int j = 0; j < nchunks; ++j) {
+        cp_wait<C::STAGES - 2>();
+        __syncthreads();
+        const int jn = j + C::STAGES - 1;
+        if (jn < nchunks) load_stage(jn % C::STAGES, jn);
+        cp_commit();
+        const bf16* a_s = sA[j % C::STAGES];
+        const bf16* b_s = sB[j % C::STAGES];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            uint32_t af[C::MI][4];
+#pragma unroll
+            for (int mi = 0; mi < C::MI; ++mi) {
+                const int row = wm * C::WM + mi * 16 + (lane & 15);
+                const int seg = kk * 2 + (lane >> 4);
+                ldsm_x4(af[mi], a_s + row * 32 + (swz4(row, seg) << 3));
+            }
+            uint32_t bfr[C::NI][2];
+#pragma unroll
+            for (int nb = 0; nb < C::NI / 2; ++nb) {
+                const int krow = kk * 16 + (lane & 15);
+                const int nseg = (wn * 32 + nb * 16) / 8 + (lane >> 4);
+                uint32_t r[4];
+                ldsm_x4_t(r, b_s + krow * BN + (swzB<BN>(krow, nseg) << 3));
+                bfr[2 * nb][0] = r[0];
+                bfr[2 * nb][1] = r[1];
+                bfr[2 * nb + 1][0] = r[2];
+                bfr[2 * nb + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int mi = 0; mi < C::MI; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < C::NI; ++ni) mma16816(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
+        }
+    }
+    cp_wait<0>();
+
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < C::MI; ++mi)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const long long m = m0 + wm * C::WM + mi * 16 + g + half * 8;
+            if (m >= M) continue;
+#pragma unroll
+            for (int ni = 0; ni < C::NI; ++ni) {
+                const int n = n0 + wn * 32 + ni * 8 + 2 * t;
+                float v0 = acc[mi][ni][2 * half], v1 = acc[mi][ni][2 * half + 1];
+                if (out.mode == CONV_FWD) {
+                    v0 = leaky(v0 + out.bias[n]);
+                    v1 = leaky(v1 + out.bias[n + 1]);
+                    *reinterpret_cast<__nv_bfloat162*>(out.y + m * N + n) = __floats2bfloat162_rn(v0, v1);
+                } else if (out.mode == CONV_MASK) {
+                    const float2 k = __bfloat1622float2(
+                        *reinterpret_cast<const __nv_bfloat162*>(out.mask + m * N + n));
+                    *reinterpret_cast<__nv_bfloat162*>(out.y + m * N + n) =
+                        __floats2bfloat162_rn(v0 * slope(k.x), v1 * slope(k.y));
+                } else if (n < out.n1) {
+                    *reinterpret_cast<float2*>(out.f1 + m * out.n1 + n) = make_float2(v0, v1);
+                } else {
+                    *reinterpret_cast<float2*>(out.f2 + m * (N - out.n1) + (n - out.n1)) =
+                        make_float2(v0, v1);
+                }
+            }
+        }
+}
+
+cudaError_t launch_conv3(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
+                         const ConvOut& out, cudaStream_t s) {
+    if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 || H <= 0 ||
+        W <= 0 || (in.up && ((H | W) & 1)))
+        return cudaErrorInvalidValue;
+    const long long M = (long long)B * H * W;
+    if (N % 64 == 0) {
+        dim3 grid((unsigned)((M + 127) / 128), N / 64);
+        conv3_kernel<64><<<grid, 128, 0, s>>>(in, Wt, Cin, N, B, H, W, out);
+    } else {
+        dim3 grid((unsigned)((M + 127) / 128), N / 32);
+        conv3_kernel<32><<<grid, 128, 0, s>>>(in, Wt, Cin, N, B, H, W, out);
+    }
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------- weight gradient
+// CTA: one tap, 32 input channels, BN output channels, one slice of pixels in
+// steps of 64; each warp multiplies one 16-pixel quarter of every step, the
+// four warps' tiles are summed in shared memory at the end.
+template <int BN>
+__global__ void __launch_bounds__(128) wgrad3_kernel(ConvIn in, const bf16* __restrict__ G, int Cin,
+                                                     int N, int B, int H, int W, long long chunk,
+                                                     float* __restrict__ part) {
+    constexpr int STAGES = 3, PX = 64;
+    constexpr int XS = PX * 32, GS = PX * BN;
+    constexpr int PIPE = STAGES * (XS + GS) * 2;
+    constexpr int RED = 4 * 32 * BN * 4;
+    __shared__ __align__(128) unsigned char smem[PIPE > RED ? PIPE : RED];
+    bf16* sX = reinterpret_cast<bf16*>(smem);
+    bf16* sG = sX + STAGES * XS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cpt = Cin / 32;
+    const int tap = blockIdx.x / cpt, cch = blockIdx.x - tap * cpt;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int n0 = blockIdx.y * BN;
+    const long long HW = (long long)H * W;
+    const long long M = (long long)B * HW;
+    const long long pb = (long long)blockIdx.z * chunk;
+    const long long pe = pb + chunk < M ? pb + chunk : M;
+    const int nst = pe > pb ? (int)((pe - pb + PX - 1) / PX) : 0;
+
+    auto load_stage = [&](int st, int it) {
+        const long long p0 = pb + (long long)it * PX;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int sid = tid + 128 * k;
+            const int row = sid >> 2, seg = sid & 3;
+            const long long p = p0 + row;
+            const bf16* src = nullptr;
+            if (p < pe) {
+                const int n = (int)(p / HW);
+                const int rem = (int)(p - (long long)n * HW);
+                const int y = rem / W, x = rem - (rem / W) * W;
+                src = in_at(in, n, y + dy, x + dx, H, W, cch * 32 + seg * 8);
+            }
+            cp16(sX + st * XS + row * 32 + (swz4(row, seg) << 3), src ? src : in.a, src ? 16 : 0);
+        }
+        constexpr int SEGS = BN / 8;
+#pragma unroll
+        for (int sid = tid; sid < PX * SEGS; sid += 128) {
+            const int row = sid / SEGS, seg = sid - row * SEGS;
+            const long long p = p0 + row;
+            const bool ok = p < pe;
+            cp16(sG + st * GS + row * BN + (swzB<BN>(row, seg) << 3),
+                 ok ? G + p * N + n0 + seg * 8 : G, ok ? 16 : 0);
+        }
+    };
+
+    constexpr int NI = BN / 8;
+    float acc[2][NI][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < NI; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (s < nst) load_stage(s, s);
+        cp_commit();
+    }
+    for (int it = 0; it < nst; ++it) {
+        cp_wait<STAGES - 2>();
+        __syncthreads();
+        const int nx = it + STAGES - 1;
+        if (nx < nst) load_stage(nx % STAGES, nx);
+        cp_commit();
+        const bf16* xs = sX + (it % STAGES) * XS;
+        const bf16* gs = sG + (it % STAGES) * GS;
+        uint32_t af[2][4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            const int krow = warp * 16 + (lane & 7) + ((lane >> 4) << 3);
+            const int mseg = mi * 2 + ((lane >> 3) & 1);
+            ldsm_x4_t(af[mi], xs + krow * 32 + (swz4(krow, mseg) << 3));
+        }
+#pragma unroll
+        for (int nb = 0; nb < NI / 2; ++nb) {
+            const int krow = warp * 16 + (lane & 15);
+            const int nseg = nb * 2 + (lane >> 4);
+            uint32_t r[4];
+            ldsm_x4_t(r, gs + krow * BN + (swzB<BN>(krow, nseg) << 3));
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                mma16816(acc[mi][2 * nb], af[mi], r[0], r[1]);
+                mma16816(acc[mi][2 * nb + 1], af[mi], r[2], r[3]);
+            }
+        }
+    }
+    cp_wait<0>();
+    __syncthreads();
+    // sum the four warps' 32 x BN tiles
+    float* red = reinterpret_cast<float*>(smem);
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < NI; ++ni)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int r = mi * 16 + g + (c >> 1) * 8;
+                const int col = ni * 8 + 2 * t + (c & 1);
+                red[(warp * 32 + r) * BN + col] = acc[mi][ni][c];
+            }
+    __syncthreads();
+    const long long K = 9LL * Cin;
+    float* dst = part + (long long)blockIdx.z * K * N;
+    for (int i = tid; i < 32 * BN; i += 128) {
+        const int r = i / BN, col = i - r * BN;
+        const float v = red[r * BN + col] + red[(32 + r) * BN + col] + red[(64 + r) * BN + col] +
+                        red[(96 + r) * BN + col];
+        dst[((long long)tap * Cin + cch * 32 + r) * N + n0 + col] = v;
+    }
+}
+
+cudaError_t launch_wgrad3(const ConvIn& in, const bf16* G, int Cin, int N, int B, int H, int W,
+                          float* part, size_t part_cap, int* splits, cudaStream_t s) {
+    if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 ||
+        (in.up && ((H | W) & 1)))
+        return cudaErrorInvalidValue;
+    const long long M = (long long)B * H * W;
+    const int BN = N % 64 == 0 ? 64 : 32;
+    const long long tiles = 9LL * (Cin / 32) * (N / BN);
+    const long long per = 9LL * Cin * N;
+    long long S = (4 * 152 + tiles - 1) / tiles;
+    const long long max_s = (M + 63) / 64;
+    if (S > max_s) S = max_s;
+    if (S > (long long)(part_cap / per)) S = (long long)(part_cap / per);
+    if (S < 1) return cudaErrorInvalidValue;
+    long long chunk = (M + S - 1) / S;
+    chunk = (chunk + 63) / 64 * 64;
+    S = (M + chunk - 1) / chunk;
+    *splits = (int)S;
+    dim3 grid((unsigned)(9 * (Cin / 32)), N / BN, (unsigned)S);
+    if (BN == 64)
+        wgrad3_kernel<64><<<grid, 128, 0, s>>>(in, G, Cin, N, B, H, W, chunk, part);
+    else
+        wgrad3_kernel<32><<<grid, 128, 0, s>>>(in, G, Cin, N, B, H, W, chunk, part);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ column sums
+__global__ void __launch_bounds__(256) colsum_kernel(const bf16* __restrict__ G, long long P, int N,
+                                                     long long chunk, float* __restrict__ part) {
+    __shared__ float red[256];
+    const int R = 256 / N;
+    const int c = threadIdx.x % N, r = threadIdx.x / N;
+    const long long pb = (long long)blockIdx.x * chunk;
+    const long long pe = pb + chunk < P ? pb + chunk : P;
+    float acc = 0.f;
+    if (r < R)
+        for (long long p = pb + r; p < pe; p += R) acc += __bfloat162float(G[p * N + c]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < N) {
+        float v = 0.f;
+        for (int k = 0; k < R; ++k) v += red[k * N + threadIdx.x];
+        part[(long long)blockIdx.x * N + threadIdx.x] = v;
+    }
+}
+
+cudaError_t launch_colsum(const bf16* G, long long P, int N, float* part, size_t part_cap, int* splits,
+                          cudaStream_t s) {
+    if (N <= 0 || N > 256 || P <= 0) return cudaErrorInvalidValue;
+    long long S = 256;
+    if (S > (long long)(part_cap / N)) S = (long long)(part_cap / N);
+    if (S > P) S = P;
+    if (S < 1) return cudaErrorInvalidValue;
+    const long long chunk = (P + S - 1) / S;
+    S = (P + chunk - 1) / chunk;
+    *splits = (int)S;
+    colsum_kernel<<<(unsigned)S, 256, 0, s>>>(G, P, N, chunk, part);
+    return cudaGetLastError();
+}
+
+__global__ void reduce_grad_kernel(const float* __restrict__ wpart, int ws, int cin, int cin_real, int N,
+                                   const float* __restrict__ bpart, int bs, float* __restrict__ grad,
+                                   long long w_off, long long b_off) {
+    const long long nW = 9LL * cin_real * N;
+    const long long per = 9LL * cin * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nW + N;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < nW) {
+            const int co = (int)(i % N);
+            const long long k = i / N;
+            const int ci = (int)(k % cin_real);
+            const int tap = (int)(k / cin_real);
+            const long long src = ((long long)tap * cin + ci) * N + co;
+            float v = 0.f;
+            for (int s = 0; s < ws; ++s) v += wpart[s * per + src];
+            grad[w_off + i] = v;
+        } else {
+            const int co = (int)(i - nW);
+            float v = 0.f;
+            for (int s = 0; s < bs; ++s) v += bpart[(long long)s * N + co];
+            grad[b_off + co] = v;
+        }
+    }
+}
+
+cudaError_t launch_reduce_grad(const float* wpart, int ws, int cin, int cin_real, int N,
+                               const float* bpart, int bs, float* grad, long long w_off,
+                               long long b_off, cudaStream_t s) {
+    const long long n = 9LL * cin_real * N + N;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    reduce_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(wpart, ws, cin, cin_real, N, bpart, bs, grad,
+                                                        w_off, b_off);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ pooling and friends
+__global__ void pool2_kernel(const bf16* __restrict__ x, bf16* __restrict__ y, int B, int H, int W,
+                             int C) {
+    const int Ho = H >> 1, Wo = W >> 1, C8 = C >> 3;
+    const long long n = (long long)B * Ho * Wo * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % C8);
+        long long q = i / C8;
+        const int xo = (int)(q % Wo);
+        q /= Wo;
+        const int yo = (int)(q % Ho);
+        const int b = (int)(q / Ho);
+        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const long long p = ((long long)b * H + 2 * yo + dy) * W + 2 * xo + dx;
+                float f[8];
+                unpack8(*reinterpret_cast<const uint4*>(x + p * C + c8 * 8), f);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) s[k] += f[k];
+            }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] *= 0.25f;
+        *reinterpret_cast<uint4*>(y + i * 8) = pack8(s);
+    }
+}
+
+cudaError_t launch_pool2(const bf16* x, bf16* y, int B, int H, int W, int C, cudaStream_t s) {
+    if (C % 8 || (H | W) & 1) return cudaErrorInvalidValue;
+    const long long n = (long long)B * (H / 2) * (W / 2) * (C / 8);
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    pool2_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, y, B, H, W, C);
+    return cudaGetLastError();
+}
+
+__global__ void combine_kernel(const float* __restrict__ dp, const float* __restrict__ skip,
+                               const bf16* __restrict__ e, bf16* __restrict__ g, int B, int H, int W,
+                               int C) {
+    const int C8 = C >> 3;
+    const long long n = (long long)B * H * W * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % C8);
+        const long long p = i / C8;
+        const int x = (int)(p % W);
+        const long long q = p / W;
+        const int y = (int)(q % H);
+        const int b = (int)(q / H);
+        const long long pc = ((long long)b * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1);
+        const float4* d4 = reinterpret_cast<const float4*>(dp + pc * C + c8 * 8);
+        const float4* s4 = reinterpret_cast<const float4*>(skip + p * C + c8 * 8);
+        const float4 d0 = d4[0], d1 = d4[1], s0 = s4[0], s1 = s4[1];
+        float ef[8];
+        unpack8(*reinterpret_cast<const uint4*>(e + p * C + c8 * 8), ef);
+        float v[8] = {0.25f * d0.x + s0.x, 0.25f * d0.y + s0.y, 0.25f * d0.z + s0.z,
+                      0.25f * d0.w + s0.w, 0.25f * d1.x + s1.x, 0.25f * d1.y + s1.y,
+                      0.25f * d1.z + s1.z, 0.25f * d1.w + s1.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] *= slope(ef[k]);
+        *reinterpret_cast<uint4*>(g + p * C + c8 * 8) = pack8(v);
+    }
+}
+
+cudaError_t launch_combine(const float* dp, const float* skip, const bf16* e, bf16* g, int B, int H,
+                           int W, int C, cudaStream_t s) {
+    if (C % 8 || (H | W) & 1) return cudaErrorInvalidValue;
+    const long long n = (long long)B * H * W * (C / 8);
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    combine_kernel<<<(unsigned)blocks, 256, 0, s>>>(dp, skip, e, g, B, H, W, C);
+    return cudaGetLastError();
+}
+
+__global__ void upback_kernel(const float* __restrict__ f, const bf16* __restrict__ d,
+                              bf16* __restrict__ g, int B, int H, int W, int C) {
+    const int Ho = H >> 1, Wo = W >> 1, C8 = C >> 3;
+    const long long n = (long long)B * Ho * Wo * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % C8);
+        const long long pc = i / C8;
+        const int xo = (int)(pc % Wo);
+        const long long q = pc / Wo;
+        const int yo = (int)(q % Ho);
+        const int b = (int)(q / Ho);
+        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const long long p = ((long long)b * H + 2 * yo + dy) * W + 2 * xo + dx;
+                const float4* f4 = reinterpret_cast<const float4*>(f + p * C + c8 * 8);
+                const float4 a = f4[0], c = f4[1];
+                v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w;
+                v[4] += c.x; v[5] += c.y; v[6] += c.z; v[7] += c.w;
+            }
+        float df[8];
+        unpack8(*reinterpret_cast<const uint4*>(d + pc * C + c8 * 8), df);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] *= slope(df[k]);
+        *reinterpret_cast<uint4*>(g + pc * C + c8 * 8) = pack8(v);
+    }
+}
+
+cudaError_t launch_upback(const float* f, const bf16* d, bf16* g, int B, int H, int W, int C,
+                          cudaStream_t s) {
+    if (C % 8 || (H | W) & 1) return cudaErrorInvalidValue;
+    const long long n = (long long)B * (H / 2) * (W / 2) * (C / 8);
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    upback_kernel<<<(unsigned)blocks, 256, 0, s>>>(f, d, g, B, H, W, C);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- input / head
+__device__ __forceinline__ float load_img(const void* p, int type, long long i) {
+    if (type == 1) return __half2float(static_cast<const __half*>(p)[i]);
+    if (type == 2) return __bfloat162float(static_cast<const bf16*>(p)[i]);
+    return static_cast<const float*>(p)[i];
+}
+
+__global__ void assemble_kernel(const Sample* __restrict__ smp, int B, int H, int W, int H8, int W8,
+                                bf16* __restrict__ x0, float* __restrict__ base,
+                                float* __restrict__ tgt) {
+    const long long n = (long long)B * H8 * W8;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % W8);
+        const long long q = p / W8;
+        const int y = (int)(q % H8);
+        const int b = (int)(q / H8);
+        float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        float b0 = 0.f, b1 = 0.f, t0 = 0.f, t1 = 0.f;
+        if (y < H && x < W) {
+            const Sample S = smp[b];
+            const float ih = 1.f / S.h;
+            const long long o = (long long)y * S.ld + x;
+            const long long oi = (long long)y * S.ld_img + x;
+            const float l0 = S.y_l[o], l1 = S.y_l[S.plane + o];
+            const float r0 = S.y_r[o], r1 = S.y_r[S.plane + o];
+            f[0] = l0 * ih;
+            f[1] = l1 * ih;
+            f[2] = r0 * ih;
+            f[3] = r1 * ih;
+            f[4] = load_img(S.T_l, S.img_type, oi);
+            f[5] = load_img(S.T_k, S.img_type, oi);
+            f[6] = load_img(S.T_r, S.img_type, oi);
+            const float wr = 1.f - S.w_l;
+            b0 = (S.w_l * l0 + wr * r0) * ih;
+            b1 = (S.w_l * l1 + wr * r1) * ih;
+            if (S.target) {
+                t0 = S.target[o] * ih;
+                t1 = S.target[S.plane + o] * ih;
+            }
+        }
+        uint4* dst = reinterpret_cast<uint4*>(x0 + p * kInPad);
+        dst[0] = pack8(f);
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        dst[1] = z;
+        dst[2] = z;
+        dst[3] = z;
+        reinterpret_cast<float2*>(base)[p] = make_float2(b0, b1);
+        if (tgt) reinterpret_cast<float2*>(tgt)[p] = make_float2(t0, t1);
+    }
+}
+
+cudaError_t launch_assemble(const Sample* smp, int B, int H, int W, int H8, int W8, bf16* x0,
+                            float* base, float* tgt, cudaStream_t s) {
+    const long long n = (long long)B * H8 * W8;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    assemble_kernel<<<(unsigned)blocks, 256, 0, s>>>(smp, B, H, W, H8, W8, x0, base, tgt);
+    return cudaGetLastError();
+}
+
+constexpr int kHeadPart = 1 + kHeadIn * kOutCh + kOutCh;   // sum e^2, dW, db
+
+__global__ void __launch_bounds__(256) head_kernel(const bf16* __restrict__ d0,
+                                                   const float* __restrict__ th,
+                                                   const float* __restrict__ base,
+                                                   const float* __restrict__ tgt,
+                                                   const Sample* __restrict__ smp, int B, int H, int W,
+                                                   int H8, int W8, int train, float inv_count,
+                                                   float* __restrict__ part, bf16* __restrict__ gd0) {
+    __shared__ float sw[kHeadIn * kOutCh + kOutCh];
+    __shared__ float red[8][kHeadPart];
+    for (int i = threadIdx.x; i < kHeadIn * kOutCh + kOutCh; i += blockDim.x) sw[i] = th[i];
+    __syncthreads();
+    float acc[kHeadPart];
+#pragma unroll
+    for (int i = 0; i < kHeadPart; ++i) acc[i] = 0.f;
+    const long long n = (long long)B * H8 * W8;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % W8);
+        const long long q = p / W8;
+        const int y = (int)(q % H8);
+        const int b = (int)(q / H8);
+        float d[kHeadIn];
+#pragma unroll
+        for (int k = 0; k < kHeadIn / 8; ++k) {
+            float f[8];
+            unpack8(reinterpret_cast<const uint4*>(d0 + p * kHeadIn)[k], f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) d[8 * k + j] = f[j];
+        }
+        float dl0 = sw[kHeadIn * kOutCh], dl1 = sw[kHeadIn * kOutCh + 1];
+#pragma unroll
+        for (int j = 0; j < kHeadIn; ++j) {
+            dl0 += sw[2 * j] * d[j];
+            dl1 += sw[2 * j + 1] * d[j];
+        }
+        const bool inside = y < H && x < W;
+        const float2 bs = reinterpret_cast<const float2*>(base)[p];
+        if (!train) {
+            if (inside) {
+                const Sample& S = smp[b];
+                const long long o = (long long)y * S.ld + x;
+                S.out[o] = S.h * (bs.x + dl0);
+                S.out[S.plane + o] = S.h * (bs.y + dl1);
+            }
+            continue;
+        }
+        float g0 = 0.f, g1 = 0.f;
+        if (inside) {
+            const float2 tg = reinterpret_cast<const float2*>(tgt)[p];
+            const float e0 = bs.x + dl0 - tg.x, e1 = bs.y + dl1 - tg.y;
+            acc[0] += e0 * e0 + e1 * e1;
+            g0 = 2.f * e0 * inv_count;
+            g1 = 2.f * e1 * inv_count;
+        }
+        float gv[kHeadIn];
+#pragma unroll
+        for (int j = 0; j < kHeadIn; ++j) {
+            acc[1 + 2 * j] += d[j] * g0;
+            acc[2 + 2 * j] += d[j] * g1;
+            gv[j] = (sw[2 * j] * g0 + sw[2 * j + 1] * g1) * slope(d[j]);
+        }
+        acc[1 + kHeadIn * kOutCh] += g0;
+        acc[2 + kHeadIn * kOutCh] += g1;
+#pragma unroll
+        for (int k = 0; k < kHeadIn / 8; ++k) {
+            float f[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) f[j] = gv[8 * k + j];
+            reinterpret_cast<uint4*>(gd0 + p * kHeadIn)[k] = pack8(f);
+        }
+    }
+    if (!train) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kHeadPart; ++i) {
+        float v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHeadPart; i += blockDim.x) {
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v += red[w][i];
+        part[(long long)blockIdx.x * kHeadPart + i] = v;
+    }
+}
+
+cudaError_t launch_head(const bf16* d0, const float* theta_head, const float* base, const float* tgt,
+                        const Sample* smp, int B, int H, int W, int H8, int W8, int train,
+                        float inv_count, float* part, int* blocks, bf16* gd0, cudaStream_t s) {
+    const long long n = (long long)B * H8 * W8;
+    long long nb = (n + 255) / 256;
+    if (nb > 1024) nb = 1024;
+    if (blocks) *blocks = (int)nb;
+    head_kernel<<<(unsigned)nb, 256, 0, s>>>(d0, theta_head, base, tgt, smp, B, H, W, H8, W8, train,
+                                            inv_count, part, gd0);
+    return cudaGetLastError();
+}
+
+__global__ void reduce_head_kernel(const float* __restrict__ part, int blocks, float* __restrict__ grad,
+                                   long long off, float inv_count, double* loss) {
+    for (int i = threadIdx.x; i < kHeadPart; i += blockDim.x) {
+        float v = 0.f;
+        for (int b = 0; b < blocks; ++b) v += part[(long long)b * kHeadPart + i];
+        if (i == 0) {
+            if (loss) *loss = (double)v * (double)inv_count;
+        } else {
+            grad[off + i - 1] = v;
+        }
+    }
+}
+
+cudaError_t launch_reduce_head(const float* part, int blocks, float* grad, long long off, float inv_count,
+                               double* loss, cudaStream_t s) {
+    reduce_head_kernel<<<1, 128, 0, s>>>(part, blocks, grad, off, inv_count, loss);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ Adam, packing
+__global__ void adam_kernel(float* __restrict__ th, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        th[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+cudaError_t launch_adam(float* theta, float* m, float* v, const float* g, long long n, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(theta, m, v, g, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+__global__ void pack_kernel(const float* __restrict__ th, PackTable t, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long r = i;
+        int l = 0;
+        bool flip = false;
+        for (; l < t.n; ++l) {
+            const long long nf = 9LL * t.cin[l] * t.cout[l];
+            if (r < nf) break;
+            r -= nf;
+            if (t.wd[l]) {
+                if (r < nf) {
+                    flip = true;
+                    break;
+                }
+                r -= nf;
+            }
+        }
+        if (l >= t.n) continue;
+        const int cin = t.cin[l], cout = t.cout[l], cr = t.cin_real[l];
+        int tap, ci, co;
+        if (!flip) {
+            co = (int)(r % cout);
+            const long long k = r / cout;
+            ci = (int)(k % cin);
+            tap = (int)(k / cin);
+        } else {
+            ci = (int)(r % cin);
+            const long long k = r / cin;
+            co = (int)(k % cout);
+            tap = 8 - (int)(k / cout);
+        }
+        const float v = ci < cr ? th[t.w_off[l] + ((long long)tap * cr + ci) * cout + co] : 0.f;
+        (flip ? t.wd[l] : t.wf[l])[r] = __float2bfloat16_rn(v);
+    }
+}
+
+cudaError_t launch_pack(const float* theta, const PackTable& t, cudaStream_t s) {
+    long long total = 0;
+    for (int l = 0; l < t.n; ++l) total += 9LL * t.cin[l] * t.cout[l] * (t.wd[l] ? 2 : 1);
+    long long blocks = (total + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(theta, t, total);
+    return cudaGetLastError();
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, bf16* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+__global__ void from_bf16_kernel(const bf16* __restrict__ src, float* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = __bfloat162float(src[i]);
+}
+
+cudaError_t launch_to_bf16(const float* src, bf16* dst, long long n, cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    to_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_from_bf16(const bf16* src, float* dst, long long n, cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    from_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace net
+}  // namespace stml

@@ -27,9 +27,10 @@ def assert_array(got, ref, rtol=RTOL, what=""):
 
 
 def header_functions():
-    txt = open(os.path.join(ROOT, "include", "stml.h")).read()
+    import glob
+    txt = "".join(open(f).read() for f in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(stml_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(stml_[a-z0-9_]+)\s*\(", txt)))
 
 
 def cuda_lib():
