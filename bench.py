@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spml", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time launch shapes and PCG paths on first use (warm-up steps)")
     ap.add_argument("--cpu-sample-frames", type=int, default=25)
@@ -280,6 +281,77 @@ def run_batch(S, torch, dev, mode):
             "speedup": t_seq / t_bat, "timing": "host wall clock around the whole batch, device-resident inputs"}
 
 
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2001_06613_gb300", "weights",
+                       "predictor_500x100x256.f32")
+
+
+def net_train_flops(B: int, H: int, W: int):
+    """(algorithmic, executed) FLOPs of one training step of the predictor
+    network on B canvases of H x W: forward, input gradient (not of the first
+    layer) and weight gradient of every 3x3 convolution, 2 FLOPs per MAC; the
+    executed count has the first layer's 7 input channels padded to 32."""
+    convs = [(0, 7, 32), (0, 32, 32), (1, 32, 64), (1, 64, 64), (2, 64, 96), (2, 96, 96), (3, 96, 128),
+             (3, 128, 128), (2, 224, 96), (2, 96, 96), (1, 160, 64), (1, 64, 64), (0, 96, 32), (0, 32, 32)]
+    alg = exe = 0.0
+    for i, (lv, ci, co) in enumerate(convs):
+        P = B * (H >> lv) * (W >> lv)
+        passes = 2 if i == 0 else 3
+        alg += 2.0 * P * 9 * ci * co * passes
+        exe += 2.0 * P * 9 * (32 if i == 0 else ci) * co * passes
+    return alg, exe
+
+
+def run_learned(S, torch, dev, peaks):
+    """The learned temporal predictor: training throughput of its kernels and
+    what the trained network (500 sequences of 100 frames of 256^2, committed
+    weights) changes in STML registration on held-out 16-frame 64^2 sequences
+    and on the paper-scale sequence."""
+    from paper_2001_06613_gb300 import predictor_training as PT
+    from paper_2001_06613_gb300 import synthetic
+    params = np.fromfile(WEIGHTS, dtype=np.float32) if os.path.exists(WEIGHTS) else None
+    trained = params is not None
+    if params is None:
+        params = synthetic.net_init_params(1000)
+    net = S.Net(params, max_batch=64, max_h=256, max_w=256)
+    # training throughput: 32 crops of 64^2 from registered fields of 4 sequences
+    prm = S.stml_default_params(n_levels=3, n_tlevels=3)
+    data = PT.collect(S, [synthetic.make_sequence(PT.training_spec(5000 + i, 64, 128), device="cuda")
+                          for i in range(4)], prm)
+    if not trained:
+        PT.train(S, net, data, 1500, batch=32, crop=64, lr=5e-4, seed=1)
+    rng = np.random.default_rng(7)
+    batches = [PT.sample_batch([d for d in data if d.T.shape[1] >= 64], rng, 32, 64) for _ in range(20)]
+    # the timed steps train a copy: restore the committed parameters afterwards
+    for smp, H, W in batches[:5]:
+        S.stml_net_train_step(net, smp, H, W, lr=1e-6, want_loss=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for smp, H, W in batches[5:]:
+        S.stml_net_train_step(net, smp, H, W, lr=1e-6, want_loss=False)
+    torch.cuda.synchronize()
+    step_s = (time.perf_counter() - t0) / 15
+    S.stml_net_set_params(net, params)
+    alg, exe = net_train_flops(32, 64, 64)
+    peak = peaks.get("bf16_tflops") if peaks else None
+    peak = peak or 1900.0
+    tiny = [synthetic.make_sequence(synthetic.spec_tiny(seed=300 + i)) for i in range(8)]
+    ev_tiny = PT.compare(S, net, tiny, S.stml_default_params(n_levels=2, n_tlevels=2), repeats=3)
+    R, _ = make_sequence("paper-scale")
+    ev_paper = PT.compare(S, net, [R], S.stml_default_params(n_levels=4, n_tlevels=3), repeats=2)
+    net.close()
+    return {"weights": "trained: 500 seqs x 100 frames x 256^2, 4000 Adam steps" if trained else
+            "untrained fallback (weights file missing): 1500 steps on 4 sequences",
+            "train_step_ms": 1e3 * step_s, "train_batch": "32 crops of 64x64",
+            "train_tflops_algorithmic": alg / step_s / 1e12, "train_tflops_executed": exe / step_s / 1e12,
+            "tensor_roofline": {"bound": "tensor", "achieved": alg / step_s / 1e12, "peak": peak,
+                                "unit": "TFLOP/s", "frac": alg / step_s / 1e12 / peak,
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)" if peaks
+                                else "fallback 1.9 PFLOP/s (of fallback)",
+                                "note": "whole training step (mma.sync BF16 convolutions plus "
+                                        "the FP32 elementwise and reduction kernels)"},
+            "held_out_16x64x64_2x2": ev_tiny, "paper_scale_200x256x256_4x3": ev_paper}
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_native(args):
     import torch
@@ -388,6 +460,9 @@ def run_native(args):
     batch = None
     if not args.no_batch and rank == 0 and world == 1:
         batch = run_batch(S, torch, dev, mode)
+    learned = None
+    if not args.no_learned and rank == 0 and world == 1 and args.mode == "stml":
+        learned = run_learned(S, torch, dev, measured_peaks())
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -445,7 +520,7 @@ def run_native(args):
                 "per_step_ms": ms_steps,
                 "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
                                                  "ls_trials", "stopped_early")} for s in stats],
-                "spml": spml, "batch": batch, "tuning": tuning}
+                "spml": spml, "batch": batch, "learned": learned, "tuning": tuning}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

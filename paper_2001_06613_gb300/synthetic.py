@@ -116,23 +116,25 @@ class _Speckle:
     coef: np.ndarray     # (J,) complex
     sigma: float
 
-    def __call__(self, pos: np.ndarray) -> np.ndarray:
-        """sigma * |sum_j coef_j exp(i <f_j, pos>)| at positions (d, *S)."""
+    def __call__(self, pos: np.ndarray, device=None) -> np.ndarray:
+        """sigma * |sum_j coef_j exp(i <f_j, pos>)| at positions (d, *S)
+        (device: a torch device for the sums, e.g. "cuda"; default the CPU)."""
         d = pos.shape[0]
         flat = pos.reshape(d, -1)
         if torch is not None:
-            P = torch.from_numpy(np.ascontiguousarray(flat))
-            F = torch.from_numpy(self.freqs)
+            dev = device or "cpu"
+            P = torch.from_numpy(np.ascontiguousarray(flat)).to(dev)
+            F = torch.from_numpy(self.freqs).to(dev)
             out = np.empty(flat.shape[1], dtype=np.float64)
-            chunk = 1 << 18
-            cr = torch.from_numpy(self.coef.real.copy())
-            ci = torch.from_numpy(self.coef.imag.copy())
+            chunk = 1 << 18 if dev == "cpu" else 1 << 22
+            cr = torch.from_numpy(self.coef.real.copy()).to(dev)
+            ci = torch.from_numpy(self.coef.imag.copy()).to(dev)
             for s in range(0, flat.shape[1], chunk):
                 ph = F @ P[:, s:s + chunk]                      # (J, chunk)
                 c, sn = torch.cos(ph), torch.sin(ph)
                 re = cr @ c - ci @ sn
                 im = cr @ sn + ci @ c
-                out[s:s + chunk] = torch.sqrt(re * re + im * im).numpy()
+                out[s:s + chunk] = torch.sqrt(re * re + im * im).cpu().numpy()
         else:
             ph = self.freqs @ flat
             z = self.coef @ np.exp(1j * ph)
@@ -164,17 +166,26 @@ class _Motion:
     def temporal(self, t: float) -> np.ndarray:
         return np.array([math.sin(2.0 * math.pi * t / p + ph) for (p, ph) in self.periods])
 
-    def __call__(self, t: float, pos: np.ndarray) -> np.ndarray:
-        """v(t, pos) for positions (d, *S) -> (d, *S)."""
+    def modes(self, pos: np.ndarray) -> List[np.ndarray]:
+        """The spatial factors sin(2 pi <f_j, pos / m> + phi_j) of every mode."""
         d = pos.shape[0]
         ext = np.asarray(self.shape, dtype=np.float64).reshape((d,) + (1,) * (pos.ndim - 1))
+        return [np.sin(2.0 * np.pi * np.tensordot(self.freqs[j], pos / ext, axes=(0, 0)) + self.phases[j])
+                for j in range(self.freqs.shape[0])]
+
+    def from_modes(self, t: float, sines: List[np.ndarray]) -> np.ndarray:
+        """v(t, pos) from the spatial factors of :meth:`modes` at pos."""
+        d = self.freqs.shape[1]
         a = self.temporal(t)
-        out = np.zeros_like(pos)
-        for j in range(self.freqs.shape[0]):
-            arg = 2.0 * np.pi * np.tensordot(self.freqs[j], pos / ext, axes=(0, 0)) + self.phases[j]
-            w = a[self.comp[j]] * np.sin(arg)
-            out += self.coefs[j].reshape((d,) + (1,) * (pos.ndim - 1)) * w[None]
+        out = np.zeros((d,) + sines[0].shape)
+        for j, sn in enumerate(sines):
+            w = a[self.comp[j]] * sn
+            out += self.coefs[j].reshape((d,) + (1,) * sn.ndim) * w[None]
         return self.scale * out
+
+    def __call__(self, t: float, pos: np.ndarray) -> np.ndarray:
+        """v(t, pos) for positions (d, *S) -> (d, *S)."""
+        return self.from_modes(t, self.modes(pos))
 
 
 def _make_motion(spec: SequenceSpec) -> _Motion:
@@ -185,10 +196,10 @@ def _make_motion(spec: SequenceSpec) -> _Motion:
     coefs = g.normal(size=(M, d))
     comp = np.arange(M) % len(spec.periods)
     mot = _Motion(freqs, phases, coefs, comp, list(spec.periods), tuple(spec.shape))
-    x = cell_centres(spec.shape)
+    sines = mot.modes(cell_centres(spec.shape))
     peak = 0.0
     for t in range(spec.n):
-        v = mot(float(t), x)
+        v = mot.from_modes(float(t), sines)
         peak = max(peak, float(np.sqrt((v * v).sum(axis=0)).max()))
     mot.scale = spec.amp / peak if peak > 0 else 0.0
     return mot
@@ -203,16 +214,18 @@ def base_image(spec: SequenceSpec, pos: np.ndarray, speckle: _Speckle = None) ->
     return band_profile(pos[0], float(spec.shape[0])) + speckle(pos)
 
 
-def make_sequence(spec: SequenceSpec, dtype=np.float32) -> np.ndarray:
-    """Frames R_k(x) = B(x + v_k(x)) + N(0, noise_sd^2), shape (n, *shape)."""
+def make_sequence(spec: SequenceSpec, dtype=np.float32, device=None) -> np.ndarray:
+    """Frames R_k(x) = B(x + v_k(x)) + N(0, noise_sd^2), shape (n, *shape)
+    (device: torch device for the speckle sums; values equal up to rounding)."""
     speckle = _make_speckle(spec)
     motion = _make_motion(spec)
     x = cell_centres(spec.shape)
+    sines = motion.modes(x)
     noise = philox(spec.seed, 3)
     out = np.empty((spec.n,) + tuple(spec.shape), dtype=dtype)
     for k in range(spec.n):
-        pos = x + motion(float(k), x)
-        img = base_image(spec, pos, speckle)
+        pos = x + motion.from_modes(float(k), sines)
+        img = band_profile(pos[0], float(spec.shape[0])) + speckle(pos, device)
         img += noise.normal(scale=spec.noise_sd, size=img.shape) if spec.noise_sd > 0 else 0.0
         out[k] = img.astype(dtype)
     return out
