@@ -21,6 +21,10 @@ Layout of the oracle:
                     by a dense solve.
 * ``multilevel`` -- image pyramid, STML predictor-corrector driver with the
                     stopping rule of eq. (3), and the spatial-only (SpML) driver.
+* ``affine``     -- affine-linear transformations per frame (Sec. 4) solved by
+                    L-BFGS (Sec. 2): parametrisation, projected gradient,
+                    two-loop recursion, and the STML/SpML drivers over the
+                    parameters.
 * ``net``        -- the learned temporal predictor: a convolutional
                     encoder-decoder proposing a skipped frame's field from its
                     two registered neighbours and three images (in place of
@@ -32,4 +36,4 @@ Every function works in float64 on numpy arrays.  Where the paper is silent the
 oracle follows one stated reading, documented on the function.
 """
 from .params import Params  # noqa: F401
-from . import grid, objective, solver, predictor, multilevel, net  # noqa: F401
+from . import grid, objective, solver, predictor, multilevel, net, affine  # noqa: F401

@@ -294,3 +294,66 @@ def net_init_params(seed: int, head_scale: float = 0.0) -> np.ndarray:
     parts.append(g.normal(scale=head_scale / math.sqrt(32.0), size=64))
     parts.append(np.zeros(2))
     return np.concatenate(parts).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# affine-linear motion (the transformations of the paper's experiments, Sec. 4)
+# ---------------------------------------------------------------------------
+def affine_motion(spec: SequenceSpec, rot_deg: float = 1.5, scale: float = 0.015,
+                  shift: float = 1.5) -> Tuple[np.ndarray, np.ndarray]:
+    """Planted affine motion about the domain centre c: frame k is sampled at
+    x + v_k(x), v_k(x) = (M_k - I)(x - c) + s_k, with M_k a rotation by
+    rot_deg sin(2 pi k / n) degrees in the plane of the first two axes scaled by
+    1 + scale sin(2 pi k / n + 1), and s_k = shift (sin(2 pi k / n + 2 + i / 2))_i.
+    Returns (M (n, d, d), s (n, d))."""
+    n, d = spec.n, spec.dim
+    M = np.zeros((n, d, d))
+    s = np.zeros((n, d))
+    for k in range(n):
+        ph = 2.0 * math.pi * k / max(n, 1)
+        a = math.radians(rot_deg) * math.sin(ph)
+        R = np.eye(d)
+        R[0, 0], R[0, 1], R[1, 0], R[1, 1] = math.cos(a), -math.sin(a), math.sin(a), math.cos(a)
+        M[k] = R * (1.0 + scale * math.sin(ph + 1.0))
+        s[k] = [shift * math.sin(ph + 2.0 + 0.5 * i) for i in range(d)]
+    return M, s
+
+
+def blob_image(spec: SequenceSpec, pos: np.ndarray, n_blobs: int = 24, margin: float = 4.0) -> np.ndarray:
+    """A smooth image: sum of n_blobs Gaussians of widths 3-6 px at seeded
+    centres and heights, times a raised-cosine window that is zero within
+    `margin` px of the border and one beyond 3 margin (images on which linear
+    interpolation is accurate and zero extension is exact)."""
+    g = philox(spec.seed, 4)
+    d = pos.shape[0]
+    ext = np.asarray(spec.shape, dtype=np.float64)
+    out = np.zeros(pos.shape[1:])
+    for _ in range(n_blobs):
+        mu = g.uniform(0.25, 0.75, size=d) * ext
+        sd = g.uniform(3.0, 6.0)
+        a = g.uniform(0.5, 1.5)
+        r2 = sum((pos[i] - mu[i]) ** 2 for i in range(d))
+        out += a * np.exp(-0.5 * r2 / (sd * sd))
+    for i in range(d):
+        for dist in (pos[i], ext[i] - pos[i]):
+            t = np.clip((dist - margin) / (2.0 * margin), 0.0, 1.0)
+            out *= 0.5 - 0.5 * np.cos(np.pi * t)
+    return out
+
+
+def make_affine_sequence(spec: SequenceSpec, dtype=np.float32, smooth: bool = False, **motion) -> np.ndarray:
+    """Frames R_k(x) = B(x + v_k(x)) + N(0, noise_sd^2) under affine_motion;
+    B the OCT-like image, or blob_image when smooth."""
+    speckle = _make_speckle(spec)
+    M, s = affine_motion(spec, **motion)
+    x = cell_centres(spec.shape)
+    d = spec.dim
+    c = (np.asarray(spec.shape, dtype=np.float64) / 2.0).reshape((d,) + (1,) * d)
+    noise = philox(spec.seed, 3)
+    out = np.empty((spec.n,) + tuple(spec.shape), dtype=dtype)
+    for k in range(spec.n):
+        v = np.tensordot(M[k] - np.eye(d), x - c, axes=(1, 0)) + s[k].reshape((d,) + (1,) * d)
+        img = blob_image(spec, x + v) if smooth else base_image(spec, x + v, speckle)
+        img += noise.normal(scale=spec.noise_sd, size=img.shape) if spec.noise_sd > 0 else 0.0
+        out[k] = img.astype(dtype)
+    return out
