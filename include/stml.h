@@ -95,6 +95,11 @@ typedef struct {
                               * streaming PCG solve, and keeps the fastest for
                               * the context (reproducible within a context);
                               * 0: built-in choices (default) */
+    int transform;           /* 0: non-parametric fields (Gauss-Newton-PCG, the default);
+                              * 1: one affine-linear map per frame (Sec. 4), solved by
+                              * L-BFGS (Sec. 2); see stml_eval_affine */
+    int lbfgs_m;             /* L-BFGS memory (pairs kept), 1..64 */
+    int max_lbfgs;           /* L-BFGS iterations per GIR */
 } stml_params;
 
 typedef struct {
@@ -219,6 +224,38 @@ stml_status stml_hessvec(stml_ctx* ctx, int level, const int* frames, int nK,
  * u (device, nK * d * N floats, overwritten with the result). */
 stml_status stml_gir(stml_ctx* ctx, int level, const int* frames, int nK, float* u,
                      stml_stats* stats);
+
+/* Affine-linear variant (params.transform = 1; Sec. 4 transformations, Sec. 2
+ * L-BFGS).  Frame k's displacement is u_k(x) = W_k (x - c) / rho + b_k with x
+ * a cell centre in finest-level pixels, c the centre of the finest grid
+ * (extent / 2 per axis), rho half of its largest extent; theta_k = (W_k row
+ * by row, b_k): d (d + 1) doubles per frame, the same on every level.  The
+ * objective is J of eq. (1) at these fields (the parameters' gradient is the
+ * projection of the field gradient).  L-BFGS: two-loop recursion with
+ * H0 = (s^T y / y^T y) I of the newest pair, lbfgs_m pairs (pairs with
+ * s^T y <= 1e-12 |s||y| dropped), first step -g scaled to move no parameter
+ * by more than one pixel, Armijo back-tracking, the Gauss-Newton stopping
+ * tests in parameter space, at most max_lbfgs iterations.  Multilevel:
+ * stml_register runs STML / SpML over theta (linear predictor on the
+ * coarsest level, eq. (2) per parameter on finer ones, eq. (3)); afterwards
+ * every level's fields (stml_get_field) are the affine fields of the result.
+ * The step API (stml_predict / stml_correct) serves transform 0 only. */
+
+/* J, D, S, P (out[0..3]) at the affine fields of theta (host, nK x d(d+1))
+ * for the frames of K on `level`, and dJ/dtheta (host, same shape) when grad
+ * is not NULL.  Synchronises the stream. */
+stml_status stml_eval_affine(stml_ctx* ctx, int level, const int* frames, int nK, const double* theta,
+                             double* out, double* grad);
+/* The affine fields u (device, nK x d x N) of theta (host) on `level`. */
+stml_status stml_affine_field(stml_ctx* ctx, int level, const int* frames, int nK, const double* theta,
+                              float* u);
+/* GIR(K) over the affine parameters (L-BFGS) from theta_io (host, updated);
+ * stats->gn_iters counts L-BFGS iterations, cg_iters is 0. */
+stml_status stml_gir_affine(stml_ctx* ctx, int level, const int* frames, int nK, double* theta_io,
+                            stml_stats* stats);
+/* The parameters of all frames after an affine stml_register (host,
+ * n x d(d+1) doubles; cap = capacity in doubles). */
+stml_status stml_get_affine(const stml_ctx* ctx, double* theta, size_t cap);
 
 /* Correlation coefficients rho_{k,k+1} of consecutive frames at `level`
  * (Sec. 4, Table 1); rho (host) receives n - 1 doubles. */

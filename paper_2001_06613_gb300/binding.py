@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("tol_J", C.c_double), ("tol_Y", C.c_double), ("tol_G", C.c_double),
                 ("g_abs", C.c_double), ("max_gn", C.c_int), ("tol_cg", C.c_double),
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double),
-                ("image_dtype", C.c_int), ("pcg_cooperative", C.c_int), ("autotune", C.c_int)]
+                ("image_dtype", C.c_int), ("pcg_cooperative", C.c_int), ("autotune", C.c_int),
+                ("transform", C.c_int), ("lbfgs_m", C.c_int), ("max_lbfgs", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +104,10 @@ _SIGS = {
     "stml_profile_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "stml_launch_count": (C.c_longlong, [_vp]),
     "stml_tuning_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "stml_eval_affine": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _dp, _dp, _dp]),
+    "stml_affine_field": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _dp, _fp]),
+    "stml_gir_affine": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _dp, C.POINTER(Stats)]),
+    "stml_get_affine": (C.c_int, [_vp, _dp, C.c_size_t]),
     # learned temporal predictor (include/stml_net.h)
     "stml_net_param_count": (C.c_size_t, []),
     "stml_net_create": (C.c_int, [_fp, C.c_size_t, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
@@ -408,6 +413,41 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------- affine variant
+def _f64_host(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def stml_eval_affine(ctx, level: int, frames: Sequence[int], theta, want_grad: bool = True):
+    """(J, D, S, P) and dJ/dtheta (nK, d(d+1)) at the affine fields of theta."""
+    th, thp = _f64_host(theta)
+    out = np.zeros(4)
+    g = np.zeros_like(th) if want_grad else None
+    _check(load().stml_eval_affine(ctx, level, _ints(frames), len(frames), thp, out.ctypes.data_as(_dp),
+                                   g.ctypes.data_as(_dp) if want_grad else None), ctx)
+    return out, g
+
+
+def stml_affine_field(ctx, level: int, frames: Sequence[int], theta, u):
+    th, thp = _f64_host(theta)
+    _check(load().stml_affine_field(ctx, level, _ints(frames), len(frames), thp, _dev(u)), ctx)
+
+
+def stml_gir_affine(ctx, level: int, frames: Sequence[int], theta):
+    """L-BFGS GIR over the affine parameters from theta; returns (theta, stats)."""
+    th = np.array(theta, dtype=np.float64, copy=True, order="C")
+    st = Stats()
+    _check(load().stml_gir_affine(ctx, level, _ints(frames), len(frames), th.ctypes.data_as(_dp), C.byref(st)), ctx)
+    return th, st.as_dict()
+
+
+def stml_get_affine(ctx, n: int, d: int) -> np.ndarray:
+    out = np.zeros((n, d * (d + 1)))
+    _check(load().stml_get_affine(ctx, out.ctypes.data_as(_dp), out.size), ctx)
+    return out
 
 
 # ------------------------------------------------- learned temporal predictor

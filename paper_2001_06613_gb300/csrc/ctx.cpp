@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <functional>
 #include <initializer_list>
 #include <map>
 #include <string>
@@ -90,6 +91,15 @@ struct stml_ctx {
     std::map<std::array<int, 3>, ObjShapeChoice> obj_tuned;
     std::map<std::array<int, 2>, int> coop_tuned;
 
+    // affine variant (params.transform = 1): parameters of all frames (host),
+    // device and pinned staging buffers for one evaluation
+    std::vector<double> theta;
+    float* d_theta = nullptr;
+    double *d_gth = nullptr, *d_aff_part = nullptr;
+    float* h_theta = nullptr;
+    double* h_gth = nullptr;
+    int aff_cap = 0;                  // frames the affine buffers hold
+
     // learned temporal predictor (stml_set_predictor_net) and its last decisions
     ::stml_net* net = nullptr;
     int pred_learned = -1;
@@ -149,6 +159,11 @@ bool valid_params(const stml_params* p, std::string& why) {
     if (!(p->tol_cg > 0) || !(p->armijo_c > 0 && p->armijo_c < 1)) { why = "tol_cg > 0 and 0 < armijo_c < 1"; return false; }
     if (p->pcg_cooperative != 0 && p->pcg_cooperative != 1) { why = "pcg_cooperative must be 0 or 1"; return false; }
     if (p->autotune != 0 && p->autotune != 1) { why = "autotune must be 0 or 1"; return false; }
+    if (p->transform != 0 && p->transform != 1) { why = "transform must be 0 or 1"; return false; }
+    if (p->lbfgs_m < 1 || p->lbfgs_m > 64 || p->max_lbfgs < 0) {
+        why = "lbfgs_m must be in 1..64 and max_lbfgs >= 0";
+        return false;
+    }
     if (p->image_dtype < STML_DTYPE_F32 || p->image_dtype > STML_DTYPE_BF16) {
         why = "image_dtype must be STML_DTYPE_F32, _F16 or _BF16";
         return false;
@@ -184,6 +199,12 @@ void free_buffers(stml_ctx* c) {
     dfree(c->w_p2); dfree(c->w_cz); dfree(c->w_sp0); dfree(c->w_sp1);
     dfree(c->d_frames); dfree(c->d_wnext); dfree(c->d_idx); dfree(c->d_lsf);
     dfree(c->d_kidx); dfree(c->d_taps); dfree(c->d_rho);
+    dfree(c->d_theta); dfree(c->d_gth); dfree(c->d_aff_part);
+    if (c->h_theta) cudaFreeHost(c->h_theta);
+    if (c->h_gth) cudaFreeHost(c->h_gth);
+    c->h_theta = nullptr;
+    c->h_gth = nullptr;
+    c->aff_cap = 0;
     c->loaded = c->built = false;
 }
 
@@ -248,12 +269,12 @@ stml_status read_scalars(stml_ctx* c) {
 
 enum ProfClass {
     PC_HESS = 0, PC_EVAL, PC_TRIAL, PC_PCG_INIT, PC_PCG_UPDATE, PC_PCG_P, PC_PCG_COOP,
-    PC_PRED_LS, PC_PRED_LIN, PC_PROLONG, PC_GATHER, PC_RESTRICT, PC_PRED_NET, PC_COUNT
+    PC_PRED_LS, PC_PRED_LIN, PC_PROLONG, PC_GATHER, PC_RESTRICT, PC_PRED_NET, PC_AFFINE, PC_COUNT
 };
 const char* const kProfNames[PC_COUNT] = {
     "gn_hessian_product", "gradient_pass", "objective_pass", "pcg_init", "pcg_update",
     "pcg_direction", "pcg_solve_cooperative", "predict_ls_eq2", "predict_linear", "prolong", "gather_scatter",
-    "restrict", "predict_learned"};
+    "restrict", "predict_learned", "affine_projection"};
 
 // Starts an event pair (returns its index, or -1 when profiling is off).
 long prof_begin(stml_ctx* c, int cls, int level) {
@@ -787,6 +808,301 @@ stml_status learned_fill(stml_ctx* c, int level, const std::vector<int>& Kp, con
     return STML_OK;
 }
 
+// ------------------------------------------------------------ affine variant
+int aff_P(const stml_ctx* c) { return c->d * (c->d + 1); }
+
+stml_status ensure_affine(stml_ctx* c) {
+    if (c->aff_cap >= c->n) return STML_OK;
+    const int P = aff_P(c);
+    dfree(c->d_theta); dfree(c->d_gth); dfree(c->d_aff_part);
+    if (c->h_theta) cudaFreeHost(c->h_theta);
+    if (c->h_gth) cudaFreeHost(c->h_gth);
+    c->h_theta = nullptr;
+    c->h_gth = nullptr;
+    CK(c, dalloc(&c->d_theta, (size_t)c->n * P));
+    CK(c, dalloc(&c->d_gth, (size_t)c->n * P));
+    CK(c, dalloc(&c->d_aff_part, (size_t)c->n * 256 * P));
+    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_theta), sizeof(float) * (size_t)c->n * P));
+    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_gth), sizeof(double) * (size_t)c->n * P));
+    c->aff_cap = c->n;
+    return STML_OK;
+}
+
+AffineFrame affine_frame(const stml_ctx* c) {
+    AffineFrame af{};
+    double ext = 0.0;
+    for (int i = 0; i < c->d; ++i) {
+        const int axis = 3 - c->d + i;           // component i belongs to array axis i
+        af.c[i] = (float)(0.5 * c->shape[axis]);
+        ext = std::max(ext, (double)c->shape[axis]);
+    }
+    af.inv_rho = (float)(2.0 / ext);
+    return af;
+}
+
+// Uploads theta (host doubles, nK x P) and writes its affine fields to u.
+stml_status affine_fields(stml_ctx* c, int level, const double* th, int nK, float* u) {
+    TRY(ensure_affine(c));
+    const int P = aff_P(c);
+    if (c->Sh) CK(c, cudaStreamSynchronize(c->stream));   // staging array free again
+    for (long long i = 0; i < (long long)nK * P; ++i) c->h_theta[i] = (float)th[i];
+    CK(c, cudaMemcpyAsync(c->d_theta, c->h_theta, sizeof(float) * (size_t)nK * P, cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, launch_affine_field(c->lv[level].g, affine_frame(c), c->d_theta, nK, u, c->stream));
+    return STML_OK;
+}
+
+// J, D, S, P and (grad not null) dJ/dtheta at theta for the frames of fs.
+stml_status affine_eval(stml_ctx* c, int level, const FrameSet& fs, const double* th, double* out4, double* grad) {
+    LevelBuf& L = c->lv[level];
+    const int nK = fs.nK, P = aff_P(c);
+    const Coef cf = make_coef(L.g, c->p, nK);
+    TRY(affine_fields(c, level, th, nK, c->w_u));
+    const double pfK = (double)nK * L.g.N;
+    const double bS = (double)store_bytes(c->img_type);
+    long pe = prof_begin(c, PC_TRIAL, level);
+    CK(c, launch_objective(Stored{L.img, c->img_type}, L.g, fs, cf, c->w_u, nullptr, 0.f, nullptr, c->w_abar,
+                           c->w_ubar, c->partials, c->partials_cap, &c->S->ticket[0], c->S->red, c->stream));
+    prof_end(c, pe, pfK * (bS + 4.0 * L.g.d), pfK);
+    if (grad) {
+        pe = prof_begin(c, PC_EVAL, level);
+        CK(c, launch_gradient(Stored{L.img, c->img_type}, L.g, fs, cf, c->w_u, nullptr, 0.f, c->w_abar, c->w_ubar,
+                              c->w_g, c->w_dT, ST_F32, nullptr, c->partials, c->partials_cap, &c->S->ticket[4],
+                              c->S->red, c->stream));
+        prof_end(c, pe, pfK * (bS + 20.0 * L.g.d), pfK);
+        pe = prof_begin(c, PC_AFFINE, level);
+        CK(c, launch_affine_project(L.g, affine_frame(c), c->w_g, nK, c->d_aff_part, c->d_gth, c->stream));
+        prof_end(c, pe, pfK * 4.0 * L.g.d, pfK);
+        CK(c, cudaMemcpyAsync(c->h_gth, c->d_gth, sizeof(double) * (size_t)nK * P, cudaMemcpyDeviceToHost,
+                              c->stream));
+    }
+    TRY(read_scalars(c));
+    for (int i = 0; i < 4; ++i) out4[i] = c->Sh->red[i];
+    if (grad) std::memcpy(grad, c->h_gth, sizeof(double) * (size_t)nK * P);
+    return std::isfinite(out4[0]) ? STML_OK : fail(c, STML_ENONFINITE, "objective is not finite");
+}
+
+double dotv(const std::vector<double>& a, const std::vector<double>& b) {
+    double s = 0.0;
+    for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+    return s;
+}
+double normv(const std::vector<double>& a) { return std::sqrt(dotv(a, a)); }
+
+// GIR(K) over the affine parameters by L-BFGS (two-loop recursion), in place.
+stml_status run_gir_affine(stml_ctx* c, int level, const std::vector<int>& K, double* th, stml_stats* st) {
+    const auto t_start = std::chrono::steady_clock::now();
+    const stml_params& p = c->p;
+    const int nK = (int)K.size(), P = aff_P(c);
+    const size_t n = (size_t)nK * P;
+    FrameSet fs;
+    TRY(upload_frameset(c, K, fs));
+    std::vector<double> x(th, th + n), g(n), xt(n), gt(n), d(n);
+    double e[4], et[4];
+    TRY(affine_eval(c, level, fs, x.data(), e, g.data()));
+    stml_stats s{};
+    s.level = level;
+    s.n_frames = nK;
+    s.status = STML_OK;
+    s.pred_learned = s.fill_learned = -1;
+    const double J0 = e[0];
+    s.J0 = J0;
+    double J = J0, J_old = 0.0, step = 0.0;
+    std::vector<std::vector<double>> S, Y;
+    int it = 0;
+    while (true) {
+        const double gnorm = normv(g);
+        if (it > 0) {
+            const bool c1 = std::fabs(J_old - J) <= p.tol_J * (1.0 + std::fabs(J0));
+            const bool c2 = step <= p.tol_Y * (1.0 + normv(x));
+            const bool c3 = gnorm <= p.tol_G * (1.0 + std::fabs(J0));
+            if (c1 && c2 && c3) break;
+        }
+        if (gnorm <= p.g_abs * (1.0 + std::fabs(J0)) || it >= p.max_lbfgs) break;
+        bool have = false;
+        if (!S.empty()) {   // two-loop recursion, H0 = gamma I from the newest pair
+            std::vector<double> q = g, alpha(S.size()), rho(S.size());
+            for (int i = (int)S.size() - 1; i >= 0; --i) {
+                rho[i] = 1.0 / dotv(Y[i], S[i]);
+                alpha[i] = rho[i] * dotv(S[i], q);
+                for (size_t j = 0; j < n; ++j) q[j] -= alpha[i] * Y[i][j];
+            }
+            const double gamma = dotv(S.back(), Y.back()) / dotv(Y.back(), Y.back());
+            for (size_t j = 0; j < n; ++j) q[j] *= gamma;
+            for (size_t i = 0; i < S.size(); ++i) {
+                const double beta = rho[i] * dotv(Y[i], q);
+                for (size_t j = 0; j < n; ++j) q[j] += (alpha[i] - beta) * S[i][j];
+            }
+            for (size_t j = 0; j < n; ++j) d[j] = -q[j];
+            have = dotv(g, d) < 0.0;
+        }
+        if (!have) {        // first step, or not a descent direction: scaled -g, memory cleared
+            S.clear();
+            Y.clear();
+            double gmax = 0.0;
+            for (double v : g) gmax = std::max(gmax, std::fabs(v));
+            for (size_t j = 0; j < n; ++j) d[j] = -g[j] / gmax;
+        }
+        const double gTd = dotv(g, d);
+        double t = 1.0;
+        bool accepted = false;
+        for (int trial = 0; trial < p.max_ls; ++trial) {
+            ++s.ls_trials;
+            for (size_t j = 0; j < n; ++j) xt[j] = x[j] + t * d[j];
+            TRY(affine_eval(c, level, fs, xt.data(), et, gt.data()));
+            if (et[0] <= J + p.armijo_c * t * gTd) {
+                accepted = true;
+                break;
+            }
+            t *= 0.5;
+        }
+        if (!accepted) {
+            s.status = STML_ELINESEARCH;
+            break;
+        }
+        std::vector<double> sv(n), yv(n);
+        for (size_t j = 0; j < n; ++j) {
+            sv[j] = xt[j] - x[j];
+            yv[j] = gt[j] - g[j];
+        }
+        if (dotv(sv, yv) > 1e-12 * normv(sv) * normv(yv)) {
+            S.push_back(sv);
+            Y.push_back(yv);
+            if ((int)S.size() > p.lbfgs_m) {
+                S.erase(S.begin());
+                Y.erase(Y.begin());
+            }
+        }
+        step = normv(sv);
+        x.swap(xt);
+        g.swap(gt);
+        J_old = J;
+        J = et[0];
+        std::memcpy(e, et, sizeof(e));
+        ++it;
+    }
+    std::copy(x.begin(), x.end(), th);
+    s.gn_iters = it;
+    s.cg_iters = 0;
+    s.J = e[0];
+    s.D = e[1];
+    s.S = e[2];
+    s.P = e[3];
+    s.J0_classic = s.J0;
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (st) *st = s;
+    return STML_OK;
+}
+
+// Linear predictor of Sec. 3 on the parameters (host): rows of `targets`
+// from the rows of thK registered on K.
+void aff_predict_linear(const std::vector<int>& K, const double* thK, const std::vector<int>& targets, int P,
+                        double* out /* indexed by frame */) {
+    for (int k : targets) {
+        auto it = std::lower_bound(K.begin(), K.end(), k);
+        double* o = out + (size_t)k * P;
+        if (it != K.end() && *it == k) {
+            std::memcpy(o, thK + (size_t)(it - K.begin()) * P, sizeof(double) * P);
+            continue;
+        }
+        const int ir = (int)(it - K.begin()), il = ir - 1;
+        const double wl = (double)(K[ir] - k) / (K[ir] - K[il]), wr = (double)(k - K[il]) / (K[ir] - K[il]);
+        for (int j = 0; j < P; ++j) o[j] = wl * thK[(size_t)il * P + j] + wr * thK[(size_t)ir * P + j];
+    }
+}
+
+// Least-squares predictor of eq. (2) per parameter (host, Thomas):
+// zeta = omega + e, (D_K + beta L) e = D_K (eta - omega).
+void aff_predict_ls(int n, const std::vector<int>& K, const double* thK, const double* omega, double beta, int P,
+                    double* zeta) {
+    std::vector<double> sub(n, 0.0), dia(n, 0.0), sup(n, 0.0), cp(n), dp(n), rhs(n);
+    std::vector<int> pos(n, -1);
+    for (size_t i = 0; i < K.size(); ++i) {
+        dia[K[i]] += 1.0;
+        pos[K[i]] = (int)i;
+    }
+    for (int k = 0; k + 1 < n; ++k) {
+        dia[k] += beta;
+        dia[k + 1] += beta;
+        sup[k] -= beta;
+        sub[k + 1] -= beta;
+    }
+    for (int j = 0; j < P; ++j) {
+        for (int k = 0; k < n; ++k)
+            rhs[k] = pos[k] >= 0 ? thK[(size_t)pos[k] * P + j] - omega[(size_t)k * P + j] : 0.0;
+        cp[0] = sup[0] / dia[0];
+        dp[0] = rhs[0] / dia[0];
+        for (int k = 1; k < n; ++k) {
+            const double den = dia[k] - sub[k] * cp[k - 1];
+            cp[k] = sup[k] / den;
+            dp[k] = (rhs[k] - sub[k] * dp[k - 1]) / den;
+        }
+        double ek = dp[n - 1];
+        zeta[(size_t)(n - 1) * P + j] = omega[(size_t)(n - 1) * P + j] + ek;
+        for (int k = n - 2; k >= 0; --k) {
+            ek = dp[k] - cp[k] * ek;
+            zeta[(size_t)k * P + j] = omega[(size_t)k * P + j] + ek;
+        }
+    }
+}
+
+// STML / SpML over the affine parameters; afterwards every level's fields
+// are the affine fields of its result.
+stml_status register_affine(stml_ctx* c, stml_mode mode, const std::function<void(const stml_stats&)>& record) {
+    const int n = c->n, P = aff_P(c), L = (int)c->lv.size();
+    c->theta.assign((size_t)n * P, 0.0);
+    std::vector<int> all(n);
+    for (int k = 0; k < n; ++k) all[k] = k;
+    for (int l = 0; l < L; ++l) {
+        if (mode == STML_MODE_SPML) {
+            stml_stats s{};
+            TRY(run_gir_affine(c, l, all, c->theta.data(), &s));
+            s.tlevel = (int)c->sets.size() - 1;
+            record(s);
+        } else {
+            std::vector<double> z = c->theta, zn((size_t)n * P);
+            double dhat_prev = 0.0;
+            const int Q = (int)c->sets.size();
+            for (int q = 0; q < Q; ++q) {
+                const std::vector<int>& K = c->sets[q];
+                std::vector<double> thK(K.size() * P);
+                for (size_t i = 0; i < K.size(); ++i)
+                    std::memcpy(&thK[i * P], &z[(size_t)K[i] * P], sizeof(double) * P);
+                stml_stats s{};
+                TRY(run_gir_affine(c, l, K, thK.data(), &s));
+                s.tlevel = q;
+                const double dhat = s.D / (double)K.size();
+                const bool stop = q > 0 && c->p.stop_rule &&
+                                  std::fabs(dhat - dhat_prev) <= c->p.eps_stop * std::fabs(dhat_prev);
+                s.stopped_early = stop ? 1 : 0;
+                record(s);
+                if (q == Q - 1 || stop) {
+                    if (q == Q - 1) {
+                        for (size_t i = 0; i < K.size(); ++i)
+                            std::memcpy(&c->theta[(size_t)K[i] * P], &thK[i * P], sizeof(double) * P);
+                    } else if (l == 0) {
+                        aff_predict_linear(K, thK.data(), all, P, c->theta.data());
+                    } else {
+                        aff_predict_ls(n, K, thK.data(), z.data(), c->p.beta, P, c->theta.data());
+                        for (size_t i = 0; i < K.size(); ++i)
+                            std::memcpy(&c->theta[(size_t)K[i] * P], &thK[i * P], sizeof(double) * P);
+                    }
+                    break;
+                }
+                if (l == 0) {
+                    aff_predict_linear(K, thK.data(), c->sets[q + 1], P, z.data());
+                } else {
+                    aff_predict_ls(n, K, thK.data(), z.data(), c->p.beta, P, zn.data());
+                    z.swap(zn);
+                }
+                dhat_prev = dhat;
+            }
+        }
+        TRY(affine_fields(c, l, c->theta.data(), n, c->lv[l].y));
+    }
+    return STML_OK;
+}
+
 // ------------------------------------------------------------------ STML steps
 stml_status do_predict(stml_ctx* c, int level, int q) {
     LevelBuf& L = c->lv[level];
@@ -906,6 +1222,9 @@ void stml_default_params(stml_params* p) {
     p->image_dtype = STML_DTYPE_F32;
     p->pcg_cooperative = 1;
     p->autotune = 0;
+    p->transform = 0;
+    p->lbfgs_m = 5;
+    p->max_lbfgs = 50;
 }
 
 stml_status stml_create(const stml_params* p, void* cuda_stream, stml_ctx** out) {
@@ -1130,6 +1449,7 @@ stml_status stml_set_field(stml_ctx* c, int level, const float* src, int src_on_
 }
 
 stml_status stml_predict(stml_ctx* c, int level, int tlevel) {
+    if (c && c->p.transform != 0) return fail(c, STML_EINVAL, "stml_predict serves transform 0 only");
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
     TRY(check_level(c, level));
     if (tlevel < 0 || tlevel >= (int)c->sets.size()) return fail(c, STML_EINVAL, "tlevel out of range");
@@ -1138,6 +1458,7 @@ stml_status stml_predict(stml_ctx* c, int level, int tlevel) {
 }
 
 stml_status stml_correct(stml_ctx* c, int level, int tlevel, stml_stats* stats, int* finished) {
+    if (c && c->p.transform != 0) return fail(c, STML_EINVAL, "stml_correct serves transform 0 only");
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
     TRY(check_level(c, level));
     if (tlevel < 0 || tlevel >= (int)c->sets.size()) return fail(c, STML_EINVAL, "tlevel out of range");
@@ -1158,6 +1479,12 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
     const int L = (int)c->lv.size();
     std::vector<int> all(c->n);
     for (int k = 0; k < c->n; ++k) all[k] = k;
+    if (c->p.transform == 1) {
+        TRY(register_affine(c, mode, record));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (n_written) *n_written = written;
+        return STML_OK;
+    }
     for (int l = 0; l < L; ++l) {
         if (mode == STML_MODE_SPML) {
             TRY(do_predict(c, l, 0));
@@ -1317,6 +1644,50 @@ stml_status stml_gir(stml_ctx* c, int level, const int* frames, int nK, float* u
     cudaSetDevice(c->device);
     std::vector<int> K(frames, frames + nK);
     return run_gir(c, level, K, u, stats);
+}
+
+stml_status stml_eval_affine(stml_ctx* c, int level, const int* frames, int nK, const double* theta, double* out,
+                             double* grad) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!theta || !out) return fail(c, STML_EINVAL, "theta and out are required");
+    cudaSetDevice(c->device);
+    std::vector<int> K(frames, frames + nK);
+    FrameSet fs;
+    TRY(upload_frameset(c, K, fs));
+    return affine_eval(c, level, fs, theta, out, grad);
+}
+
+stml_status stml_affine_field(stml_ctx* c, int level, const int* frames, int nK, const double* theta, float* u) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!theta || !u) return fail(c, STML_EINVAL, "theta and u are required");
+    TRY(check_aligned(c, {u}));
+    cudaSetDevice(c->device);
+    TRY(affine_fields(c, level, theta, nK, u));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+stml_status stml_gir_affine(stml_ctx* c, int level, const int* frames, int nK, double* theta_io,
+                            stml_stats* stats) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!theta_io) return fail(c, STML_EINVAL, "theta_io is required");
+    cudaSetDevice(c->device);
+    std::vector<int> K(frames, frames + nK);
+    return run_gir_affine(c, level, K, theta_io, stats);
+}
+
+stml_status stml_get_affine(const stml_ctx* c, double* theta, size_t cap) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (c->theta.empty()) return fail(const_cast<stml_ctx*>(c), STML_ESTATE, "no affine registration yet");
+    if (!theta || cap < c->theta.size()) return fail(const_cast<stml_ctx*>(c), STML_EINVAL, "theta too small");
+    std::memcpy(theta, c->theta.data(), sizeof(double) * c->theta.size());
+    return STML_OK;
 }
 
 stml_status stml_corr_coeff(stml_ctx* c, int level, double* rho) {

@@ -50,6 +50,22 @@ inline unsigned blocks_for(long long n, int threads = kThreads, long long cap = 
 constexpr int kPixPerCta = 32;
 constexpr int kFrameGroups = kThreads / kPixPerCta;
 
+// ------------------------------------------------------------ affine (Sec. 4)
+// Centre c (finest-level pixels, per array axis) and 1 / rho of the affine
+// parametrisation u_k(x) = W_k (x - c) / rho + b_k.
+struct AffineFrame {
+    float c[3];
+    float inv_rho;
+};
+// u (nK, d, N) from theta (nK, d(d+1)) on the device.
+cudaError_t launch_affine_field(const Geom& g, const AffineFrame& af, const float* theta, int nK, float* u,
+                                cudaStream_t s);
+// out (nK, d(d+1), FP64) = projection of the field gradient gu (nK, d, N);
+// part holds nK * affine_project_blocks(g) * d(d+1) doubles.
+int affine_project_blocks(const Geom& g);
+cudaError_t launch_affine_project(const Geom& g, const AffineFrame& af, const float* gu, int nK, double* part,
+                                  double* out, cudaStream_t s);
+
 // ---------------------------------------------------------- transfer ops
 // 2^d block mean of `planes` stored arrays of 2 gc (type: StoreType).
 cudaError_t launch_restrict(const void* fine, void* coarse, int type, int planes, const Geom& gc,
