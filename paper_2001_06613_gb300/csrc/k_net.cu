@@ -104,35 +104,43 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 }  // namespace
 
 // ------------------------------------------------------------ convolution
-template <int BN>
+// CTA tile: BM = 32 WM pixels x BN output channels, WM x 2 warps (warp tile
+// 32 x BN/2), K in chunks of one tap x 32 input channels, STAGES-deep
+// cp.async pipeline.  Shared rows are padded by 16 bytes (row strides of
+// 20 + 8j words), which puts the eight rows of every ldmatrix phase on
+// distinct banks for all tile widths.
+template <int BN, int WM>
 struct ConvCfg {
-    static constexpr int BM = 128, BK = 32, STAGES = 3, THREADS = 128;
-    static constexpr int WARPS_N = BN / 32, WARPS_M = 4 / WARPS_N;
-    static constexpr int WM = BM / WARPS_M;
-    static constexpr int MI = WM / 16, NI = 4;
+    static constexpr int BM = 32 * WM, BK = 32, STAGES = 4, THREADS = 64 * WM;
+    static constexpr int NI = BN / 16;                 // n8 blocks per warp
+    static constexpr int AS = BK + 8, BS = BN + 8;     // padded row lengths (elements)
+    static constexpr int A_ELEMS = BM * AS, B_ELEMS = BK * BS;
+    static constexpr int SMEM = STAGES * (A_ELEMS + B_ELEMS) * 2;
 };
 
-template <int BN>
-__global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __restrict__ Wt, int Cin,
-                                                    int N, int B, int H, int W, ConvOut out) {
-    using C = ConvCfg<BN>;
-    __shared__ __align__(128) bf16 sA[C::STAGES][C::BM * C::BK];
-    __shared__ __align__(128) bf16 sB[C::STAGES][C::BK * BN];
+template <int BN, int WM>
+__global__ void __launch_bounds__(64 * WM) conv3_kernel(ConvIn in, const bf16* __restrict__ Wt, int Cin, int N,
+                                                        int B, int H, int W, ConvOut out) {
+    using C = ConvCfg<BN, WM>;
+    extern __shared__ __align__(128) unsigned char conv_smem[];
+    bf16* sA = reinterpret_cast<bf16*>(conv_smem);
+    bf16* sB = sA + C::STAGES * C::A_ELEMS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp / C::WARPS_N, wn = warp % C::WARPS_N;
+    const int wm = warp >> 1, wn = warp & 1;
     const long long HW = (long long)H * W;
     const long long M = (long long)B * HW;
     const long long m0 = (long long)blockIdx.x * C::BM;
     const int n0 = blockIdx.y * BN;
     const int cpt = Cin / 32, nchunks = 9 * cpt;
 
-    // the 4 rows (pixels) of the A tile this thread copies, one 8-channel segment each
+    // A tile: BM rows x 4 segments of 8 channels; each thread copies 2 rows
+    constexpr int AROWS = C::BM * 4 / C::THREADS;       // = 2
     const int aseg = tid & 3;
-    int an[4], ay[4], ax[4];
-    bool av[4];
+    int an[AROWS], ay[AROWS], ax[AROWS];
+    bool av[AROWS];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const long long m = m0 + (tid >> 2) + 32 * i;
+    for (int i = 0; i < AROWS; ++i) {
+        const long long m = m0 + (tid >> 2) + (C::THREADS / 4) * i;
         av[i] = m < M;
         const long long mm = av[i] ? m : 0;
         an[i] = (int)(mm / HW);
@@ -145,24 +153,25 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         const int tap = j / cpt;
         const int ci = (j - tap * cpt) * 32 + aseg * 8;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        bf16* a_s = sA + st * C::A_ELEMS;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = (tid >> 2) + 32 * i;
+        for (int i = 0; i < AROWS; ++i) {
+            const int r = (tid >> 2) + (C::THREADS / 4) * i;
             const bf16* src = av[i] ? in_at(in, an[i], ay[i] + dy, ax[i] + dx, H, W, ci) : nullptr;
-            cp16(&sA[st][r * 32 + (swz4(r, aseg) << 3)], src ? src : in.a, src ? 16 : 0);
+            cp16(a_s + r * C::AS + aseg * 8, src ? src : in.a, src ? 16 : 0);
         }
         constexpr int SEGS = BN / 8;
-#pragma unroll
+        bf16* b_s = sB + st * C::B_ELEMS;
+        const bf16* wrow = Wt + (long long)j * 32 * N + n0;
         for (int s = tid; s < 32 * SEGS; s += C::THREADS) {
             const int row = s / SEGS, seg = s - row * SEGS;
-            cp16(&sB[st][row * BN + (swzB<BN>(row, seg) << 3)],
-                 Wt + (long long)(j * 32 + row) * N + n0 + seg * 8, 16);
+            cp16(b_s + row * C::BS + seg * 8, wrow + (long long)row * N + seg * 8, 16);
         }
     };
 
-    float acc[C::MI][C::NI][4];
+    float acc[2][C::NI][4];
 #pragma unroll
-    for (int a = 0; a < C::MI; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < C::NI; ++b)
 #pragma unroll
@@ -179,47 +188,42 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         const int jn = j + C::STAGES - 1;
         if (jn < nchunks) load_stage(jn % C::STAGES, jn);
         cp_commit();
-        const bf16* a_s = sA[j % C::STAGES];
-        const bf16* b_s = sB[j % C::STAGES];
+        const bf16* a_s = sA + (j % C::STAGES) * C::A_ELEMS;
+        const bf16* b_s = sB + (j % C::STAGES) * C::B_ELEMS;
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
-            uint32_t af[C::MI][4];
+            uint32_t af[2][4];
 #pragma unroll
-            for (int mi = 0; mi < C::MI; ++mi) {
-                const int row = wm * C::WM + mi * 16 + (lane & 15);
-                const int seg = kk * 2 + (lane >> 4);
-                ldsm_x4(af[mi], a_s + row * 32 + (swz4(row, seg) << 3));
+            for (int mi = 0; mi < 2; ++mi) {
+                const int row = wm * 32 + mi * 16 + (lane & 15);
+                ldsm_x4(af[mi], a_s + row * C::AS + kk * 16 + ((lane >> 4) << 3));
             }
-            uint32_t bfr[C::NI][2];
 #pragma unroll
             for (int nb = 0; nb < C::NI / 2; ++nb) {
                 const int krow = kk * 16 + (lane & 15);
-                const int nseg = (wn * 32 + nb * 16) / 8 + (lane >> 4);
+                const int col = wn * (BN / 2) + nb * 16 + ((lane >> 4) << 3);
                 uint32_t r[4];
-                ldsm_x4_t(r, b_s + krow * BN + (swzB<BN>(krow, nseg) << 3));
-                bfr[2 * nb][0] = r[0];
-                bfr[2 * nb][1] = r[1];
-                bfr[2 * nb + 1][0] = r[2];
-                bfr[2 * nb + 1][1] = r[3];
+                ldsm_x4_t(r, b_s + krow * C::BS + col);
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    mma16816(acc[mi][2 * nb], af[mi], r[0], r[1]);
+                    mma16816(acc[mi][2 * nb + 1], af[mi], r[2], r[3]);
+                }
             }
-#pragma unroll
-            for (int mi = 0; mi < C::MI; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < C::NI; ++ni) mma16816(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
         }
     }
     cp_wait<0>();
 
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int mi = 0; mi < C::MI; ++mi)
+    for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-            const long long m = m0 + wm * C::WM + mi * 16 + g + half * 8;
+            const long long m = m0 + wm * 32 + mi * 16 + g + half * 8;
             if (m >= M) continue;
 #pragma unroll
             for (int ni = 0; ni < C::NI; ++ni) {
-                const int n = n0 + wn * 32 + ni * 8 + 2 * t;
+                const int n = n0 + wn * (BN / 2) + ni * 8 + 2 * t;
                 float v0 = acc[mi][ni][2 * half], v1 = acc[mi][ni][2 * half + 1];
                 if (out.mode == CONV_FWD) {
                     v0 = leaky(v0 + out.bias[n]);
@@ -240,20 +244,41 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         }
 }
 
+template <int BN, int WM>
+static cudaError_t conv3_go(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
+                            const ConvOut& out, cudaStream_t s) {
+    using C = ConvCfg<BN, WM>;
+    static bool attr = false;   // benign race: every caller sets the same value
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv3_kernel<BN, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long M = (long long)B * H * W;
+    dim3 grid((unsigned)((M + C::BM - 1) / C::BM), N / BN);
+    conv3_kernel<BN, WM><<<grid, C::THREADS, C::SMEM, s>>>(in, Wt, Cin, N, B, H, W, out);
+    return cudaGetLastError();
+}
+
+template <int WM>
+static cudaError_t conv3_bn(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
+                            const ConvOut& out, cudaStream_t s) {
+    if (N % 128 == 0) return conv3_go<128, WM>(in, Wt, Cin, N, B, H, W, out, s);
+    if (N % 96 == 0) return conv3_go<96, WM>(in, Wt, Cin, N, B, H, W, out, s);
+    if (N % 64 == 0) return conv3_go<64, WM>(in, Wt, Cin, N, B, H, W, out, s);
+    return conv3_go<32, WM>(in, Wt, Cin, N, B, H, W, out, s);
+}
+
 cudaError_t launch_conv3(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
                          const ConvOut& out, cudaStream_t s) {
     if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 || H <= 0 ||
         W <= 0 || (in.up && ((H | W) & 1)))
         return cudaErrorInvalidValue;
     const long long M = (long long)B * H * W;
-    if (N % 64 == 0) {
-        dim3 grid((unsigned)((M + 127) / 128), N / 64);
-        conv3_kernel<64><<<grid, 128, 0, s>>>(in, Wt, Cin, N, B, H, W, out);
-    } else {
-        dim3 grid((unsigned)((M + 127) / 128), N / 32);
-        conv3_kernel<32><<<grid, 128, 0, s>>>(in, Wt, Cin, N, B, H, W, out);
-    }
-    return cudaGetLastError();
+    // 128-pixel tiles while they give every SM two CTAs, else 64-pixel tiles
+    if ((M + 127) / 128 >= 2 * 152) return conv3_bn<4>(in, Wt, Cin, N, B, H, W, out, s);
+    return conv3_bn<2>(in, Wt, Cin, N, B, H, W, out, s);
 }
 
 // --------------------------------------------------------- weight gradient
