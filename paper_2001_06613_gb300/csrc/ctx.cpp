@@ -794,6 +794,7 @@ stml_status learned_fill(stml_ctx* c, int level, const std::vector<int>& Kp, con
     double Jc = 0.0, Jn = 0.0;
     TRY(objective_of(c, level, Kj, dst, &Jc));
     TRY(objective_of(c, level, Kj, c->w_z2, &Jn));
+    if (net::timed_out(c->net)) return fail(c, STML_ETIMEOUT, "a convolution of the predictor network timed out");
     *J_classic = Jc;
     if (std::isfinite(Jn) && Jn < Jc) {
         for (int k : used)

@@ -5,9 +5,9 @@
 // only where the objective of eq. (1) is lower there than at the classical
 // predictor's.
 //
-// Convolutions are implicit GEMMs on the tensor cores: BF16 operands staged
-// into shared memory by cp.async (zero-filled at the image border), loaded
-// with ldmatrix, multiplied by mma.sync m16n8k16 with FP32 accumulators.
+// Convolutions are implicit GEMMs on the tensor cores.  Forward and input
+// gradient: tcgen05.mma into tensor memory (conv3_kernel); weight gradient:
+// mma.sync m16n8k16 from ldmatrix fragments (wgrad3_kernel).
 //   forward:        Y[p][co]  = sum_{tap, ci} X[p + off(tap)][ci] W[tap][ci][co]
 //   input gradient: dX[p][ci] = sum_{tap, co} G[p + off(tap)][co] W[8 - tap][ci][co]
 //                   (the same kernel with the flipped, transposed weights)
@@ -38,11 +38,6 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
 __device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -104,181 +99,284 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 }  // namespace
 
 // ------------------------------------------------------------ convolution
-// CTA tile: BM = 32 WM pixels x BN output channels, WM x 2 warps (warp tile
-// 32 x BN/2), K in chunks of one tap x 32 input channels, STAGES-deep
-// cp.async pipeline.  Shared rows are padded by 16 bytes (row strides of
-// 20 + 8j words), which puts the eight rows of every ldmatrix phase on
-// distinct banks for all tile widths.
-template <int BN, int WM>
-struct ConvCfg {
-    static constexpr int BM = 32 * WM, BK = 32, STAGES = 4, THREADS = 64 * WM;
-    static constexpr int NI = BN / 16;                 // n8 blocks per warp
-    static constexpr int AS = BK + 8, BS = BN + 8;     // padded row lengths (elements)
-    static constexpr int A_ELEMS = BM * AS, B_ELEMS = BK * BS;
-    static constexpr int SMEM = STAGES * (A_ELEMS + B_ELEMS) * 2;
+// Blackwell tensor-core implicit GEMM: D[128 pixels][BN channels] accumulates
+// in tensor memory (TMEM) from tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulator, M = 128, N = BN, K = 16 per instruction) issued by one thread.
+// K runs over chunks of 64 = 4 x 16 consecutive (tap, channel) indices: every
+// thread gathers its pixel's 8 segments of 8 channels (cp.async, zero-filled
+// outside the image and beyond 9 Cin), the weights arrive as 64-wide K-major
+// rows; both tiles use the 128-byte swizzled K-major layout (8-row atoms of
+// 1024 bytes, 16-byte chunk c of row r stored at chunk c ^ (r & 7)).  A
+// 4-stage ring: the MMAs of a chunk commit to that stage's mbarrier, which
+// must complete before the stage is refilled.  The epilogue reads TMEM with
+// tcgen05.ld (warp w owns lanes = pixels 32w..32w+31).  Every wait is bounded;
+// on expiry the kernel sets *err, skips the remaining work and still frees
+// its TMEM.
+namespace {
+
+constexpr int kTcStages = 3;
+constexpr int kTcA = 128 * 128;           // bytes of one A stage (128 rows x 128 B)
+
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                    // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                              // descriptor version
+    d |= (uint64_t)2 << 61;                              // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+
+// Waits for the completion of phase `parity` of the mbarrier; false after
+// 2^22 polls (well beyond any MMA chunk's latency).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+template <int BN>
+struct TcCfg {
+    static constexpr int B_BYTES = BN * 128;                     // one B stage
+    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+    static constexpr int SMEM = 1024 + kTcStages * (kTcA + B_BYTES) + 64;
+    // instruction descriptor: F32 accumulator, BF16 A and B, both K-major, N, M = 128
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(128 >> 4) << 24);
 };
 
-template <int BN, int WM>
-__global__ void __launch_bounds__(64 * WM) conv3_kernel(ConvIn in, const bf16* __restrict__ Wt, int Cin, int N,
-                                                        int B, int H, int W, ConvOut out) {
-    using C = ConvCfg<BN, WM>;
-    extern __shared__ __align__(128) unsigned char conv_smem[];
-    bf16* sA = reinterpret_cast<bf16*>(conv_smem);
-    bf16* sB = sA + C::STAGES * C::A_ELEMS;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
+template <int BN>
+__global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __restrict__ Wk, int Cin, int N, int Kp,
+                                                    int B, int H, int W, ConvOut out, int* __restrict__ err) {
+    using C = TcCfg<BN>;
+    extern __shared__ unsigned char tc_smem_raw[];
+    const uint32_t raw = smem_u32(tc_smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = tc_smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + kTcStages * kTcA;
+    const uint32_t bars = sB + kTcStages * C::B_BYTES;           // kTcStages mbarriers
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (bars - base) + 8 * kTcStages);
+    unsigned char* gA = gbase;
+    unsigned char* gB = gbase + kTcStages * kTcA;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
     const long long HW = (long long)H * W;
     const long long M = (long long)B * HW;
-    const long long m0 = (long long)blockIdx.x * C::BM;
+    const long long m = (long long)blockIdx.x * 128 + tid;     // this thread's pixel (A row tid)
     const int n0 = blockIdx.y * BN;
-    const int cpt = Cin / 32, nchunks = 9 * cpt;
+    const int nch = Kp / 64;
 
-    // A tile: BM rows x 4 segments of 8 channels; each thread copies 2 rows
-    constexpr int AROWS = C::BM * 4 / C::THREADS;       // = 2
-    const int aseg = tid & 3;
-    int an[AROWS], ay[AROWS], ax[AROWS];
-    bool av[AROWS];
-#pragma unroll
-    for (int i = 0; i < AROWS; ++i) {
-        const long long m = m0 + (tid >> 2) + (C::THREADS / 4) * i;
-        av[i] = m < M;
-        const long long mm = av[i] ? m : 0;
-        an[i] = (int)(mm / HW);
-        const int rem = (int)(mm - (long long)an[i] * HW);
-        ay[i] = rem / W;
-        ax[i] = rem - ay[i] * W;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    if (tid == 0) {
+        for (int i = 0; i < kTcStages; ++i) mbar_init(bars + 8 * i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
 
-    auto load_stage = [&](int st, int j) {
-        const int tap = j / cpt;
-        const int ci = (j - tap * cpt) * 32 + aseg * 8;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        bf16* a_s = sA + st * C::A_ELEMS;
+    // this pixel, the taps inside the image (9-bit mask), and the (tap,
+    // channel) of the first segment of the next chunk to load
+    const bool valid = m < M;
+    int pn = 0, py = 0, px = 0;
+    if (valid) {
+        pn = (int)(m / HW);
+        const int rem = (int)(m - (long long)pn * HW);
+        py = rem / W;
+        px = rem - py * W;
+    }
+    uint32_t inside = 0;
 #pragma unroll
-        for (int i = 0; i < AROWS; ++i) {
-            const int r = (tid >> 2) + (C::THREADS / 4) * i;
-            const bf16* src = av[i] ? in_at(in, an[i], ay[i] + dy, ax[i] + dx, H, W, ci) : nullptr;
-            cp16(a_s + r * C::AS + aseg * 8, src ? src : in.a, src ? 16 : 0);
+    for (int t = 0; t < 9; ++t) {
+        const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+        inside |= ((valid && yy >= 0 && yy < H && xx >= 0 && xx < W) ? 1u : 0u) << t;
+    }
+    const long long pix = ((long long)pn * H + py) * W + px;
+    int ld_tap = 0, ld_ci = 0;
+    // sources of channel 0 at a tap (only dereferenced for taps inside the image)
+    auto tap_src = [&](int t, const bf16*& pa, const bf16*& pb) {
+        const int dy = t / 3 - 1, dx = t - 3 * (t / 3) - 1;
+        const long long sh = (long long)dy * W + dx;
+        if (in.up)
+            pa = in.a + (((long long)pn * (H >> 1) + ((py + dy) >> 1)) * (W >> 1) + ((px + dx) >> 1)) * in.ca;
+        else
+            pa = in.a + (pix + sh) * in.ca;
+        pb = in.b + (pix + sh) * in.cb;
+    };
+    auto load_stage = [&](int st, int j) {
+        unsigned char* a_row = gA + st * kTcA + tid * 128;
+        int tap = ld_tap, ci = ld_ci;
+        const bf16 *pa, *pb;
+        tap_src(tap, pa, pb);
+#pragma unroll
+        for (int sg = 0; sg < 8; ++sg) {
+            const bool use = tap < 9 && ((inside >> tap) & 1u);
+            const bf16* src = ci < in.ca ? pa + ci : pb + (ci - in.ca);
+            cp16(a_row + ((sg ^ (tid & 7)) << 4), use ? src : in.a, use ? 16 : 0);
+            ci += 8;
+            if (ci == Cin) {
+                ci = 0;
+                ++tap;
+                tap_src(tap, pa, pb);
+            }
         }
-        constexpr int SEGS = BN / 8;
-        bf16* b_s = sB + st * C::B_ELEMS;
-        const bf16* wrow = Wt + (long long)j * 32 * N + n0;
-        for (int s = tid; s < 32 * SEGS; s += C::THREADS) {
-            const int row = s / SEGS, seg = s - row * SEGS;
-            cp16(b_s + row * C::BS + seg * 8, wrow + (long long)row * N + seg * 8, 16);
+        ld_tap = tap;
+        ld_ci = ci;
+        unsigned char* b_st = gB + st * C::B_BYTES;
+        const bf16* wsrc = Wk + (long long)n0 * Kp + j * 64;
+#pragma unroll
+        for (int s = tid; s < BN * 8; s += 128) {
+            const int r = s >> 3, sg = s & 7;
+            cp16(b_st + r * 128 + ((sg ^ (r & 7)) << 4), wsrc + (long long)r * Kp + sg * 8, 16);
         }
     };
 
-    float acc[2][C::NI][4];
+    bool ok = true;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < C::NI; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-
-#pragma unroll
-    for (int s = 0; s < C::STAGES - 1; ++s) {
-        if (s < nchunks) load_stage(s, s);
+    for (int s = 0; s < kTcStages - 1; ++s) {
+        if (s < nch) load_stage(s, s);
         cp_commit();
     }
-    for (int j = 0; j < nchunks; ++j) {
-        cp_wait<C::STAGES - 2>();
-        __syncthreads();
-        const int jn = j + C::STAGES - 1;
-        if (jn < nchunks) load_stage(jn % C::STAGES, jn);
-        cp_commit();
-        const bf16* a_s = sA + (j % C::STAGES) * C::A_ELEMS;
-        const bf16* b_s = sB + (j % C::STAGES) * C::B_ELEMS;
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int row = wm * 32 + mi * 16 + (lane & 15);
-                ldsm_x4(af[mi], a_s + row * C::AS + kk * 16 + ((lane >> 4) << 3));
-            }
-#pragma unroll
-            for (int nb = 0; nb < C::NI / 2; ++nb) {
-                const int krow = kk * 16 + (lane & 15);
-                const int col = wn * (BN / 2) + nb * 16 + ((lane >> 4) << 3);
-                uint32_t r[4];
-                ldsm_x4_t(r, b_s + krow * C::BS + col);
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi) {
-                    mma16816(acc[mi][2 * nb], af[mi], r[0], r[1]);
-                    mma16816(acc[mi][2 * nb + 1], af[mi], r[2], r[3]);
-                }
-            }
+    for (int j = 0; j < nch; ++j) {
+        const int st = j % kTcStages;
+        cp_wait<kTcStages - 2>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        // thread 0 also waits for the MMAs of chunk j-1: their stage is refilled below
+        if (tid == 0 && j >= 1 && ok)
+            ok = mbar_wait(bars + 8 * ((j - 1) % kTcStages), (uint32_t)(((j - 1) / kTcStages) & 1));
+        if (!__syncthreads_and(ok)) {     // uniform: every thread leaves together
+            ok = false;
+            break;
         }
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = sw128_desc(sA + st * kTcA + kk * 32);
+                const uint64_t bd = sw128_desc(sB + st * C::B_BYTES + kk * 32);
+                tc_mma(tmem, ad, bd, C::IDESC, (j > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc_commit(bars + 8 * st);
+        }
+        const int jn = j + kTcStages - 1;
+        if (jn < nch) load_stage(jn % kTcStages, jn);
+        cp_commit();
     }
     cp_wait<0>();
-
-    const int g = lane >> 2, t = lane & 3;
+    // all MMAs done: the last commit arrives after every earlier MMA of the thread
+    if (tid == 0 && ok && nch > 0)
+        ok = mbar_wait(bars + 8 * ((nch - 1) % kTcStages), (uint32_t)(((nch - 1) / kTcStages) & 1));
+    ok = __syncthreads_and(ok) != 0;      // the epilogue's tcgen05.ld is warp-collective
+    tc_fence_after();
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 8) {
+            float v[8];
+            tc_ld8(trow + (uint32_t)c0, v);
+            if (!valid) continue;
+            const int n = n0 + c0;
+            if (out.mode == CONV_FWD) {
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+                for (int i = 0; i < 8; ++i) v[i] = leaky(v[i] + out.bias[n + i]);
+                *reinterpret_cast<uint4*>(out.y + m * N + n) = pack8(v);
+            } else if (out.mode == CONV_MASK) {
+                float k[8];
+                unpack8(*reinterpret_cast<const uint4*>(out.mask + m * N + n), k);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const long long m = m0 + wm * 32 + mi * 16 + g + half * 8;
-            if (m >= M) continue;
-#pragma unroll
-            for (int ni = 0; ni < C::NI; ++ni) {
-                const int n = n0 + wn * (BN / 2) + ni * 8 + 2 * t;
-                float v0 = acc[mi][ni][2 * half], v1 = acc[mi][ni][2 * half + 1];
-                if (out.mode == CONV_FWD) {
-                    v0 = leaky(v0 + out.bias[n]);
-                    v1 = leaky(v1 + out.bias[n + 1]);
-                    *reinterpret_cast<__nv_bfloat162*>(out.y + m * N + n) = __floats2bfloat162_rn(v0, v1);
-                } else if (out.mode == CONV_MASK) {
-                    const float2 k = __bfloat1622float2(
-                        *reinterpret_cast<const __nv_bfloat162*>(out.mask + m * N + n));
-                    *reinterpret_cast<__nv_bfloat162*>(out.y + m * N + n) =
-                        __floats2bfloat162_rn(v0 * slope(k.x), v1 * slope(k.y));
-                } else if (n < out.n1) {
-                    *reinterpret_cast<float2*>(out.f1 + m * out.n1 + n) = make_float2(v0, v1);
-                } else {
-                    *reinterpret_cast<float2*>(out.f2 + m * (N - out.n1) + (n - out.n1)) =
-                        make_float2(v0, v1);
-                }
+                for (int i = 0; i < 8; ++i) v[i] *= slope(k[i]);
+                *reinterpret_cast<uint4*>(out.y + m * N + n) = pack8(v);
+            } else {
+                float* dst = n < out.n1 ? out.f1 + m * out.n1 + n : out.f2 + m * (N - out.n1) + (n - out.n1);
+                reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
         }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+    }
 }
 
-template <int BN, int WM>
-static cudaError_t conv3_go(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
-                            const ConvOut& out, cudaStream_t s) {
-    using C = ConvCfg<BN, WM>;
+template <int BN>
+static cudaError_t conv3_go(const ConvIn& in, const bf16* Wk, int Cin, int N, int B, int H, int W,
+                            const ConvOut& out, int* err, cudaStream_t s) {
+    using C = TcCfg<BN>;
     static bool attr = false;   // benign race: every caller sets the same value
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv3_kernel<BN, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             C::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(conv3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const long long M = (long long)B * H * W;
-    dim3 grid((unsigned)((M + C::BM - 1) / C::BM), N / BN);
-    conv3_kernel<BN, WM><<<grid, C::THREADS, C::SMEM, s>>>(in, Wt, Cin, N, B, H, W, out);
+    const int Kp = conv_kpad(Cin);
+    dim3 grid((unsigned)((M + 127) / 128), N / BN);
+    conv3_kernel<BN><<<grid, 128, C::SMEM, s>>>(in, Wk, Cin, N, Kp, B, H, W, out, err);
     return cudaGetLastError();
 }
 
-template <int WM>
-static cudaError_t conv3_bn(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
-                            const ConvOut& out, cudaStream_t s) {
-    if (N % 128 == 0) return conv3_go<128, WM>(in, Wt, Cin, N, B, H, W, out, s);
-    if (N % 96 == 0) return conv3_go<96, WM>(in, Wt, Cin, N, B, H, W, out, s);
-    if (N % 64 == 0) return conv3_go<64, WM>(in, Wt, Cin, N, B, H, W, out, s);
-    return conv3_go<32, WM>(in, Wt, Cin, N, B, H, W, out, s);
-}
-
-cudaError_t launch_conv3(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
-                         const ConvOut& out, cudaStream_t s) {
+cudaError_t launch_conv3(const ConvIn& in, const bf16* Wk, int Cin, int N, int B, int H, int W,
+                         const ConvOut& out, int* err, cudaStream_t s) {
     if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 || H <= 0 ||
-        W <= 0 || (in.up && ((H | W) & 1)))
+        W <= 0 || (in.up && ((H | W) & 1)) || !err)
         return cudaErrorInvalidValue;
-    const long long M = (long long)B * H * W;
-    // 128-pixel tiles while they give every SM two CTAs, else 64-pixel tiles
-    if ((M + 127) / 128 >= 2 * 152) return conv3_bn<4>(in, Wt, Cin, N, B, H, W, out, s);
-    return conv3_bn<2>(in, Wt, Cin, N, B, H, W, out, s);
+    if (N % 128 == 0) return conv3_go<128>(in, Wk, Cin, N, B, H, W, out, err, s);
+    if (N % 96 == 0) return conv3_go<96>(in, Wk, Cin, N, B, H, W, out, err, s);
+    if (N % 64 == 0) return conv3_go<64>(in, Wk, Cin, N, B, H, W, out, err, s);
+    return conv3_go<32>(in, Wk, Cin, N, B, H, W, out, err, s);
 }
 
 // --------------------------------------------------------- weight gradient
@@ -828,39 +926,44 @@ __global__ void pack_kernel(const float* __restrict__ th, PackTable t, long long
         int l = 0;
         bool flip = false;
         for (; l < t.n; ++l) {
-            const long long nf = 9LL * t.cin[l] * t.cout[l];
+            const long long nf = (long long)t.cout[l] * conv_kpad(t.cin[l]);
             if (r < nf) break;
             r -= nf;
             if (t.wd[l]) {
-                if (r < nf) {
+                const long long nd = (long long)t.cin[l] * conv_kpad(t.cout[l]);
+                if (r < nd) {
                     flip = true;
                     break;
                 }
-                r -= nf;
+                r -= nd;
             }
         }
         if (l >= t.n) continue;
         const int cin = t.cin[l], cout = t.cout[l], cr = t.cin_real[l];
-        int tap, ci, co;
-        if (!flip) {
-            co = (int)(r % cout);
-            const long long k = r / cout;
-            ci = (int)(k % cin);
-            tap = (int)(k / cin);
-        } else {
-            ci = (int)(r % cin);
-            const long long k = r / cin;
-            co = (int)(k % cout);
-            tap = 8 - (int)(k / cout);
+        float v = 0.f;
+        if (!flip) {   // wf[co][k], k = tap cin + ci
+            const int Kp = conv_kpad(cin);
+            const int co = (int)(r / Kp), k = (int)(r % Kp);
+            if (k < 9 * cin) {
+                const int tap = k / cin, ci = k % cin;
+                if (ci < cr) v = th[t.w_off[l] + ((long long)tap * cr + ci) * cout + co];
+            }
+        } else {       // wd[ci][k'], k' = tap' cout + co, tap = 8 - tap'
+            const int Kp = conv_kpad(cout);
+            const int ci = (int)(r / Kp), k = (int)(r % Kp);
+            if (k < 9 * cout && ci < cr) {
+                const int tap = 8 - k / cout, co = k % cout;
+                v = th[t.w_off[l] + ((long long)tap * cr + ci) * cout + co];
+            }
         }
-        const float v = ci < cr ? th[t.w_off[l] + ((long long)tap * cr + ci) * cout + co] : 0.f;
         (flip ? t.wd[l] : t.wf[l])[r] = __float2bfloat16_rn(v);
     }
 }
 
 cudaError_t launch_pack(const float* theta, const PackTable& t, cudaStream_t s) {
     long long total = 0;
-    for (int l = 0; l < t.n; ++l) total += 9LL * t.cin[l] * t.cout[l] * (t.wd[l] ? 2 : 1);
+    for (int l = 0; l < t.n; ++l)
+        total += (long long)t.cout[l] * conv_kpad(t.cin[l]) + (t.wd[l] ? (long long)t.cin[l] * conv_kpad(t.cout[l]) : 0);
     long long blocks = (total + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(theta, t, total);

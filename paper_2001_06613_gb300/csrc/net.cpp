@@ -56,6 +56,7 @@ struct stml_net {
     float *wpart = nullptr, *bpart = nullptr, *hpart = nullptr;
     size_t wpart_cap = 0, bpart_cap = 0;
     double *loss_d = nullptr, *loss_h = nullptr;
+    int *err_d = nullptr, *err_h = nullptr;      // set by a convolution whose bounded wait expired
     Sample *smp_d = nullptr, *smp_h = nullptr;
     cudaEvent_t smp_ev = nullptr;
     bool smp_pending = false;
@@ -101,8 +102,10 @@ void free_all(stml_net* n) {
     for (auto& a : n->pool) f(a);
     f(n->base); f(n->tgt); f(n->gz1); f(n->gz2); f(n->fup);
     for (auto& a : n->skip) f(a);
-    f(n->dp); f(n->wpart); f(n->bpart); f(n->hpart); f(n->loss_d); f(n->smp_d);
+    f(n->dp); f(n->wpart); f(n->bpart); f(n->hpart); f(n->loss_d); f(n->smp_d); f(n->err_d);
     if (n->loss_h) cudaFreeHost(n->loss_h);
+    if (n->err_h) cudaFreeHost(n->err_h);
+    n->err_h = nullptr;
     if (n->smp_h) cudaFreeHost(n->smp_h);
     n->loss_h = nullptr;
     n->smp_h = nullptr;
@@ -125,21 +128,25 @@ cudaError_t alloc_all(stml_net* n) {
     ECK(nalloc(&n->v, kParams));
     ECK(nalloc(&n->grad, kParams));
     long long wtot = 0;
-    for (int l = 0; l < kLayers; ++l) wtot += 9LL * kDefs[l].cin * kDefs[l].cout * (l == E0A ? 1 : 2);
+    for (int l = 0; l < kLayers; ++l)
+        wtot += (long long)kDefs[l].cout * conv_kpad(kDefs[l].cin) +
+                (l == E0A ? 0 : (long long)kDefs[l].cin * conv_kpad(kDefs[l].cout));
     ECK(nalloc(&n->wbuf, wtot));
     bf16* w = n->wbuf;
     n->pt.n = kLayers;
     for (int l = 0; l < kLayers; ++l) {
-        const long long nf = 9LL * kDefs[l].cin * kDefs[l].cout;
         n->pt.cin_real[l] = kDefs[l].cin_real;
         n->pt.cin[l] = kDefs[l].cin;
         n->pt.cout[l] = kDefs[l].cout;
         n->pt.w_off[l] = n->w_off[l];
         n->pt.wf[l] = w;
-        w += nf;
+        w += (long long)kDefs[l].cout * conv_kpad(kDefs[l].cin);
         n->pt.wd[l] = l == E0A ? nullptr : w;
-        if (l != E0A) w += nf;
+        if (l != E0A) w += (long long)kDefs[l].cin * conv_kpad(kDefs[l].cout);
     }
+    ECK(nalloc(&n->err_d, 1));
+    ECK(cudaMemset(n->err_d, 0, sizeof(int)));
+    ECK(cudaMallocHost(reinterpret_cast<void**>(&n->err_h), sizeof(int)));
     for (int l = 0; l < kLayers; ++l)
         ECK(nalloc(&n->act[l], (size_t)((P0 >> (2 * kDefs[l].level)) * kDefs[l].cout)));
     ECK(nalloc(&n->x0, (size_t)(P0 * kInPad)));
@@ -218,7 +225,8 @@ cudaError_t forward_pass(stml_net* n, int B, int H, int W, bool train, cudaStrea
             ++launches;
         }
         ConvOut o{CONV_FWD, n->theta + n->b_off[l], n->act[l], nullptr, nullptr, nullptr, 0};
-        ECK(launch_conv3(layer_input(n, l), n->pt.wf[l], kDefs[l].cin, kDefs[l].cout, B, H8 >> lv, W8 >> lv, o, s));
+        ECK(launch_conv3(layer_input(n, l), n->pt.wf[l], kDefs[l].cin, kDefs[l].cout, B, H8 >> lv, W8 >> lv, o,
+                         n->err_d, s));
         ++launches;
     }
     count_launches(launches);
@@ -244,7 +252,7 @@ cudaError_t layer_dgrad(stml_net* n, int l, const bf16* G, int B, int H8, int W8
     const int lv = kDefs[l].level;
     count_launches(1);
     return launch_conv3(cin1(G, kDefs[l].cout), n->pt.wd[l], kDefs[l].cout, kDefs[l].cin, B, H8 >> lv, W8 >> lv,
-                        o, s);
+                        o, n->err_d, s);
 }
 
 ConvOut mask_out(bf16* y, const bf16* mask) { return ConvOut{CONV_MASK, nullptr, y, mask, nullptr, nullptr, 0}; }
@@ -318,6 +326,17 @@ cudaError_t backward_pass(stml_net* n, int B, int H, int W, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// STML_ETIMEOUT (and the flag cleared) if a convolution's bounded wait
+// expired since the last check; the stream must be synchronised.
+stml_status check_err(stml_net* n) {
+    NCK(n, cudaMemcpy(n->err_h, n->err_d, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*n->err_h) {
+        NCK(n, cudaMemset(n->err_d, 0, sizeof(int)));
+        return net_fail(n, STML_ETIMEOUT, "a convolution's bounded wait expired");
+    }
+    return STML_OK;
+}
+
 stml_status check_batch(stml_net* n, const stml_net_sample* smp, int B, int H, int W, bool need_target,
                         bool need_out) {
     if (!n) return net_fail(nullptr, STML_EINVAL, "net is NULL");
@@ -348,6 +367,12 @@ void to_internal(const stml_net_sample* smp, int B, std::vector<Sample>& out) {
 // ---------------------------------------------------- used by the registration
 bool stml::net::fits(const ::stml_net* n, int H, int W) { return n && pad8(H) <= n->maxH8 && pad8(W) <= n->maxW8; }
 int stml::net::max_batch(const ::stml_net* n) { return n ? n->maxB : 0; }
+bool stml::net::timed_out(::stml_net* n) {
+    if (cudaMemcpy(n->err_h, n->err_d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+    if (!*n->err_h) return false;
+    cudaMemset(n->err_d, 0, sizeof(int));
+    return true;
+}
 
 cudaError_t stml::net::forward_on(::stml_net* n, const Sample* smp, int B, int H, int W, cudaStream_t s) {
     if (B < 1 || B > n->maxB || !fits(n, H, W)) return cudaErrorInvalidValue;
@@ -416,7 +441,7 @@ stml_status stml_net_get_params(stml_net* n, float* params, size_t n_params) {
     cudaSetDevice(n->device);
     NCK(n, cudaMemcpyAsync(params, n->theta, kParams * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     NCK(n, cudaStreamSynchronize(n->stream));
-    return STML_OK;
+    return check_err(n);
 }
 
 stml_status stml_net_forward(stml_net* n, const stml_net_sample* smp, int B, int H, int W) {
@@ -443,7 +468,7 @@ stml_status stml_net_loss_grad(stml_net* n, const stml_net_sample* smp, int B, i
     if (grad) NCK(n, cudaMemcpyAsync(grad, n->grad, kParams * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     NCK(n, cudaStreamSynchronize(n->stream));
     if (loss) *loss = *n->loss_h;
-    return STML_OK;
+    return check_err(n);
 }
 
 stml_status stml_net_train_step(stml_net* n, const stml_net_sample* smp, int B, int H, int W, const stml_adam* opt,
@@ -471,6 +496,7 @@ stml_status stml_net_train_step(stml_net* n, const stml_net_sample* smp, int B, 
         NCK(n, cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
         NCK(n, cudaStreamSynchronize(n->stream));
         *loss = *n->loss_h;
+        return check_err(n);
     }
     return STML_OK;
 }
@@ -485,12 +511,16 @@ stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const
     const long long nw = 9LL * Cin * Cout;
     bf16 *xb = nullptr, *ab = nullptr, *yb = nullptr, *wf = nullptr, *wd = nullptr;
     float *wpart = nullptr, *bpart = nullptr;
+    int* errd = nullptr;
+    int errh = 0;
     const size_t wcap = (size_t)nw * 64, bcap = 256 * 256;
     cudaError_t e = cudaSuccess;
     auto run = [&]() -> cudaError_t {
         ECK(nalloc(&xb, (size_t)(P * (mode == 0 ? Cin : Cout))));
-        ECK(nalloc(&wf, (size_t)nw));
-        ECK(nalloc(&wd, (size_t)nw));
+        ECK(nalloc(&wf, (size_t)Cout * conv_kpad(Cin)));
+        ECK(nalloc(&wd, (size_t)Cin * conv_kpad(Cout)));
+        ECK(nalloc(&errd, 1));
+        ECK(cudaMemsetAsync(errd, 0, sizeof(int), s));
         PackTable t{};
         t.n = 1;
         t.cin_real[0] = Cin;
@@ -504,10 +534,10 @@ stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const
         if (mode == 0) {
             ECK(nalloc(&yb, (size_t)(P * Cout)));
             ConvOut o{CONV_FWD, b, yb, nullptr, nullptr, nullptr, 0};
-            ECK(launch_conv3(cin1(xb, Cin), wf, Cin, Cout, B, H, W_, o, s));
+            ECK(launch_conv3(cin1(xb, Cin), wf, Cin, Cout, B, H, W_, o, errd, s));
             ECK(launch_from_bf16(yb, y, P * Cout, s));
         } else if (mode == 1) {
-            ECK(launch_conv3(cin1(xb, Cout), wd, Cout, Cin, B, H, W_, split_out(y, Cin, nullptr), s));
+            ECK(launch_conv3(cin1(xb, Cout), wd, Cout, Cin, B, H, W_, split_out(y, Cin, nullptr), errd, s));
         } else {
             ECK(nalloc(&ab, (size_t)(P * Cin)));
             ECK(launch_to_bf16(a, ab, P * Cin, s));
@@ -518,12 +548,15 @@ stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const
             ECK(launch_colsum(xb, P, Cout, bpart, bcap, &bs, s));
             ECK(launch_reduce_grad(wpart, ws, Cin, Cin, Cout, bpart, bs, y, 0, nw, s));
         }
-        return cudaStreamSynchronize(s);
+        ECK(cudaStreamSynchronize(s));
+        if (errd) ECK(cudaMemcpy(&errh, errd, sizeof(int), cudaMemcpyDeviceToHost));
+        return cudaSuccess;
     };
     e = run();
-    for (void* p : {(void*)xb, (void*)ab, (void*)yb, (void*)wf, (void*)wd, (void*)wpart, (void*)bpart})
+    for (void* p : {(void*)xb, (void*)ab, (void*)yb, (void*)wf, (void*)wd, (void*)wpart, (void*)bpart, (void*)errd})
         if (p) cudaFree(p);
     if (e != cudaSuccess) return net_fail(nullptr, STML_ECUDA, std::string("stml_net_conv3_block: ") + cudaGetErrorString(e));
+    if (errh) return net_fail(nullptr, STML_ETIMEOUT, "stml_net_conv3_block: a bounded wait expired");
     return STML_OK;
 }
 

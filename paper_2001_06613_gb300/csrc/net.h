@@ -69,13 +69,17 @@ struct ConvOut {
     int n1;
 };
 
+// Row length of the K-major weights of a convolution with `cin` input
+// channels: 9 cin rounded up to the 64-wide K chunks of the tensor-core kernel.
+__host__ __device__ inline int conv_kpad(int cin) { return (9 * cin + 63) / 64 * 64; }
+
 // Layer table of the packing kernel: parameter offsets and packed weights.
 constexpr int kLayers = 14;
 struct PackTable {
     int cin_real[kLayers], cin[kLayers], cout[kLayers];
     long long w_off[kLayers];           // offset of W[ky][kx][ci][co] in theta
-    bf16* wf[kLayers];                  // [9 cin][cout], ci >= cin_real zero
-    bf16* wd[kLayers];                  // [9 cout][cin] flipped (null: not needed)
+    bf16* wf[kLayers];                  // [cout][conv_kpad(cin)], k = tap cin + ci (ci >= cin_real zero)
+    bf16* wd[kLayers];                  // [cin][conv_kpad(cout)], k = tap' cout + co of W[8 - tap'] (null: not needed)
     int n;
 };
 
@@ -83,9 +87,10 @@ struct PackTable {
 // (device array `smp` of B entries), canvases H8 x W8 with the real H x W.
 cudaError_t launch_assemble(const Sample* smp, int B, int H, int W, int H8, int W8, bf16* x0,
                             float* base, float* tgt, cudaStream_t s);
-// 3x3 convolution of the B x H x W maps of `in` with Wt [9 Cin][N].
-cudaError_t launch_conv3(const ConvIn& in, const bf16* Wt, int Cin, int N, int B, int H, int W,
-                         const ConvOut& out, cudaStream_t s);
+// 3x3 convolution of the B x H x W maps of `in` with K-major weights
+// Wk [N][conv_kpad(Cin)]; *err (device) is set to 1 if a bounded wait expired.
+cudaError_t launch_conv3(const ConvIn& in, const bf16* Wk, int Cin, int N, int B, int H, int W,
+                         const ConvOut& out, int* err, cudaStream_t s);
 // Partial weight gradients: part[s][9 Cin][N] (FP32) = sum over the s-th slice
 // of pixels of im2col(in)^T G; returns the number of slices used in *splits.
 cudaError_t launch_wgrad3(const ConvIn& in, const bf16* G, int Cin, int N, int B, int H, int W,
@@ -136,6 +141,8 @@ namespace net {
 // True when a level of H x W pixels fits the network's canvas.
 bool fits(const ::stml_net* n, int H, int W);
 int max_batch(const ::stml_net* n);
+// True (and the flag cleared) if a convolution's bounded wait expired; synchronous.
+bool timed_out(::stml_net* n);
 // Proposals of B <= max_batch samples (host descriptors) on stream s.
 cudaError_t forward_on(::stml_net* n, const Sample* host_smp, int B, int H, int W, cudaStream_t s);
 }  // namespace net

@@ -9,6 +9,11 @@ the measured HBM copy bandwidth; "kernel_us_per_launch" gives the device
 time of each kernel class from the library's own CUDA-event profiling.
 Inputs are larger than L2 at the default size, and L2 is flushed before every
 timed call.
+
+    python -m paper_2001_06613_gb300.opbench --op net_forward --shape 256 256 --frames 32
+
+times the learned predictor's forward pass on a batch of `frames` canvases
+(TFLOP/s of its 3x3 convolutions against the measured BF16 peak).
 """
 from __future__ import annotations
 
@@ -32,7 +37,7 @@ def _peak():
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="all",
-                    choices=["all", "hessvec", "eval", "objective", "trial", "predict_ls"])
+                    choices=["all", "hessvec", "eval", "objective", "trial", "predict_ls", "net_forward"])
     ap.add_argument("--shape", type=int, nargs="+", default=[256, 256])
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--iters", type=int, default=20)
@@ -44,6 +49,8 @@ def main(argv=None):
     from paper_2001_06613_gb300 import synthetic
     S.load()
     dev = torch.device("cuda", 0)
+    if args.op == "net_forward":
+        return net_forward(S, torch, synthetic, dev, args)
     shape = tuple(args.shape)
     d = len(shape)
     n = args.frames
@@ -119,6 +126,43 @@ def main(argv=None):
             b = 16 + 8 * len(K) / n        # omega (all + K), zeta x3 (in-place sweep), eta on K
             timed(lambda: S.stml_predict_ls(eta, K, omega, zeta, n, 1e-5, d * N), b * d * pf, op, b * d)
     ctx.close()
+
+
+def net_forward(S, torch, synthetic, dev, args):
+    """Forward pass of the predictor network on B = --frames canvases."""
+    H, W = args.shape[0], args.shape[1]
+    B = args.frames
+    rng = np.random.default_rng(0)
+    f = torch.from_numpy(synthetic.random_field(rng, 2 * B, 2, (H, W), amp=2.0)).to(dev)
+    T = torch.rand((3, B, H, W), device=dev)
+    out = torch.empty((B, 2, H, W), device=dev)
+    net = S.Net(synthetic.net_init_params(0, head_scale=1.0), max_batch=B, max_h=H, max_w=W)
+    smp = S.net_samples(f[:B].contiguous(), f[B:].contiguous(), T[0], T[1], T[2], 1.0, 0.5, out=out)
+    convs = [(0, 7, 32), (0, 32, 32), (1, 32, 64), (1, 64, 64), (2, 64, 96), (2, 96, 96), (3, 96, 128),
+             (3, 128, 128), (2, 224, 96), (2, 96, 96), (1, 160, 64), (1, 64, 64), (0, 96, 32), (0, 32, 32)]
+    H8, W8 = (H + 7) // 8 * 8, (W + 7) // 8 * 8
+    flops = sum(2.0 * B * (H8 >> lv) * (W8 >> lv) * 9 * ci * co for lv, ci, co in convs)
+    for _ in range(args.warmup):
+        S.stml_net_forward(net, smp, H, W)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        S.stml_net_forward(net, smp, H, W)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    net.close()
+    ms = float(np.median(ts))
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    except Exception:
+        peak = 1900.0
+    tf = flops / (ms / 1e3) / 1e12
+    print(json.dumps({"op": "net_forward", "batch": B, "shape": [H, W], "ms": ms, "GFLOP": flops / 1e9,
+                      "TFLOP/s": tf, "frac_of_measured_bf16": tf / peak}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
