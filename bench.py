@@ -161,7 +161,7 @@ def matvec_traffic_per_pixel_frame():
         vals = {}
         for ln in txt.splitlines():
             if ":" in ln and ln.strip().startswith("- "):
-                k, v = ln.strip()[2:].split(":", 1)
+                k, v = ln.strip()[2:].rsplit(":", 1)
                 vals[k.strip()] = v.strip()
         if vals.get("k_gn.cu sha256[:16]") != digest:
             return None
