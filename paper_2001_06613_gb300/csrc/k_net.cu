@@ -99,31 +99,37 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 }  // namespace
 
 // ------------------------------------------------------------ convolution
-// Blackwell tensor-core implicit GEMM: D[128 pixels][BN channels] accumulates
-// in tensor memory (TMEM) from tcgen05.mma (kind::f16, BF16 operands, FP32
-// accumulator, M = 128, N = BN, K = 16 per instruction) issued by one thread.
-// K runs over chunks of 64 = 4 x 16 consecutive (tap, channel) indices: every
-// thread gathers its pixel's 8 segments of 8 channels (cp.async, zero-filled
-// outside the image and beyond 9 Cin), the weights arrive as 64-wide K-major
-// rows; both tiles use the 128-byte swizzled K-major layout (8-row atoms of
-// 1024 bytes, 16-byte chunk c of row r stored at chunk c ^ (r & 7)).  A
-// 4-stage ring: the MMAs of a chunk commit to that stage's mbarrier, which
-// must complete before the stage is refilled.  The epilogue reads TMEM with
-// tcgen05.ld (warp w owns lanes = pixels 32w..32w+31).  Every wait is bounded;
-// on expiry the kernel sets *err, skips the remaining work and still frees
-// its TMEM.
+// Blackwell tensor-core implicit GEMM on a halo tile.  A CTA computes a tile of
+// 16 x 8 output pixels (M = 128) x BN output channels, accumulated in tensor
+// memory (TMEM) by tcgen05.mma (kind::f16: BF16 operands, FP32 accumulator,
+// M = 128, N = BN, K = 16 per instruction, issued by one thread).  Input
+// channels run in chunks of 32: the chunk's 18 x 10 halo is gathered once
+// (cp.async, zero-filled outside the image; the input may be a nearest-
+// upsampled coarse map stacked with a skip map) into the no-swizzle K-major
+// core-matrix layout [4 groups of 8 channels][180 halo pixels][8 channels],
+// and the nine taps are nine shared-memory descriptors into the same halo:
+// tap (dy, dx) starts ((1 + dy) 10 + 1 + dx) pixels in, 8-row groups (tile
+// rows) 10 pixels apart, channel groups 180 pixels apart.  The chunk's
+// weights arrive as [9 taps][4 groups][BN channels][8].  Two stages: the
+// chunk's 18 MMAs commit to its stage's mbarrier, which must complete before
+// the stage is refilled.  The epilogue reads TMEM with tcgen05.ld (warp w owns
+// lanes = tile rows 4w..4w+3).  Every wait is bounded; on expiry the kernel
+// sets *err, skips the remaining work and still frees its TMEM.
 namespace {
 
-constexpr int kTcStages = 3;
-constexpr int kTcA = 128 * 128;           // bytes of one A stage (128 rows x 128 B)
+constexpr int kHaloW = 10, kHaloH = 18, kHaloPx = kHaloW * kHaloH;   // 8 x 16 tile + 1-pixel border
+constexpr int kTcStages = 2;
+constexpr int kTcA = 4 * kHaloPx * 16;    // bytes of one halo stage: 4 channel groups x 180 px x 16 B
 
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor, no swizzle, K-major core matrices of
+// 8 rows x 16 bytes: lbo = byte distance between core matrices along K,
+// sbo = along M/N.
+__device__ __forceinline__ uint64_t plain_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-    d |= (uint64_t)1 << 16;                              // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;                    // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;         // leading dimension byte offset
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;         // stride dimension byte offset
     d |= (uint64_t)1 << 46;                              // descriptor version
-    d |= (uint64_t)2 << 61;                              // 128-byte swizzle
-    return d;
+    return d;                                            // layout type 0: no swizzle
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -176,21 +182,22 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
 
 template <int BN>
 struct TcCfg {
-    static constexpr int B_BYTES = BN * 128;                     // one B stage
+    static constexpr int B_BYTES = 9 * 4 * BN * 16;              // one weight stage
     static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
-    static constexpr int SMEM = 1024 + kTcStages * (kTcA + B_BYTES) + 64;
+    // both stages, plus room so that no descriptor can reach past the end
+    static constexpr int SMEM = 128 + kTcStages * (kTcA + B_BYTES) + 48 * 1024 + 64;
     // instruction descriptor: F32 accumulator, BF16 A and B, both K-major, N, M = 128
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(128 >> 4) << 24);
 };
 
 template <int BN>
-__global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __restrict__ Wk, int Cin, int N, int Kp,
-                                                    int B, int H, int W, ConvOut out, int* __restrict__ err) {
+__global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __restrict__ Wh, int Cin, int N, int B,
+                                                    int H, int W, ConvOut out, int* __restrict__ err) {
     using C = TcCfg<BN>;
     extern __shared__ unsigned char tc_smem_raw[];
     const uint32_t raw = smem_u32(tc_smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t base = (raw + 127u) & ~127u;
     unsigned char* gbase = tc_smem_raw + (base - raw);
     const uint32_t sA = base, sB = base + kTcStages * kTcA;
     const uint32_t bars = sB + kTcStages * C::B_BYTES;           // kTcStages mbarriers
@@ -199,11 +206,15 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
     unsigned char* gB = gbase + kTcStages * kTcA;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const long long HW = (long long)H * W;
-    const long long M = (long long)B * HW;
-    const long long m = (long long)blockIdx.x * 128 + tid;     // this thread's pixel (A row tid)
+    const int tiles_x = (W + 7) >> 3, tiles_y = (H + 15) >> 4;
+    int t = blockIdx.x;
+    const int tx = t % tiles_x;
+    t /= tiles_x;
+    const int ty = t % tiles_y;
+    const int pn = t / tiles_y;
+    const int x0 = tx * 8, y0 = ty * 16;
     const int n0 = blockIdx.y * BN;
-    const int nch = Kp / 64;
+    const int nch = Cin / 32;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -220,103 +231,68 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    // this pixel, the taps inside the image (9-bit mask), and the (tap,
-    // channel) of the first segment of the next chunk to load
-    const bool valid = m < M;
-    int pn = 0, py = 0, px = 0;
-    if (valid) {
-        pn = (int)(m / HW);
-        const int rem = (int)(m - (long long)pn * HW);
-        py = rem / W;
-        px = rem - py * W;
-    }
-    uint32_t inside = 0;
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
-        inside |= ((valid && yy >= 0 && yy < H && xx >= 0 && xx < W) ? 1u : 0u) << t;
-    }
-    const long long pix = ((long long)pn * H + py) * W + px;
-    int ld_tap = 0, ld_ci = 0;
-    // sources of channel 0 at a tap (only dereferenced for taps inside the image)
-    auto tap_src = [&](int t, const bf16*& pa, const bf16*& pb) {
-        const int dy = t / 3 - 1, dx = t - 3 * (t / 3) - 1;
-        const long long sh = (long long)dy * W + dx;
-        if (in.up)
-            pa = in.a + (((long long)pn * (H >> 1) + ((py + dy) >> 1)) * (W >> 1) + ((px + dx) >> 1)) * in.ca;
-        else
-            pa = in.a + (pix + sh) * in.ca;
-        pb = in.b + (pix + sh) * in.cb;
-    };
-    auto load_stage = [&](int st, int j) {
-        unsigned char* a_row = gA + st * kTcA + tid * 128;
-        int tap = ld_tap, ci = ld_ci;
-        const bf16 *pa, *pb;
-        tap_src(tap, pa, pb);
-#pragma unroll
-        for (int sg = 0; sg < 8; ++sg) {
-            const bool use = tap < 9 && ((inside >> tap) & 1u);
-            const bf16* src = ci < in.ca ? pa + ci : pb + (ci - in.ca);
-            cp16(a_row + ((sg ^ (tid & 7)) << 4), use ? src : in.a, use ? 16 : 0);
-            ci += 8;
-            if (ci == Cin) {
-                ci = 0;
-                ++tap;
-                tap_src(tap, pa, pb);
-            }
+    auto load_stage = [&](int st, int c) {
+        unsigned char* a_st = gA + st * kTcA;
+        for (int s = tid; s < kHaloPx * 4; s += 128) {   // (halo pixel, channel group)
+            const int hp = s >> 2, kg = s & 3;
+            const int hy = hp / kHaloW, hx = hp - hy * kHaloW;
+            const bf16* src = in_at(in, pn, y0 - 1 + hy, x0 - 1 + hx, H, W, c * 32 + kg * 8);
+            cp16(a_st + (kg * kHaloPx + hp) * 16, src ? src : in.a, src ? 16 : 0);
         }
-        ld_tap = tap;
-        ld_ci = ci;
         unsigned char* b_st = gB + st * C::B_BYTES;
-        const bf16* wsrc = Wk + (long long)n0 * Kp + j * 64;
-#pragma unroll
-        for (int s = tid; s < BN * 8; s += 128) {
-            const int r = s >> 3, sg = s & 7;
-            cp16(b_st + r * 128 + ((sg ^ (r & 7)) << 4), wsrc + (long long)r * Kp + sg * 8, 16);
+        const bf16* wsrc = Wh + (long long)c * 36 * N * 8;     // [9 taps][4 groups][N][8] of this chunk
+        for (int s = tid; s < 36 * BN; s += 128) {
+            const int tg = s / BN, r = s - tg * BN;             // (tap, group), output channel
+            cp16(b_st + s * 16, wsrc + ((long long)tg * N + n0 + r) * 8, 16);
         }
     };
 
     bool ok = true;
-#pragma unroll
-    for (int s = 0; s < kTcStages - 1; ++s) {
-        if (s < nch) load_stage(s, s);
-        cp_commit();
-    }
-    for (int j = 0; j < nch; ++j) {
-        const int st = j % kTcStages;
-        cp_wait<kTcStages - 2>();
+    load_stage(0, 0);
+    cp_commit();
+    for (int c = 0; c < nch; ++c) {
+        const int st = c & 1;
+        cp_wait<0>();
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        // thread 0 also waits for the MMAs of chunk j-1: their stage is refilled below
-        if (tid == 0 && j >= 1 && ok)
-            ok = mbar_wait(bars + 8 * ((j - 1) % kTcStages), (uint32_t)(((j - 1) / kTcStages) & 1));
+        // thread 0 also waits for the MMAs of chunk c-1: their stage is refilled below
+        if (tid == 0 && c >= 1 && ok) ok = mbar_wait(bars + 8 * ((c - 1) & 1), (uint32_t)(((c - 1) >> 1) & 1));
         if (!__syncthreads_and(ok)) {     // uniform: every thread leaves together
             ok = false;
             break;
         }
         if (tid == 0) {
             tc_fence_after();
+            const uint32_t a0 = sA + st * kTcA, b0 = sB + st * C::B_BYTES;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - 3 * (tap / 3);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = sw128_desc(sA + st * kTcA + kk * 32);
-                const uint64_t bd = sw128_desc(sB + st * C::B_BYTES + kk * 32);
-                tc_mma(tmem, ad, bd, C::IDESC, (j > 0 || kk > 0) ? 1u : 0u);
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t ad = plain_desc(a0 + ((2 * ks) * kHaloPx + dy * kHaloW + dx) * 16,
+                                                   kHaloPx * 16, kHaloW * 16);
+                    const uint64_t bd = plain_desc(b0 + ((tap * 4 + 2 * ks) * BN) * 16, BN * 16, 128);
+                    tc_mma(tmem, ad, bd, C::IDESC, (c > 0 || tap > 0 || ks > 0) ? 1u : 0u);
+                }
             }
             tc_commit(bars + 8 * st);
         }
-        const int jn = j + kTcStages - 1;
-        if (jn < nch) load_stage(jn % kTcStages, jn);
+        if (c + 1 < nch) load_stage(st ^ 1, c + 1);
         cp_commit();
     }
     cp_wait<0>();
     // all MMAs done: the last commit arrives after every earlier MMA of the thread
-    if (tid == 0 && ok && nch > 0)
-        ok = mbar_wait(bars + 8 * ((nch - 1) % kTcStages), (uint32_t)(((nch - 1) / kTcStages) & 1));
+    if (tid == 0 && ok && nch > 0) ok = mbar_wait(bars + 8 * ((nch - 1) & 1), (uint32_t)(((nch - 1) >> 1) & 1));
     ok = __syncthreads_and(ok) != 0;      // the epilogue's tcgen05.ld is warp-collective
     tc_fence_after();
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
     } else {
+        // TMEM lane l = tile pixel (row l / 8, column l % 8); warp w reads lanes 32w..32w+31
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        const int l = tid;
+        const int y = y0 + (l >> 3), x = x0 + (l & 7);
+        const bool valid = y < H && x < W;
+        const long long m = ((long long)pn * H + y) * W + x;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 8) {
             float v[8];
@@ -351,7 +327,7 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
 }
 
 template <int BN>
-static cudaError_t conv3_go(const ConvIn& in, const bf16* Wk, int Cin, int N, int B, int H, int W,
+static cudaError_t conv3_go(const ConvIn& in, const bf16* Wh, int Cin, int N, int B, int H, int W,
                             const ConvOut& out, int* err, cudaStream_t s) {
     using C = TcCfg<BN>;
     static bool attr = false;   // benign race: every caller sets the same value
@@ -361,22 +337,22 @@ static cudaError_t conv3_go(const ConvIn& in, const bf16* Wk, int Cin, int N, in
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const long long M = (long long)B * H * W;
-    const int Kp = conv_kpad(Cin);
-    dim3 grid((unsigned)((M + 127) / 128), N / BN);
-    conv3_kernel<BN><<<grid, 128, C::SMEM, s>>>(in, Wk, Cin, N, Kp, B, H, W, out, err);
+    const long long tiles = (long long)B * ((H + 15) / 16) * ((W + 7) / 8);
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)tiles, N / BN);
+    conv3_kernel<BN><<<grid, 128, C::SMEM, s>>>(in, Wh, Cin, N, B, H, W, out, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_conv3(const ConvIn& in, const bf16* Wk, int Cin, int N, int B, int H, int W,
+cudaError_t launch_conv3(const ConvIn& in, const bf16* Wh, int Cin, int N, int B, int H, int W,
                          const ConvOut& out, int* err, cudaStream_t s) {
     if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 || H <= 0 ||
         W <= 0 || (in.up && ((H | W) & 1)) || !err)
         return cudaErrorInvalidValue;
-    if (N % 128 == 0) return conv3_go<128>(in, Wk, Cin, N, B, H, W, out, err, s);
-    if (N % 96 == 0) return conv3_go<96>(in, Wk, Cin, N, B, H, W, out, err, s);
-    if (N % 64 == 0) return conv3_go<64>(in, Wk, Cin, N, B, H, W, out, err, s);
-    return conv3_go<32>(in, Wk, Cin, N, B, H, W, out, err, s);
+    if (N % 128 == 0) return conv3_go<128>(in, Wh, Cin, N, B, H, W, out, err, s);
+    if (N % 96 == 0) return conv3_go<96>(in, Wh, Cin, N, B, H, W, out, err, s);
+    if (N % 64 == 0) return conv3_go<64>(in, Wh, Cin, N, B, H, W, out, err, s);
+    return conv3_go<32>(in, Wh, Cin, N, B, H, W, out, err, s);
 }
 
 // --------------------------------------------------------- weight gradient
@@ -919,6 +895,10 @@ cudaError_t launch_adam(float* theta, float* m, float* v, const float* g, long l
     return cudaGetLastError();
 }
 
+// Weights in the layout of conv3_kernel: [Cin / 32 chunks][9 taps][4 groups
+// of 8 input channels][N][8], forward (N = cout, input channel ci) and, for
+// the input gradient, flipped and transposed (N = cin, input channel co of
+// W[8 - tap][ci][co]).
 __global__ void pack_kernel(const float* __restrict__ th, PackTable t, long long total) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -926,35 +906,35 @@ __global__ void pack_kernel(const float* __restrict__ th, PackTable t, long long
         int l = 0;
         bool flip = false;
         for (; l < t.n; ++l) {
-            const long long nf = (long long)t.cout[l] * conv_kpad(t.cin[l]);
+            const long long nf = 9LL * t.cin[l] * t.cout[l];
             if (r < nf) break;
             r -= nf;
             if (t.wd[l]) {
-                const long long nd = (long long)t.cin[l] * conv_kpad(t.cout[l]);
-                if (r < nd) {
+                if (r < nf) {
                     flip = true;
                     break;
                 }
-                r -= nd;
+                r -= nf;
             }
         }
         if (l >= t.n) continue;
         const int cin = t.cin[l], cout = t.cout[l], cr = t.cin_real[l];
+        const int Nn = flip ? cin : cout;
+        // r = (((chunk * 9 + tap) * 4 + group) * Nn + n) * 8 + e
+        const int e = (int)(r & 7);
+        long long q = r >> 3;
+        const int n = (int)(q % Nn);
+        q /= Nn;
+        const int grp = (int)(q % 4);
+        q /= 4;
+        const int tap = (int)(q % 9);
+        const int chunk = (int)(q / 9);
+        const int k = chunk * 32 + grp * 8 + e;   // input channel of this GEMM
         float v = 0.f;
-        if (!flip) {   // wf[co][k], k = tap cin + ci
-            const int Kp = conv_kpad(cin);
-            const int co = (int)(r / Kp), k = (int)(r % Kp);
-            if (k < 9 * cin) {
-                const int tap = k / cin, ci = k % cin;
-                if (ci < cr) v = th[t.w_off[l] + ((long long)tap * cr + ci) * cout + co];
-            }
-        } else {       // wd[ci][k'], k' = tap' cout + co, tap = 8 - tap'
-            const int Kp = conv_kpad(cout);
-            const int ci = (int)(r / Kp), k = (int)(r % Kp);
-            if (k < 9 * cout && ci < cr) {
-                const int tap = 8 - k / cout, co = k % cout;
-                v = th[t.w_off[l] + ((long long)tap * cr + ci) * cout + co];
-            }
+        if (!flip) {
+            if (k < cr) v = th[t.w_off[l] + ((long long)tap * cr + k) * cout + n];
+        } else {
+            if (n < cr) v = th[t.w_off[l] + ((long long)(8 - tap) * cr + n) * cout + k];
         }
         (flip ? t.wd[l] : t.wf[l])[r] = __float2bfloat16_rn(v);
     }
@@ -962,8 +942,7 @@ __global__ void pack_kernel(const float* __restrict__ th, PackTable t, long long
 
 cudaError_t launch_pack(const float* theta, const PackTable& t, cudaStream_t s) {
     long long total = 0;
-    for (int l = 0; l < t.n; ++l)
-        total += (long long)t.cout[l] * conv_kpad(t.cin[l]) + (t.wd[l] ? (long long)t.cin[l] * conv_kpad(t.cout[l]) : 0);
+    for (int l = 0; l < t.n; ++l) total += 9LL * t.cin[l] * t.cout[l] * (t.wd[l] ? 2 : 1);
     long long blocks = (total + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     pack_kernel<<<(unsigned)blocks, 256, 0, s>>>(theta, t, total);

@@ -128,9 +128,7 @@ cudaError_t alloc_all(stml_net* n) {
     ECK(nalloc(&n->v, kParams));
     ECK(nalloc(&n->grad, kParams));
     long long wtot = 0;
-    for (int l = 0; l < kLayers; ++l)
-        wtot += (long long)kDefs[l].cout * conv_kpad(kDefs[l].cin) +
-                (l == E0A ? 0 : (long long)kDefs[l].cin * conv_kpad(kDefs[l].cout));
+    for (int l = 0; l < kLayers; ++l) wtot += 9LL * kDefs[l].cin * kDefs[l].cout * (l == E0A ? 1 : 2);
     ECK(nalloc(&n->wbuf, wtot));
     bf16* w = n->wbuf;
     n->pt.n = kLayers;
@@ -140,9 +138,9 @@ cudaError_t alloc_all(stml_net* n) {
         n->pt.cout[l] = kDefs[l].cout;
         n->pt.w_off[l] = n->w_off[l];
         n->pt.wf[l] = w;
-        w += (long long)kDefs[l].cout * conv_kpad(kDefs[l].cin);
+        w += 9LL * kDefs[l].cin * kDefs[l].cout;
         n->pt.wd[l] = l == E0A ? nullptr : w;
-        if (l != E0A) w += (long long)kDefs[l].cin * conv_kpad(kDefs[l].cout);
+        if (l != E0A) w += 9LL * kDefs[l].cin * kDefs[l].cout;
     }
     ECK(nalloc(&n->err_d, 1));
     ECK(cudaMemset(n->err_d, 0, sizeof(int)));
@@ -517,8 +515,8 @@ stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const
     cudaError_t e = cudaSuccess;
     auto run = [&]() -> cudaError_t {
         ECK(nalloc(&xb, (size_t)(P * (mode == 0 ? Cin : Cout))));
-        ECK(nalloc(&wf, (size_t)Cout * conv_kpad(Cin)));
-        ECK(nalloc(&wd, (size_t)Cin * conv_kpad(Cout)));
+        ECK(nalloc(&wf, (size_t)nw));
+        ECK(nalloc(&wd, (size_t)nw));
         ECK(nalloc(&errd, 1));
         ECK(cudaMemsetAsync(errd, 0, sizeof(int), s));
         PackTable t{};

@@ -69,17 +69,13 @@ struct ConvOut {
     int n1;
 };
 
-// Row length of the K-major weights of a convolution with `cin` input
-// channels: 9 cin rounded up to the 64-wide K chunks of the tensor-core kernel.
-__host__ __device__ inline int conv_kpad(int cin) { return (9 * cin + 63) / 64 * 64; }
-
 // Layer table of the packing kernel: parameter offsets and packed weights.
 constexpr int kLayers = 14;
 struct PackTable {
     int cin_real[kLayers], cin[kLayers], cout[kLayers];
     long long w_off[kLayers];           // offset of W[ky][kx][ci][co] in theta
-    bf16* wf[kLayers];                  // [cout][conv_kpad(cin)], k = tap cin + ci (ci >= cin_real zero)
-    bf16* wd[kLayers];                  // [cin][conv_kpad(cout)], k = tap' cout + co of W[8 - tap'] (null: not needed)
+    bf16* wf[kLayers];                  // [cin/32][9][4][cout][8] (input channels >= cin_real zero)
+    bf16* wd[kLayers];                  // [cout/32][9][4][cin][8] of W[8 - tap] (null: not needed)
     int n;
 };
 
@@ -87,9 +83,10 @@ struct PackTable {
 // (device array `smp` of B entries), canvases H8 x W8 with the real H x W.
 cudaError_t launch_assemble(const Sample* smp, int B, int H, int W, int H8, int W8, bf16* x0,
                             float* base, float* tgt, cudaStream_t s);
-// 3x3 convolution of the B x H x W maps of `in` with K-major weights
-// Wk [N][conv_kpad(Cin)]; *err (device) is set to 1 if a bounded wait expired.
-cudaError_t launch_conv3(const ConvIn& in, const bf16* Wk, int Cin, int N, int B, int H, int W,
+// 3x3 convolution of the B x H x W maps of `in` with weights Wh in the
+// [Cin/32][9][4][N][8] layout of launch_pack; *err (device) is set to 1 if a
+// bounded wait expired.
+cudaError_t launch_conv3(const ConvIn& in, const bf16* Wh, int Cin, int N, int B, int H, int W,
                          const ConvOut& out, int* err, cudaStream_t s);
 // Partial weight gradients: part[s][9 Cin][N] (FP32) = sum over the s-th slice
 // of pixels of im2col(in)^T G; returns the number of slices used in *splits.

@@ -68,7 +68,7 @@ def test_judge_keeps_the_lower_objective(S):
             assert s["J_fill"] <= s["J_fill_classic"]
     J, J0 = _final_J(R, y, prm), _final_J(R, y0, prm)
     print(f"\nrandom-head network: decisions {[s['pred_learned'] for s in stats]}, final J {J:.6g} vs {J0:.6g}")
-    assert abs(J - J0) <= 1e-2 * J0
+    assert J <= J0 * (1 + 1e-2)          # no worse than the classical predictor's result
 
 
 def test_zero_head_network_changes_nothing_on_the_coarsest_level(S):
@@ -116,7 +116,7 @@ def test_trained_network_gains_on_held_out_sequences(S):
         starts = [(round(s["J0"], 6), round(s["J0_classic"], 6)) for s in st if s["pred_learned"] >= 0]
         print(f"  learned kept {kept}; starts (learned-or-kept, classical) {starts}; PCG iterations {cg} vs "
               f"{cg0}; GN {gn} vs {gn0}; final J {J:.6g} vs {J0:.6g}")
-        assert abs(J - J0) <= 1e-2 * J0
+        assert J <= J0 * (1 + 1e-2)      # a lower final objective is a gain, not a mismatch
         for s in st:
             if s["pred_learned"] >= 0:
                 assert s["J0"] <= s["J0_classic"] * (1 + 1e-6) + 1e-12
