@@ -184,8 +184,7 @@ template <int BN>
 struct TcCfg {
     static constexpr int B_BYTES = 9 * 4 * BN * 16;              // one weight stage
     static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
-    // both stages, plus room so that no descriptor can reach past the end
-    static constexpr int SMEM = 128 + kTcStages * (kTcA + B_BYTES) + 48 * 1024 + 64;
+    static constexpr int SMEM = 128 + kTcStages * (kTcA + B_BYTES) + 64;
     // instruction descriptor: F32 accumulator, BF16 A and B, both K-major, N, M = 128
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(128 >> 4) << 24);
@@ -207,12 +206,7 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int tiles_x = (W + 7) >> 3, tiles_y = (H + 15) >> 4;
-    int t = blockIdx.x;
-    const int tx = t % tiles_x;
-    t /= tiles_x;
-    const int ty = t % tiles_y;
-    const int pn = t / tiles_y;
-    const int x0 = tx * 8, y0 = ty * 16;
+    const int tiles = B * tiles_y * tiles_x;
     const int n0 = blockIdx.y * BN;
     const int nch = Cin / 32;
 
@@ -231,7 +225,17 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    auto load_stage = [&](int st, int c) {
+    // tile index -> (image, first row, first column)
+    auto tile_origin = [&](int t, int& pn, int& y0, int& x0) {
+        const int tx = t % tiles_x;
+        t /= tiles_x;
+        x0 = tx * 8;
+        y0 = (t % tiles_y) * 16;
+        pn = t / tiles_y;
+    };
+    auto load_stage = [&](int st, int tile, int c) {
+        int pn, y0, x0;
+        tile_origin(tile, pn, y0, x0);
         unsigned char* a_st = gA + st * kTcA;
         for (int s = tid; s < kHaloPx * 4; s += 128) {   // (halo pixel, channel group)
             const int hp = s >> 2, kg = s & 3;
@@ -247,50 +251,57 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         }
     };
 
+    // the CTA's (tile, chunk) items run in one sequence q = 0, 1, ...: item q
+    // uses stage q & 1 and commits to that stage's mbarrier (use q >> 1)
     bool ok = true;
-    load_stage(0, 0);
+    int q = 0;
+    if ((int)blockIdx.x < tiles) load_stage(0, blockIdx.x, 0);
     cp_commit();
-    for (int c = 0; c < nch; ++c) {
-        const int st = c & 1;
-        cp_wait<0>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        // thread 0 also waits for the MMAs of chunk c-1: their stage is refilled below
-        if (tid == 0 && c >= 1 && ok) ok = mbar_wait(bars + 8 * ((c - 1) & 1), (uint32_t)(((c - 1) >> 1) & 1));
-        if (!__syncthreads_and(ok)) {     // uniform: every thread leaves together
-            ok = false;
-            break;
-        }
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = sA + st * kTcA, b0 = sB + st * C::B_BYTES;
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint64_t ad = plain_desc(a0 + ((2 * ks) * kHaloPx + dy * kHaloW + dx) * 16,
-                                                   kHaloPx * 16, kHaloW * 16);
-                    const uint64_t bd = plain_desc(b0 + ((tap * 4 + 2 * ks) * BN) * 16, BN * 16, 128);
-                    tc_mma(tmem, ad, bd, C::IDESC, (c > 0 || tap > 0 || ks > 0) ? 1u : 0u);
-                }
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        for (int c = 0; c < nch; ++c, ++q) {
+            const int st = q & 1;
+            cp_wait<0>();
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            // thread 0 also waits for the MMAs of item q-1: their stage is refilled below
+            if (tid == 0 && q >= 1 && ok) ok = mbar_wait(bars + 8 * ((q - 1) & 1), (uint32_t)(((q - 1) >> 1) & 1));
+            if (!__syncthreads_and(ok)) {     // uniform: every thread leaves together
+                ok = false;
+                break;
             }
-            tc_commit(bars + 8 * st);
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = sA + st * kTcA, b0 = sB + st * C::B_BYTES;
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ad = plain_desc(a0 + ((2 * ks) * kHaloPx + dy * kHaloW + dx) * 16,
+                                                       kHaloPx * 16, kHaloW * 16);
+                        const uint64_t bd = plain_desc(b0 + ((tap * 4 + 2 * ks) * BN) * 16, BN * 16, 128);
+                        tc_mma(tmem, ad, bd, C::IDESC, (c > 0 || tap > 0 || ks > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(bars + 8 * st);
+            }
+            // prefetch the next item (this tile's next chunk, or the next tile's first)
+            if (c + 1 < nch)
+                load_stage(st ^ 1, tile, c + 1);
+            else if (tile + (int)gridDim.x < tiles)
+                load_stage(st ^ 1, tile + gridDim.x, 0);
+            cp_commit();
         }
-        if (c + 1 < nch) load_stage(st ^ 1, c + 1);
-        cp_commit();
-    }
-    cp_wait<0>();
-    // all MMAs done: the last commit arrives after every earlier MMA of the thread
-    if (tid == 0 && ok && nch > 0) ok = mbar_wait(bars + 8 * ((nch - 1) & 1), (uint32_t)(((nch - 1) >> 1) & 1));
-    ok = __syncthreads_and(ok) != 0;      // the epilogue's tcgen05.ld is warp-collective
-    tc_fence_after();
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-    } else {
+        if (!ok) break;
+        // the tile's MMAs are done when its last commit arrives
+        if (tid == 0) ok = mbar_wait(bars + 8 * ((q - 1) & 1), (uint32_t)(((q - 1) >> 1) & 1));
+        ok = __syncthreads_and(ok) != 0;      // the epilogue's tcgen05.ld is warp-collective
+        tc_fence_after();
+        if (!ok) break;
         // TMEM lane l = tile pixel (row l / 8, column l % 8); warp w reads lanes 32w..32w+31
+        int pn, y0, x0;
+        tile_origin(tile, pn, y0, x0);
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        const int l = tid;
-        const int y = y0 + (l >> 3), x = x0 + (l & 7);
+        const int y = y0 + (tid >> 3), x = x0 + (tid & 7);
         const bool valid = y < H && x < W;
         const long long m = ((long long)pn * H + y) * W + x;
 #pragma unroll 1
@@ -315,7 +326,12 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
                 reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
         }
+        // the next tile's first MMA overwrites the accumulator: TMEM reads first
+        tc_fence_before();
+        __syncthreads();
     }
+    cp_wait<0>();
+    if (!ok && tid == 0) atomicExch(err, 1);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -339,7 +355,12 @@ static cudaError_t conv3_go(const ConvIn& in, const bf16* Wh, int Cin, int N, in
     }
     const long long tiles = (long long)B * ((H + 15) / 16) * ((W + 7) / 8);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)tiles, N / BN);
+    // a few CTAs per SM, each running a sequence of tiles
+    const long long per_sm = BN <= 32 ? 3 : BN <= 64 ? 2 : 1;
+    long long ctas = 152 * per_sm * 2 / (N / BN);
+    if (ctas < 1) ctas = 1;
+    if (ctas > tiles) ctas = tiles;
+    dim3 grid((unsigned)ctas, N / BN);
     conv3_kernel<BN><<<grid, 128, C::SMEM, s>>>(in, Wh, Cin, N, B, H, W, out, err);
     return cudaGetLastError();
 }
