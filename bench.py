@@ -282,6 +282,80 @@ def run_batch(S, torch, dev, mode):
             "speedup": t_seq / t_bat, "timing": "host wall clock around the whole batch, device-resident inputs"}
 
 
+def run_combined(S, torch, dev, mode):
+    """The combined form against the plain one on the batch workload (16
+    seeded sequences of 20-120 frames of 128^2/192^2/256^2, 3 x 3 levels):
+    plain = one sequence after the other, FP32 images, classical predictors;
+    combined = stml_register_batch (one stream per sequence), BF16 image
+    storage, the learned predictor (one network per context, the committed
+    weights).  Frames/s of both, and the final objective of each sequence
+    relative to the plain run (FP32 frames, finest level, all frames)."""
+    from paper_2001_06613_gb300 import synthetic
+    if not os.path.exists(WEIGHTS):
+        return {"unavailable": "predictor weights file missing"}
+    params = np.fromfile(WEIGHTS, dtype=np.float32)
+    rng = np.random.default_rng(1000)
+    seqs = []
+    for i in range(BATCH_SEQUENCES):
+        n = int(rng.integers(20, 121))
+        m = int(rng.choice([128, 192, 256]))
+        seqs.append(torch.from_numpy(synthetic.make_sequence(
+            synthetic.spec_custom(n, (m, m), seed=1000 + i, amp=3.0))).to(dev))
+    frames = sum(int(r.shape[0]) for r in seqs)
+
+    def final_J(ctx, R):
+        n = int(R.shape[0])
+        y = torch.empty((n, 2) + tuple(R.shape[1:]), device=dev)
+        S.stml_get_field(ctx.ptr, 2, y)
+        ref = S.Context(S.stml_default_params(n_levels=3, n_tlevels=3))
+        S.stml_load_sequence(ref.ptr, R)
+        S.stml_build_pyramid(ref.ptr)
+        J = float(S.stml_eval(ref.ptr, 2, list(range(n)), y)[0])
+        ref.close()
+        return J
+
+    plain = S.Context(S.stml_default_params(n_levels=3, n_tlevels=3))
+    J_plain, t_plain = [], 0.0
+    for R in seqs:
+        S.stml_load_sequence(plain.ptr, R)
+        S.stml_build_pyramid(plain.ptr)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.stml_register(plain.ptr, mode)
+        torch.cuda.synchronize()
+        t_plain += time.perf_counter() - t0
+        J_plain.append(final_J(plain, R))
+    plain.close()
+
+    streams = [torch.cuda.Stream(dev) for _ in seqs]
+    prm = S.stml_default_params(n_levels=3, n_tlevels=3, pcg_cooperative=0, image_dtype=2)
+    ctxs = [S.Context(prm, st.cuda_stream) for st in streams]
+    nets = [S.Net(params, max_batch=32, max_h=256, max_w=256, stream=st.cuda_stream) for st in streams]
+    for c, R, net in zip(ctxs, seqs, nets):
+        S.stml_load_sequence(c.ptr, R)
+        S.stml_build_pyramid(c.ptr)
+        S.stml_set_predictor_net(c, net)
+    S.stml_register_batch(ctxs, mode)                  # first round allocates the workspaces
+    for c, R in zip(ctxs, seqs):
+        S.stml_load_sequence(c.ptr, R)
+        S.stml_build_pyramid(c.ptr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.stml_register_batch(ctxs, mode)
+    torch.cuda.synchronize()
+    t_comb = time.perf_counter() - t0
+    rel = [final_J(c, R) / Jp - 1.0 for c, R, Jp in zip(ctxs, seqs, J_plain)]
+    for c in ctxs:
+        c.close()
+    for net in nets:
+        net.close()
+    return {"sequences": len(seqs), "frames": frames, "plain_frames_per_s": frames / t_plain,
+            "combined_frames_per_s": frames / t_comb, "speedup": t_plain / t_comb,
+            "final_J_rel_change_mean": float(np.mean(rel)), "final_J_rel_change_max_abs": float(np.max(np.abs(rel))),
+            "combined": "stml_register_batch + BF16 image storage + learned predictor",
+            "timing": "host wall clock around the registrations, device-resident inputs"}
+
+
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2001_06613_gb300", "weights",
                        "predictor_500x100x256.f32")
 
@@ -510,6 +584,9 @@ def run_native(args):
     affine = None
     if not args.no_affine and rank == 0 and world == 1:
         affine = run_affine(S, torch, dev)
+    combined = None
+    if not args.no_batch and not args.no_learned and rank == 0 and world == 1 and args.mode == "stml":
+        combined = run_combined(S, torch, dev, mode)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -567,7 +644,8 @@ def run_native(args):
                 "per_step_ms": ms_steps,
                 "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
                                                  "ls_trials", "stopped_early")} for s in stats],
-                "spml": spml, "batch": batch, "learned": learned, "affine": affine, "tuning": tuning}
+                "spml": spml, "batch": batch, "learned": learned, "affine": affine, "combined": combined,
+                "tuning": tuning}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

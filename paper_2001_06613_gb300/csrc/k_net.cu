@@ -532,8 +532,10 @@ __global__ void __launch_bounds__(256) colsum_kernel(const bf16* __restrict__ G,
     const long long pb = (long long)blockIdx.x * chunk;
     const long long pe = pb + chunk < P ? pb + chunk : P;
     float acc = 0.f;
-    if (r < R)
+    if (r < R) {
+#pragma unroll 8
         for (long long p = pb + r; p < pe; p += R) acc += __bfloat162float(G[p * N + c]);
+    }
     red[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < N) {
@@ -570,8 +572,17 @@ __global__ void reduce_grad_kernel(const float* __restrict__ wpart, int ws, int 
             const int ci = (int)(k % cin_real);
             const int tap = (int)(k / cin_real);
             const long long src = ((long long)tap * cin + ci) * N + co;
+            // slices summed in order; loads issued eight at a time
             float v = 0.f;
-            for (int s = 0; s < ws; ++s) v += wpart[s * per + src];
+            int s = 0;
+            for (; s + 8 <= ws; s += 8) {
+                float t[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t[k] = wpart[(s + k) * per + src];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v += t[k];
+            }
+            for (; s < ws; ++s) v += wpart[s * per + src];
             grad[w_off + i] = v;
         } else {
             const int co = (int)(i - nW);
