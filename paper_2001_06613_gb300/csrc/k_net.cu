@@ -110,11 +110,14 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 // and the nine taps are nine shared-memory descriptors into the same halo:
 // tap (dy, dx) starts ((1 + dy) 10 + 1 + dx) pixels in, 8-row groups (tile
 // rows) 10 pixels apart, channel groups 180 pixels apart.  The chunk's
-// weights arrive as [9 taps][4 groups][BN channels][8].  Two stages: the
-// chunk's 18 MMAs commit to its stage's mbarrier, which must complete before
-// the stage is refilled.  The epilogue reads TMEM with tcgen05.ld (warp w owns
-// lanes = tile rows 4w..4w+3).  Every wait is bounded; on expiry the kernel
-// sets *err, skips the remaining work and still frees its TMEM.
+// weights arrive as [9 taps][4 groups][BN channels][8] (loaded once per CTA
+// when the input has a single chunk).  A CTA runs a sequence of tiles; two
+// stages: an item's 18 MMAs commit to its stage's mbarrier, which must
+// complete before the stage is refilled.  Tiles alternate between two TMEM
+// accumulators, and a tile's epilogue (tcgen05.ld; warp w owns lanes = tile
+// rows 4w..4w+3) runs while the next tile's first MMAs execute.  Every wait
+// is bounded; on expiry the kernel sets *err, skips the remaining work and
+// still frees its TMEM.
 namespace {
 
 constexpr int kHaloW = 10, kHaloH = 18, kHaloPx = kHaloW * kHaloH;   // 8 x 16 tile + 1-pixel border
@@ -183,7 +186,7 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
 template <int BN>
 struct TcCfg {
     static constexpr int B_BYTES = 9 * 4 * BN * 16;              // one weight stage
-    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+    static constexpr int TMEM_COLS = BN <= 32 ? 64 : BN <= 64 ? 128 : 256;   // two accumulators
     static constexpr int SMEM = 128 + kTcStages * (kTcA + B_BYTES) + 64;
     // instruction descriptor: F32 accumulator, BF16 A and B, both K-major, N, M = 128
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -233,6 +236,9 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         y0 = (t % tiles_y) * 16;
         pn = t / tiles_y;
     };
+    // with a single channel chunk the weights are the same for every item:
+    // they are loaded once (with the first item) into stage 0's weight buffer
+    const bool resident = nch == 1;
     auto load_stage = [&](int st, int tile, int c) {
         int pn, y0, x0;
         tile_origin(tile, pn, y0, x0);
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
             const bf16* src = in_at(in, pn, y0 - 1 + hy, x0 - 1 + hx, H, W, c * 32 + kg * 8);
             cp16(a_st + (kg * kHaloPx + hp) * 16, src ? src : in.a, src ? 16 : 0);
         }
+        if (resident && tile != (int)blockIdx.x) return;
         unsigned char* b_st = gB + st * C::B_BYTES;
         const bf16* wsrc = Wh + (long long)c * 36 * N * 8;     // [9 taps][4 groups][N][8] of this chunk
         for (int s = tid; s < 36 * BN; s += 128) {
@@ -251,56 +258,12 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         }
     };
 
-    // the CTA's (tile, chunk) items run in one sequence q = 0, 1, ...: item q
-    // uses stage q & 1 and commits to that stage's mbarrier (use q >> 1)
-    bool ok = true;
-    int q = 0;
-    if ((int)blockIdx.x < tiles) load_stage(0, blockIdx.x, 0);
-    cp_commit();
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        for (int c = 0; c < nch; ++c, ++q) {
-            const int st = q & 1;
-            cp_wait<0>();
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            // thread 0 also waits for the MMAs of item q-1: their stage is refilled below
-            if (tid == 0 && q >= 1 && ok) ok = mbar_wait(bars + 8 * ((q - 1) & 1), (uint32_t)(((q - 1) >> 1) & 1));
-            if (!__syncthreads_and(ok)) {     // uniform: every thread leaves together
-                ok = false;
-                break;
-            }
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t a0 = sA + st * kTcA, b0 = sB + st * C::B_BYTES;
-#pragma unroll 1
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-#pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-                        const uint64_t ad = plain_desc(a0 + ((2 * ks) * kHaloPx + dy * kHaloW + dx) * 16,
-                                                       kHaloPx * 16, kHaloW * 16);
-                        const uint64_t bd = plain_desc(b0 + ((tap * 4 + 2 * ks) * BN) * 16, BN * 16, 128);
-                        tc_mma(tmem, ad, bd, C::IDESC, (c > 0 || tap > 0 || ks > 0) ? 1u : 0u);
-                    }
-                }
-                tc_commit(bars + 8 * st);
-            }
-            // prefetch the next item (this tile's next chunk, or the next tile's first)
-            if (c + 1 < nch)
-                load_stage(st ^ 1, tile, c + 1);
-            else if (tile + (int)gridDim.x < tiles)
-                load_stage(st ^ 1, tile + gridDim.x, 0);
-            cp_commit();
-        }
-        if (!ok) break;
-        // the tile's MMAs are done when its last commit arrives
-        if (tid == 0) ok = mbar_wait(bars + 8 * ((q - 1) & 1), (uint32_t)(((q - 1) >> 1) & 1));
-        ok = __syncthreads_and(ok) != 0;      // the epilogue's tcgen05.ld is warp-collective
-        tc_fence_after();
-        if (!ok) break;
-        // TMEM lane l = tile pixel (row l / 8, column l % 8); warp w reads lanes 32w..32w+31
+    // Epilogue of the tile whose accumulator is TMEM buffer `buf`: TMEM lane
+    // l = tile pixel (row l / 8, column l % 8); warp w reads lanes 32w..32w+31.
+    auto epilogue = [&](int tile, int buf) {
         int pn, y0, x0;
         tile_origin(tile, pn, y0, x0);
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * BN);
         const int y = y0 + (tid >> 3), x = x0 + (tid & 7);
         const bool valid = y < H && x < W;
         const long long m = ((long long)pn * H + y) * W + x;
@@ -326,9 +289,63 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
                 reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
         }
-        // the next tile's first MMA overwrites the accumulator: TMEM reads first
-        tc_fence_before();
-        __syncthreads();
+        tc_fence_before();   // ordered before the barrier that precedes the buffer's next MMA
+    };
+
+    // The CTA's (tile, chunk) items run in one sequence q = 0, 1, ...: item q
+    // uses stage q & 1 and commits to that stage's mbarrier (use q >> 1); the
+    // k-th tile of the CTA accumulates in TMEM buffer k & 1, and its epilogue
+    // runs while the MMAs of the (k+1)-th tile's first chunk execute.
+    bool ok = true;
+    int q = 0, k = 0, prev_tile = -1;
+    if ((int)blockIdx.x < tiles) load_stage(0, blockIdx.x, 0);
+    cp_commit();
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++k) {
+        const int buf = k & 1;
+        for (int c = 0; c < nch; ++c, ++q) {
+            const int st = q & 1;
+            cp_wait<0>();
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            // thread 0 waits for the MMAs of item q-1: their stage is refilled below,
+            // and when c == 0 they finish the previous tile, whose epilogue follows
+            if (tid == 0 && q >= 1 && ok) ok = mbar_wait(bars + 8 * ((q - 1) & 1), (uint32_t)(((q - 1) >> 1) & 1));
+            if (!__syncthreads_and(ok)) {     // uniform: every thread leaves together
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t a0 = sA + st * kTcA, b0 = sB + (resident ? 0 : st * C::B_BYTES);
+                const uint32_t dacc = tmem + (uint32_t)(buf * BN);
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ad = plain_desc(a0 + ((2 * ks) * kHaloPx + dy * kHaloW + dx) * 16,
+                                                       kHaloPx * 16, kHaloW * 16);
+                        const uint64_t bd = plain_desc(b0 + ((tap * 4 + 2 * ks) * BN) * 16, BN * 16, 128);
+                        tc_mma(dacc, ad, bd, C::IDESC, (c > 0 || tap > 0 || ks > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(bars + 8 * st);
+            }
+            if (c == 0 && prev_tile >= 0) epilogue(prev_tile, buf ^ 1);
+            // prefetch the next item (this tile's next chunk, or the next tile's first)
+            if (c + 1 < nch)
+                load_stage(st ^ 1, tile, c + 1);
+            else if (tile + (int)gridDim.x < tiles)
+                load_stage(st ^ 1, tile + gridDim.x, 0);
+            cp_commit();
+        }
+        prev_tile = tile;
+    }
+    // the last tile: wait for its MMAs, then drain it
+    if (ok && prev_tile >= 0) {
+        if (tid == 0) ok = mbar_wait(bars + 8 * ((q - 1) & 1), (uint32_t)(((q - 1) >> 1) & 1));
+        ok = __syncthreads_and(ok) != 0;
+        tc_fence_after();
+        if (ok) epilogue(prev_tile, (k - 1) & 1);
     }
     cp_wait<0>();
     if (!ok && tid == 0) atomicExch(err, 1);
