@@ -99,6 +99,11 @@ struct stml_ctx {
     float* h_theta = nullptr;
     double* h_gth = nullptr;
     int aff_cap = 0;                  // frames the affine buffers hold
+    // one evaluation of the affine objective (upload, field, objective,
+    // gradient, projection, download) as a CUDA graph per (level, nK, grad);
+    // captured on a private stream, launched on the context's stream
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::array<int, 3>, cudaGraphExec_t> aff_graphs;
 
     // learned temporal predictor (stml_set_predictor_net) and its last decisions
     ::stml_net* net = nullptr;
@@ -205,6 +210,8 @@ void free_buffers(stml_ctx* c) {
     c->h_theta = nullptr;
     c->h_gth = nullptr;
     c->aff_cap = 0;
+    for (auto& kv : c->aff_graphs) cudaGraphExecDestroy(kv.second);
+    c->aff_graphs.clear();
     c->loaded = c->built = false;
 }
 
@@ -814,6 +821,8 @@ int aff_P(const stml_ctx* c) { return c->d * (c->d + 1); }
 
 stml_status ensure_affine(stml_ctx* c) {
     if (c->aff_cap >= c->n) return STML_OK;
+    for (auto& kv : c->aff_graphs) cudaGraphExecDestroy(kv.second);
+    c->aff_graphs.clear();
     const int P = aff_P(c);
     dfree(c->d_theta); dfree(c->d_gth); dfree(c->d_aff_part);
     if (c->h_theta) cudaFreeHost(c->h_theta);
@@ -853,29 +862,64 @@ stml_status affine_fields(stml_ctx* c, int level, const double* th, int nK, floa
     return STML_OK;
 }
 
-// J, D, S, P and (grad not null) dJ/dtheta at theta for the frames of fs.
-stml_status affine_eval(stml_ctx* c, int level, const FrameSet& fs, const double* th, double* out4, double* grad) {
+// One evaluation on stream st (h_theta already holds theta): upload, affine
+// field, objective, and with grad the gradient pass, projection and download
+// of dJ/dtheta.  Returns the number of kernels launched.
+cudaError_t affine_enqueue(stml_ctx* c, int level, const FrameSet& fs, bool grad, cudaStream_t st) {
     LevelBuf& L = c->lv[level];
     const int nK = fs.nK, P = aff_P(c);
     const Coef cf = make_coef(L.g, c->p, nK);
-    TRY(affine_fields(c, level, th, nK, c->w_u));
-    const double pfK = (double)nK * L.g.N;
-    const double bS = (double)store_bytes(c->img_type);
-    long pe = prof_begin(c, PC_TRIAL, level);
-    CK(c, launch_objective(Stored{L.img, c->img_type}, L.g, fs, cf, c->w_u, nullptr, 0.f, nullptr, c->w_abar,
-                           c->w_ubar, c->partials, c->partials_cap, &c->S->ticket[0], c->S->red, c->stream));
-    prof_end(c, pe, pfK * (bS + 4.0 * L.g.d), pfK);
-    if (grad) {
-        pe = prof_begin(c, PC_EVAL, level);
-        CK(c, launch_gradient(Stored{L.img, c->img_type}, L.g, fs, cf, c->w_u, nullptr, 0.f, c->w_abar, c->w_ubar,
-                              c->w_g, c->w_dT, ST_F32, nullptr, c->partials, c->partials_cap, &c->S->ticket[4],
-                              c->S->red, c->stream));
-        prof_end(c, pe, pfK * (bS + 20.0 * L.g.d), pfK);
-        pe = prof_begin(c, PC_AFFINE, level);
-        CK(c, launch_affine_project(L.g, affine_frame(c), c->w_g, nK, c->d_aff_part, c->d_gth, c->stream));
-        prof_end(c, pe, pfK * 4.0 * L.g.d, pfK);
-        CK(c, cudaMemcpyAsync(c->h_gth, c->d_gth, sizeof(double) * (size_t)nK * P, cudaMemcpyDeviceToHost,
-                              c->stream));
+    cudaError_t e = cudaMemcpyAsync(c->d_theta, c->h_theta, sizeof(float) * (size_t)nK * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_affine_field(L.g, affine_frame(c), c->d_theta, nK, c->w_u, st);
+    if (e == cudaSuccess)
+        e = launch_objective(Stored{L.img, c->img_type}, L.g, fs, cf, c->w_u, nullptr, 0.f, nullptr, c->w_abar,
+                             c->w_ubar, c->partials, c->partials_cap, &c->S->ticket[0], c->S->red, st);
+    if (grad && e == cudaSuccess)
+        e = launch_gradient(Stored{L.img, c->img_type}, L.g, fs, cf, c->w_u, nullptr, 0.f, c->w_abar, c->w_ubar, c->w_g,
+                            c->w_dT, ST_F32, nullptr, c->partials, c->partials_cap, &c->S->ticket[4], c->S->red, st);
+    if (grad && e == cudaSuccess)
+        e = launch_affine_project(L.g, affine_frame(c), c->w_g, nK, c->d_aff_part, c->d_gth, st);
+    if (grad && e == cudaSuccess)
+        e = cudaMemcpyAsync(c->h_gth, c->d_gth, sizeof(double) * (size_t)nK * P, cudaMemcpyDeviceToHost, st);
+    return e;
+}
+
+// J, D, S, P and (grad not null) dJ/dtheta at theta for the frames of fs.
+// Without profiling, the second and later evaluations of a (level, nK, grad)
+// replay a CUDA graph of the sequence.
+stml_status affine_eval(stml_ctx* c, int level, const FrameSet& fs, const double* th, double* out4, double* grad) {
+    LevelBuf& L = c->lv[level];
+    const int nK = fs.nK, P = aff_P(c);
+    TRY(ensure_affine(c));
+    CK(c, cudaStreamSynchronize(c->stream));   // the staging arrays are free
+    for (long long i = 0; i < (long long)nK * P; ++i) c->h_theta[i] = (float)th[i];
+    const bool g = grad != nullptr;
+    const std::array<int, 3> key{level, nK, g ? 1 : 0};
+    auto it = c->prof ? c->aff_graphs.end() : c->aff_graphs.find(key);
+    if (it != c->aff_graphs.end()) {
+        CK(c, cudaGraphLaunch(it->second, c->stream));
+        count_launches(g ? 5 : 2);
+    } else {
+        const double pfK = (double)nK * L.g.N;
+        const double bS = (double)store_bytes(c->img_type);
+        const long pe = prof_begin(c, g ? PC_EVAL : PC_TRIAL, level);
+        CK(c, affine_enqueue(c, level, fs, g, c->stream));
+        prof_end(c, pe, pfK * (bS + 4.0 * L.g.d + (g ? bS + 24.0 * L.g.d : 0.0)), pfK);
+        if (!c->prof) {   // capture the sequence for the next evaluations (best effort)
+            if (!c->cap_stream) cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            if (c->cap_stream &&
+                cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const cudaError_t e1 = affine_enqueue(c, level, fs, g, c->cap_stream);
+                const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+                if (e1 == cudaSuccess && e2 == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+                    c->aff_graphs[key] = exec;
+                if (graph) cudaGraphDestroy(graph);
+            }
+            cudaGetLastError();   // a failed capture leaves no error behind: the eager path stays
+        }
     }
     TRY(read_scalars(c));
     for (int i = 0; i < 4; ++i) out4[i] = c->Sh->red[i];
@@ -1263,6 +1307,7 @@ void stml_destroy(stml_ctx* c) {
     }
     dfree(c->S);
     if (c->Sh) cudaFreeHost(c->Sh);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
