@@ -18,6 +18,15 @@ leaves their details to FAIR):
   Sec. 2) evaluated at the affine fields, so its gradient is the projection
   ``dJ/dtheta_k = sum_x Phi(x)^T (dJ/du_k)(x)`` with Phi(x) = [xhat^T, 1] for
   each component.
+* Distance.  Sec. 2 names a correlation-based measure, the SVD-based SqN
+  distance of its reference [Kai2019], whose definition is not in the paper.
+  Reading (p.distance = "nc"): with a_k = T_k o y_k, centred a_k - mean(a_k),
+  normalised m_k and rho_ij = <m_i, m_j>,
+  ``D_NC = 1/2 sum_{i, j in K} (1 - rho_ij^2) = 1/2 (|K|^2 - ||M^T M||_F^2)``,
+  i.e. one half of |K|^2 minus the fourth power of the Schatten-4 norm of the
+  matrix M of normalised frames (sum of sigma^4 of its singular values): it
+  vanishes when all frames agree up to per-frame brightness and contrast.
+  S and P stay as in eq. (1).
 * L-BFGS (Nocedal & Wright, Algorithm 7.4 two-loop recursion with
   H0 = gamma I, gamma = s^T y / y^T y of the newest pair; memory m; a pair
   with s^T y <= 1e-12 |s| |y| is not stored).  The first step (and any step
@@ -83,10 +92,37 @@ def project(v: np.ndarray, xhat: np.ndarray) -> np.ndarray:
     return out
 
 
+def nc_distance(a: np.ndarray):
+    """D_NC of the warped frames a (K, *m) and dD_NC/da (same shape).
+
+    With c = mean-free a, n_k = |c_k|, m_k = c_k / n_k, rho = M M^T:
+    dD/dm_i = -2 sum_j rho_ij m_j, and through the centring and normalisation
+    dD/da_i = -(2 / n_i) (sum_j rho_ij m_j - m_i sum_j rho_ij^2)."""
+    K = a.shape[0]
+    A = a.reshape(K, -1)
+    C = A - A.mean(axis=1, keepdims=True)
+    n = np.linalg.norm(C, axis=1)
+    M = C / n[:, None]
+    R = M @ M.T
+    D = 0.5 * (K * K - float(np.sum(R * R)))
+    s = np.sum(R * R, axis=1)
+    G = -(2.0 / n[:, None]) * (R @ M - M * s[:, None])
+    return D, G.reshape(a.shape)
+
+
 def evaluate(T: np.ndarray, theta: np.ndarray, frames: Sequence[int], h: float, xhat: np.ndarray,
              p: Params, want_grad: bool = True) -> dict:
     """J, D, S, P at the affine fields of theta and dJ/dtheta (key "g")."""
-    ev = objective.evaluate(T, field(theta, xhat), frames, h, p, want_grad=want_grad)
+    u = field(theta, xhat)
+    ev = objective.evaluate(T, u, frames, h, p, want_grad=want_grad)
+    if p.distance == "nc":
+        D, Ga = nc_distance(ev["a"])
+        out = dict(J=D + ev["S"] + ev["P"], D=D, S=ev["S"], P=ev["P"])
+        if want_grad:
+            hd = h ** u.shape[1]
+            g_reg = ev["g"] - hd * ev["r"][:, None] * ev["dT"]      # S and P terms of dJ/du
+            out["g"] = project(Ga[:, None] * ev["dT"] + g_reg, xhat)
+        return out
     out = {k: ev[k] for k in ("J", "D", "S", "P")}
     if want_grad:
         out["g"] = project(ev["g"], xhat)

@@ -27,6 +27,9 @@ class Params:
     max_ls: int = 10
     armijo_c: float = 1e-4
     g_abs: float = 1e-12       # ||g|| below g_abs (1 + |J0|) counts as stationary
+    # distance of the affine variant: "ssd" (eq. 1 as in the non-parametric
+    # path) or "nc" (normalised-correlation reading of the SqN distance, Sec. 2)
+    distance: str = "ssd"
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)

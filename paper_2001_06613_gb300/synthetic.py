@@ -341,9 +341,11 @@ def blob_image(spec: SequenceSpec, pos: np.ndarray, n_blobs: int = 24, margin: f
     return out
 
 
-def make_affine_sequence(spec: SequenceSpec, dtype=np.float32, smooth: bool = False, **motion) -> np.ndarray:
-    """Frames R_k(x) = B(x + v_k(x)) + N(0, noise_sd^2) under affine_motion;
-    B the OCT-like image, or blob_image when smooth."""
+def make_affine_sequence(spec: SequenceSpec, dtype=np.float32, smooth: bool = False, gain=None, offset=None,
+                         **motion) -> np.ndarray:
+    """Frames R_k(x) = gain_k B(x + v_k(x)) + offset_k + N(0, noise_sd^2)
+    under affine_motion; B the OCT-like image, or blob_image when smooth;
+    gain and offset per frame (default 1 and 0)."""
     speckle = _make_speckle(spec)
     M, s = affine_motion(spec, **motion)
     x = cell_centres(spec.shape)
@@ -354,6 +356,10 @@ def make_affine_sequence(spec: SequenceSpec, dtype=np.float32, smooth: bool = Fa
     for k in range(spec.n):
         v = np.tensordot(M[k] - np.eye(d), x - c, axes=(1, 0)) + s[k].reshape((d,) + (1,) * d)
         img = blob_image(spec, x + v) if smooth else base_image(spec, x + v, speckle)
+        if gain is not None:
+            img = img * float(gain[k])
+        if offset is not None:
+            img = img + float(offset[k])
         img += noise.normal(scale=spec.noise_sd, size=img.shape) if spec.noise_sd > 0 else 0.0
         out[k] = img.astype(dtype)
     return out
