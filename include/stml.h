@@ -100,6 +100,13 @@ typedef struct {
                               * L-BFGS (Sec. 2); see stml_eval_affine */
     int lbfgs_m;             /* L-BFGS memory (pairs kept), 1..64 */
     int max_lbfgs;           /* L-BFGS iterations per GIR */
+    int distance;            /* 0: sum of squared differences (eq. 1 as above);
+                              * 1 (transform 1 only): normalised correlation,
+                              * D = 1/2 sum_{i,j in K} (1 - rho_ij^2) with rho_ij the
+                              * correlation of the warped frames i and j over the
+                              * grid -- a reading of the SqN distance named in Sec. 2
+                              * (1/2 (|K|^2 - sum of sigma^4 of the matrix of
+                              * normalised frames)); S and P unchanged */
 } stml_params;
 
 typedef struct {

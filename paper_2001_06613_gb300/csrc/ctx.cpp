@@ -104,6 +104,10 @@ struct stml_ctx {
     // captured on a private stream, launched on the context's stream
     cudaStream_t cap_stream = nullptr;
     std::map<std::array<int, 3>, cudaGraphExec_t> aff_graphs;
+    // normalised-correlation distance: frame means, Gram matrix and its
+    // partials, the K x K gradient matrix (device and pinned host copies)
+    float *d_mu = nullptr, *d_Q = nullptr, *h_Q = nullptr;
+    double *d_G = nullptr, *d_gpart = nullptr, *h_G = nullptr;
 
     // learned temporal predictor (stml_set_predictor_net) and its last decisions
     ::stml_net* net = nullptr;
@@ -165,6 +169,8 @@ bool valid_params(const stml_params* p, std::string& why) {
     if (p->pcg_cooperative != 0 && p->pcg_cooperative != 1) { why = "pcg_cooperative must be 0 or 1"; return false; }
     if (p->autotune != 0 && p->autotune != 1) { why = "autotune must be 0 or 1"; return false; }
     if (p->transform != 0 && p->transform != 1) { why = "transform must be 0 or 1"; return false; }
+    if (p->distance != 0 && p->distance != 1) { why = "distance must be 0 or 1"; return false; }
+    if (p->distance == 1 && p->transform != 1) { why = "distance 1 (normalised correlation) needs transform 1"; return false; }
     if (p->lbfgs_m < 1 || p->lbfgs_m > 64 || p->max_lbfgs < 0) {
         why = "lbfgs_m must be in 1..64 and max_lbfgs >= 0";
         return false;
@@ -212,6 +218,11 @@ void free_buffers(stml_ctx* c) {
     c->aff_cap = 0;
     for (auto& kv : c->aff_graphs) cudaGraphExecDestroy(kv.second);
     c->aff_graphs.clear();
+    dfree(c->d_mu); dfree(c->d_Q); dfree(c->d_G); dfree(c->d_gpart);
+    if (c->h_Q) cudaFreeHost(c->h_Q);
+    if (c->h_G) cudaFreeHost(c->h_G);
+    c->h_Q = nullptr;
+    c->h_G = nullptr;
     c->loaded = c->built = false;
 }
 
@@ -834,6 +845,18 @@ stml_status ensure_affine(stml_ctx* c) {
     CK(c, dalloc(&c->d_aff_part, (size_t)c->n * 256 * P));
     CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_theta), sizeof(float) * (size_t)c->n * P));
     CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_gth), sizeof(double) * (size_t)c->n * P));
+    dfree(c->d_mu); dfree(c->d_Q); dfree(c->d_G); dfree(c->d_gpart);
+    if (c->h_Q) cudaFreeHost(c->h_Q);
+    if (c->h_G) cudaFreeHost(c->h_G);
+    c->h_Q = nullptr;
+    c->h_G = nullptr;
+    const size_t n2 = (size_t)c->n * c->n;
+    CK(c, dalloc(&c->d_mu, (size_t)c->n));
+    CK(c, dalloc(&c->d_Q, n2));
+    CK(c, dalloc(&c->d_G, n2));
+    CK(c, dalloc(&c->d_gpart, 64 * n2));
+    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_Q), sizeof(float) * n2));
+    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_G), sizeof(double) * n2));
     c->aff_cap = c->n;
     return STML_OK;
 }
@@ -884,10 +907,146 @@ cudaError_t affine_enqueue(stml_ctx* c, int level, const FrameSet& fs, bool grad
     return e;
 }
 
+// S (spatial diffusion and temporal terms) and P of eq. (1) at the affine
+// fields of theta for the sorted frames K, in closed form (FP64), and their
+// gradients added to grad (nK x P, may be null).  An affine field has
+// constant forward differences W_ci / rho; sums of quadratic forms over the
+// grid use the moments N, sum xhat_i and sum xhat_i xhat_j of the level.
+void affine_reg_terms(const stml_ctx* c, int level, const std::vector<int>& K, const double* th, double* S_out,
+                      double* P_out, double* grad) {
+    const LevelBuf& L = c->lv[level];
+    const int d = c->d, P = aff_P(c), nK = (int)K.size();
+    const AffineFrame af = affine_frame(c);
+    const double h = L.g.h, hd = std::pow(h, d), rho = 1.0 / af.inv_rho;
+    int m[3];
+    for (int i = 0; i < d; ++i) m[i] = L.shape3[3 - d + i];
+    double N = 1.0;
+    for (int i = 0; i < d; ++i) N *= m[i];
+    double s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0}, E[3];
+    for (int i = 0; i < d; ++i) {
+        for (int j = 0; j < m[i]; ++j) {
+            const double xh = ((j + 0.5) * h - (double)af.c[i]) / rho;
+            s1[i] += xh;
+            s2[i] += xh * xh;
+        }
+        E[i] = (m[i] - 1) * N / m[i];
+    }
+    double S1[3], Mm[3][3];
+    for (int i = 0; i < d; ++i) {
+        S1[i] = N / m[i] * s1[i];
+        for (int j = 0; j < d; ++j) Mm[i][j] = i == j ? N / m[i] * s2[i] : N / ((double)m[i] * m[j]) * s1[i] * s1[j];
+    }
+    // Q(t) = sum_x |W xhat + b|^2 and its gradient for a parameter vector t
+    auto quad = [&](const double* t, double* gq) {
+        double q = 0.0;
+        for (int cc = 0; cc < d; ++cc) {
+            const double* w = t + cc * d;
+            const double b = t[d * d + cc];
+            double ws = 0.0;
+            for (int i = 0; i < d; ++i) {
+                double mw = 0.0;
+                for (int j = 0; j < d; ++j) mw += Mm[i][j] * w[j];
+                q += w[i] * mw;
+                ws += w[i] * S1[i];
+                if (gq) gq[cc * d + i] = 2.0 * mw + 2.0 * b * S1[i];
+            }
+            q += 2.0 * b * ws + N * b * b;
+            if (gq) gq[d * d + cc] = 2.0 * ws + 2.0 * N * b;
+        }
+        return q;
+    };
+    const stml_params& p = c->p;
+    double Sx = 0.0;
+    for (int k = 0; k < nK; ++k)
+        for (int cc = 0; cc < d; ++cc)
+            for (int i = 0; i < d; ++i) {
+                const double w = th[(size_t)k * P + cc * d + i];
+                Sx += 0.5 * p.alpha * hd * E[i] * w * w / (rho * rho);
+                if (grad) grad[(size_t)k * P + cc * d + i] += p.alpha * hd * E[i] * w / (rho * rho);
+            }
+    double St = 0.0;
+    std::vector<double> dt(P), gq(P);
+    if (p.alpha_t != 0.0)
+        for (int k = 0; k + 1 < nK; ++k) {
+            const double wk = 1.0 / ((double)(K[k + 1] - K[k]) * (K[k + 1] - K[k]));
+            for (int j = 0; j < P; ++j) dt[j] = th[(size_t)(k + 1) * P + j] - th[(size_t)k * P + j];
+            St += 0.5 * p.alpha_t * hd * wk * quad(dt.data(), gq.data());
+            if (grad)
+                for (int j = 0; j < P; ++j) {
+                    grad[(size_t)(k + 1) * P + j] += 0.5 * p.alpha_t * hd * wk * gq[j];
+                    grad[(size_t)k * P + j] -= 0.5 * p.alpha_t * hd * wk * gq[j];
+                }
+        }
+    std::vector<double> mean(P, 0.0);
+    for (int k = 0; k < nK; ++k)
+        for (int j = 0; j < P; ++j) mean[j] += th[(size_t)k * P + j] / nK;
+    const double Pv = p.lambda * hd * quad(mean.data(), gq.data());
+    if (grad)
+        for (int k = 0; k < nK; ++k)
+            for (int j = 0; j < P; ++j) grad[(size_t)k * P + j] += p.lambda * hd / nK * gq[j];
+    *S_out = Sx + St;
+    *P_out = Pv;
+}
+
+// Normalised-correlation evaluation (params.distance = 1): D_NC from the
+// Gram matrix of the warped frames, its gradient through Q, S and P in
+// closed form.
+stml_status affine_eval_nc(stml_ctx* c, int level, const std::vector<int>& K, const FrameSet& fs, const double* th,
+                           double* out4, double* grad) {
+    LevelBuf& L = c->lv[level];
+    const int nK = fs.nK, P = aff_P(c);
+    TRY(ensure_affine(c));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (long long i = 0; i < (long long)nK * P; ++i) c->h_theta[i] = (float)th[i];
+    CK(c, cudaMemcpyAsync(c->d_theta, c->h_theta, sizeof(float) * (size_t)nK * P, cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, launch_affine_field(L.g, affine_frame(c), c->d_theta, nK, c->w_u, c->stream));
+    CK(c, launch_nc_warp(Stored{L.img, c->img_type}, L.g, fs, c->w_u, c->w_ut, c->w_dT, c->d_aff_part, c->d_mu,
+                         c->stream));
+    CK(c, launch_nc_gram(L.g, c->w_ut, c->d_mu, nK, c->d_gpart, c->d_G, c->stream));
+    CK(c, cudaMemcpyAsync(c->h_G, c->d_G, sizeof(double) * (size_t)nK * nK, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double* G = c->h_G;
+    std::vector<double> nrm(nK), srow(nK, 0.0);
+    for (int i = 0; i < nK; ++i) nrm[i] = std::sqrt(G[(size_t)i * nK + i]);
+    double sum2 = 0.0;
+    for (int i = 0; i < nK; ++i)
+        for (int j = 0; j < nK; ++j) {
+            const double r = G[(size_t)i * nK + j] / (nrm[i] * nrm[j]);
+            sum2 += r * r;
+            srow[i] += r * r;
+        }
+    const double D = 0.5 * ((double)nK * nK - sum2);
+    double S = 0.0, Pv = 0.0;
+    if (grad) std::fill(grad, grad + (size_t)nK * P, 0.0);
+    affine_reg_terms(c, level, K, th, &S, &Pv, grad);
+    out4[0] = D + S + Pv;
+    out4[1] = D;
+    out4[2] = S;
+    out4[3] = Pv;
+    if (!std::isfinite(out4[0])) return fail(c, STML_ENONFINITE, "objective is not finite");
+    if (!grad) return STML_OK;
+    // dD/da_i = sum_j Q_ij (a_j - mu_j): Q_ij = -(2 / n_i) (rho_ij / n_j - delta_ij s_i / n_i)
+    for (int i = 0; i < nK; ++i)
+        for (int j = 0; j < nK; ++j) {
+            const double r = G[(size_t)i * nK + j] / (nrm[i] * nrm[j]);
+            c->h_Q[(size_t)i * nK + j] = (float)(-(2.0 / nrm[i]) * (r / nrm[j] - (i == j ? srow[i] / nrm[i] : 0.0)));
+        }
+    CK(c, cudaMemcpyAsync(c->d_Q, c->h_Q, sizeof(float) * (size_t)nK * nK, cudaMemcpyHostToDevice, c->stream));
+    CK(c, launch_nc_grad(L.g, c->w_ut, c->d_mu, c->d_Q, c->w_dT, nK, c->w_g, c->stream));
+    CK(c, launch_affine_project(L.g, affine_frame(c), c->w_g, nK, c->d_aff_part, c->d_gth, c->stream));
+    CK(c, cudaMemcpyAsync(c->h_gth, c->d_gth, sizeof(double) * (size_t)nK * P, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (long long i = 0; i < (long long)nK * P; ++i) grad[i] += c->h_gth[i];
+    return STML_OK;
+}
+
 // J, D, S, P and (grad not null) dJ/dtheta at theta for the frames of fs.
 // Without profiling, the second and later evaluations of a (level, nK, grad)
 // replay a CUDA graph of the sequence.
-stml_status affine_eval(stml_ctx* c, int level, const FrameSet& fs, const double* th, double* out4, double* grad) {
+stml_status affine_eval(stml_ctx* c, int level, const std::vector<int>& K, const FrameSet& fs, const double* th,
+                        double* out4, double* grad) {
+    if (c->p.distance == 1) return affine_eval_nc(c, level, K, fs, th, out4, grad);
     LevelBuf& L = c->lv[level];
     const int nK = fs.nK, P = aff_P(c);
     TRY(ensure_affine(c));
@@ -944,7 +1103,7 @@ stml_status run_gir_affine(stml_ctx* c, int level, const std::vector<int>& K, do
     TRY(upload_frameset(c, K, fs));
     std::vector<double> x(th, th + n), g(n), xt(n), gt(n), d(n);
     double e[4], et[4];
-    TRY(affine_eval(c, level, fs, x.data(), e, g.data()));
+    TRY(affine_eval(c, level, K, fs, x.data(), e, g.data()));
     stml_stats s{};
     s.level = level;
     s.n_frames = nK;
@@ -994,7 +1153,7 @@ stml_status run_gir_affine(stml_ctx* c, int level, const std::vector<int>& K, do
         for (int trial = 0; trial < p.max_ls; ++trial) {
             ++s.ls_trials;
             for (size_t j = 0; j < n; ++j) xt[j] = x[j] + t * d[j];
-            TRY(affine_eval(c, level, fs, xt.data(), et, gt.data()));
+            TRY(affine_eval(c, level, K, fs, xt.data(), et, gt.data()));
             if (et[0] <= J + p.armijo_c * t * gTd) {
                 accepted = true;
                 break;
@@ -1270,6 +1429,7 @@ void stml_default_params(stml_params* p) {
     p->transform = 0;
     p->lbfgs_m = 5;
     p->max_lbfgs = 50;
+    p->distance = 0;
 }
 
 stml_status stml_create(const stml_params* p, void* cuda_stream, stml_ctx** out) {
@@ -1702,7 +1862,7 @@ stml_status stml_eval_affine(stml_ctx* c, int level, const int* frames, int nK, 
     std::vector<int> K(frames, frames + nK);
     FrameSet fs;
     TRY(upload_frameset(c, K, fs));
-    return affine_eval(c, level, fs, theta, out, grad);
+    return affine_eval(c, level, K, fs, theta, out, grad);
 }
 
 stml_status stml_affine_field(stml_ctx* c, int level, const int* frames, int nK, const double* theta, float* u) {

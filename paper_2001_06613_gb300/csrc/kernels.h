@@ -66,6 +66,18 @@ int affine_project_blocks(const Geom& g);
 cudaError_t launch_affine_project(const Geom& g, const AffineFrame& af, const float* gu, int nK, double* part,
                                   double* out, cudaStream_t s);
 
+// Normalised-correlation distance of the affine variant: warped frames a
+// (nK x N), grad T (nK x d x N), per-frame means mu (part: nK * 256 * 2
+// doubles); Gram matrix G (nK x nK doubles) about the means (part:
+// nc_gram_splits * nK^2 doubles); gu = (Q (a - mu)) grad T for the K x K Q.
+cudaError_t launch_nc_warp(const Stored& T, const Geom& g, const FrameSet& fs, const float* u, float* a, float* dT,
+                           double* part, float* mu, cudaStream_t s);
+int nc_gram_splits(const Geom& g, int nK);
+cudaError_t launch_nc_gram(const Geom& g, const float* a, const float* mu, int nK, double* part, double* G,
+                           cudaStream_t s);
+cudaError_t launch_nc_grad(const Geom& g, const float* a, const float* mu, const float* Q, const float* dT, int nK,
+                           float* gu, cudaStream_t s);
+
 // ---------------------------------------------------------- transfer ops
 // 2^d block mean of `planes` stored arrays of 2 gc (type: StoreType).
 cudaError_t launch_restrict(const void* fine, void* coarse, int type, int planes, const Geom& gc,
