@@ -119,6 +119,13 @@ stml_status stml_net_train_step(stml_net* net, const stml_net_sample* samples, i
 stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const float* W, const float* b,
                                  float* y, int B, int H, int W_, int Cin, int Cout, void* cuda_stream);
 
+/* Failure-detection self-check: one CTA waits, with the bound of the
+ * convolution kernels' mbarrier waits, on an mbarrier that nothing completes;
+ * *expired = 1 when the wait gave up and the kernel returned (the designed
+ * behaviour: the network calls then report STML_ETIMEOUT).  Takes up to a
+ * second; synchronises `cuda_stream`. */
+stml_status stml_check_bounded_wait(void* cuda_stream, int* expired);
+
 /* Attaches a network to a context as its temporal predictor (NULL detaches).
  * The network must outlive the attachment and serve one context at a time;
  * stml_register_batch refuses contexts that share a network. */

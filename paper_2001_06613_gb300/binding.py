@@ -122,6 +122,7 @@ _SIGS = {
     "stml_set_predictor_net": (C.c_int, [_vp, _vp]),
     "stml_net_conv3_block": (C.c_int, [C.c_int, _fp, _fp, _fp, _fp, _fp, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_int, _vp]),
+    "stml_check_bounded_wait": (C.c_int, [_vp, _ip]),
 }
 
 
@@ -556,3 +557,10 @@ def stml_net_conv3_block(mode: int, x, a, W, b, y, stream=None):
     Cin, Cout = W.shape[2], W.shape[3]
     _check(load().stml_net_conv3_block(int(mode), _dev(x), _dev(a), _dev(W), _dev(b), _dev(y), Bn, H, Wd,
                                        Cin, Cout, _stream(stream)))
+
+
+def stml_check_bounded_wait(stream=None) -> bool:
+    """True when a device wait on an mbarrier nothing completes gave up as designed."""
+    out = C.c_int()
+    _check(load().stml_check_bounded_wait(_stream(stream), C.byref(out)))
+    return bool(out.value)

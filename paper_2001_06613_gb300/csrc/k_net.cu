@@ -183,6 +183,22 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
 
 }  // namespace
 
+// One CTA waits, with the convolution kernels' bound, on an mbarrier that
+// nothing completes: the wait must give up and report it (*expired = 1).
+__global__ void wait_probe_kernel(int* __restrict__ expired) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *expired = mbar_wait(smem_u32(&bar), 0u) ? 0 : 1;
+    }
+}
+
+cudaError_t launch_wait_probe(int* expired, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(expired);
+    return cudaGetLastError();
+}
+
 template <int BN>
 struct TcCfg {
     static constexpr int B_BYTES = 9 * 4 * BN * 16;              // one weight stage

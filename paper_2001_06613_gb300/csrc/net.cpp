@@ -558,4 +558,20 @@ stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const
     return STML_OK;
 }
 
+stml_status stml_check_bounded_wait(void* cuda_stream, int* expired) {
+    if (!expired) return net_fail(nullptr, STML_EINVAL, "expired is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int* d = nullptr;
+    cudaError_t e = nalloc(&d, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_wait_probe(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return net_fail(nullptr, STML_ECUDA, std::string("stml_check_bounded_wait: ") + cudaGetErrorString(e));
+    *expired = h;
+    return STML_OK;
+}
+
 }  // extern "C"

@@ -121,6 +121,9 @@ cudaError_t launch_reduce_head(const float* part, int blocks, float* grad, long 
 // Adam (FP32): m, v, theta updated in place; c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t).
 cudaError_t launch_adam(float* theta, float* m, float* v, const float* g, long long n, float lr,
                         float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+// One CTA waiting, with the convolutions' bound, on an mbarrier nothing
+// completes; *expired (device) = 1 when the wait gave up as designed.
+cudaError_t launch_wait_probe(int* expired, cudaStream_t s);
 // BF16 copies of every layer's weights in the GEMM layouts.
 cudaError_t launch_pack(const float* theta, const PackTable& t, cudaStream_t s);
 // dst[i] = bf16(src[i]) and back.
