@@ -17,6 +17,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/stml.h"
 #include "../../include/stml_net.h"
 #include "kernels.h"
@@ -27,6 +29,20 @@ using namespace stml;
 namespace {
 
 thread_local std::string g_free_error;   // error text of the context-free calls
+
+// NVTX range for profilers (no cost without one attached): spatial level,
+// temporal level / GIR, Gauss-Newton iteration, learned proposals.
+struct Range {
+    template <typename... A>
+    explicit Range(const char* fmt, A... a) {
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), fmt, a...);
+        nvtxRangePushA(buf);
+    }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct LevelBuf {
     Geom g{};
@@ -392,6 +408,7 @@ const ObjShapeChoice* obj_choice(stml_ctx* c, int level, const Geom& g, const Fr
 // ------------------------------------------------------------------ GIR
 // Gauss-Newton on the frames K of `level`, from and into u (nK * d * N floats).
 stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_io, stml_stats* st) {
+    Range rg("GIR level %d |K| %d", level, (int)K.size());
     const auto t_start = std::chrono::steady_clock::now();
     LevelBuf& L = c->lv[level];
     const Geom& g = L.g;
@@ -565,6 +582,7 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         started = true;
     }
     while (started) {
+        Range rit("Gauss-Newton iteration %d", it);
         // --- finish the PCG solve: all coefficients stay on the device; chunks of
         // launches whose kernels return at once when the device cleared cg_active
         while (c->Sh->cg_active && launched < p.max_cg) {
@@ -801,6 +819,7 @@ stml_status learned_fill(stml_ctx* c, int level, const std::vector<int>& Kp, con
         used.push_back(k);
     }
     if (smp.empty()) return STML_OK;
+    Range rn("learned proposals level %d: %d frames", level, (int)smp.size());
     const long pe = prof_begin(c, PC_PRED_NET, level);
     CK(c, cudaMemcpyAsync(c->w_z2, dst, (size_t)c->n * plane * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     const int mb = net::max_batch(c->net);
@@ -1095,6 +1114,7 @@ double normv(const std::vector<double>& a) { return std::sqrt(dotv(a, a)); }
 
 // GIR(K) over the affine parameters by L-BFGS (two-loop recursion), in place.
 stml_status run_gir_affine(stml_ctx* c, int level, const std::vector<int>& K, double* th, stml_stats* st) {
+    Range rg("affine GIR level %d |K| %d", level, (int)K.size());
     const auto t_start = std::chrono::steady_clock::now();
     const stml_params& p = c->p;
     const int nK = (int)K.size(), P = aff_P(c);
@@ -1692,6 +1712,7 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
         return STML_OK;
     }
     for (int l = 0; l < L; ++l) {
+        Range rl("level %d", l);
         if (mode == STML_MODE_SPML) {
             TRY(do_predict(c, l, 0));
             LevelBuf& B = c->lv[l];
@@ -1704,6 +1725,7 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
             c->level_done = true;
         } else {
             for (int q = 0; q < (int)c->sets.size(); ++q) {
+                Range rq("level %d temporal level %d", l, q);
                 TRY(do_predict(c, l, q));
                 stml_stats s{};
                 int fin = 0;
