@@ -178,7 +178,8 @@ def compare(S, net, sequences, params, repeats: int = 3) -> dict:
             cg_learned=sum(s["cg_iters"] for s in st1), cg_classic=sum(s["cg_iters"] for s in st0),
             gn_learned=sum(s["gn_iters"] for s in st1), gn_classic=sum(s["gn_iters"] for s in st0),
             kept=sum(1 for s in st1 if s["pred_learned"] == 1) + sum(1 for s in st1 if s["fill_learned"] == 1),
-            judged=sum(1 for s in st1 if s["pred_learned"] >= 0) + sum(1 for s in st1 if s["fill_learned"] >= 0)))
+            judged=sum(1 for s in st1 if s["pred_learned"] >= 0) + sum(1 for s in st1 if s["fill_learned"] >= 0),
+            decisions=[(s["level"], s["tlevel"], s["pred_learned"]) for s in st1 if s["pred_learned"] >= 0]))
     frames = sum(r["frames"] for r in rows)
     return dict(
         frames_per_s_learned=frames / sum(r["seconds_learned"] for r in rows),
@@ -186,6 +187,9 @@ def compare(S, net, sequences, params, repeats: int = 3) -> dict:
         cg_learned=sum(r["cg_learned"] for r in rows), cg_classic=sum(r["cg_classic"] for r in rows),
         gn_learned=sum(r["gn_learned"] for r in rows), gn_classic=sum(r["gn_classic"] for r in rows),
         kept=sum(r["kept"] for r in rows), judged=sum(r["judged"] for r in rows),
+        decisions_by_level={str(lv): [sum(1 for r in rows for (l, _, d) in r["decisions"] if l == lv and d == 1),
+                                      sum(1 for r in rows for (l, _, d) in r["decisions"] if l == lv)]
+                            for lv in sorted({l for r in rows for (l, _, _) in r["decisions"]})},
         max_rel_J_change=max(abs(r["J_learned"] - r["J_classic"]) / abs(r["J_classic"]) for r in rows),
         mean_rel_J_change=float(np.mean([(r["J_learned"] - r["J_classic"]) / abs(r["J_classic"]) for r in rows])))
 
