@@ -4,7 +4,8 @@ forward (bias, leaky ReLU, BF16 output), input gradient and weight/bias
 gradient (FP32 outputs).  One layer starts no rounding cascade, so the only
 differences are FP32 against FP64 accumulation (and, forward, the final BF16
 rounding): tight tolerances.  Shapes cover every channel count of the network,
-ragged pixel tiles and both tile widths of the kernels."""
+ragged pixel tiles, every output-channel tile width, and CTAs that run
+several tiles."""
 import numpy as np
 import pytest
 
@@ -51,7 +52,13 @@ def _operands(seed, B, H, W, Cin, Cout):
     return x, g, Wt, b
 
 
-@pytest.mark.parametrize("B,H,W,Cin,Cout", CASES)
+# more 16 x 8 tiles than the kernel launches CTAs: each CTA runs a sequence of
+# tiles (double-buffered TMEM accumulator, epilogue under the next tile's MMAs;
+# resident weights for a single 32-channel chunk, reloaded per chunk otherwise)
+BIG = [(8, 128, 128, 32, 32), (8, 128, 124, 96, 64)]
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", CASES + BIG)
 def test_forward(S, B, H, W, Cin, Cout):
     import torch
     x, _, Wt, b = _operands(1, B, H, W, Cin, Cout)
@@ -65,7 +72,7 @@ def test_forward(S, B, H, W, Cin, Cout):
     assert np.mean(got != onet.bf16(ref)) < 2e-3
 
 
-@pytest.mark.parametrize("B,H,W,Cin,Cout", CASES)
+@pytest.mark.parametrize("B,H,W,Cin,Cout", CASES + BIG)
 def test_input_gradient(S, B, H, W, Cin, Cout):
     import torch
     x, g, Wt, b = _operands(2, B, H, W, Cin, Cout)
