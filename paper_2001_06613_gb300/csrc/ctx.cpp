@@ -1572,7 +1572,6 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
     }
     const Geom& G = c->lv[L - 1].g;
     const size_t fieldN = (size_t)n_frames * dim * G.N;
-    const size_t imgN = (size_t)n_frames * G.N;
     size_t pcap = 0;
     for (int l = 0; l < L; ++l)
         pcap = std::max(pcap, std::max(eval_partials(c->lv[l].g, n_frames), gn_partials(c->lv[l].g, n_frames)));
