@@ -120,9 +120,10 @@ struct stml_ctx {
     // captured on a private stream, launched on the context's stream
     cudaStream_t cap_stream = nullptr;
     std::map<std::array<int, 3>, cudaGraphExec_t> aff_graphs;
-    // normalised-correlation distance: frame means, Gram matrix and its
-    // partials, the K x K gradient matrix (device and pinned host copies)
-    float *d_mu = nullptr, *d_Q = nullptr, *h_Q = nullptr;
+    // normalised-correlation distance: frame means, Gram matrix, D_NC with
+    // the row sums and the Gram partials, the K x K gradient matrix, and a
+    // pinned slot for D_NC
+    float *d_mu = nullptr, *d_Q = nullptr;
     double *d_G = nullptr, *d_gpart = nullptr, *h_G = nullptr;
 
     // learned temporal predictor (stml_set_predictor_net) and its last decisions
@@ -235,9 +236,7 @@ void free_buffers(stml_ctx* c) {
     for (auto& kv : c->aff_graphs) cudaGraphExecDestroy(kv.second);
     c->aff_graphs.clear();
     dfree(c->d_mu); dfree(c->d_Q); dfree(c->d_G); dfree(c->d_gpart);
-    if (c->h_Q) cudaFreeHost(c->h_Q);
     if (c->h_G) cudaFreeHost(c->h_G);
-    c->h_Q = nullptr;
     c->h_G = nullptr;
     c->loaded = c->built = false;
 }
@@ -865,17 +864,14 @@ stml_status ensure_affine(stml_ctx* c) {
     CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_theta), sizeof(float) * (size_t)c->n * P));
     CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_gth), sizeof(double) * (size_t)c->n * P));
     dfree(c->d_mu); dfree(c->d_Q); dfree(c->d_G); dfree(c->d_gpart);
-    if (c->h_Q) cudaFreeHost(c->h_Q);
     if (c->h_G) cudaFreeHost(c->h_G);
-    c->h_Q = nullptr;
     c->h_G = nullptr;
     const size_t n2 = (size_t)c->n * c->n;
     CK(c, dalloc(&c->d_mu, (size_t)c->n));
     CK(c, dalloc(&c->d_Q, n2));
     CK(c, dalloc(&c->d_G, n2));
-    CK(c, dalloc(&c->d_gpart, 64 * n2));
-    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_Q), sizeof(float) * n2));
-    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_G), sizeof(double) * n2));
+    CK(c, dalloc(&c->d_gpart, 64 * n2 + 1 + (size_t)c->n));    // Gram partials, D_NC, row sums
+    CK(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_G), sizeof(double)));
     c->aff_cap = c->n;
     return STML_OK;
 }
@@ -1007,35 +1003,66 @@ void affine_reg_terms(const stml_ctx* c, int level, const std::vector<int>& K, c
     *P_out = Pv;
 }
 
-// Normalised-correlation evaluation (params.distance = 1): D_NC from the
-// Gram matrix of the warped frames, its gradient through Q, S and P in
-// closed form.
+// Normalised-correlation evaluation on stream st (h_theta already holds
+// theta): field, warped frames and grad T, Gram matrix, D_NC and Q on the
+// device, and with grad the field gradient, its projection and the download
+// of dJ/dtheta (D_NC lands in d_G's last slot and is downloaded too).
+cudaError_t nc_enqueue(stml_ctx* c, int level, const FrameSet& fs, bool grad, cudaStream_t st) {
+    LevelBuf& L = c->lv[level];
+    const int nK = fs.nK, P = aff_P(c);
+    double* dD = c->d_gpart;                    // slot 0: D_NC; slots 1..nK: srow
+    double* srow = c->d_gpart + 1;
+    double* gpart = c->d_gpart + 1 + c->n;
+    cudaError_t e = cudaMemcpyAsync(c->d_theta, c->h_theta, sizeof(float) * (size_t)nK * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_affine_field(L.g, affine_frame(c), c->d_theta, nK, c->w_u, st);
+    if (e == cudaSuccess)
+        e = launch_nc_warp(Stored{L.img, c->img_type}, L.g, fs, c->w_u, c->w_ut, c->w_dT, c->d_aff_part, c->d_mu, st);
+    if (e == cudaSuccess) e = launch_nc_gram(L.g, c->w_ut, c->d_mu, nK, gpart, c->d_G, st);
+    if (e == cudaSuccess) e = launch_nc_coeff(c->d_G, nK, srow, c->d_Q, dD, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_G, dD, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (grad && e == cudaSuccess) e = launch_nc_grad(L.g, c->w_ut, c->d_mu, c->d_Q, c->w_dT, nK, c->w_g, st);
+    if (grad && e == cudaSuccess)
+        e = launch_affine_project(L.g, affine_frame(c), c->w_g, nK, c->d_aff_part, c->d_gth, st);
+    if (grad && e == cudaSuccess)
+        e = cudaMemcpyAsync(c->h_gth, c->d_gth, sizeof(double) * (size_t)nK * P, cudaMemcpyDeviceToHost, st);
+    return e;
+}
+
+// Normalised-correlation evaluation (params.distance = 1): D_NC and dD/dtheta
+// on the device (one host wait; the second and later evaluations of a
+// (level, nK, grad) replay a CUDA graph), S and P in closed form on the host.
 stml_status affine_eval_nc(stml_ctx* c, int level, const std::vector<int>& K, const FrameSet& fs, const double* th,
                            double* out4, double* grad) {
-    LevelBuf& L = c->lv[level];
     const int nK = fs.nK, P = aff_P(c);
     TRY(ensure_affine(c));
     CK(c, cudaStreamSynchronize(c->stream));
     for (long long i = 0; i < (long long)nK * P; ++i) c->h_theta[i] = (float)th[i];
-    CK(c, cudaMemcpyAsync(c->d_theta, c->h_theta, sizeof(float) * (size_t)nK * P, cudaMemcpyHostToDevice,
-                          c->stream));
-    CK(c, launch_affine_field(L.g, affine_frame(c), c->d_theta, nK, c->w_u, c->stream));
-    CK(c, launch_nc_warp(Stored{L.img, c->img_type}, L.g, fs, c->w_u, c->w_ut, c->w_dT, c->d_aff_part, c->d_mu,
-                         c->stream));
-    CK(c, launch_nc_gram(L.g, c->w_ut, c->d_mu, nK, c->d_gpart, c->d_G, c->stream));
-    CK(c, cudaMemcpyAsync(c->h_G, c->d_G, sizeof(double) * (size_t)nK * nK, cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    const double* G = c->h_G;
-    std::vector<double> nrm(nK), srow(nK, 0.0);
-    for (int i = 0; i < nK; ++i) nrm[i] = std::sqrt(G[(size_t)i * nK + i]);
-    double sum2 = 0.0;
-    for (int i = 0; i < nK; ++i)
-        for (int j = 0; j < nK; ++j) {
-            const double r = G[(size_t)i * nK + j] / (nrm[i] * nrm[j]);
-            sum2 += r * r;
-            srow[i] += r * r;
+    const bool g = grad != nullptr;
+    const std::array<int, 3> key{level, nK, g ? 3 : 2};    // distinct from the SSD graphs
+    auto it = c->prof ? c->aff_graphs.end() : c->aff_graphs.find(key);
+    if (it != c->aff_graphs.end()) {
+        CK(c, cudaGraphLaunch(it->second, c->stream));
+        count_launches(g ? 11 : 8);
+    } else {
+        CK(c, nc_enqueue(c, level, fs, g, c->stream));
+        if (!c->prof) {
+            if (!c->cap_stream) cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            if (c->cap_stream &&
+                cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const cudaError_t e1 = nc_enqueue(c, level, fs, g, c->cap_stream);
+                const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+                if (e1 == cudaSuccess && e2 == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+                    c->aff_graphs[key] = exec;
+                if (graph) cudaGraphDestroy(graph);
+            }
+            cudaGetLastError();
         }
-    const double D = 0.5 * ((double)nK * nK - sum2);
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double D = c->h_G[0];
     double S = 0.0, Pv = 0.0;
     if (grad) std::fill(grad, grad + (size_t)nK * P, 0.0);
     affine_reg_terms(c, level, K, th, &S, &Pv, grad);
@@ -1044,19 +1071,8 @@ stml_status affine_eval_nc(stml_ctx* c, int level, const std::vector<int>& K, co
     out4[2] = S;
     out4[3] = Pv;
     if (!std::isfinite(out4[0])) return fail(c, STML_ENONFINITE, "objective is not finite");
-    if (!grad) return STML_OK;
-    // dD/da_i = sum_j Q_ij (a_j - mu_j): Q_ij = -(2 / n_i) (rho_ij / n_j - delta_ij s_i / n_i)
-    for (int i = 0; i < nK; ++i)
-        for (int j = 0; j < nK; ++j) {
-            const double r = G[(size_t)i * nK + j] / (nrm[i] * nrm[j]);
-            c->h_Q[(size_t)i * nK + j] = (float)(-(2.0 / nrm[i]) * (r / nrm[j] - (i == j ? srow[i] / nrm[i] : 0.0)));
-        }
-    CK(c, cudaMemcpyAsync(c->d_Q, c->h_Q, sizeof(float) * (size_t)nK * nK, cudaMemcpyHostToDevice, c->stream));
-    CK(c, launch_nc_grad(L.g, c->w_ut, c->d_mu, c->d_Q, c->w_dT, nK, c->w_g, c->stream));
-    CK(c, launch_affine_project(L.g, affine_frame(c), c->w_g, nK, c->d_aff_part, c->d_gth, c->stream));
-    CK(c, cudaMemcpyAsync(c->h_gth, c->d_gth, sizeof(double) * (size_t)nK * P, cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    for (long long i = 0; i < (long long)nK * P; ++i) grad[i] += c->h_gth[i];
+    if (grad)
+        for (long long i = 0; i < (long long)nK * P; ++i) grad[i] += c->h_gth[i];
     return STML_OK;
 }
 

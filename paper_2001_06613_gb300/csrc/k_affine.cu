@@ -276,7 +276,49 @@ __global__ void __launch_bounds__(256) nc_grad_kernel(const float* __restrict__ 
     }
 }
 
+// Row i of rho = G_ij / (n_i n_j): srow[i] = sum_j rho_ij^2 (FP64, fixed
+// order) and Q_ij = -(2 / n_i) (rho_ij / n_j - delta_ij srow_i / n_i).
+__global__ void __launch_bounds__(128) nc_coeff_kernel(const double* __restrict__ G, int nK, double* __restrict__ srow,
+                                                       float* __restrict__ Q) {
+    __shared__ double red[4];
+    const int i = blockIdx.x;
+    const double ni = sqrt(G[(size_t)i * nK + i]);
+    double s = 0.0;
+    for (int j = threadIdx.x; j < nK; j += blockDim.x) {
+        const double nj = sqrt(G[(size_t)j * nK + j]);
+        const double r = G[(size_t)i * nK + j] / (ni * nj);
+        s += r * r;
+        Q[(size_t)i * nK + j] = (float)(-(2.0 / ni) * (r / nj));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double si = red[0] + red[1] + red[2] + red[3];
+        srow[i] = si;
+        const double r_ii = G[(size_t)i * nK + i] / (ni * ni);
+        Q[(size_t)i * nK + i] = (float)(-(2.0 / ni) * (r_ii / ni - si / ni));
+    }
+}
+
+// D_NC = 1/2 (K^2 - sum_i srow_i), summed in row order.
+__global__ void nc_d_kernel(const double* __restrict__ srow, int nK, double* __restrict__ D) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nK; ++i) s += srow[i];
+        *D = 0.5 * ((double)nK * nK - s);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_nc_coeff(const double* G, int nK, double* srow, float* Q, double* D, cudaStream_t s) {
+    nc_coeff_kernel<<<nK, 128, 0, s>>>(G, nK, srow, Q);
+    nc_d_kernel<<<1, 32, 0, s>>>(srow, nK, D);
+    count_launches(2);
+    return cudaGetLastError();
+}
 
 int nc_gram_splits(const Geom& g, int nK) {
     const long long tiles = (long long)((nK + 15) / 16) * ((nK + 15) / 16);

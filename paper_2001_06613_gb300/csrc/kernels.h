@@ -77,6 +77,9 @@ cudaError_t launch_nc_gram(const Geom& g, const float* a, const float* mu, int n
                            cudaStream_t s);
 cudaError_t launch_nc_grad(const Geom& g, const float* a, const float* mu, const float* Q, const float* dT, int nK,
                            float* gu, cudaStream_t s);
+// From the Gram matrix G: srow_i = sum_j rho_ij^2, the gradient matrix Q and
+// D_NC (device double) -- the host needs no step between Gram and gradient.
+cudaError_t launch_nc_coeff(const double* G, int nK, double* srow, float* Q, double* D, cudaStream_t s);
 
 // ---------------------------------------------------------- transfer ops
 // 2^d block mean of `planes` stored arrays of 2 gc (type: StoreType).
