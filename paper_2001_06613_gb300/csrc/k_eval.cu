@@ -614,7 +614,7 @@ grad_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, long 
 // ----------------------------------------------------------------- launchers
 namespace {
 
-constexpr int kGridStride = 152 * 8;   // CTAs of the grid-stride launches (8 per SM of a GB300)
+constexpr int kGridStride = 152 * 8;   // most CTAs of a grid-stride launch (8 of 256 threads per SM of a GB300)
 
 bool v4ok(const Geom& g, std::initializer_list<const void*> ptrs) {
     if (g.nx % 4) return false;
@@ -760,8 +760,6 @@ cudaError_t launch_gradient(const Stored& T, const Geom& g, const FrameSet& fs, 
     const int vec = v4 ? 4 : 1;
     const long long cpf = (g.N + (long long)kThreads * vec - 1) / ((long long)kThreads * vec);
     const long long items = cpf * fs.nK;
-    const unsigned blocks = (unsigned)(items < kGridStride ? items : kGridStride);
-    if ((size_t)blocks * 2 > partials_cap) return cudaErrorInvalidValue;
     const FastDiv chunks = FastDiv::make((unsigned)cpf);
     const FView U{u, du, t};
     auto go = [&](auto ti_tag, auto td_tag) {
@@ -769,8 +767,14 @@ cudaError_t launch_gradient(const Stored& T, const Geom& g, const FrameSet& fs, 
         using TD = decltype(td_tag);
         const TI* Ti = static_cast<const TI*>(T.p);
         TD* Td = static_cast<TD*>(dT);
-#define STML_GRAD(D_, V_) \
-    grad_kernel<D_, V_, TI, TD><<<blocks, kThreads, 0, s>>>(Ti, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, Td, unew, partials, ticket, out, gate)
+#define STML_GRAD(D_, V_)                                                                                 \
+    do {                                                                                                  \
+        auto k = grad_kernel<D_, V_, TI, TD>;                                                             \
+        const unsigned blocks = resident_grid((const void*)k, items, kGridStride);                        \
+        if ((size_t)blocks * 2 > partials_cap) return cudaErrorInvalidValue;                              \
+        k<<<blocks, kThreads, 0, s>>>(Ti, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, Td, unew, partials, \
+                                      ticket, out, gate);                                                 \
+    } while (0)
         if (g.d == 2) {
             if (v4) STML_GRAD(2, 4); else STML_GRAD(2, 1);
         } else {

@@ -544,21 +544,20 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
     }
 }
 
-// Hessian product stream (grid-stride over (frame, chunk) items).  With
-// pcg != nullptr the launch is a PCG step: it does nothing once cg_active is
-// 0, FUSED forms the direction on the fly with beta from the device, and the
-// last CTA sets alpha = rho / <p, Hp> (or flags a breakdown).
-template <int D, int VEC, bool FUSED, typename TD>
+// Hessian product stream (grid-stride over (frame, chunk) items) of
+// v = src.z with its frame sums src.ms_z / src.sv_z.  With pcg != nullptr the
+// launch is a PCG step: it does nothing once cg_active is 0 and the last CTA
+// sets alpha = rho / <p, Hp> (or flags a breakdown).
+template <int D, int VEC, typename TD>
 __global__ void __launch_bounds__(kThreads)
 apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
              const TD* __restrict__ dT, DirSrc src, float* __restrict__ Hv, double* __restrict__ partials,
              unsigned int* ticket, double* out, DevScalars* pcg) {
     if (pcg && !pcg->cg_active) return;
-    if (FUSED) src.beta = src.pold ? pcg->beta : 0.f;
     float acc[1] = {0.f};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int j = (int)chunks.div((unsigned)it);
-        apply_item<D, VEC, FUSED, TD>(g, pi, fs, cf, dT, src, Hv, j, (unsigned)it - (unsigned)j * chunks.d, acc[0]);
+        apply_item<D, VEC, false, TD>(g, pi, fs, cf, dT, src, Hv, j, (unsigned)it - (unsigned)j * chunks.d, acc[0]);
     }
     if (grid_reduce<1>(acc, partials, ticket, out) && threadIdx.x == 0 && pcg) {
         CgState st = cg_load(pcg);
@@ -646,7 +645,7 @@ PixIndex make_pix_index(const Geom& g) {
 
 namespace {
 
-constexpr int kGridStride = 152 * 8;   // CTAs of the grid-stride launches (8 per SM of a GB300)
+constexpr int kGridStride = 152 * 8;   // most CTAs of a grid-stride launch (8 of 256 threads per SM of a GB300)
 
 bool vec4_ok(const Geom& g, std::initializer_list<const void*> ptrs) {
     if (g.nx % 4) return false;
@@ -688,34 +687,26 @@ cudaError_t tile_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const
     return cudaGetLastError();
 }
 
-template <bool FUSED>
 cudaError_t apply_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const DirSrc& src,
                          float* Hv, double* partials, size_t partials_cap, unsigned int* ticket, double* out,
                          DevScalars* pcg, cudaStream_t s) {
     const PixIndex pi = make_pix_index(g);
-    const bool v4 = vec4_ok(g, {dT.p, src.z, src.pold, src.pout, Hv, src.ms_z, src.sv_z, src.ms_p, src.sv_p,
-                                src.ms_out, src.sv_out});
+    const bool v4 = vec4_ok(g, {dT.p, src.z, Hv, src.ms_z, src.sv_z});
     const int vec = v4 ? 4 : 1;
     const long long cpf = (g.N + (long long)kThreads * vec - 1) / ((long long)kThreads * vec);
     const long long items = cpf * fs.nK;
-    const unsigned grid = (unsigned)(items < kGridStride ? items : kGridStride);
-    if ((size_t)grid > partials_cap) return cudaErrorInvalidValue;
     const FastDiv chunks = FastDiv::make((unsigned)cpf);
-#define STML_APPLY(D_, V_) \
-    apply_kernel<D_, V_, FUSED, TD><<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, src, Hv, partials, ticket, out, pcg)
-    with_store_type(dT.type, [&](auto tag) {
+    return with_store_type(dT.type, [&](auto tag) -> cudaError_t {
         using TD = decltype(tag);
         const TD* Td = static_cast<const TD*>(dT.p);
-        if (g.d == 2) {
-            if (v4) STML_APPLY(2, 4); else STML_APPLY(2, 1);
-        } else {
-            if (v4) STML_APPLY(3, 4); else STML_APPLY(3, 1);
-        }
-        return 0;
+        auto k = g.d == 2 ? (v4 ? apply_kernel<2, 4, TD> : apply_kernel<2, 1, TD>)
+                          : (v4 ? apply_kernel<3, 4, TD> : apply_kernel<3, 1, TD>);
+        const unsigned grid = resident_grid((const void*)k, items, kGridStride);
+        if ((size_t)grid > partials_cap) return cudaErrorInvalidValue;
+        k<<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, src, Hv, partials, ticket, out, pcg);
+        count_launches(1);
+        return cudaGetLastError();
     });
-#undef STML_APPLY
-    count_launches(1);
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -739,7 +730,7 @@ cudaError_t launch_hess_apply(const Geom& g, const FrameSet& fs, const Coef& cf,
                               size_t partials_cap, unsigned int* ticket, double* out, DevScalars* pcg,
                               cudaStream_t s) {
     const DirSrc src{v, nullptr, 0.f, nullptr, mean_s, sum_v, nullptr, nullptr, nullptr, nullptr};
-    return apply_launch<false>(g, fs, cf, Stored{dT, ST_F32}, src, Hv, partials, partials_cap, ticket, out, pcg, s);
+    return apply_launch(g, fs, cf, Stored{dT, ST_F32}, src, Hv, partials, partials_cap, ticket, out, pcg, s);
 }
 
 cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const Stored& dT,
@@ -752,7 +743,7 @@ cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, c
 cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
                              double* partials, size_t partials_cap, DevScalars* S, cudaStream_t s) {
     const DirSrc src{b.p[0], nullptr, 0.f, nullptr, b.ms_z, b.sv_z, nullptr, nullptr, nullptr, nullptr};
-    return apply_launch<false>(g, fs, cf, dT, src, b.q, partials, partials_cap, &S->ticket[1], S->dots + 4, S, s);
+    return apply_launch(g, fs, cf, dT, src, b.q, partials, partials_cap, &S->ticket[1], S->dots + 4, S, s);
 }
 
 cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
@@ -762,24 +753,18 @@ cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf,
     const int vec = v4 ? 4 : 1;
     const long long cpf = (g.N + (long long)kThreads * vec - 1) / ((long long)kThreads * vec);
     const long long items = cpf * fs.nK * g.d;
-    const unsigned grid = (unsigned)(items < kGridStride ? items : kGridStride);
-    if ((size_t)grid * 2 > partials_cap) return cudaErrorInvalidValue;
     const FastDiv chunks = FastDiv::make((unsigned)cpf);
-#define STML_UPD(D_, V_) \
-    update_kernel<D_, V_, TD><<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, b.x, b.r, b.p[0], b.q, partials, S, a)
-    with_store_type(dT.type, [&](auto tag) {
+    return with_store_type(dT.type, [&](auto tag) -> cudaError_t {
         using TD = decltype(tag);
         const TD* Td = static_cast<const TD*>(dT.p);
-        if (g.d == 2) {
-            if (v4) STML_UPD(2, 4); else STML_UPD(2, 1);
-        } else {
-            if (v4) STML_UPD(3, 4); else STML_UPD(3, 1);
-        }
-        return 0;
+        auto k = g.d == 2 ? (v4 ? update_kernel<2, 4, TD> : update_kernel<2, 1, TD>)
+                          : (v4 ? update_kernel<3, 4, TD> : update_kernel<3, 1, TD>);
+        const unsigned grid = resident_grid((const void*)k, items, kGridStride);
+        if ((size_t)grid * 2 > partials_cap) return cudaErrorInvalidValue;
+        k<<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, b.x, b.r, b.p[0], b.q, partials, S, a);
+        count_launches(1);
+        return cudaGetLastError();
     });
-#undef STML_UPD
-    count_launches(1);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_direction(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT,

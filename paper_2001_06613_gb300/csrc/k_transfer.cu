@@ -7,6 +7,8 @@
 // * linear temporal predictor (Sec. 3) and the least-squares predictor of
 //   eq. (2) solved by Thomas' algorithm (one factorisation for all series).
 #include <atomic>
+#include <mutex>
+#include <unordered_map>
 
 #include "kernels.h"
 
@@ -15,6 +17,32 @@ namespace stml {
 static std::atomic<long long> g_launches{0};
 long long launches_total() { return g_launches.load(); }
 void count_launches(int k) { g_launches.fetch_add(k); }
+
+unsigned resident_grid(const void* kernel, long long items, unsigned cap) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, unsigned> per_gpu;
+    unsigned n = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = per_gpu.find(kernel);
+        if (it != per_gpu.end()) {
+            n = it->second;
+        } else {
+            int dev = 0, sms = 0, per_sm = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) == cudaSuccess &&
+                sms > 0 && per_sm > 0)
+                n = (unsigned)(sms * per_sm);
+            else
+                n = cap;   // the query failed: the caller's cap (the launch reports any real error)
+            per_gpu.emplace(kernel, n);
+        }
+    }
+    if (n > cap) n = cap;
+    if ((long long)n > items) n = (unsigned)(items > 0 ? items : 1);
+    return n;
+}
 
 Geom make_geom(const int shape3[3], int d, float h) {
     Geom g;

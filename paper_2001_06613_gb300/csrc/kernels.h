@@ -34,6 +34,14 @@ void set_context_free_error(const std::string& msg);
 long long launches_total();
 void count_launches(int k);
 
+// CTAs of a grid-stride launch of `kernel` at kThreads per CTA: the CTAs
+// that are resident at once (SMs x CTAs per SM at the kernel's register and
+// shared-memory use, queried once per kernel), at most `items` and at most
+// `cap`.  A grid larger than that runs in waves, and a CTA of the second wave
+// works on items far from those in flight, losing the L2 reuse of the
+// neighbouring frames and rows.
+unsigned resident_grid(const void* kernel, long long items, unsigned cap);
+
 // Geometry of a level from its shape (nz, ny, nx), dimension and cell width.
 Geom make_geom(const int shape3[3], int d, float h);
 
