@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-affine", action="store_true")
+    ap.add_argument("--no-volume", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time launch shapes and PCG paths on first use (warm-up steps)")
     ap.add_argument("--cpu-sample-frames", type=int, default=25)
@@ -454,6 +455,83 @@ def run_learned(S, torch, dev, peaks):
             "paper_scale_canvas128": ev_paper128}
 
 
+def run_volume(S, torch, dev, peak_gbs: float):
+    """Three-dimensional sequence: 40 volumes of 64x128x128 (depth first; 6
+    modes, 4 voxel max, sin(2 pi t / 40)), 3 spatial x 3 temporal levels,
+    STML, with the image pyramid and grad T stored in FP32, FP16 and BF16
+    (arithmetic in FP32).  Per storage type: frames/s (one warm-up, then the
+    mean of two registrations, L2 flushed before each), the Hessian
+    product's achieved bandwidth (36 B per voxel-frame, 30 with 16-bit
+    grad T) over all its launches and on the finest level, and for the
+    16-bit types the final objective on the FP32 volumes and the field
+    difference against the FP32 run."""
+    from paper_2001_06613_gb300 import synthetic
+    spec = synthetic.spec_volume()
+    t0 = time.perf_counter()
+    R = synthetic.make_sequence(spec, device=dev)
+    gen_s = time.perf_counter() - t0
+    n, shape, L, Q = spec.n, tuple(spec.shape), 3, 3
+    d = len(shape)
+    stream = torch.cuda.current_stream(dev)
+    R_dev = torch.from_numpy(R).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": f"{n} volumes {shape[0]}x{shape[1]}x{shape[2]} fp32, 6 modes, 4 voxel max, "
+                       f"{L} spatial x {Q} temporal levels, STML", "generation_s": gen_s, "runs": {}}
+    ctx32 = None
+    y32 = None
+    J32 = None
+    try:
+        for name, code in (("f32", 0), ("f16", 1), ("bf16", 2)):
+            ctx = S.Context(S.stml_default_params(n_levels=L, n_tlevels=Q, image_dtype=code), stream.cuda_stream)
+
+            def reg():
+                S.stml_load_sequence(ctx.ptr, R_dev)
+                S.stml_build_pyramid(ctx.ptr)
+                return S.stml_register(ctx.ptr, S.MODE_STML)
+
+            reg()
+            S.stml_profile_enable(ctx.ptr, 2)
+            times = []
+            for _ in range(2):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                stats = reg()
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            prof = S.stml_profile_read(ctx.ptr)
+            levels = S.stml_profile_report(ctx.ptr)
+            S.stml_profile_enable(ctx.ptr, 0)
+            y = torch.empty((n, d) + shape, dtype=torch.float32, device=dev)
+            S.stml_get_field(ctx.ptr, L - 1, y)
+            fin = [r for r in levels if r["kernel"] == "gn_hessian_product" and r["level"] == L - 1]
+            gbs = prof["bytes"] / (prof["ms"] / 1e3) / 1e9 if prof["ms"] > 0 else None
+            fgbs = fin[0]["bytes"] / (fin[0]["ms"] / 1e3) / 1e9 if fin and fin[0]["ms"] > 0 else None
+            row = {"frames_per_s": n / (statistics.mean(times) / 1e3), "ms": times,
+                   "hessian_product": {"GB/s": gbs, "frac": gbs / peak_gbs if gbs else None,
+                                       "finest_GB/s": fgbs, "finest_frac": fgbs / peak_gbs if fgbs else None,
+                                       "bytes_per_voxel_frame": (8.0 + (4.0 if code == 0 else 2.0)) * d,
+                                       "launches": prof["launches"]},
+                   "gn_iters": sum(s["gn_iters"] for s in stats), "cg_iters": sum(s["cg_iters"] for s in stats)}
+            if code == 0:
+                ctx32, y32 = ctx, y
+                J32 = S.stml_eval(ctx32.ptr, L - 1, list(range(n)), y32)[0]
+                row["final_J"] = J32
+            else:
+                ctx.close()
+                J = S.stml_eval(ctx32.ptr, L - 1, list(range(n)), y)[0]
+                row["final_J_on_fp32_volumes"] = J
+                row["final_J_rel_diff"] = (J - J32) / J32
+                row["field_rms_diff_vs_fp32"] = float(torch.sqrt(torch.mean((y - y32) ** 2)).item())
+                row["field_max_diff_vs_fp32"] = float(torch.max(torch.abs(y - y32)).item())
+            out["runs"][name] = row
+    finally:
+        if ctx32 is not None:
+            ctx32.close()
+    return out
+
+
 def run_affine(S, torch, dev, repeats: int = 2):
     """The paper's own setting (Sec. 4): one affine-linear map per frame,
     L-BFGS (Sec. 2), 129 frames with |K_0| = 17, |K_1| = 33 (4 temporal
@@ -637,6 +715,10 @@ def run_native(args):
     affine = None
     if not args.no_affine and rank == 0 and world == 1:
         affine = run_affine(S, torch, dev)
+    volume = None
+    if not args.no_volume and rank == 0 and world == 1:
+        pk = measured_peaks()
+        volume = run_volume(S, torch, dev, pk["hbm_gbs"] if pk else 6800.0)
     combined = None
     if not args.no_batch and not args.no_learned and rank == 0 and world == 1 and args.mode == "stml":
         combined = run_combined(S, torch, dev, mode)
@@ -697,7 +779,8 @@ def run_native(args):
                 "per_step_ms": ms_steps,
                 "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
                                                  "ls_trials", "stopped_early")} for s in stats],
-                "spml": spml, "batch": batch, "learned": learned, "affine": affine, "combined": combined,
+                "spml": spml, "batch": batch, "learned": learned, "affine": affine, "volume": volume,
+                "combined": combined,
                 "tuning": tuning}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -548,8 +548,14 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
 // v = src.z with its frame sums src.ms_z / src.sv_z.  With pcg != nullptr the
 // launch is a PCG step: it does nothing once cg_active is 0 and the last CTA
 // sets alpha = rho / <p, Hp> (or flags a breakdown).
+// CTAs per SM the Hessian-product kernel is compiled for (a register cap):
+// 3 for the 3-D float4 form, where 80 registers instead of 84 let a third
+// CTA in; otherwise the count its register use gives anyway.
+template <int D, int VEC>
+constexpr int apply_min_ctas() { return VEC == 4 ? (D == 3 ? 3 : 4) : (D == 3 ? 5 : 6); }
+
 template <int D, int VEC, typename TD>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (apply_min_ctas<D, VEC>()))
 apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
              const TD* __restrict__ dT, DirSrc src, float* __restrict__ Hv, double* __restrict__ partials,
              unsigned int* ticket, double* out, DevScalars* pcg) {

@@ -163,6 +163,22 @@ def test_single_frame_and_3d_sequence(S):
     assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
 
 
+def test_3d_streaming_pcg_matches_oracle(S):
+    """A 3-D sequence solved with the streaming PCG passes (start, Hessian
+    product, update and direction kernels in 3-D; the cooperative solve is
+    switched off): the final objective agrees with the oracle's."""
+    spec = synthetic.spec_custom(5, (12, 16, 20), seed=5, amp=1.0)
+    R3 = synthetic.make_sequence(spec)
+    stats, y3, prm = _register(S, R3, 0, n_levels=2, n_tlevels=2, pcg_cooperative=0)
+    assert sum(s["cg_iters"] for s in stats) > 0
+    op = _oparams(prm)
+    res = multilevel.register(R3.astype(np.float64), op, "stml")
+    Jg = multilevel.final_objective(R3.astype(np.float64), y3.astype(np.float64), op)["J"]
+    Jo = multilevel.final_objective(R3.astype(np.float64), res.y, op)["J"]
+    assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
+    assert float(np.sqrt(np.mean((y3 - res.y) ** 2))) <= 0.05
+
+
 def test_autotune_is_reproducible_and_close(S, tiny):
     """params.autotune: the tuned launch shapes and PCG path are kept for the
     context (a second registration is bit-identical) and the result stays
