@@ -193,6 +193,27 @@ def oracle_sample(R: np.ndarray, workload: str, frames: int):
     return frames / dt, dt
 
 
+def oracle_hessvec_ns(workload: str, frames: int, reps: int = 3):
+    """FP64 oracle's Gauss-Newton Hessian product on the finest level (first
+    `frames` frames, seeded random direction and grad T, single thread):
+    nanoseconds per pixel-frame and seconds per call.  The CPU side of the
+    per-operation comparison in the bench line."""
+    from oracle import Params, objective
+    n, shape, L, Q, _ = WORKLOADS[workload]
+    rng = np.random.default_rng(5)
+    d = len(shape)
+    dT = rng.normal(size=(frames, d) + tuple(shape))
+    v = rng.normal(size=(frames, d) + tuple(shape))
+    p = Params(n_levels=L, n_tlevels=Q)
+    K = list(range(frames))
+    objective.hessvec(dT, v, K, 1.0, p)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        objective.hessvec(dT, v, K, 1.0, p)
+    dt = (time.perf_counter() - t0) / reps
+    return 1e9 * dt / (frames * float(np.prod(shape))), dt
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if world > 1:
@@ -730,6 +751,10 @@ def run_native(args):
         cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                "sample": f"first {frames} of {n} frames, full 256x256, same levels; numpy FP64 "
                          f"single thread; {dt:.1f} s"}
+        ns, call_s = oracle_hessvec_ns(args.workload, frames)
+        cpu["ops"] = {"gn_hessian_product": {"oracle_ns_per_pixel_frame": ns,
+                                             "sample": f"finest level, {frames} frames, mean of 3 calls "
+                                                       f"({call_s:.2f} s each)"}}
 
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -749,6 +774,10 @@ def run_native(args):
             "algorithmic_bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
             "launches": prof["launches"], "ms_total": prof["ms"], "finest_level": fin,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s (of fallback)"}
+    if cpu and fin:
+        op = cpu["ops"]["gn_hessian_product"]
+        op["gpu_ns_per_pixel_frame"] = 1e6 * finest[0]["ms"] / finest[0]["pixel_frames"]
+        op["oracle_over_gpu"] = op["oracle_ns_per_pixel_frame"] / op["gpu_ns_per_pixel_frame"]
     per_kernel = {}
     for r in table:
         k = per_kernel.setdefault(r["kernel"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
