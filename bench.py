@@ -180,7 +180,7 @@ def make_sequence(workload: str, seed_offset: int = 0):
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_sample(R: np.ndarray, workload: str, frames: int):
+def oracle_sample(R: np.ndarray, workload: str, frames: int, mode: str = "stml"):
     """Register the first `frames` frames (full spatial size, same level
     structure) with the FP64 oracle; returns (frames/s, seconds)."""
     from oracle import Params, multilevel
@@ -188,7 +188,7 @@ def oracle_sample(R: np.ndarray, workload: str, frames: int):
     p = Params(n_levels=L, n_tlevels=Q)
     sub = R[:frames].astype(np.float64)
     t0 = time.perf_counter()
-    multilevel.register(sub, p, "stml")
+    multilevel.register(sub, p, mode)
     dt = time.perf_counter() - t0
     return frames / dt, dt
 
@@ -214,6 +214,13 @@ def oracle_hessvec_ns(workload: str, frames: int, reps: int = 3):
     return 1e9 * dt / (frames * float(np.prod(shape))), dt
 
 
+def workload_label(args) -> str:
+    """The workload as both arms name it in their config."""
+    n, shape, L, Q, _ = WORKLOADS[args.workload]
+    return (f"{args.workload}: {n} frames {shape[0]}x{shape[1]} fp32, "
+            f"{L} spatial x {Q} temporal levels, {args.mode.upper()}")
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if world > 1:
@@ -227,10 +234,10 @@ def run_reference(args):
     n = WORKLOADS[args.workload][0]
     frames = min(args.cpu_sample_frames, n)
     for _ in range(args.warmup):
-        oracle_sample(R, args.workload, frames)
+        oracle_sample(R, args.workload, frames, args.mode)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_sample(R, args.workload, frames)
+        _, dt = oracle_sample(R, args.workload, frames, args.mode)
         times.append(dt)
     total = sum(times)
     value = frames * len(times) / total
@@ -240,7 +247,9 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n_frames": n, "sample_frames": frames},
+            "config": {"workload": workload_label(args), "n_frames": n,
+                       "shape": list(WORKLOADS[args.workload][1]), "levels": WORKLOADS[args.workload][2],
+                       "tlevels": WORKLOADS[args.workload][3], "mode": args.mode, "sample_frames": frames},
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
@@ -747,7 +756,7 @@ def run_native(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         frames = min(args.cpu_sample_frames, n)
-        fps, dt = oracle_sample(R, args.workload, frames)
+        fps, dt = oracle_sample(R, args.workload, frames, args.mode)
         cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                "sample": f"first {frames} of {n} frames, full 256x256, same levels; numpy FP64 "
                          f"single thread; {dt:.1f} s"}
@@ -793,8 +802,7 @@ def run_native(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"{args.workload}: {n} frames {shape[0]}x{shape[1]} fp32, "
-                                       f"{L} spatial x {Q} temporal levels, {args.mode.upper()}",
+                "config": {"workload": workload_label(args),
                            "n_frames": n, "shape": list(shape), "levels": L, "tlevels": Q,
                            "mode": args.mode, "image_storage": args.image_dtype, "autotune": bool(args.autotune),
                            "l2": "flushed (256 MB write) before every timed step",
