@@ -6,7 +6,7 @@ pairs come from the registration itself: every sequence is registered (STML,
 classical predictors), and at every spatial level the registered fields
 y_{l,all} of all frames give inputs (y_l, y_r) and targets y_k for triples
 (l, k, r) at the gaps the temporal tree of Sec. 3 makes (r - l = 2, 4, 8 with
-k in the middle) and at uneven gaps (k one frame from l or r).
+k in the middle) and at uneven gaps (1-3 frames on either side of k).
 
 Everything here is host bookkeeping (which frames, which crop); the network's
 forward and backward passes and Adam run in the library's kernels.
