@@ -31,8 +31,11 @@ from .params import Params
 
 
 def pcg(apply_H: Callable[[np.ndarray], np.ndarray], b: np.ndarray, Minv: np.ndarray,
-        tol: float, maxit: int):
-    """Jacobi-preconditioned CG for H x = b from x = 0; returns (x, steps, flag)."""
+        tol: float, maxit: int, record: list | None = None):
+    """Jacobi-preconditioned CG for H x = b from x = 0; returns (x, steps, flag).
+
+    With ``record`` given, ||r|| / ||b|| after every step is appended to it
+    (the quantity the stopping test compares with ``tol``)."""
     x = np.zeros_like(b)
     bnorm = float(np.sqrt(np.sum(b * b)))
     if bnorm == 0.0:
@@ -55,6 +58,8 @@ def pcg(apply_H: Callable[[np.ndarray], np.ndarray], b: np.ndarray, Minv: np.nda
         x += alpha * p
         r -= alpha * q
         steps += 1
+        if record is not None:
+            record.append(float(np.sqrt(np.sum(r * r))) / bnorm)
         if float(np.sqrt(np.sum(r * r))) <= tol * bnorm:
             flag = "converged"
             break
@@ -64,6 +69,23 @@ def pcg(apply_H: Callable[[np.ndarray], np.ndarray], b: np.ndarray, Minv: np.nda
         rho = rho_new
         p = z + beta * p
     return x, steps, flag
+
+
+def armijo(phi: Callable[[float], float], J: float, gTd: float, c: float, max_ls: int):
+    """Back-tracking line search with the sufficient-decrease test of Armijo.
+
+    phi(t) is the objective at u + t d, J = phi(0) and gTd the directional
+    derivative <g, d> < 0.  Trial k takes t = 2^-k and accepts when
+    phi(t) <= J + c t gTd; at most max_ls trials.  Returns (t, trials, accepted);
+    on failure t is the last step tried.
+    """
+    t = 1.0
+    for k in range(max_ls):
+        if phi(t) <= J + c * t * gTd:
+            return t, k + 1, True
+        if k + 1 < max_ls:
+            t *= 0.5
+    return t, max_ls, False
 
 
 @dataclass
@@ -77,7 +99,9 @@ class GirStats:
     cg_iters: int = 0
     ls_trials: int = 0
     status: str = "ok"
-    history: list = field(default_factory=list)
+    history: list = field(default_factory=list)    # (J, ||g||) at every iterate
+    steps: list = field(default_factory=list)      # (CG steps, Armijo trials) of every GN step
+    cg_residuals: list = field(default_factory=list)   # ||r|| / ||g|| after each CG step, per solve
 
 
 def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float, p: Params):
@@ -103,22 +127,20 @@ def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float,
             break
         Minv = 1.0 / objective.jacobi_diag(ev["dT"], frames, h, p)
         dT = ev["dT"]
+        rec = []
         d, steps, _ = pcg(lambda v: objective.hessvec(dT, v, frames, h, p), -g, Minv,
-                          p.tol_cg, p.max_cg)
+                          p.tol_cg, p.max_cg, rec)
+        st.cg_residuals.append(rec)
         st.cg_iters += steps
         gTd = float(np.sum(g * d))
         if not gTd < 0.0:
             st.status = "no-descent"
             break
-        t = 1.0
-        accepted = False
-        for _ in range(p.max_ls):
-            st.ls_trials += 1
-            Jt = objective.evaluate(T, u + t * d, frames, h, p, want_grad=False)["J"]
-            if Jt <= J + p.armijo_c * t * gTd:
-                accepted = True
-                break
-            t *= 0.5
+        t, trials, accepted = armijo(
+            lambda s: objective.evaluate(T, u + s * d, frames, h, p, want_grad=False)["J"],
+            J, gTd, p.armijo_c, p.max_ls)
+        st.ls_trials += trials
+        st.steps.append((steps, trials))
         if not accepted:
             st.status = "line-search"
             break

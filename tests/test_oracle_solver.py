@@ -111,3 +111,93 @@ def test_corr_coeff_of_synthetic_sequence():
     rho = multilevel.corr_coeff(R.astype(np.float64))
     assert rho.shape == (15,)
     assert 0.9 < rho.min() <= rho.max() < 1.0       # Table 1 reports 0.915 - 0.996
+
+
+# ---------------------------------------------------------------- Armijo
+def _quadratic_line(a: float, g: float, scale: float):
+    """f(u) = a/2 u^2 at u0 = g / a (gradient g), direction d = -scale g / a:
+    phi(t) = f(u0 + t d), phi(0), phi'(0) = <g, d>."""
+    u0 = g / a
+    d = -scale * g / a
+    return (lambda t: 0.5 * a * (u0 + t * d) ** 2), 0.5 * a * u0 * u0, g * d
+
+
+@pytest.mark.parametrize("scale,c,t_expected", [
+    (1.0, 1e-4, 1.0),      # the Newton step is accepted at once
+    (4.0, 1e-4, 0.25),     # phi(t) - phi(0) = (g^2/a)(-4t + 8t^2): accepted iff t <= (1 - c)/2
+    (4.0, 0.6, 0.125),     # a stricter c: t <= (1 - c)/2 = 0.2
+    (3.0, 1e-4, 0.5),      # (g^2/a)(-3t + 4.5t^2): t <= 2(1 - c)/3
+])
+def test_armijo_accepts_the_largest_dyadic_step_of_the_closed_form(scale, c, t_expected):
+    """For a quadratic along d the sufficient-decrease test reads
+    t <= 2 (1 - c) |<g, d>| / (d^T H d); back-tracking from t = 1 by halving
+    accepts the largest power of two below that bound."""
+    phi, J, gTd = _quadratic_line(a=2.0, g=3.0, scale=scale)
+    bound = 2.0 * (1.0 - c) * abs(gTd) / (2.0 * (scale * 3.0 / 2.0) ** 2)
+    assert t_expected <= bound < 2 * t_expected
+    t, trials, ok = solver.armijo(phi, J, gTd, c, 10)
+    assert ok and t == t_expected
+    assert trials == 1 + int(round(-np.log2(t_expected)))
+
+
+def test_armijo_gives_up_after_max_ls_trials():
+    phi, J, gTd = _quadratic_line(a=1.0, g=1.0, scale=16.0)     # accepted only for t <= (1 - c)/8
+    t, trials, ok = solver.armijo(phi, J, gTd, 1e-4, 4)           # 1, 1/2, 1/4, 1/8 all fail
+    assert not ok and trials == 4
+    t, trials, ok = solver.armijo(phi, J, gTd, 1e-4, 5)
+    assert ok and t == 0.0625 and trials == 5
+
+
+# ---------------------------------------------------------------- PCG breakdown
+def test_pcg_breakdown_on_first_step_returns_preconditioned_gradient():
+    """An indefinite H with p0^T H p0 < 0 for p0 = M^-1 b: the solver returns
+    M^-1 b (the preconditioned gradient step) and reports the breakdown."""
+    H = np.diag([1.0, -1.0])
+    b = np.array([1.0, 2.0])
+    Minv = np.array([0.5, 2.0])           # p0 = (0.5, 4): p0^T H p0 = 0.25 - 16 < 0
+    x, steps, flag = solver.pcg(lambda v: H @ v, b, Minv, 1e-12, 10)
+    assert flag == "breakdown" and steps == 0
+    assert np.array_equal(x, Minv * b)
+
+
+def test_pcg_breakdown_after_one_step_keeps_the_first_iterate():
+    """H = diag(2, 1, -1), b = (1, .1, .1), M = I: the first step is the exact
+    line minimiser along b, x1 = (b.b / b.Hb) b; the second direction has
+    negative curvature, so x1 is returned."""
+    H = np.diag([2.0, 1.0, -1.0])
+    b = np.array([1.0, 0.1, 0.1])
+    x, steps, flag = solver.pcg(lambda v: H @ v, b, np.ones(3), 1e-12, 10)
+    assert flag == "breakdown" and steps == 1
+    x1 = (b @ b) / (b @ H @ b) * b
+    assert np.allclose(x, x1, rtol=0, atol=1e-15)
+    r1 = b - H @ x1                       # the next direction r1 + beta b has p^T H p < 0
+    p1 = r1 + (r1 @ r1) / (b @ b) * b
+    assert p1 @ H @ p1 < 0
+
+
+# ---------------------------------------------------------------- correlation (Table 1)
+def test_corr_coeff_hand_computed_and_affine_invariance():
+    """Two 2x2 frames (1, 2, 3, 4) and (1, 3, 2, 4): centred (-1.5, -.5, .5, 1.5)
+    and (-1.5, .5, -.5, 1.5), inner product 4, squared norms 5 and 5: rho = 0.8.
+    A frame that is an increasing affine map of its predecessor has rho = 1,
+    a decreasing one rho = -1; the values equal numpy's corrcoef."""
+    a = np.array([[1.0, 2.0], [3.0, 4.0]])
+    b = np.array([[1.0, 3.0], [2.0, 4.0]])
+    assert multilevel.corr_coeff(np.stack([a, b])) == pytest.approx([0.8], abs=1e-15)
+    rng = np.random.default_rng(5)
+    f = rng.uniform(size=(6, 7))
+    R = np.stack([f, 0.3 + 2.5 * f, 1.0 - 0.5 * (0.3 + 2.5 * f)])
+    rho = multilevel.corr_coeff(R)
+    assert rho == pytest.approx([1.0, -1.0], abs=1e-14)
+    S = rng.uniform(size=(5, 4, 3))
+    ref = [np.corrcoef(S[k].ravel(), S[k + 1].ravel())[0, 1] for k in range(4)]
+    assert multilevel.corr_coeff(S) == pytest.approx(ref, abs=1e-14)
+
+
+def test_gauss_newton_records_cg_steps_and_trials_per_iteration():
+    sp = synthetic.spec_custom(4, (16, 16), seed=7, amp=1.0)
+    R = synthetic.make_sequence(sp).astype(np.float64)
+    _, st = solver.gauss_newton(R, np.zeros((4, 2, 16, 16)), [0, 1, 2, 3], 1.0, Params(max_gn=3))
+    assert len(st.steps) == st.gn_iters
+    assert sum(s for s, _ in st.steps) == st.cg_iters
+    assert sum(t for _, t in st.steps) == st.ls_trials
