@@ -123,7 +123,11 @@ stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const
  * convolution kernels' mbarrier waits, on an mbarrier that nothing completes;
  * *expired = 1 when the wait gave up and the kernel returned (the designed
  * behaviour: the network calls then report STML_ETIMEOUT).  Takes up to a
- * second; synchronises `cuda_stream`. */
+ * second; synchronises `cuda_stream`.  A convolution whose wait expires
+ * gives its tensor-core work still in flight one more bounded wait before it
+ * releases its tensor memory; if that wait expires as well, the error text of
+ * STML_ETIMEOUT says so, results are undefined and the CUDA context should be
+ * discarded. */
 stml_status stml_check_bounded_wait(void* cuda_stream, int* expired);
 
 /* Attaches a network to a context as its temporal predictor (NULL detaches).

@@ -678,14 +678,10 @@ static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const TI* T, const
     lc.blockDim = dim3(kThreads, 1, 1);
     lc.stream = s;
     if constexpr (D == 2) {   // the copy ring of the staged 2-D pass
-        static std::atomic<bool> attr_set{false};   // per instantiation; setting it twice is harmless
         const size_t ring = ObjStage<D, VEC, TRIAL>::ring_bytes;
-        if (!attr_set.load()) {
-            const cudaError_t e = cudaFuncSetAttribute(obj_kernel<D, VEC, TRIAL, GDOT, TI>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
-            if (e != cudaSuccess) return e;
-            attr_set.store(true);
-        }
+        const cudaError_t e =
+            set_max_dynamic_smem(reinterpret_cast<const void*>(obj_kernel<D, VEC, TRIAL, GDOT, TI>), (int)ring);
+        if (e != cudaSuccess) return e;
         lc.dynamicSmemBytes = ring;
     }
     cudaLaunchAttribute at[1];

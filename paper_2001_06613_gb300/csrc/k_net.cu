@@ -19,6 +19,12 @@
 #include "net.h"
 
 namespace stml {
+// per-device caches of the SM count and of the dynamic shared-memory limit (k_transfer.cu)
+int device_sms();
+cudaError_t set_max_dynamic_smem(const void* kernel, int bytes);
+}  // namespace stml
+
+namespace stml {
 namespace net {
 
 namespace {
@@ -116,8 +122,9 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 // complete before the stage is refilled.  Tiles alternate between two TMEM
 // accumulators, and a tile's epilogue (tcgen05.ld; warp w owns lanes = tile
 // rows 4w..4w+3) runs while the next tile's first MMAs execute.  Every wait
-// is bounded; on expiry the kernel sets *err, skips the remaining work and
-// still frees its TMEM.
+// is bounded; on expiry the kernel skips the remaining work, gives the MMAs
+// still in flight one more bounded wait, sets *err (1, or 2 if that wait
+// expired too: results undefined, discard the context) and frees its TMEM.
 namespace {
 
 constexpr int kHaloW = 10, kHaloH = 18, kHaloPx = kHaloW * kHaloH;   // 8 x 16 tile + 1-pixel border
@@ -364,7 +371,15 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         if (ok) epilogue(prev_tile, (k - 1) & 1);
     }
     cp_wait<0>();
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok && tid == 0) {
+        // The wait that expired was for the MMAs of item q - 1, which may still
+        // be running (writing TMEM, reading this CTA's shared memory).  They get
+        // one more bounded wait before the TMEM is released; if that expires
+        // too, *err = 2: results are undefined and the context should be
+        // discarded.  Otherwise *err = 1 (the launch stopped early).
+        const bool drained = q < 1 || mbar_wait(bars + 8 * ((q - 1) & 1), (uint32_t)(((q - 1) >> 1) & 1));
+        atomicMax(err, drained ? 1 : 2);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -379,18 +394,14 @@ template <int BN>
 static cudaError_t conv3_go(const ConvIn& in, const bf16* Wh, int Cin, int N, int B, int H, int W,
                             const ConvOut& out, int* err, cudaStream_t s) {
     using C = TcCfg<BN>;
-    static bool attr = false;   // benign race: every caller sets the same value
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(conv3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(conv3_kernel<BN>), C::SMEM);
+    if (e != cudaSuccess) return e;
     const long long tiles = (long long)B * ((H + 15) / 16) * ((W + 7) / 8);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     // a few CTAs per SM, each running a sequence of tiles
     const long long per_sm = BN <= 32 ? 3 : BN <= 64 ? 2 : 1;
-    long long ctas = 152 * per_sm * 2 / (N / BN);
+    const int sms = device_sms();
+    long long ctas = (long long)(sms > 0 ? sms : 152) * per_sm * 2 / (N / BN);
     if (ctas < 1) ctas = 1;
     if (ctas > tiles) ctas = tiles;
     dim3 grid((unsigned)ctas, N / BN);

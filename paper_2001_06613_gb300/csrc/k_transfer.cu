@@ -7,8 +7,9 @@
 // * linear temporal predictor (Sec. 3) and the least-squares predictor of
 //   eq. (2) solved by Thomas' algorithm (one factorisation for all series).
 #include <atomic>
+#include <map>
 #include <mutex>
-#include <unordered_map>
+#include <utility>
 
 #include "kernels.h"
 
@@ -18,25 +19,60 @@ static std::atomic<long long> g_launches{0};
 long long launches_total() { return g_launches.load(); }
 void count_launches(int k) { g_launches.fetch_add(k); }
 
+namespace {
+std::mutex g_cache_mu;
+// keyed by (device ordinal, kernel): occupancy and attributes are per device
+std::map<std::pair<int, const void*>, unsigned> g_resident;
+std::map<std::pair<int, const void*>, int> g_smem_attr;
+std::map<int, int> g_sms;
+}  // namespace
+
+int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    const auto it = g_sms.find(dev);
+    if (it != g_sms.end()) return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
+    if (sms > 0) g_sms.emplace(dev, sms);
+    return sms;
+}
+
+cudaError_t set_max_dynamic_smem(const void* kernel, int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    const auto key = std::make_pair(dev, kernel);
+    const auto it = g_smem_attr.find(key);
+    if (it != g_smem_attr.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) g_smem_attr[key] = bytes;
+    return e;
+}
+
 unsigned resident_grid(const void* kernel, long long items, unsigned cap) {
-    static std::mutex mu;
-    static std::unordered_map<const void*, unsigned> per_gpu;
     unsigned n = 0;
+    const int sms = device_sms();
+    int dev = 0;
+    const bool have_dev = cudaGetDevice(&dev) == cudaSuccess;
     {
-        std::lock_guard<std::mutex> lock(mu);
-        auto it = per_gpu.find(kernel);
-        if (it != per_gpu.end()) {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        const auto key = std::make_pair(have_dev ? dev : -1, kernel);
+        auto it = g_resident.find(key);
+        if (it != g_resident.end()) {
             n = it->second;
         } else {
-            int dev = 0, sms = 0, per_sm = 0;
-            if (cudaGetDevice(&dev) == cudaSuccess &&
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            int per_sm = 0;
+            if (have_dev && sms > 0 &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) == cudaSuccess &&
-                sms > 0 && per_sm > 0)
+                per_sm > 0) {
                 n = (unsigned)(sms * per_sm);
-            else
+                g_resident.emplace(key, n);
+            } else {
                 n = cap;   // the query failed: the caller's cap (the launch reports any real error)
-            per_gpu.emplace(kernel, n);
+            }
         }
     }
     if (n > cap) n = cap;

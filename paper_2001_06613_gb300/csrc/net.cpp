@@ -329,8 +329,11 @@ cudaError_t backward_pass(stml_net* n, int B, int H, int W, cudaStream_t s) {
 stml_status check_err(stml_net* n) {
     NCK(n, cudaMemcpy(n->err_h, n->err_d, sizeof(int), cudaMemcpyDeviceToHost));
     if (*n->err_h) {
+        const bool drained = *n->err_h == 1;
         NCK(n, cudaMemset(n->err_d, 0, sizeof(int)));
-        return net_fail(n, STML_ETIMEOUT, "a convolution's bounded wait expired");
+        return net_fail(n, STML_ETIMEOUT, drained ? "a convolution's bounded wait expired"
+                                                  : "a convolution's bounded wait expired with tensor-core work "
+                                                    "still in flight: results undefined, discard the context");
     }
     return STML_OK;
 }

@@ -11,13 +11,20 @@
 // The array is a file-scope __device__ variable of kScratchBytes; every GPU
 // that loads this library holds it until the process exits.  Its name is a
 // host-side stand-in in host code, so the device address is fetched with
-// cudaGetSymbolAddress once per device (on the first call made with that
-// device current) and passed to the kernels.  That first call should come
-// before any stream capture.  All calls share the array and it keeps the last
-// call's contents: the reduction ticket is cleared on every call, and calls
-// that overlap on the GPU (other streams, other threads) race on it.
+// cudaGetSymbolAddress on the first call made with that device current, and
+// passed to the kernels.  The address is kept per CUDA context, so a context
+// that replaces the device's (after cudaDeviceReset, say) looks it up again on
+// its first call.  That first call should come before any stream capture.
+// The frame numbers and temporal weights reach the array through the
+// arguments of small set-up kernels, not through copies from host memory.
+// All calls share the array and it keeps the last call's contents: the
+// reduction ticket is cleared on every call, and calls that overlap on the
+// GPU (other streams, other threads) race on it.
+#include <cuda.h>   // driver API types; the two functions used come from cudaGetDriverEntryPointByVersion
+
+#include <map>
 #include <mutex>
-#include <vector>
+#include <utility>
 
 #include "../../include/stml.h"
 #include "kernels.h"
@@ -27,9 +34,51 @@ namespace {
 constexpr size_t kScratchBytes = 24u << 20;   // 24 MiB per device
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_dev[kMaxDevices] = {};
+std::map<std::pair<int, unsigned long long>, void*> g_scratch_dev;   // (device, context id) -> address
+
+// Identity of the calling thread's current CUDA context (0 when none is
+// current or the driver entry points are unavailable).
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {   // under g_mu
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        looked_up = true;
+    }
+    CUcontext c = nullptr;
+    if (!get_current || get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    if (get_id && get_id(c, &id) == CUDA_SUCCESS) return id + 1;
+    return (unsigned long long)(uintptr_t)c;
+}
+
+// Frame numbers and temporal weights of up to kSetupChunk frames, passed by
+// value as kernel arguments.
+constexpr int kSetupChunk = 256;
+struct SetupChunk {
+    int first, count;
+    int frames[kSetupChunk];
+    float w_next[kSetupChunk];
+};
+
+__global__ void noalloc_setup_kernel(SetupChunk c, int* frames, float* w_next) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
+        frames[c.first + i] = c.frames[i];
+        w_next[c.first + i] = c.w_next[i];
+    }
+}
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -73,31 +122,41 @@ extern "C" stml_status stml_hessvec_noalloc(const float* dT, const float* v, flo
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return err(STML_ECUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return err(STML_EINVAL, "device ordinal out of range");
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_dev[dev]) {
-            void* ptr = nullptr;
+        unsigned long long ctx = current_context_id();
+        auto it = ctx ? g_scratch_dev.find({dev, ctx}) : g_scratch_dev.end();
+        if (it != g_scratch_dev.end()) {
+            base = (unsigned char*)it->second;
+        } else {
+            void* ptr = nullptr;   // also makes the runtime's context current if it was not yet
             e = cudaGetSymbolAddress(&ptr, g_scratch);
             if (e != cudaSuccess || !ptr) return err(STML_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_scratch_dev[dev] = ptr;
+            if (!ctx) ctx = current_context_id();
+            if (ctx) g_scratch_dev[{dev, ctx}] = ptr;
+            base = (unsigned char*)ptr;
         }
-        base = (unsigned char*)g_scratch_dev[dev];
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    std::vector<float> w(nK, 0.f);
-    for (int j = 0; j + 1 < nK; ++j) {
-        const double dk = (double)(frames[j + 1] - frames[j]);
-        w[j] = (float)(1.0 / (dk * dk));
-    }
     unsigned int* ticket = (unsigned int*)base;
     double* out = (double*)(base + 8);
     e = cudaMemsetAsync(base, 0, 256, s);                       // ticket and result start at zero
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + off_frames, frames, (size_t)nK * sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + off_w, w.data(), (size_t)nK * sizeof(float), cudaMemcpyHostToDevice, s);
+    // frames and w_next = 1 / (k_{j+1} - k_j)^2 (0 for the last frame of K)
+    SetupChunk chunk;
+    for (int j0 = 0; e == cudaSuccess && j0 < nK; j0 += kSetupChunk) {
+        chunk.first = j0;
+        chunk.count = nK - j0 < kSetupChunk ? nK - j0 : kSetupChunk;
+        for (int i = 0; i < chunk.count; ++i) {
+            const int j = j0 + i;
+            chunk.frames[i] = frames[j];
+            const double dk = j + 1 < nK ? (double)(frames[j + 1] - frames[j]) : 0.0;
+            chunk.w_next[i] = j + 1 < nK ? (float)(1.0 / (dk * dk)) : 0.f;
+        }
+        noalloc_setup_kernel<<<1, 256, 0, s>>>(chunk, (int*)(base + off_frames), (float*)(base + off_w));
+        count_launches(1);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return err(STML_ECUDA, cudaGetErrorString(e));
 
     FrameSet fs{(const int*)(base + off_frames), (const float*)(base + off_w), nK};
