@@ -40,7 +40,17 @@ void count_launches(int k);
 // `cap`.  A grid larger than that runs in waves, and a CTA of the second wave
 // works on items far from those in flight, losing the L2 reuse of the
 // neighbouring frames and rows.
+// Cached per (device, kernel), so a process that uses several GPUs sizes each
+// grid for the device it launches on.
 unsigned resident_grid(const void* kernel, long long items, unsigned cap);
+
+// Streaming multiprocessors of the current device (cached per device; 0 if
+// the query fails).
+int device_sms();
+
+// Raises the dynamic shared-memory limit of `kernel` on the current device to
+// `bytes` (cudaFuncSetAttribute is per device; done once per device and kernel).
+cudaError_t set_max_dynamic_smem(const void* kernel, int bytes);
 
 // Geometry of a level from its shape (nz, ny, nx), dimension and cell width.
 Geom make_geom(const int shape3[3], int d, float h);
@@ -231,5 +241,75 @@ bool pcg_coop_preferred(const Geom& g, int nK);
 cudaError_t launch_pcg_coop(const Geom& g, const FrameSet& fs, const Coef& cf, const float* grad, const Stored& dT,
                             const PcgBufs& b, double* partials, size_t partials_cap, DevScalars* S, PcgArgs a,
                             cudaStream_t s, const int* gate = nullptr);
+
+// ---------------------------------------------------------- batched solver (k_batch.cu)
+// One sequence of a batched stage: its level geometry and frame set, the
+// solver buffers of its context (all nK d N floats unless noted) and the
+// counts of its work items.
+struct BatchSeq {
+    Geom g;
+    PixIndex pi;
+    FrameSet fs;
+    Coef cf;
+    FastDiv cpf;             // chunks of kThreads * VEC pixels per frame (Hessian-product items)
+    unsigned eval_tiles;     // tiles of 32 VEC pixels (objective and gradient)
+    unsigned pcg_tiles;      // tiles of TPR VEC pixels (PCG start and update)
+    unsigned chunks;         // nK * cpf
+    const void* T;           // images of the level, all frames (storage type of the batch)
+    float* u[2];             // the iterate and the next point (they swap at every accepted step)
+    float* grad;
+    void* dT;                // grad T in the image storage type
+    float *x, *r, *z, *q;
+    float* p[2];
+    float *ms_z, *sv_z;      // frame sums of z: mean of grad T . z (N), sum of z (d N)
+    float* ms_p[2];
+    float* sv_p[2];
+    float *abar, *ubar;      // per-pixel frame means (N, d N)
+};
+
+// Phases of a sequence's state machine.
+enum BatchPhase { BPH_EVAL0 = 0, BPH_INIT, BPH_APPLY, BPH_UPDATE, BPH_TRIAL, BPH_GRAD, BPH_DONE };
+
+// Device state of one sequence (written by the first CTA of its range only).
+struct BatchState {
+    int phase, cur;          // next phase; u[cur] is the iterate
+    int it, cg_total, ls_total;
+    int ls_k, dir_p0;        // Armijo trial index; the direction is p[0] (first CG step broke down)
+    int status;              // stml_status of the GIR
+    int cg_k, cg_iter, cg_flag, cg_active;
+    float cg_rho, cg_bnorm2, cg_rnorm2, cg_pq, cg_alpha, cg_beta;
+    float t;                 // step of the current / accepted trial
+    int pad;
+    double J0, J, Jold, D, S, P, gnorm2, unorm2, step;
+    double gTd, dnorm2;
+    double Jt, Dt, St, Pt;   // totals of the last trial
+};
+
+// Solver parameters of the batch (stml_params of its contexts).
+struct BatchCtl {
+    float tol_cg;
+    int max_cg, max_gn, max_ls;
+    double armijo_c, tol_J, tol_Y, tol_G, g_abs;
+};
+
+// Barrier words and the error flag (bit 0: a bounded wait expired); zero at launch.
+struct BatchSync {
+    unsigned count, gen, err, steps;
+};
+
+// Launch shapes of the batched kernel: CTAs per SM and lanes per pixel row
+// of the PCG tiles (4 or 16; the evaluation tiles are one warp wide).
+struct BatchShape {
+    int ctas_per_sm;
+    int tpr;
+};
+// VEC: 4 when every sequence has nx % 4 == 0 and 16-byte aligned buffers, else 1.
+// d: 2 or 3; img_type: StoreType of images and grad T.  part: gridDim * 8
+// float2 slots (batch_partials); the launch is cooperative (all CTAs resident).
+size_t batch_partials(int ctas);
+int batch_grid(int d, int vec, int img_type, const BatchShape& sh);
+cudaError_t launch_batch_gir(const BatchSeq* seqs_dev, int nseq, BatchState* states, const BatchCtl& ctl, int d,
+                             int vec, int img_type, const BatchShape& sh, float2* part, BatchSync* sync,
+                             int max_steps, cudaStream_t s);
 
 }  // namespace stml
