@@ -107,6 +107,15 @@ typedef struct {
                               * grid -- a reading of the SqN distance named in Sec. 2
                               * (1/2 (|K|^2 - sum of sigma^4 of the matrix of
                               * normalised frames)); S and P unchanged */
+    double target_J;         /* > 0: the last GIR over all frames on the finest
+                              * level (and stml_gir) stops where its objective
+                              * first reaches target_J: the step that crosses it
+                              * is shortened (regula falsi on its length) until
+                              * |J - target_J| <= target_tol * target_J; a GIR
+                              * that starts at or below target_J takes no step.
+                              * Lets registrations that follow different paths
+                              * end at the same objective.  0: off (default) */
+    double target_tol;       /* relative tolerance of that landing (default 1e-5) */
 } stml_params;
 
 typedef struct {
@@ -313,9 +322,13 @@ stml_status stml_predict_ls(const float* eta, const int* K, int nK, const float*
  * receives <v, Hv>.  All scratch comes from one static 24 MiB device array per
  * GPU that loads the library (held until the process exits); a problem that
  * needs more returns STML_EINVAL.  The first call on a device looks up that
- * array's device address (make it before any stream capture).  Calls share
- * the array, so calls that overlap on the GPU race; run them on one stream.
- * Errors are reported through stml_last_error(NULL). */
+ * array's device address (make that first call before any stream capture);
+ * the address is kept per CUDA context, so after cudaDeviceReset the next
+ * call looks it up again.  Frame numbers and weights reach the array as
+ * kernel arguments (no host-to-device copy); with vHv != NULL the call copies
+ * <v, Hv> to the host and synchronises `cuda_stream`.  Calls share the array,
+ * so calls that overlap on the GPU race; run them on one stream.  Errors are
+ * reported through stml_last_error(NULL). */
 stml_status stml_hessvec_noalloc(const float* dT, const float* v, float* Hv, int dim,
                                  const int* shape, double h, const int* frames, int nK,
                                  const stml_params* p, double* vHv, void* cuda_stream);

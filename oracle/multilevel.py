@@ -84,15 +84,17 @@ def register(R: np.ndarray, p: Params, mode: str = "stml") -> Result:
         h = grid.level_h(L, ell)
         m = T.shape[1:]
         z_all = np.zeros((n, d) + m) if ell == 0 else grid.prolong_fields(y_prev)
+        target = p.target_J if ell == L - 1 else 0.0     # the last GIR over all frames
         if mode == "spml":
-            y_all, st = solver.gauss_newton(T, z_all, allK, h, p)
+            y_all, st = solver.gauss_newton(T, z_all, allK, h, p, target)
             res.stats.append(LevelStats(ell, p.n_tlevels - 1, n, st.gn_iters, st.cg_iters,
                                         st.ls_trials, st.J, st.D, st.S, st.P))
         elif mode == "stml":
             y_all = None
             dhat_prev = None
             for q, K in enumerate(sets):
-                yK, st = solver.gauss_newton(T[K], z_all[K], K, h, p)
+                yK, st = solver.gauss_newton(T[K], z_all[K], K, h, p,
+                                             target if q == len(sets) - 1 else 0.0)
                 dhat = st.D / len(K)
                 stop = (q > 0 and p.stop_rule and
                         abs(dhat - dhat_prev) <= p.eps_stop * abs(dhat_prev))

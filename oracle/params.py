@@ -21,12 +21,16 @@ class Params:
     tol_J: float = 1e-3
     tol_Y: float = 1e-2
     tol_G: float = 5e-2
-    max_gn: int = 10
+    max_gn: int = 40           # a safeguard: the GIRs end on the stopping tests below it
     tol_cg: float = 1e-1
     max_cg: int = 20
     max_ls: int = 10
     armijo_c: float = 1e-4
     g_abs: float = 1e-12       # ||g|| below g_abs (1 + |J0|) counts as stationary
+    # target objective of the last GIR over all frames on the finest level
+    # (0: none): it stops where J first reaches target_J, within target_tol
+    target_J: float = 0.0
+    target_tol: float = 1e-5
     # distance of the affine variant: "ssd" (eq. 1 as in the non-parametric
     # path) or "nc" (normalised-correlation reading of the SqN distance, Sec. 2)
     distance: str = "ssd"

@@ -18,6 +18,13 @@ Stopping after iteration i >= 1 when all of
 |J_old - J| <= tol_J (1 + |J0|), ||t d|| <= tol_Y (1 + ||u||),
 ||g|| <= tol_G (1 + |J0|) hold, or at once when ||g|| <= g_abs (1 + |J0|),
 or when max_gn iterations were taken.
+
+Target objective (a measurement device, not part of the paper's method: it
+makes registrations that follow different paths end at the same objective):
+with a target J* > 0 the loop stops as soon as an accepted step reaches
+J <= J*, after shortening that step so that J(u + t d) = J* within
+target_tol J* (Illinois regula falsi on t between 0 and the accepted step);
+a start with J0 <= J* takes no step.
 """
 from __future__ import annotations
 
@@ -88,6 +95,41 @@ def armijo(phi: Callable[[float], float], J: float, gTd: float, c: float, max_ls
     return t, max_ls, False
 
 
+def land(phi: Callable[[float], float], J_start: float, t_acc: float, J_acc: float, target: float,
+         tol: float, max_it: int = 40):
+    """Step length t in (0, t_acc] with |phi(t) - target| <= tol * target.
+
+    phi(0) = J_start > target >= J_acc = phi(t_acc).  Regula falsi with the
+    Illinois modification (the retained end's function value is halved when
+    the same end is kept twice in a row).  Returns (t, phi(t), evaluations);
+    after max_it evaluations the point of smallest |phi - target| seen."""
+    a, fa = 0.0, J_start - target
+    b, fb = t_acc, J_acc - target
+    best = (abs(fb), b, J_acc)
+    if abs(fb) <= tol * target:
+        return b, J_acc, 0
+    side = 0
+    for i in range(max_it):
+        t = (a * fb - b * fa) / (fb - fa)
+        Jt = phi(t)
+        ft = Jt - target
+        if abs(ft) < best[0]:
+            best = (abs(ft), t, Jt)
+        if abs(ft) <= tol * target:
+            return t, Jt, i + 1
+        if ft > 0.0:
+            a, fa = t, ft
+            if side == 1:
+                fb *= 0.5
+            side = 1
+        else:
+            b, fb = t, ft
+            if side == -1:
+                fa *= 0.5
+            side = -1
+    return best[1], best[2], max_it
+
+
 @dataclass
 class GirStats:
     J: float = 0.0
@@ -99,13 +141,16 @@ class GirStats:
     cg_iters: int = 0
     ls_trials: int = 0
     status: str = "ok"
+    landing_evals: int = 0                          # objective evaluations of the target landing
     history: list = field(default_factory=list)    # (J, ||g||) at every iterate
     steps: list = field(default_factory=list)      # (CG steps, Armijo trials) of every GN step
     cg_residuals: list = field(default_factory=list)   # ||r|| / ||g|| after each CG step, per solve
 
 
-def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float, p: Params):
-    """GIR(K): minimise eq. (1) over the fields of the frames in K, from u0."""
+def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float, p: Params,
+                 target: float = 0.0):
+    """GIR(K): minimise eq. (1) over the fields of the frames in K, from u0
+    (with target > 0: until J reaches the target objective, see above)."""
     u = np.array(u0, dtype=np.float64, copy=True)
     ev = objective.evaluate(T, u, frames, h, p)
     J0 = ev["J"]
@@ -114,6 +159,10 @@ def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float,
     J_old = None
     step_norm = None
     it = 0
+    if target > 0.0 and J0 <= target:
+        st.status = "target"
+        st.J, st.D, st.S, st.P = ev["J"], ev["D"], ev["S"], ev["P"]
+        return u, st
     while True:
         gnorm = float(np.sqrt(np.sum(g * g)))
         st.history.append((J, gnorm))
@@ -144,6 +193,17 @@ def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float,
         if not accepted:
             st.status = "line-search"
             break
+        if target > 0.0:
+            Jt = objective.evaluate(T, u + t * d, frames, h, p, want_grad=False)["J"]
+            if Jt <= target:
+                t, _, st.landing_evals = land(
+                    lambda s: objective.evaluate(T, u + s * d, frames, h, p, want_grad=False)["J"],
+                    J, t, Jt, target, p.target_tol)
+                u = u + t * d
+                ev = objective.evaluate(T, u, frames, h, p)
+                it += 1
+                st.status = "target"
+                break
         u = u + t * d
         step_norm = t * float(np.sqrt(np.sum(d * d)))
         J_old = J

@@ -36,7 +36,8 @@ class Params(C.Structure):
                 ("g_abs", C.c_double), ("max_gn", C.c_int), ("tol_cg", C.c_double),
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double),
                 ("image_dtype", C.c_int), ("pcg_cooperative", C.c_int), ("autotune", C.c_int),
-                ("transform", C.c_int), ("lbfgs_m", C.c_int), ("max_lbfgs", C.c_int), ("distance", C.c_int)]
+                ("transform", C.c_int), ("lbfgs_m", C.c_int), ("max_lbfgs", C.c_int), ("distance", C.c_int),
+                ("target_J", C.c_double), ("target_tol", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

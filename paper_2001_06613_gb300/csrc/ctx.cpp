@@ -192,6 +192,10 @@ bool valid_params(const stml_params* p, std::string& why) {
         why = "lbfgs_m must be in 1..64 and max_lbfgs >= 0";
         return false;
     }
+    if (!(p->target_J >= 0) || !(p->target_tol > 0 && p->target_tol < 1)) {
+        why = "target_J must be >= 0 and 0 < target_tol < 1";
+        return false;
+    }
     if (p->image_dtype < STML_DTYPE_F32 || p->image_dtype > STML_DTYPE_BF16) {
         why = "image_dtype must be STML_DTYPE_F32, _F16 or _BF16";
         return false;
@@ -406,7 +410,12 @@ const ObjShapeChoice* obj_choice(stml_ctx* c, int level, const Geom& g, const Fr
 
 // ------------------------------------------------------------------ GIR
 // Gauss-Newton on the frames K of `level`, from and into u (nK * d * N floats).
-stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_io, stml_stats* st) {
+// With target > 0 the GIR stops as soon as an accepted step reaches
+// J <= target, after shortening that step (Illinois regula falsi on its
+// length) so that J lands within params.target_tol * target of the target; a
+// start with J0 <= target takes no step.
+stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_io, stml_stats* st,
+                    double target = 0.0) {
     Range rg("GIR level %d |K| %d", level, (int)K.size());
     const auto t_start = std::chrono::steady_clock::now();
     LevelBuf& L = c->lv[level];
@@ -573,8 +582,9 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         return STML_OK;
     };
 
+    const bool targeted = target > 0.0;
     bool started = false;     // a PCG solve (with its first chunk) is already queued and read
-    if (!should_stop()) {
+    if (!(targeted && J0 <= target) && !should_stop()) {
         if (p.autotune && p.pcg_cooperative && (long long)g.N * nK <= (1LL << 23)) TRY(tune_coop());
         TRY(start_cg());
         TRY(read_scalars(c));
@@ -621,7 +631,8 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         };
         // gradient pass at the accepted point (writes u + t d to ut, g, grad T)
         // and the speculative start of the next solve
-        const bool next_solve = it + 1 < p.max_gn;
+        // (with a target the direction must survive the step: no speculative start)
+        const bool next_solve = it + 1 < p.max_gn && !targeted;
         auto drop_accept = [&]() {   // a queued gated step and start that did not run
             prof_discount(c, PC_EVAL, level, 1, pfK * B_grad, pfK);
             if (next_solve && !coop) discount_cg(launched, 0, 0, 0, false);
@@ -667,12 +678,80 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
         Sv = c->Sh->trial[2];
         Pv = c->Sh->trial[3];
         ++it;
+        gnorm2 = c->Sh->red[4];
+        unorm2 = c->Sh->red[5];
+        if (targeted && J <= target) {
+            // land on the target between the previous iterate (now in ut) and
+            // the accepted point: J(ut + s x) for s in (0, t]
+            auto phi = [&](double sv, double* out4) -> stml_status {
+                const ObjShapeChoice* sh = obj_choice(c, level, g, fs, cf, Stored{L.img, c->img_type}, ut, c->w_x,
+                                                      (float)sv, nullptr, 1);
+                pe = prof_begin(c, PC_TRIAL, level);
+                CK(c, launch_objective(Stored{L.img, c->img_type}, g, fs, cf, ut, c->w_x, (float)sv, nullptr,
+                                       c->w_abar, c->w_ubar, c->partials, c->partials_cap, &S->ticket[0], S->trial,
+                                       c->stream, nullptr, sh));
+                prof_end(c, pe, pfK * B_trial, pfK);
+                TRY(read_scalars(c));
+                for (int i = 0; i < 4; ++i) out4[i] = c->Sh->trial[i];
+                return STML_OK;
+            };
+            const double tol = p.target_tol * target;
+            double a = 0.0, fa = J_old - target, b = c->Sh->ls_t, fb = J - target;
+            double best_t = b, best_f = std::fabs(fb), cur[4] = {J, D, Sv, Pv}, best4[4] = {J, D, Sv, Pv};
+            int side = 0;
+            for (int i = 0; i < 40 && best_f > tol; ++i) {
+                const double tv = (a * fb - b * fa) / (fb - fa);
+                TRY(phi(tv, cur));
+                const double ft = cur[0] - target;
+                if (std::fabs(ft) < best_f) {
+                    best_f = std::fabs(ft);
+                    best_t = tv;
+                    for (int k = 0; k < 4; ++k) best4[k] = cur[k];
+                }
+                if (ft > 0.0) {
+                    a = tv;
+                    fa = ft;
+                    if (side == 1) fb *= 0.5;
+                    side = 1;
+                } else {
+                    b = tv;
+                    fb = ft;
+                    if (side == -1) fa *= 0.5;
+                    side = -1;
+                }
+            }
+            if (best_t != c->Sh->ls_t) {
+                // the landed point: objective (abar, ubar) then gradient pass writing u = ut + s x
+                double chk[4];
+                if ((double)(float)best_t != (double)(float)c->Sh->ls_t) {
+                    TRY(phi(best_t, chk));
+                    pe = prof_begin(c, PC_EVAL, level);
+                    CK(c, launch_gradient(Stored{L.img, c->img_type}, g, fs, cf, ut, c->w_x, (float)best_t, c->w_abar,
+                                          c->w_ubar, c->w_g, c->w_dT, c->img_type, u, c->partials, c->partials_cap,
+                                          &S->ticket[4], S->red, c->stream));
+                    prof_end(c, pe, pfK * B_grad, pfK);
+                    TRY(read_scalars(c));
+                    for (int k = 0; k < 4; ++k) best4[k] = chk[k];
+                    gnorm2 = c->Sh->red[4];
+                    unorm2 = c->Sh->red[5];
+                }
+            }
+            J = best4[0];
+            D = best4[1];
+            Sv = best4[2];
+            Pv = best4[3];
+            break;
+        }
         // the next solve was queued before |g| of the new iterate was known; it
         // is dropped if the stopping tests fire
         started = next_solve;
-        gnorm2 = c->Sh->red[4];
-        unorm2 = c->Sh->red[5];
-        if (should_stop()) started = false;
+        if (should_stop()) {
+            started = false;
+        } else if (targeted) {
+            TRY(start_cg());
+            TRY(read_scalars(c));
+            started = true;
+        }
     }
     if (u != u_io) {
         CK(c, cudaMemcpyAsync(u_io, u, M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
@@ -1394,7 +1473,8 @@ stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finis
     CK(c, launch_gather_planes(c->w_z, c->w_u, c->d_idx, (int)K.size(), plane, c->stream));
     prof_end(c, pe, 8.0 * plane * K.size(), (double)K.size() * L.g.N);
     stml_stats s{};
-    TRY(run_gir(c, level, K, c->w_u, &s));
+    const bool last_gir = level == (int)c->lv.size() - 1 && q == Q - 1;   // the GIR over all frames
+    TRY(run_gir(c, level, K, c->w_u, &s, last_gir ? c->p.target_J : 0.0));
     s.tlevel = q;
     s.pred_learned = c->pred_learned;
     s.J0_classic = s.pred_learned >= 0 ? c->J0_classic : s.J0;
@@ -1454,7 +1534,7 @@ void stml_default_params(stml_params* p) {
     p->tol_Y = 1e-2;
     p->tol_G = 5e-2;
     p->g_abs = 1e-12;
-    p->max_gn = 10;
+    p->max_gn = 40;
     p->tol_cg = 1e-1;
     p->max_cg = 20;
     p->max_ls = 10;
@@ -1466,6 +1546,8 @@ void stml_default_params(stml_params* p) {
     p->lbfgs_m = 5;
     p->max_lbfgs = 50;
     p->distance = 0;
+    p->target_J = 0.0;
+    p->target_tol = 1e-5;
 }
 
 stml_status stml_create(const stml_params* p, void* cuda_stream, stml_ctx** out) {
@@ -1734,7 +1816,7 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
             const size_t total = (size_t)c->n * c->d * B.g.N;
             CK(c, cudaMemcpyAsync(B.y, c->w_z, total * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
             stml_stats s{};
-            TRY(run_gir(c, l, all, B.y, &s));
+            TRY(run_gir(c, l, all, B.y, &s, l == L - 1 ? c->p.target_J : 0.0));
             s.tlevel = (int)c->sets.size() - 1;
             record(s);
             c->level_done = true;
@@ -1886,7 +1968,7 @@ stml_status stml_gir(stml_ctx* c, int level, const int* frames, int nK, float* u
     TRY(check_aligned(c, {u}));
     cudaSetDevice(c->device);
     std::vector<int> K(frames, frames + nK);
-    return run_gir(c, level, K, u, stats);
+    return run_gir(c, level, K, u, stats, c->p.target_J);
 }
 
 stml_status stml_eval_affine(stml_ctx* c, int level, const int* frames, int nK, const double* theta, double* out,

@@ -30,7 +30,7 @@ def _oparams(prm, **kw):
                 eps_stop=prm.eps_stop, stop_rule=bool(prm.stop_rule), n_levels=prm.n_levels,
                 n_tlevels=prm.n_tlevels, tol_J=prm.tol_J, tol_Y=prm.tol_Y, tol_G=prm.tol_G,
                 max_gn=prm.max_gn, tol_cg=prm.tol_cg, max_cg=prm.max_cg, max_ls=prm.max_ls,
-                armijo_c=prm.armijo_c, g_abs=prm.g_abs)
+                armijo_c=prm.armijo_c, g_abs=prm.g_abs, target_J=prm.target_J, target_tol=prm.target_tol)
     base.update(kw)
     return Params(**base)
 
@@ -53,13 +53,15 @@ def test_gir_matches_oracle_gauss_newton(S, max_gn):
         ud = _dev(u0)
         st = S.stml_gir(ctx.ptr, 0, frames, ud)
         uo, so = solver.gauss_newton(R.astype(np.float64), u0, frames, 1.0, _oparams(ctx.params))
+        # the oracle's CG residual ratios stay >= 1 % away from tol_cg here,
+        # so every stopping decision must be the same
         assert st["gn_iters"] == so.gn_iters
         assert st["ls_trials"] == so.ls_trials
-        assert abs(st["cg_iters"] - so.cg_iters) <= max_gn
+        assert st["cg_iters"] == so.cg_iters
         assert_scalar(st["J0"], so.J0, 1e-5, "J0")
-        assert_scalar(st["J"], so.J, 1e-4 * max_gn, "J after GN")
+        assert_scalar(st["J"], so.J, 1e-5 * max_gn, "J after GN")
         diff = ud.cpu().numpy() - uo
-        assert np.sqrt(np.mean(diff ** 2)) <= 1e-3 * max(1.0, np.sqrt(np.mean(uo ** 2)))
+        assert np.sqrt(np.mean(diff ** 2)) <= 1e-4 * max(1.0, np.sqrt(np.mean(uo ** 2)))
     finally:
         ctx.close()
 
@@ -102,22 +104,58 @@ def _centred_rms(y, truth):
     return float(np.sqrt((e ** 2).sum(axis=1).mean()))
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_register_tiny_matches_oracle(S, tiny, mode):
-    """16 frames of 64x64, 2 spatial x 2 temporal levels (STML) or spatial only (SpML)."""
+# End-to-end contract (per-call quantities are compared at 1e-5 elsewhere):
+# final objective within 1e-4 relative, fields within 1e-3 px RMS.  Measured
+# on GB300: 2-D registrations agree to 1e-8 in J and 1e-7 px, 3-D ones to 2e-6
+# and 4e-5 px, with identical Gauss-Newton, CG and Armijo counts.
+E2E_J, E2E_RMS = 1e-4, 1e-3
+
+
+def _counts(stats, res):
+    return ([(s["level"], s["tlevel"], s["n_frames"], s["gn_iters"], s["cg_iters"], s["ls_trials"]) for s in stats],
+            [(s.level, s.tlevel, s.n_frames, s.gn_iters, s.cg_iters, s.ls_trials) for s in res.stats])
+
+
+@pytest.mark.parametrize("mode,coop", [(0, 1), (1, 1), (0, 0), (1, 0)])
+def test_register_tiny_matches_oracle(S, tiny, mode, coop):
+    """16 frames of 64x64, 2 spatial x 2 temporal levels (STML) or spatial
+    only (SpML), with the cooperative or the streaming PCG solve."""
     spec, R = tiny
-    stats, y, prm = _register(S, R, mode, n_levels=2, n_tlevels=2)
+    stats, y, prm = _register(S, R, mode, n_levels=2, n_tlevels=2, pcg_cooperative=coop)
     op = _oparams(prm)
     res = multilevel.register(R.astype(np.float64), op, "stml" if mode == 0 else "spml")
-    assert [(s["level"], s["tlevel"], s["n_frames"]) for s in stats] == \
-        [(s.level, s.tlevel, s.n_frames) for s in res.stats]
+    got, want = _counts(stats, res)
+    assert got == want
     Jg = multilevel.final_objective(R.astype(np.float64), y.astype(np.float64), op)["J"]
     Jo = multilevel.final_objective(R.astype(np.float64), res.y, op)["J"]
-    assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
+    assert abs(Jg - Jo) <= E2E_J * Jo, (Jg, Jo)
     rms = float(np.sqrt(np.mean((y - res.y) ** 2)))
-    assert rms <= 0.05, rms
+    assert rms <= E2E_RMS, rms
     truth = synthetic.planted_registration(spec)
     assert _centred_rms(y.astype(np.float64), truth) < 0.2
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_target_objective_lands_like_the_oracle(S, tiny, mode):
+    """params.target_J: the last GIR over all frames stops where J reaches the
+    target (its crossing step shortened by regula falsi); the GPU run and the
+    oracle take the same steps and both end within target_tol of the target."""
+    spec, R = tiny
+    free, _, _ = _register(S, R, mode, n_levels=2, n_tlevels=2)
+    last = free[-1]
+    assert last["gn_iters"] >= 3
+    target = 0.5 * (last["J0"] + last["J"])          # crossed inside the last GIR
+    stats, y, prm = _register(S, R, mode, n_levels=2, n_tlevels=2, target_J=target)
+    op = _oparams(prm)
+    res = multilevel.register(R.astype(np.float64), op, "stml" if mode == 0 else "spml")
+    got, want = _counts(stats, res)
+    assert got == want
+    assert stats[-1]["gn_iters"] < last["gn_iters"]
+    Jg = multilevel.final_objective(R.astype(np.float64), y.astype(np.float64), op)["J"]
+    Jo = multilevel.final_objective(R.astype(np.float64), res.y, op)["J"]
+    assert abs(Jo - target) <= prm.target_tol * target
+    assert abs(Jg - target) <= 2 * prm.target_tol * target, (Jg, target)
+    assert float(np.sqrt(np.mean((y - res.y) ** 2))) <= E2E_RMS
 
 
 def test_stepwise_api_equals_register(S, tiny):
@@ -146,7 +184,7 @@ def test_stopping_rule_fills_from_predictor(S):
     op = _oparams(prm)
     res = multilevel.register(R.astype(np.float64), op, "stml")
     assert np.all(np.isfinite(y))
-    assert float(np.sqrt(np.mean((y - res.y) ** 2))) <= 0.05
+    assert float(np.sqrt(np.mean((y - res.y) ** 2))) <= E2E_RMS
 
 
 def test_single_frame_and_3d_sequence(S):
@@ -160,7 +198,8 @@ def test_single_frame_and_3d_sequence(S):
     res = multilevel.register(R3.astype(np.float64), op, "stml")
     Jg = multilevel.final_objective(R3.astype(np.float64), y3.astype(np.float64), op)["J"]
     Jo = multilevel.final_objective(R3.astype(np.float64), res.y, op)["J"]
-    assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
+    assert abs(Jg - Jo) <= E2E_J * Jo, (Jg, Jo)
+    assert float(np.sqrt(np.mean((y3 - res.y) ** 2))) <= E2E_RMS
 
 
 def test_3d_streaming_pcg_matches_oracle(S):
@@ -173,10 +212,12 @@ def test_3d_streaming_pcg_matches_oracle(S):
     assert sum(s["cg_iters"] for s in stats) > 0
     op = _oparams(prm)
     res = multilevel.register(R3.astype(np.float64), op, "stml")
+    got, want = _counts(stats, res)
+    assert got == want
     Jg = multilevel.final_objective(R3.astype(np.float64), y3.astype(np.float64), op)["J"]
     Jo = multilevel.final_objective(R3.astype(np.float64), res.y, op)["J"]
-    assert abs(Jg - Jo) <= 1e-2 * Jo, (Jg, Jo)
-    assert float(np.sqrt(np.mean((y3 - res.y) ** 2))) <= 0.05
+    assert abs(Jg - Jo) <= E2E_J * Jo, (Jg, Jo)
+    assert float(np.sqrt(np.mean((y3 - res.y) ** 2))) <= E2E_RMS
 
 
 def test_autotune_is_reproducible_and_close(S, tiny):
@@ -203,7 +244,7 @@ def test_autotune_is_reproducible_and_close(S, tiny):
         op = _oparams(prm)
         J_ref = multilevel.final_objective(R.astype(np.float64), y_ref.astype(np.float64), op)["J"]
         J_tun = multilevel.final_objective(R.astype(np.float64), ys[0].astype(np.float64), op)["J"]
-        assert abs(J_tun - J_ref) <= 1e-2 * J_ref, (J_tun, J_ref)
-        assert float(np.sqrt(np.mean((ys[0] - y_ref) ** 2))) <= 0.05
+        assert abs(J_tun - J_ref) <= E2E_J * J_ref, (J_tun, J_ref)
+        assert float(np.sqrt(np.mean((ys[0] - y_ref) ** 2))) <= E2E_RMS
     finally:
         ctx.close()

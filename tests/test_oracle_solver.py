@@ -201,3 +201,37 @@ def test_gauss_newton_records_cg_steps_and_trials_per_iteration():
     assert len(st.steps) == st.gn_iters
     assert sum(s for s, _ in st.steps) == st.cg_iters
     assert sum(t for _, t in st.steps) == st.ls_trials
+
+
+# ---------------------------------------------------------------- target objective
+def test_land_finds_the_crossing_of_a_quadratic():
+    """phi(t) = 3 - 2t + t^2 crosses J* = 2.25 at t = 1/2 on [0, 1] (the other
+    root, 3/2, lies outside the bracket)."""
+    phi = lambda t: 3.0 - 2.0 * t + t * t
+    t, J, evals = solver.land(phi, 3.0, 1.0, phi(1.0), 2.25, 1e-10)
+    assert abs(J - 2.25) <= 1e-10 * 2.25
+    assert abs(t - 0.5) <= 1e-9
+    assert 1 <= evals <= 40
+    # an accepted step already within the tolerance needs no evaluation
+    t, J, evals = solver.land(phi, 3.0, 0.5, 2.25 * (1 + 1e-7), 2.25, 1e-6)
+    assert (t, evals) == (0.5, 0)
+
+
+def test_gauss_newton_stops_at_the_target_objective():
+    sp = synthetic.spec_custom(4, (16, 16), seed=7, amp=1.0)
+    R = synthetic.make_sequence(sp).astype(np.float64)
+    K = [0, 1, 2, 3]
+    u0 = np.zeros((4, 2, 16, 16))
+    _, free = solver.gauss_newton(R, u0, K, 1.0, Params())
+    Js = [J for J, _ in free.history]
+    assert len(Js) >= 3
+    target = 0.5 * (Js[1] + Js[2])            # crossed during the second step
+    u, st = solver.gauss_newton(R, u0, K, 1.0, Params(target_tol=1e-7), target)
+    assert st.status == "target" and st.gn_iters == 2
+    assert abs(st.J - target) <= 1e-7 * target
+    assert st.history[-1][0] > target          # the iterate before the shortened step
+    J_check = objective.evaluate(R, u, K, 1.0, Params(), want_grad=False)["J"]
+    assert J_check == pytest.approx(st.J, rel=1e-14)
+    # a start at or below the target takes no step
+    _, st0 = solver.gauss_newton(R, u0, K, 1.0, Params(), Js[0] * 1.01)
+    assert st0.gn_iters == 0 and st0.status == "target"
