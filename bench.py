@@ -152,21 +152,17 @@ def measured_peaks():
 
 
 def matvec_traffic_per_pixel_frame():
-    """DRAM bytes per pixel-frame of the Hessian-product kernel from the
-    committed ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "gn_matvec_paper_scale.md")
+    """DRAM bytes per pixel-frame of the Hessian-product kernel from the ncu
+    capture recorded in profiles/gn_matvec_paper_scale.json, if that capture
+    was taken on the current kernel source (same hash of csrc/k_gn.cu)."""
+    path = os.path.join(ROOT, "profiles", "gn_matvec_paper_scale.json")
     src = os.path.join(ROOT, "paper_2001_06613_gb300", "csrc", "k_gn.cu")
     try:
-        txt = open(path).read()
+        rec = json.load(open(path))
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        vals = {}
-        for ln in txt.splitlines():
-            if ":" in ln and ln.strip().startswith("- "):
-                k, v = ln.strip()[2:].rsplit(":", 1)
-                vals[k.strip()] = v.strip()
-        if vals.get("k_gn.cu sha256[:16]") != digest:
+        if rec.get("k_gn_cu_sha256_16") != digest:
             return None
-        return float(vals["dram bytes per pixel-frame"])
+        return float(rec["dram_bytes_per_pixel_frame"])
     except Exception:
         return None
 
@@ -180,9 +176,21 @@ def make_sequence(workload: str, seed_offset: int = 0):
 
 
 # ----------------------------------------------------------------- CPU oracle
+def _oracle_register_chunk(job):
+    """One oracle registration of frames [lo, hi) (runs in a spawned worker)."""
+    workload, lo, hi, mode = job
+    from oracle import Params, multilevel
+    n, shape, L, Q, _ = WORKLOADS[workload]
+    R, _ = make_sequence(workload)
+    sub = R[lo:hi].astype(np.float64)
+    t0 = time.perf_counter()
+    multilevel.register(sub, Params(n_levels=L, n_tlevels=Q), mode)
+    return hi - lo, time.perf_counter() - t0
+
+
 def oracle_sample(R: np.ndarray, workload: str, frames: int, mode: str = "stml"):
     """Register the first `frames` frames (full spatial size, same level
-    structure) with the FP64 oracle; returns (frames/s, seconds)."""
+    structure) with the FP64 oracle on one thread; returns (frames/s, seconds)."""
     from oracle import Params, multilevel
     n, shape, L, Q, _ = WORKLOADS[workload]
     p = Params(n_levels=L, n_tlevels=Q)
@@ -193,25 +201,101 @@ def oracle_sample(R: np.ndarray, workload: str, frames: int, mode: str = "stml")
     return frames / dt, dt
 
 
-def oracle_hessvec_ns(workload: str, frames: int, reps: int = 3):
-    """FP64 oracle's Gauss-Newton Hessian product on the finest level (first
-    `frames` frames, seeded random direction and grad T, single thread):
-    nanoseconds per pixel-frame and seconds per call.  The CPU side of the
+def host_cpu():
+    """(logical cores, model name) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def oracle_sample_all_cores(workload: str, frames: int, mode: str = "stml"):
+    """The oracle on all host cores: the sequence is cut into consecutive
+    chunks of `frames` frames, each registered by its own single-threaded
+    worker process (started with spawn), all at once.  Returns (frames/s over
+    the longest worker's registration time, workers, that time, frames
+    registered)."""
+    import multiprocessing as mp
+    n = WORKLOADS[workload][0]
+    cores, _ = host_cpu()
+    chunks = [(lo, min(lo + frames, n)) for lo in range(0, n, frames)]
+    chunks = [c for c in chunks if c[1] - c[0] == frames][:max(1, cores)]
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"       # one thread per worker; inherited by the spawned processes
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(len(chunks)) as pool:
+            res = pool.map(_oracle_register_chunk, [(workload, lo, hi, mode) for lo, hi in chunks])
+        wall = max(t for _, t in res)   # the workers register at the same time; input generation excluded
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    done = sum(f for f, _ in res)
+    return done / wall, len(chunks), wall, done
+
+
+def oracle_op_ns(workload: str, frames: int, reps: int = 3):
+    """FP64 oracle's per-operation cost on the finest level of `frames`
+    frames (seeded inputs, one thread), in nanoseconds per pixel-frame:
+    the Gauss-Newton Hessian product, the objective + gradient pass (warp,
+    grad T, residual, regulariser, penalty) and the least-squares predictor
+    of eq. (2) over all frames of the sequence.  The CPU side of the
     per-operation comparison in the bench line."""
-    from oracle import Params, objective
+    from oracle import Params, grid, objective, predictor
     n, shape, L, Q, _ = WORKLOADS[workload]
     rng = np.random.default_rng(5)
     d = len(shape)
-    dT = rng.normal(size=(frames, d) + tuple(shape))
-    v = rng.normal(size=(frames, d) + tuple(shape))
+    N = float(np.prod(shape))
     p = Params(n_levels=L, n_tlevels=Q)
     K = list(range(frames))
-    objective.hessvec(dT, v, K, 1.0, p)
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        objective.hessvec(dT, v, K, 1.0, p)
-    dt = (time.perf_counter() - t0) / reps
-    return 1e9 * dt / (frames * float(np.prod(shape))), dt
+    out = {}
+
+    def timed(f):
+        f()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            f()
+        return (time.perf_counter() - t0) / reps
+
+    dT = rng.normal(size=(frames, d) + tuple(shape))
+    v = rng.normal(size=(frames, d) + tuple(shape))
+    dt = timed(lambda: objective.hessvec(dT, v, K, 1.0, p))
+    out["gn_hessian_product"] = {"oracle_ns_per_pixel_frame": 1e9 * dt / (frames * N),
+                                 "sample": f"finest level, {frames} frames, mean of {reps} calls ({dt:.2f} s each)"}
+    R, _ = make_sequence(workload)
+    T = R[:frames].astype(np.float64)
+    u = 0.5 * rng.normal(size=(frames, d) + tuple(shape))
+    dt = timed(lambda: objective.evaluate(T, u, K, 1.0, p))
+    out["gradient_pass"] = {"oracle_ns_per_pixel_frame": 1e9 * dt / (frames * N),
+                            "sample": f"finest level, {frames} frames, objective and gradient, mean of {reps} "
+                                      f"calls ({dt:.2f} s each)"}
+    Kq = grid.temporal_sets(n, Q)[Q - 2] if Q > 1 else list(range(n))
+    omega = rng.normal(size=(n, d) + tuple(shape))
+    eta = omega[Kq] + rng.normal(size=(len(Kq), d) + tuple(shape))
+    dt = timed(lambda: predictor.predict_ls(eta, omega, Kq, p.beta))
+    out["predict_ls_eq2"] = {"oracle_ns_per_pixel_frame": 1e9 * dt / (n * N),
+                             "sample": f"finest level, all {n} frames from |K| = {len(Kq)}, mean of {reps} calls "
+                                       f"({dt:.2f} s each)"}
+    return out
 
 
 def workload_label(args) -> str:
@@ -229,20 +313,25 @@ def run_reference(args):
         if rank != 0:
             dist.barrier()
             return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    R, _ = make_sequence(args.workload)
     n = WORKLOADS[args.workload][0]
-    frames = min(args.cpu_sample_frames, n)
+    # frames per chunk: the whole run (warm-up and timed steps) within about
+    # 2.5 minutes at the oracle's measured ~0.55 s per frame and core of this
+    # workload (between 4 and --cpu-sample-frames frames)
+    per_step_s = 150.0 / max(1, args.steps + args.warmup)
+    frames = max(4, min(args.cpu_sample_frames, n, int(per_step_s / 0.55)))
     for _ in range(args.warmup):
-        oracle_sample(R, args.workload, frames, args.mode)
-    times = []
+        oracle_sample_all_cores(args.workload, frames, args.mode)
+    times, done = [], 0
     for _ in range(args.steps):
-        _, dt = oracle_sample(R, args.workload, frames, args.mode)
-        times.append(dt)
+        _, workers, wall, f = oracle_sample_all_cores(args.workload, frames, args.mode)
+        times.append(wall)
+        done += f
     total = sum(times)
-    value = frames * len(times) / total
-    sample = (f"first {frames} of {n} frames at full size, same spatial/temporal levels, "
-              f"numpy FP64, one registration per step")
+    value = done / total
+    host_cores, model = host_cpu()
+    sample = (f"{workers} chunks of {frames} consecutive frames of {n} at full size, same spatial/temporal "
+              f"levels, each registered by its own single-threaded numpy FP64 worker process, all at once; "
+              f"one such batch per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
@@ -250,8 +339,8 @@ def run_reference(args):
             "config": {"workload": workload_label(args), "n_frames": n,
                        "shape": list(WORKLOADS[args.workload][1]), "levels": WORKLOADS[args.workload][2],
                        "tlevels": WORKLOADS[args.workload][3], "mode": args.mode, "sample_frames": frames},
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": workers, "kind": "oracle",
+                             "sample": sample, "host_cores": host_cores, "cpu_model": model},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -713,27 +802,50 @@ def run_native(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = sum_over_ranks(float(n * e2e_steps), world, dev) / e2e_s
 
-    # spatial-only multilevel on the same data (the paper's comparison)
+    # spatial-only multilevel on the same data (the paper's comparison), each
+    # strategy with its own stopping tests, then at equal final objective:
+    # STML with target_J = SpML's final objective (its last GIR over all
+    # frames stops where J reaches that value, within target_tol)
     spml = None
     if not args.no_spml and mode == S.MODE_STML:
-        sp_steps = max(1, min(args.steps, 2))
-        torch.cuda.synchronize()
-        t = []
-        for _ in range(sp_steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            S.stml_load_sequence(ctx.ptr, R_dev)
-            S.stml_build_pyramid(ctx.ptr)
-            S.stml_register(ctx.ptr, S.MODE_SPML)
-            b.record(stream)
-            torch.cuda.synchronize()
-            t.append(a.elapsed_time(b))
-        S.stml_get_field(ctx.ptr, L - 1, y)
-        outJs = S.stml_eval(ctx.ptr, L - 1, list(range(n)), y)
-        spml_fps = n / (statistics.mean(t) / 1e3)
-        spml = {"frames_per_s": spml_fps, "final_J": outJs[0],
+        sp_steps = max(2, min(args.steps, 3))
+
+        def timed_register(m, prm_run):
+            S.stml_set_params(ctx.ptr, prm_run)
+            t = []
+            for _ in range(sp_steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                S.stml_load_sequence(ctx.ptr, R_dev)
+                S.stml_build_pyramid(ctx.ptr)
+                st = S.stml_register(ctx.ptr, m)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t.append(a.elapsed_time(b))
+            S.stml_get_field(ctx.ptr, L - 1, y)
+            J = S.stml_eval(ctx.ptr, L - 1, list(range(n)), y)[0]
+            return statistics.median(t), J, st
+
+        sp_ms, J_sp, st_sp = timed_register(S.MODE_SPML, prm)
+        prm_t = S.stml_default_params(n_levels=L, n_tlevels=Q,
+                                      image_dtype={"f32": 0, "f16": 1, "bf16": 2}[args.image_dtype],
+                                      autotune=int(args.autotune), target_J=J_sp)
+        st_ms, J_st, st_st = timed_register(S.MODE_STML, prm_t)
+        S.stml_set_params(ctx.ptr, prm)
+        spml_fps = n / (sp_ms / 1e3)
+        spml = {"frames_per_s": spml_fps, "final_J": J_sp, "stml_final_J": outJ[0],
                 "stml_over_spml_speedup": (value / world) / spml_fps if world else None,
+                "note": "each strategy with the same stopping tests (its own final objective)",
+                "gn_iters": sum(x["gn_iters"] for x in st_sp),
+                "matched": {"target_J": J_sp, "spml_final_J": J_sp, "stml_final_J": J_st,
+                            "rel_diff": abs(J_st - J_sp) / abs(J_sp), "spml_ms": sp_ms, "stml_ms": st_ms,
+                            "stml_frames_per_s": n / (st_ms / 1e3), "spml_frames_per_s": spml_fps,
+                            "stml_over_spml_speedup": sp_ms / st_ms,
+                            "stml_last_gir_gn_iters": st_st[-1]["gn_iters"],
+                            "how": "STML with target_J = SpML's final objective over all frames on the finest "
+                                   "level (the step that crosses it is shortened until |J - target| <= 1e-5 "
+                                   "target); median of %d registrations each" % sp_steps},
                 "paper_speedup": "2.5x average (Sec. 4, Table 1; hardware not stated)"}
 
     batch = None
@@ -756,14 +868,17 @@ def run_native(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         frames = min(args.cpu_sample_frames, n)
-        fps, dt = oracle_sample(R, args.workload, frames, args.mode)
-        cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {frames} of {n} frames, full 256x256, same levels; numpy FP64 "
-                         f"single thread; {dt:.1f} s"}
-        ns, call_s = oracle_hessvec_ns(args.workload, frames)
-        cpu["ops"] = {"gn_hessian_product": {"oracle_ns_per_pixel_frame": ns,
-                                             "sample": f"finest level, {frames} frames, mean of 3 calls "
-                                                       f"({call_s:.2f} s each)"}}
+        fps1, dt1 = oracle_sample(R, args.workload, frames, args.mode)
+        fpsN, workers, wall, done = oracle_sample_all_cores(args.workload, frames, args.mode)
+        host_cores, model = host_cpu()
+        cpu = {"value": fpsN, "unit": "frames/s", "cores": workers, "kind": "oracle",
+               "sample": f"{workers} chunks of {frames} consecutive frames ({done} of {n}) at full size, same "
+                         f"levels, each registered by its own single-threaded numpy FP64 worker process, all at "
+                         f"once; {wall:.1f} s wall",
+               "host_cores": host_cores, "cpu_model": model,
+               "single_core": {"value": fps1, "unit": "frames/s", "cores": 1,
+                               "sample": f"first {frames} of {n} frames, one thread; {dt1:.1f} s"},
+               "ops": oracle_op_ns(args.workload, frames)}
 
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -783,10 +898,21 @@ def run_native(args):
             "algorithmic_bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
             "launches": prof["launches"], "ms_total": prof["ms"], "finest_level": fin,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s (of fallback)"}
-    if cpu and fin:
-        op = cpu["ops"]["gn_hessian_product"]
-        op["gpu_ns_per_pixel_frame"] = 1e6 * finest[0]["ms"] / finest[0]["pixel_frames"]
-        op["oracle_over_gpu"] = op["oracle_ns_per_pixel_frame"] / op["gpu_ns_per_pixel_frame"]
+    if cpu:
+        # GPU side of each per-operation entry: finest-level device time per
+        # pixel-frame from the kernel table (objective + gradient for the
+        # oracle's evaluate, which computes both)
+        def gpu_ns(kernel):
+            rows = [r for r in table if r["kernel"] == kernel and r["level"] == L - 1 and r["pixel_frames"] > 0]
+            return 1e6 * sum(r["ms"] for r in rows) / sum(r["pixel_frames"] for r in rows) if rows else None
+        per_pf = {"gn_hessian_product": [gpu_ns("gn_hessian_product")],
+                  "gradient_pass": [gpu_ns("gradient_pass"), gpu_ns("objective_pass")],
+                  "predict_ls_eq2": [gpu_ns("predict_ls_eq2")]}
+        for name, op in cpu["ops"].items():
+            vals = per_pf.get(name, [None])
+            if all(v is not None for v in vals):
+                op["gpu_ns_per_pixel_frame"] = sum(vals)
+                op["oracle_over_gpu"] = op["oracle_ns_per_pixel_frame"] / op["gpu_ns_per_pixel_frame"]
     per_kernel = {}
     for r in table:
         k = per_kernel.setdefault(r["kernel"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
