@@ -309,6 +309,58 @@ stml_status stml_predict_ls(const float* eta, const int* K, int nK, const float*
                             float* zeta, int n, double beta, size_t n_comp,
                             void* cuda_stream);
 
+/* ------------------------------------------ batched persistent solver */
+
+/* A batch of contexts solved together (batched serving of many sequences of
+ * uneven frame counts and sizes; the paper has no counterpart).  For every
+ * (spatial level, temporal level) stage of the multilevel sweep, the
+ * predictors, gathers and the stopping rule eq. (3) run per context on its own
+ * stream, and the GIRs of all contexts run in ONE persistent cooperative
+ * kernel: each sequence's Gauss-Newton / PCG / Armijo loop is a state machine
+ * on the device, every step of the kernel splits the grid into contiguous CTA
+ * ranges (one per active sequence, sized by the bytes its current phase
+ * moves) that stride over the sequence's (tile or frame-chunk) items, and the
+ * first CTA of each range reduces its range's sums in a fixed order and takes
+ * the sequence's decisions; the grid barriers are bounded (STML_ETIMEOUT).
+ * Each stage's uploads, kernel and download replay a CUDA graph captured on
+ * the stage's first use.  With params.autotune = 1 the first stage of every
+ * level times four launch shapes (1 or 2 CTAs per SM, 4 or 16 lanes per
+ * PCG tile row) and keeps the fastest for the batch.
+ *
+ * stml_batch_create: ctxs (host array of n_ctx distinct contexts of one
+ * device, not sharing a predictor network) stay owned by the caller and must
+ * outlive the batch.  stml_batch_register: every context must hold a built
+ * pyramid; all need the same dimension, image storage, level counts and
+ * solver parameters (alpha, alpha_t, lambda, tolerances, iteration limits),
+ * transform 0, and at most 2 x SMs sequences (target_J may differ: each
+ * sequence's last GIR stops at its own target); else
+ * STML_EINVAL before any work.  status (host, n_ctx entries, may be NULL)
+ * receives each context's result; the return value is STML_OK or the first
+ * failure.  Decisions are those of stml_register (same tests on the same
+ * kinds of totals); results agree with it to rounding.  Per-GIR statistics:
+ * stml_last_stats on each context.  stml_batch_report writes a JSON array
+ * (per stage: level, tlevel, sequences, kernel steps, ms, launch shape; the
+ * autotuner's trials) to buf (host, cap bytes, NUL-terminated; *needed gets
+ * the full length plus one).  Errors of batch calls: stml_batch_last_error. */
+typedef struct stml_batch stml_batch;
+stml_status stml_batch_create(stml_ctx* const* ctxs, int n_ctx, stml_batch** out);
+stml_status stml_batch_register(stml_batch* batch, stml_mode mode, stml_status* status);
+stml_status stml_batch_report(const stml_batch* batch, char* buf, size_t cap, size_t* needed);
+const char* stml_batch_last_error(const stml_batch* batch);
+void stml_batch_destroy(stml_batch* batch);
+
+/* Failure-detection self-check of the batched solver's bounded grid
+ * barrier: one CTA enters a barrier that expects two CTAs, so nothing
+ * completes it; *expired (host) = 1 when the wait gave up after its bound
+ * (about 2 s) and reported it -- the behaviour a stalled batched solve shows
+ * as STML_ETIMEOUT.  Synchronises `cuda_stream`. */
+stml_status stml_check_batch_barrier(void* cuda_stream, int* expired);
+
+/* Statistics of every GIR of the context's last registration (stml_register
+ * or stml_batch_register), in order: stats (host, cap entries, may be NULL),
+ * *n_written (may be NULL) the number of GIRs. */
+stml_status stml_last_stats(const stml_ctx* ctx, stml_stats* stats, int cap, int* n_written);
+
 /* ----------------------------------------------- allocation-free variant */
 
 /* Gauss-Newton Hessian product (as stml_hessvec) for callers that cannot

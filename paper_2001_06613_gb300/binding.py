@@ -86,6 +86,13 @@ _SIGS = {
     "stml_set_field": (C.c_int, [_vp, C.c_int, _fp, C.c_int]),
     "stml_register": (C.c_int, [_vp, C.c_int, C.POINTER(Stats), C.c_int, _ip]),
     "stml_register_batch": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, _ip]),
+    "stml_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
+    "stml_batch_register": (C.c_int, [_vp, C.c_int, _ip]),
+    "stml_batch_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "stml_batch_last_error": (C.c_char_p, [_vp]),
+    "stml_batch_destroy": (None, [_vp]),
+    "stml_last_stats": (C.c_int, [_vp, C.POINTER(Stats), C.c_int, _ip]),
+    "stml_check_batch_barrier": (C.c_int, [_vp, _ip]),
     "stml_predict": (C.c_int, [_vp, C.c_int, C.c_int]),
     "stml_correct": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(Stats), _ip]),
     "stml_eval": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _fp, _dp, _fp, _fp]),
@@ -284,6 +291,82 @@ def stml_register_batch(ctxs: Sequence, mode: int = MODE_STML, max_threads: int 
         raise StmlError(status, stml_last_error(None) or "; ".join(
             stml_last_error(c.ptr if hasattr(c, "ptr") else c) for c in ctxs))
     return list(st)
+
+
+def stml_batch_create(ctxs: Sequence):
+    """A batch over the given contexts (Context objects or raw pointers)."""
+    arr = (_vp * len(ctxs))(*[c.ptr if hasattr(c, "ptr") else c for c in ctxs])
+    out = _vp()
+    _check(load().stml_batch_create(arr, len(ctxs), C.byref(out)))
+    return out
+
+
+def stml_batch_last_error(batch) -> str:
+    msg = load().stml_batch_last_error(batch)
+    return msg.decode() if msg else ""
+
+
+def stml_batch_register(batch, n_ctx: int, mode: int = MODE_STML) -> List[int]:
+    """Registers every context of the batch with the persistent solver;
+    returns each context's status (raises on the first failure)."""
+    st = (C.c_int * n_ctx)()
+    status = load().stml_batch_register(batch, mode, st)
+    if status != 0:
+        raise StmlError(status, stml_batch_last_error(batch))
+    return list(st)
+
+
+def stml_batch_report(batch) -> list:
+    import json
+    need = C.c_size_t()
+    _check(load().stml_batch_report(batch, None, 0, C.byref(need)))
+    buf = C.create_string_buffer(need.value)
+    _check(load().stml_batch_report(batch, buf, need.value, C.byref(need)))
+    return json.loads(buf.value.decode())
+
+
+def stml_batch_destroy(batch):
+    load().stml_batch_destroy(batch)
+
+
+class Batch:
+    """Owns one stml_batch over a list of Context objects."""
+
+    def __init__(self, ctxs: Sequence):
+        self.ctxs = list(ctxs)
+        self.ptr = stml_batch_create(self.ctxs)
+
+    def register(self, mode: int = MODE_STML) -> List[int]:
+        return stml_batch_register(self.ptr, len(self.ctxs), mode)
+
+    def report(self) -> list:
+        return stml_batch_report(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            stml_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stml_last_stats(ctx, cap: int = 512) -> list:
+    stats = (Stats * cap)()
+    n = C.c_int()
+    _check(load().stml_last_stats(ctx, stats, cap, C.byref(n)), ctx)
+    return [stats[i].as_dict() for i in range(min(n.value, cap))]
+
+
+def stml_check_batch_barrier(stream=None) -> bool:
+    """True when a grid barrier of the batched solver that cannot complete
+    gives up after its bound and reports it (takes about 2 s)."""
+    out = C.c_int(0)
+    _check(load().stml_check_batch_barrier(_stream(stream), C.byref(out)))
+    return out.value == 1
 
 
 def stml_predict(ctx, level: int, tlevel: int):

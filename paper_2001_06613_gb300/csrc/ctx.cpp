@@ -131,6 +131,7 @@ struct stml_ctx {
     int pred_learned = -1;
     double J0_classic = 0.0;
 
+    std::vector<stml_stats> last_stats;   // per GIR of the last registration
     std::string err;
 };
 
@@ -1461,20 +1462,38 @@ stml_status do_predict(stml_ctx* c, int level, int q) {
     return STML_OK;
 }
 
-stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finished) {
+// The correction of temporal level q in two halves around its GIR: the
+// start fields of K_q gathered into w_u, then (with the GIR's statistics)
+// the stopping rule eq. (3) and the fields of the level.
+stml_status correct_begin(stml_ctx* c, int level, int q) {
     if (c->cur_level != level || c->last_q != q - 1 || c->level_done)
         return fail(c, STML_ESTATE, "stml_correct(level, q) needs stml_predict(level, q) first");
     LevelBuf& L = c->lv[level];
     const size_t plane = (size_t)L.g.d * L.g.N;
     const std::vector<int>& K = c->sets[q];
-    const int Q = (int)c->sets.size();
     TRY(upload_idx(c, K));
     long pe = prof_begin(c, PC_GATHER, level);
     CK(c, launch_gather_planes(c->w_z, c->w_u, c->d_idx, (int)K.size(), plane, c->stream));
     prof_end(c, pe, 8.0 * plane * K.size(), (double)K.size() * L.g.N);
+    return STML_OK;
+}
+
+stml_status correct_end(stml_ctx* c, int level, int q, stml_stats s, stml_stats* st, int* finished);
+
+stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finished) {
+    TRY(correct_begin(c, level, q));
+    const int Q = (int)c->sets.size();
     stml_stats s{};
     const bool last_gir = level == (int)c->lv.size() - 1 && q == Q - 1;   // the GIR over all frames
-    TRY(run_gir(c, level, K, c->w_u, &s, last_gir ? c->p.target_J : 0.0));
+    TRY(run_gir(c, level, c->sets[q], c->w_u, &s, last_gir ? c->p.target_J : 0.0));
+    return correct_end(c, level, q, s, st, finished);
+}
+
+stml_status correct_end(stml_ctx* c, int level, int q, stml_stats s, stml_stats* st, int* finished) {
+    LevelBuf& L = c->lv[level];
+    const size_t plane = (size_t)L.g.d * L.g.N;
+    const std::vector<int>& K = c->sets[q];
+    const int Q = (int)c->sets.size();
     s.tlevel = q;
     s.pred_learned = c->pred_learned;
     s.J0_classic = s.pred_learned >= 0 ? c->J0_classic : s.J0;
@@ -1512,6 +1531,426 @@ stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finis
     if (st) *st = s;
     if (finished) *finished = done;
     return STML_OK;
+}
+
+}  // namespace
+
+
+// ==================================================================== batched persistent solver
+struct stml_batch {
+    std::vector<stml_ctx*> ctxs;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_done = nullptr, ev_a = nullptr, ev_b = nullptr;
+    std::vector<cudaEvent_t> ev_ready;    // per context
+    int cap = 0;                          // sequences the buffers below hold
+    BatchSeq *d_seqs = nullptr, *h_seqs = nullptr;
+    BatchState *d_states = nullptr, *h_states = nullptr;
+    float2* d_part = nullptr;
+    BatchSync *d_sync = nullptr, *h_sync = nullptr;
+    // one stage (descriptor and state upload, barrier reset, the persistent
+    // kernel, state download) as a CUDA graph per (sequences, d, vec, storage,
+    // CTAs per SM, tpr); the uploads copy from the pinned buffers, whose
+    // contents are rewritten before every launch
+    std::map<std::array<int, 6>, cudaGraphExec_t> graphs;
+    // launch shapes chosen by the autotuner per (level, d, vec, storage, sequences)
+    std::map<std::array<int, 5>, BatchShape> tuned;
+    std::string report;                   // JSON rows of the last registration
+    std::string err;
+};
+
+namespace {
+
+stml_status bfail(stml_batch* b, stml_status s, const std::string& msg) {
+    if (b) b->err = msg;
+    else g_free_error = msg;
+    return s;
+}
+
+#define BCK(b, call)                                                                                      \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return bfail((b), STML_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Runs f(i) for i < n on up to `threads` host threads (each context is
+// touched by one thread at a time; its work goes to its own stream).
+template <class F>
+void parallel_for(int n, F&& f) {
+    const int nt = std::max(1, std::min(n, (int)std::max(1u, std::thread::hardware_concurrency())));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+}
+
+bool same_solver(const stml_params& a, const stml_params& b) {
+    return a.alpha == b.alpha && a.alpha_t == b.alpha_t && a.lambda == b.lambda && a.tol_J == b.tol_J &&
+           a.tol_Y == b.tol_Y && a.tol_G == b.tol_G && a.g_abs == b.g_abs && a.max_gn == b.max_gn &&
+           a.tol_cg == b.tol_cg && a.max_cg == b.max_cg && a.max_ls == b.max_ls && a.armijo_c == b.armijo_c &&
+           a.n_levels == b.n_levels && a.n_tlevels == b.n_tlevels && a.image_dtype == b.image_dtype;
+}
+
+// The descriptor of context c's GIR over K at `level` from u0 (all nK d N floats).
+BatchSeq batch_seq(stml_ctx* c, int level, const FrameSet& fs, float* u0, int vec, int tpr) {
+    LevelBuf& L = c->lv[level];
+    const Geom& g = L.g;
+    BatchSeq b{};
+    b.g = g;
+    b.pi = make_pix_index(g);
+    b.fs = fs;
+    b.cf = make_coef(g, c->p, fs.nK);
+    const long long cpf = (g.N + (long long)kThreads * vec - 1) / ((long long)kThreads * vec);
+    b.cpf = FastDiv::make((unsigned)cpf);
+    b.eval_tiles = (unsigned)((g.N + 32LL * vec - 1) / (32LL * vec));
+    b.pcg_tiles = (unsigned)((g.N + (long long)tpr * vec - 1) / ((long long)tpr * vec));
+    b.chunks = (unsigned)(cpf * fs.nK);
+    b.T = L.img;
+    b.u[0] = u0;
+    b.u[1] = c->w_ut;
+    b.grad = c->w_g;
+    b.dT = c->w_dT;
+    b.x = c->w_x;
+    b.r = c->w_r;
+    b.z = c->w_cz;
+    b.q = c->w_q;
+    b.p[0] = c->w_p;
+    b.p[1] = c->w_p2;
+    b.ms_z = c->w_m1;
+    b.sv_z = c->w_m2;
+    b.ms_p[0] = c->w_sp0;
+    b.ms_p[1] = c->w_sp1;
+    b.sv_p[0] = c->w_sp0 + g.N;
+    b.sv_p[1] = c->w_sp1 + g.N;
+    b.abar = c->w_abar;
+    b.ubar = c->w_ubar;
+    return b;
+}
+
+stml_status batch_buffers(stml_batch* b, int n) {
+    if (n <= b->cap) return STML_OK;
+    if (b->d_seqs) cudaFree(b->d_seqs);
+    if (b->d_states) cudaFree(b->d_states);
+    if (b->h_seqs) cudaFreeHost(b->h_seqs);
+    if (b->h_states) cudaFreeHost(b->h_states);
+    b->d_seqs = nullptr;
+    b->d_states = nullptr;
+    b->h_seqs = nullptr;
+    b->h_states = nullptr;
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    b->cap = 0;
+    BCK(b, cudaMalloc((void**)&b->d_seqs, n * sizeof(BatchSeq)));
+    BCK(b, cudaMalloc((void**)&b->d_states, n * sizeof(BatchState)));
+    BCK(b, cudaMallocHost((void**)&b->h_seqs, n * sizeof(BatchSeq)));
+    BCK(b, cudaMallocHost((void**)&b->h_states, n * sizeof(BatchState)));
+    b->cap = n;
+    return STML_OK;
+}
+
+// One stage's launches on b->stream: through a graph captured on first use
+// of this (sequences, launch shape).
+stml_status batch_stage_launch(stml_batch* b, int nseq, const BatchCtl& ctl, int d, int vec, int img, BatchShape sh,
+                               int max_steps) {
+    const std::array<int, 6> key{nseq, d, vec, img, sh.ctas_per_sm, sh.tpr};
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        cudaGraph_t gph = nullptr;
+        BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemcpyAsync(b->d_seqs, b->h_seqs, nseq * sizeof(BatchSeq), cudaMemcpyHostToDevice,
+                                        b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_states, b->h_states, nseq * sizeof(BatchState), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
+        if (e == cudaSuccess)
+            e = launch_batch_gir(b->d_seqs, nseq, b->d_states, ctl, d, vec, img, sh, b->d_part, b->d_sync, max_steps,
+                                 b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->h_states, b->d_states, nseq * sizeof(BatchState), cudaMemcpyDeviceToHost,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->h_sync, b->d_sync, sizeof(BatchSync), cudaMemcpyDeviceToHost, b->stream);
+        const cudaError_t e2 = cudaStreamEndCapture(b->stream, &gph);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, gph, 0);
+        if (gph) cudaGraphDestroy(gph);
+        if (e != cudaSuccess) return bfail(b, STML_ECUDA, std::string("batched stage graph: ") + cudaGetErrorString(e));
+        it = b->graphs.emplace(key, ex).first;
+    }
+    BCK(b, cudaGraphLaunch(it->second, b->stream));
+    return STML_OK;
+}
+
+}  // namespace
+
+
+namespace {
+
+// STML / SpML over the sequences of a batch: per (spatial level, temporal
+// level) stage the predictors and gathers of every context (on its own
+// stream, several host threads), then one persistent launch for all GIRs of
+// the stage, then the stopping rule eq. (3) and the fields of each context.
+stml_status batch_register(stml_batch* b, stml_mode mode, stml_status* status) {
+    const int n = (int)b->ctxs.size();
+    stml_ctx* c0 = b->ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        stml_ctx* c = b->ctxs[i];
+        if (!c->built) return bfail(b, STML_ESTATE, "stml_batch_register: a context has no pyramid");
+        if (c->device != b->device) return bfail(b, STML_EINVAL, "stml_batch_register: contexts on several devices");
+        if (c->p.transform != 0) return bfail(b, STML_EINVAL, "stml_batch_register: transform 0 only");
+        if (c->d != c0->d || c->img_type != c0->img_type || !same_solver(c->p, c0->p) ||
+            c->lv.size() != c0->lv.size() || c->sets.size() != c0->sets.size())
+            return bfail(b, STML_EINVAL,
+                         "stml_batch_register: contexts need the same dimension, image storage, level counts and "
+                         "solver parameters");
+    }
+    const stml_params& P = c0->p;
+    const int d = c0->d, img = c0->img_type, L = (int)c0->lv.size(), Q = (int)c0->sets.size();
+    int vec = 4;
+    for (stml_ctx* c : b->ctxs)
+        for (const LevelBuf& B : c->lv)
+            if (B.g.nx % 4) vec = 1;
+    const BatchCtl ctl{(float)P.tol_cg, P.max_cg, P.max_gn, P.max_ls, P.armijo_c, P.tol_J, P.tol_Y, P.tol_G, P.g_abs};
+    const int max_steps = P.max_gn * (2 * P.max_cg + P.max_ls + 3) + 8;
+    TRY(batch_buffers(b, n));
+    for (stml_ctx* c : b->ctxs) c->last_stats.clear();
+    std::vector<stml_status> st(n, STML_OK);
+    std::string rep = "[";
+    auto fail_ctx = [&](int i, stml_status r) {
+        if (st[i] == STML_OK) st[i] = r;
+    };
+    for (int l = 0; l < L; ++l) {
+        parallel_for(n, [&](int i) {
+            if (st[i] != STML_OK) return;
+            stml_ctx* c = b->ctxs[i];
+            cudaSetDevice(c->device);
+            stml_status r = do_predict(c, l, 0);
+            if (r == STML_OK && mode == STML_MODE_SPML) {
+                LevelBuf& B = c->lv[l];
+                const cudaError_t e = cudaMemcpyAsync(B.y, c->w_z, (size_t)c->n * c->d * B.g.N * sizeof(float),
+                                                      cudaMemcpyDeviceToDevice, c->stream);
+                if (e != cudaSuccess) r = cuda_fail(c, e, "cudaMemcpyAsync");
+            }
+            fail_ctx(i, r);
+        });
+        const int stages = mode == STML_MODE_SPML ? 1 : Q;
+        for (int q = 0; q < stages; ++q) {
+            std::vector<int> act;
+            for (int i = 0; i < n; ++i)
+                if (st[i] == STML_OK && !(mode == STML_MODE_STML && b->ctxs[i]->level_done)) act.push_back(i);
+            if (act.empty()) break;
+            if (mode == STML_MODE_STML && q > 0) {   // z_{l,q}: the predictor from the fields of K_{q-1}
+                parallel_for((int)act.size(), [&](int a) {
+                    stml_ctx* c = b->ctxs[act[a]];
+                    cudaSetDevice(c->device);
+                    fail_ctx(act[a], do_predict(c, l, q));
+                });
+                std::vector<int> keep;
+                for (int i : act)
+                    if (st[i] == STML_OK) keep.push_back(i);
+                act.swap(keep);
+                if (act.empty()) break;
+            }
+            // the starts of the stage (re-made for every launch shape the autotuner tries)
+            auto prepare = [&](const BatchShape& sh, std::vector<int>& run) {
+                std::vector<int> ok(act.size(), 0);
+                parallel_for((int)act.size(), [&](int a) {
+                    const int i = act[a];
+                    stml_ctx* c = b->ctxs[i];
+                    cudaSetDevice(c->device);
+                    stml_status r = STML_OK;
+                    float* u0 = nullptr;
+                    std::vector<int> K;
+                    if (mode == STML_MODE_STML) {
+                        r = correct_begin(c, l, q);
+                        u0 = c->w_u;
+                        K = c->sets[q];
+                    } else {
+                        LevelBuf& B = c->lv[l];
+                        K.resize(c->n);
+                        for (int k = 0; k < c->n; ++k) K[k] = k;
+                        u0 = B.y;
+                        const cudaError_t e = cudaMemcpyAsync(B.y, c->w_z, (size_t)c->n * c->d * B.g.N * sizeof(float),
+                                                              cudaMemcpyDeviceToDevice, c->stream);
+                        if (e != cudaSuccess) r = cuda_fail(c, e, "cudaMemcpyAsync");
+                    }
+                    FrameSet fs{};
+                    if (r == STML_OK) r = upload_frameset(c, K, fs);
+                    if (r == STML_OK) {
+                        b->h_seqs[a] = batch_seq(c, l, fs, u0, vec, sh.tpr);
+                        // the last GIR over all frames on the finest level may stop at the target objective
+                        const bool last_gir = l == L - 1 && (mode == STML_MODE_SPML || q == Q - 1);
+                        b->h_seqs[a].target = last_gir ? c->p.target_J : 0.0;
+                        b->h_seqs[a].target_tol = c->p.target_tol;
+                        const cudaError_t e = cudaEventRecord(b->ev_ready[i], c->stream);
+                        if (e != cudaSuccess) r = cuda_fail(c, e, "cudaEventRecord");
+                    }
+                    if (r == STML_OK) ok[a] = 1;
+                    else fail_ctx(i, r);
+                });
+                // compact the slots of the contexts that are still in the stage
+                run.clear();
+                int w = 0;
+                for (size_t a = 0; a < act.size(); ++a) {
+                    if (!ok[a]) continue;
+                    b->h_seqs[w] = b->h_seqs[a];
+                    BatchState z{};
+                    z.phase = BPH_EVAL0;
+                    z.status = STML_OK;
+                    b->h_states[w] = z;
+                    run.push_back(act[a]);
+                    ++w;
+                }
+            };
+            auto launch = [&](const BatchShape& sh, const std::vector<int>& run, float* ms) -> stml_status {
+                if (run.empty()) return STML_OK;
+                const int grid = batch_grid(d, vec, img, sh);
+                if (grid < (int)run.size())
+                    return bfail(b, STML_EINVAL, "stml_batch_register: " + std::to_string(run.size()) +
+                                                     " sequences, the persistent grid holds " + std::to_string(grid));
+                for (int i : run) BCK(b, cudaStreamWaitEvent(b->stream, b->ev_ready[i], 0));
+                BCK(b, cudaEventRecord(b->ev_a, b->stream));
+                TRY(batch_stage_launch(b, (int)run.size(), ctl, d, vec, img, sh, max_steps));
+                BCK(b, cudaEventRecord(b->ev_b, b->stream));
+                BCK(b, cudaEventRecord(b->ev_done, b->stream));
+                BCK(b, cudaStreamSynchronize(b->stream));
+                BCK(b, cudaEventElapsedTime(ms, b->ev_a, b->ev_b));
+                if (b->h_sync->err & 1u) return bfail(b, STML_ETIMEOUT, "a grid barrier of the batched solver expired");
+                if (b->h_sync->err & 6u) return bfail(b, STML_ESTATE, "the batched solver ran out of steps");
+                return STML_OK;
+            };
+            BatchShape sh{2, 16};
+            std::vector<int> run;
+            const std::array<int, 5> tkey{l, d, vec, img, (int)act.size()};
+            const auto tk = b->tuned.find(tkey);
+            if (tk != b->tuned.end()) {
+                sh = tk->second;
+            } else if (P.autotune && q == 0) {
+                // time one launch of this stage per candidate shape and keep the fastest
+                float best = 1e30f;
+                const BatchShape cands[4] = {{2, 16}, {2, 4}, {1, 16}, {1, 4}};
+                std::string rows;
+                for (const BatchShape& cs : cands) {
+                    if (batch_grid(d, vec, img, cs) < (int)act.size()) continue;
+                    prepare(cs, run);
+                    float ms = 0.f;
+                    TRY(launch(cs, run, &ms));
+                    for (int i : run) BCK(b, cudaStreamWaitEvent(b->ctxs[i]->stream, b->ev_done, 0));
+                    char row[96];
+                    std::snprintf(row, sizeof(row), "%s{\"ctas_per_sm\": %d, \"tpr\": %d, \"ms\": %.4f}",
+                                  rows.empty() ? "" : ", ", cs.ctas_per_sm, cs.tpr, ms);
+                    rows += row;
+                    if (ms < best) {
+                        best = ms;
+                        sh = cs;
+                    }
+                }
+                b->tuned[tkey] = sh;
+                char row[160];
+                std::snprintf(row, sizeof(row), "%s{\"tuned_level\": %d, \"sequences\": %d, \"chosen\": {\"ctas_per_sm\": %d, \"tpr\": %d}, \"tried\": [",
+                              rep.size() > 1 ? ", " : "", l, (int)act.size(), sh.ctas_per_sm, sh.tpr);
+                rep += row + rows + "]}";
+            }
+            prepare(sh, run);
+            float ms = 0.f;
+            const stml_status lr = launch(sh, run, &ms);
+            if (lr != STML_OK) {
+                for (int i : run) fail_ctx(i, lr);
+                break;
+            }
+            {
+                char row[200];
+                std::snprintf(row, sizeof(row),
+                              "%s{\"level\": %d, \"tlevel\": %d, \"sequences\": %d, \"steps\": %u, \"ms\": %.4f, "
+                              "\"ctas_per_sm\": %d, \"tpr\": %d}",
+                              rep.size() > 1 ? ", " : "", l, mode == STML_MODE_STML ? q : Q - 1, (int)run.size(),
+                              b->h_sync->steps, ms, sh.ctas_per_sm, sh.tpr);
+                rep += row;
+            }
+            parallel_for((int)run.size(), [&](int a) {
+                const int i = run[a];
+                stml_ctx* c = b->ctxs[i];
+                cudaSetDevice(c->device);
+                const BatchState S = b->h_states[a];
+                const BatchSeq& D = b->h_seqs[a];
+                stml_status r = STML_OK;
+                cudaError_t e = cudaStreamWaitEvent(c->stream, b->ev_done, 0);
+                if (e == cudaSuccess && S.cur == 1)
+                    e = cudaMemcpyAsync(D.u[0], D.u[1], (size_t)D.fs.nK * c->d * D.g.N * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, c->stream);
+                if (e != cudaSuccess) r = cuda_fail(c, e, "cudaMemcpyAsync");
+                stml_stats s{};
+                s.level = l;
+                s.n_frames = D.fs.nK;
+                s.gn_iters = S.it;
+                s.cg_iters = S.cg_total;
+                s.ls_trials = S.ls_total;
+                s.status = S.status;
+                s.J0 = S.J0;
+                s.J = S.J;
+                s.D = S.D;
+                s.S = S.S;
+                s.P = S.P;
+                s.seconds = ms / 1e3;
+                s.pred_learned = -1;
+                s.fill_learned = -1;
+                if (r == STML_OK && mode == STML_MODE_STML) {
+                    stml_stats out{};
+                    int fin = 0;
+                    r = correct_end(c, l, q, s, &out, &fin);
+                    if (r == STML_OK) c->last_stats.push_back(out);
+                } else if (r == STML_OK) {
+                    s.tlevel = Q - 1;
+                    s.J0_classic = s.J0;
+                    c->last_stats.push_back(s);
+                    c->level_done = true;
+                }
+                fail_ctx(i, r);
+            });
+        }
+    }
+    parallel_for(n, [&](int i) {
+        stml_ctx* c = b->ctxs[i];
+        cudaSetDevice(c->device);
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) fail_ctx(i, cuda_fail(c, e, "cudaStreamSynchronize"));
+    });
+    rep += "]";
+    b->report = rep;
+    stml_status first = STML_OK;
+    for (int i = 0; i < n; ++i) {
+        if (status) status[i] = st[i];
+        if (first == STML_OK && st[i] != STML_OK) {
+            first = st[i];
+            b->err = "context " + std::to_string(i) + ": " + b->ctxs[i]->err;
+        }
+    }
+    return first;
+}
+
+void batch_free(stml_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    if (b->d_seqs) cudaFree(b->d_seqs);
+    if (b->d_states) cudaFree(b->d_states);
+    if (b->d_part) cudaFree(b->d_part);
+    if (b->d_sync) cudaFree(b->d_sync);
+    if (b->h_seqs) cudaFreeHost(b->h_seqs);
+    if (b->h_states) cudaFreeHost(b->h_states);
+    if (b->h_sync) cudaFreeHost(b->h_sync);
+    for (cudaEvent_t e : b->ev_ready) cudaEventDestroy(e);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    if (b->ev_a) cudaEventDestroy(b->ev_a);
+    if (b->ev_b) cudaEventDestroy(b->ev_b);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 }  // namespace
@@ -1795,8 +2234,10 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
     if (mode != STML_MODE_STML && mode != STML_MODE_SPML) return fail(c, STML_EINVAL, "unknown mode");
     cudaSetDevice(c->device);
     int written = 0;
+    c->last_stats.clear();
     auto record = [&](const stml_stats& s) {
         if (stats && written < cap) stats[written] = s;
+        c->last_stats.push_back(s);
         ++written;
     };
     const int L = (int)c->lv.size();
@@ -2224,6 +2665,93 @@ stml_status stml_tuning_report(const stml_ctx* c, char* buf, size_t cap, size_t*
 long long stml_launch_count(const stml_ctx* c) {
     (void)c;
     return launches_total();
+}
+
+
+stml_status stml_batch_create(stml_ctx* const* ctxs, int n_ctx, stml_batch** out) {
+    if (!out) return fail(nullptr, STML_EINVAL, "stml_batch_create: out is NULL");
+    *out = nullptr;
+    if (!ctxs || n_ctx < 1) return fail(nullptr, STML_EINVAL, "stml_batch_create: need contexts");
+    for (int i = 0; i < n_ctx; ++i) {
+        if (!ctxs[i]) return fail(nullptr, STML_EINVAL, "stml_batch_create: a context is NULL");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return fail(nullptr, STML_EINVAL, "stml_batch_create: a context appears twice");
+        if (ctxs[i]->device != ctxs[0]->device)
+            return fail(nullptr, STML_EINVAL, "stml_batch_create: contexts on several devices");
+        if (ctxs[i]->net)
+            for (int k = 0; k < i; ++k)
+                if (ctxs[k]->net == ctxs[i]->net)
+                    return fail(nullptr, STML_EINVAL, "stml_batch_create: contexts share a predictor network");
+    }
+    stml_batch* b = new stml_batch();
+    b->ctxs.assign(ctxs, ctxs + n_ctx);
+    b->device = ctxs[0]->device;
+    cudaSetDevice(b->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_b);
+    b->ev_ready.assign(n_ctx, nullptr);
+    for (int i = 0; i < n_ctx && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev_ready[i], cudaEventDisableTiming);
+    const int sms = device_sms();
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_part, batch_partials(2 * (sms > 0 ? sms : 152)) * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_sync, sizeof(BatchSync));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_sync, sizeof(BatchSync));
+    if (e != cudaSuccess) {
+        const std::string msg = std::string("stml_batch_create: ") + cudaGetErrorString(e);
+        batch_free(b);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? STML_ENOMEM : STML_ECUDA, msg);
+    }
+    std::memset(b->h_sync, 0, sizeof(BatchSync));
+    *out = b;
+    return STML_OK;
+}
+
+stml_status stml_batch_register(stml_batch* b, stml_mode mode, stml_status* status) {
+    if (!b) return fail(nullptr, STML_EINVAL, "batch is NULL");
+    if (mode != STML_MODE_STML && mode != STML_MODE_SPML) return bfail(b, STML_EINVAL, "unknown mode");
+    cudaSetDevice(b->device);
+    return batch_register(b, mode, status);
+}
+
+stml_status stml_batch_report(const stml_batch* b, char* buf, size_t cap, size_t* needed) {
+    if (!b) return fail(nullptr, STML_EINVAL, "batch is NULL");
+    if (needed) *needed = b->report.size() + 1;
+    if (buf && cap > 0) {
+        const size_t k = std::min(cap - 1, b->report.size());
+        std::memcpy(buf, b->report.data(), k);
+        buf[k] = 0;
+    }
+    return STML_OK;
+}
+
+const char* stml_batch_last_error(const stml_batch* b) { return b ? b->err.c_str() : g_free_error.c_str(); }
+
+void stml_batch_destroy(stml_batch* b) { batch_free(b); }
+
+stml_status stml_check_batch_barrier(void* cuda_stream, int* expired) {
+    if (!expired) return fail(nullptr, STML_EINVAL, "expired is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    BatchSync* sync = nullptr;
+    int* flag = nullptr;
+    cudaError_t e = cudaMalloc((void**)&sync, sizeof(BatchSync));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_batch_barrier_probe(sync, flag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(expired, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (sync) cudaFree(sync);
+    if (flag) cudaFree(flag);
+    if (e != cudaSuccess) return fail(nullptr, STML_ECUDA, std::string("stml_check_batch_barrier: ") + cudaGetErrorString(e));
+    return STML_OK;
+}
+
+stml_status stml_last_stats(const stml_ctx* c, stml_stats* stats, int cap, int* n_written) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    const int n = (int)c->last_stats.size();
+    for (int i = 0; i < n && stats && i < cap; ++i) stats[i] = c->last_stats[i];
+    if (n_written) *n_written = n;
+    return STML_OK;
 }
 
 }  // extern "C"

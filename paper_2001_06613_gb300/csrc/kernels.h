@@ -55,6 +55,9 @@ cudaError_t set_max_dynamic_smem(const void* kernel, int bytes);
 // Geometry of a level from its shape (nz, ny, nx), dimension and cell width.
 Geom make_geom(const int shape3[3], int d, float h);
 
+// Divisors of a level's pixel index (x, y, z).
+PixIndex make_pix_index(const Geom& g);
+
 // CTAs for n work items at `threads` per CTA, capped for grid-stride loops.
 inline unsigned blocks_for(long long n, int threads = kThreads, long long cap = 1 << 20) {
     long long b = (n + threads - 1) / threads;
@@ -265,10 +268,14 @@ struct BatchSeq {
     float* ms_p[2];
     float* sv_p[2];
     float *abar, *ubar;      // per-pixel frame means (N, d N)
+    double target;           // target objective of this GIR (0: none), see stml_params.target_J
+    double target_tol;
 };
 
 // Phases of a sequence's state machine.
-enum BatchPhase { BPH_EVAL0 = 0, BPH_INIT, BPH_APPLY, BPH_UPDATE, BPH_TRIAL, BPH_GRAD, BPH_DONE };
+// LAND: objective at u + t d during the regula falsi that shortens the step
+// crossing the target objective.
+enum BatchPhase { BPH_EVAL0 = 0, BPH_INIT, BPH_APPLY, BPH_UPDATE, BPH_TRIAL, BPH_GRAD, BPH_LAND, BPH_DONE };
 
 // Device state of one sequence (written by the first CTA of its range only).
 struct BatchState {
@@ -283,6 +290,10 @@ struct BatchState {
     double J0, J, Jold, D, S, P, gnorm2, unorm2, step;
     double gTd, dnorm2;
     double Jt, Dt, St, Pt;   // totals of the last trial
+    // landing on the target: the bracket [la, lb] of the step, J - target at
+    // its ends, the best point so far; land_final: the next GRAD ends the GIR
+    double la, lfa, lb, lfb, best_t, best_f, best_J, best_D, best_S, best_P;
+    int side, land_it, land_final, land_pad;
 };
 
 // Solver parameters of the batch (stml_params of its contexts).
@@ -308,6 +319,9 @@ struct BatchShape {
 // float2 slots (batch_partials); the launch is cooperative (all CTAs resident).
 size_t batch_partials(int ctas);
 int batch_grid(int d, int vec, int img_type, const BatchShape& sh);
+// Self-check of the bounded grid barrier: one CTA waits on a barrier that
+// expects two; *expired (device int) = 1 when the wait gave up (about 2 s).
+cudaError_t launch_batch_barrier_probe(BatchSync* sync, int* expired, cudaStream_t s);
 cudaError_t launch_batch_gir(const BatchSeq* seqs_dev, int nseq, BatchState* states, const BatchCtl& ctl, int d,
                              int vec, int img_type, const BatchShape& sh, float2* part, BatchSync* sync,
                              int max_steps, cudaStream_t s);
