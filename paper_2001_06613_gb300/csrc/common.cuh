@@ -93,7 +93,8 @@ struct DevScalars {
     double trial[kMaxRed];    // totals of the last objective-only evaluation
     double dots[kMaxRed];     // totals of the last dot-product kernel
     float rho, bnorm2, pq, alpha, beta, rnorm2;   // CG coefficients (device only)
-    int cg_active, cg_iter, cg_flag, cg_pad;
+    int cg_active, cg_iter, cg_flag;
+    int pq_parts;              // CTA partials of <p, Hp> left by the last streaming Hessian product
     // Armijo line search decided on the device (trial k has t = 2^-k)
     double ls_gTd, ls_dnorm2;  // <g, d> and |d|^2 from trial 0
     float ls_t;                // the accepted step

@@ -96,14 +96,29 @@ __device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, c
     rv.store(r + e0);
 }
 
+// The PCG update.  It first completes the Hessian-product pass before it:
+// every CTA sums that pass's CTA partials of <p, Hp> (fixed order, the same
+// total everywhere) and takes the CG decision alpha = rho / <p, Hp>, so the
+// Hessian-product pass ends without a serial last-CTA reduction.  On a
+// breakdown (p^T H p <= 0) nothing is updated and CTA 0 records it.
 template <int D, int VEC, typename TD>
 __global__ void __launch_bounds__(kThreads)
 update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
               const TD* __restrict__ dT, float* __restrict__ x, float* __restrict__ r,
               const float* __restrict__ p, const float* __restrict__ q, double* __restrict__ partials,
-              DevScalars* S, PcgArgs a) {
+              const double* __restrict__ pq_partials, DevScalars* S, PcgArgs a) {
     if (!S->cg_active) return;
-    const float al = S->alpha;
+    CgState st = cg_load(S);
+    {
+        dfloat tot[1];
+        cta_total<1>(reinterpret_cast<const float2*>(pq_partials), (unsigned)S->pq_parts, tot);
+        cg_after_apply(st, df_val(tot[0]));
+    }
+    if (!st.active) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cg_store(S, st);
+        return;
+    }
+    const float al = st.alpha;
     float acc[2] = {0.f, 0.f};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int plane = (int)chunks.div((unsigned)it);
@@ -112,16 +127,16 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
     }
     double tot[2];
     if (grid_reduce<2>(acc, partials, &S->ticket[2], tot) && threadIdx.x == 0) {
-        CgState st = cg_load(S);
         cg_after_update(st, (float)tot[0], (float)tot[1], a.tol_cg, a.max_cg);
         cg_store(S, st);
     }
 }
 
 // Hessian product stream (grid-stride over (frame, chunk) items) of
-// v = src.z with its frame sums src.ms_z / src.sv_z.  With pcg != nullptr the
-// launch is a PCG step: it does nothing once cg_active is 0 and the last CTA
-// sets alpha = rho / <p, Hp> (or flags a breakdown).
+// v = src.z with its frame sums src.ms_z / src.sv_z.  Plain product: the
+// last CTA writes <v, Hv> to out[0].  With pcg != nullptr the launch is a PCG
+// step: it does nothing once cg_active is 0, and each CTA stores its partial
+// of <p, Hp> (double-float) for the update pass, which completes the sum.
 // CTAs per SM the Hessian-product kernel is compiled for (a register cap):
 // 3 for the 3-D float4 form, where 80 registers instead of 84 let a third
 // CTA in; otherwise the count its register use gives anyway.
@@ -139,11 +154,12 @@ apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, 
         const int j = (int)chunks.div((unsigned)it);
         apply_item<D, VEC, false, TD>(g, pi, fs, cf, dT, src, Hv, j, (unsigned)it - (unsigned)j * chunks.d, acc[0]);
     }
-    if (grid_reduce<1>(acc, partials, ticket, out) && threadIdx.x == 0 && pcg) {
-        CgState st = cg_load(pcg);
-        cg_after_apply(st, (float)out[0]);
-        cg_store(pcg, st);
+    if (pcg) {
+        cta_partials<1>(acc, reinterpret_cast<float2*>(partials), blockIdx.x);
+        if (blockIdx.x == 0 && threadIdx.x == 0) pcg->pq_parts = (int)gridDim.x;
+        return;
     }
+    grid_reduce<1>(acc, partials, ticket, out);
 }
 
 // ----------------------------------------------------------------- cooperative solve
@@ -226,6 +242,9 @@ PixIndex make_pix_index(const Geom& g) {
 namespace {
 
 constexpr int kGridStride = 152 * 8;   // most CTAs of a grid-stride launch (8 of 256 threads per SM of a GB300)
+// The PCG Hessian product's CTA partials of <p, Hp> (one double each) start
+// here in the partials buffer, after the update pass's own (2 per CTA).
+constexpr size_t kPqOffset = 2 * (size_t)kGridStride;
 
 bool vec4_ok(const Geom& g, std::initializer_list<const void*> ptrs) {
     if (g.nx % 4) return false;
@@ -293,7 +312,7 @@ cudaError_t apply_launch(const Geom& g, const FrameSet& fs, const Coef& cf, cons
 
 size_t gn_partials(const Geom& g, int nK) {
     const size_t tile = (size_t)((g.N + 7) / 8) * 2;
-    const size_t gs = (size_t)kGridStride * 2;
+    const size_t gs = (size_t)kGridStride * 3;   // the update's partials, then the PCG <p, Hp> partials
     (void)nK;
     return tile > gs ? tile : gs;
 }
@@ -323,7 +342,9 @@ cudaError_t launch_pcg_init(const Geom& g, const FrameSet& fs, const Coef& cf, c
 cudaError_t launch_pcg_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
                              double* partials, size_t partials_cap, DevScalars* S, cudaStream_t s) {
     const DirSrc src{b.p[0], nullptr, 0.f, nullptr, b.ms_z, b.sv_z, nullptr, nullptr, nullptr, nullptr};
-    return apply_launch(g, fs, cf, dT, src, b.q, partials, partials_cap, &S->ticket[1], S->dots + 4, S, s);
+    if (partials_cap < kPqOffset) return cudaErrorInvalidValue;
+    return apply_launch(g, fs, cf, dT, src, b.q, partials + kPqOffset, partials_cap - kPqOffset, &S->ticket[1],
+                        S->dots + 4, S, s);
 }
 
 cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const PcgBufs& b,
@@ -340,8 +361,9 @@ cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf,
         auto k = g.d == 2 ? (v4 ? update_kernel<2, 4, TD> : update_kernel<2, 1, TD>)
                           : (v4 ? update_kernel<3, 4, TD> : update_kernel<3, 1, TD>);
         const unsigned grid = resident_grid((const void*)k, items, kGridStride);
-        if ((size_t)grid * 2 > partials_cap) return cudaErrorInvalidValue;
-        k<<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, b.x, b.r, b.p[0], b.q, partials, S, a);
+        if ((size_t)grid * 2 > kPqOffset || partials_cap < kPqOffset + kGridStride) return cudaErrorInvalidValue;
+        k<<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, b.x, b.r, b.p[0], b.q, partials,
+                                    partials + kPqOffset, S, a);
         count_launches(1);
         return cudaGetLastError();
     });
