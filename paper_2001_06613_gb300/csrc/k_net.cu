@@ -14,6 +14,7 @@
 //   weight grad.:   dW[tap][ci][co] = sum_p X[p + off(tap)][ci] G[p][co]
 //                   (split over pixel slices, slices summed in a fixed order)
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_fp16.h>
 
 #include "net.h"
@@ -421,136 +422,213 @@ cudaError_t launch_conv3(const ConvIn& in, const bf16* Wh, int Cin, int N, int B
 }
 
 // --------------------------------------------------------- weight gradient
-// CTA: one tap, 32 input channels, BN output channels, one slice of pixels in
-// steps of 64; each warp multiplies one 16-pixel quarter of every step, the
-// four warps' tiles are summed in shared memory at the end.
+// dW[tap][ci][co] = sum_p X[p + off(tap)][ci] G[p][co] as a tensor-core GEMM
+// (tcgen05.mma kind::f16, BF16 operands, FP32 accumulator in TMEM) with
+// M = 4 taps x 32 input channels (TMEM lane = tap-in-group * 32 + ci),
+// N = BN output channels and K = pixels.  A CTA owns one group of four taps
+// (the third group holds tap 8 and three zero taps), one chunk of 32 input
+// channels, BN output channels and one slice of pixels, in stages of 64
+// pixels: the shifted inputs of its four taps and the output gradients are
+// gathered (cp.async; zero outside the image and past the slice) straight
+// from the channels-last maps into the no-swizzle MN-major core-matrix layout
+// -- a core matrix holds 8 pixels (rows of 16 bytes) x 8 consecutive
+// channels, core matrices along M (or N) 128 bytes apart, along K (8-pixel
+// groups) one stage row apart -- and one thread issues 4 MMAs (K = 16) per
+// stage, committed to the stage's mbarrier; three stages in flight.  Every
+// wait is bounded (*err as in conv3_kernel).
 template <int BN>
-__global__ void __launch_bounds__(128) wgrad3_kernel(ConvIn in, const bf16* __restrict__ G, int Cin,
-                                                     int N, int B, int H, int W, long long chunk,
-                                                     float* __restrict__ part) {
-    constexpr int STAGES = 3, PX = 64;
-    constexpr int XS = PX * 32, GS = PX * BN;
-    constexpr int PIPE = STAGES * (XS + GS) * 2;
-    constexpr int RED = 4 * 32 * BN * 4;
-    __shared__ __align__(128) unsigned char smem[PIPE > RED ? PIPE : RED];
-    bf16* sX = reinterpret_cast<bf16*>(smem);
-    bf16* sG = sX + STAGES * XS;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+struct WgCfg {
+    static constexpr int PX = 64;                      // pixels per stage
+    static constexpr int STAGES = 3;
+    static constexpr uint32_t A_SBO = 128;             // between 8-lane groups (M)
+    static constexpr uint32_t A_LBO = 16 * 128;        // between 8-pixel groups (K)
+    static constexpr uint32_t B_SBO = 128;             // between 8-channel groups (N)
+    static constexpr uint32_t B_LBO = (BN / 8) * 128;
+    static constexpr int A_BYTES = (PX / 8) * (int)A_LBO;   // 16 KB
+    static constexpr int B_BYTES = (PX / 8) * (int)B_LBO;
+    static constexpr int SMEM = 128 + STAGES * (A_BYTES + B_BYTES) + 64;
+    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
+    // F32 accumulator, BF16 A and B, both MN-major (transposed), N = BN, M = 128
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                      ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128) wgrad_tc_kernel(ConvIn in, const bf16* __restrict__ G, int Cin, int N,
+                                                       int B, int H, int W, long long chunk,
+                                                       float* __restrict__ part, int* __restrict__ err) {
+    using C = WgCfg<BN>;
+    extern __shared__ unsigned char wg_smem_raw[];
+    const uint32_t raw = smem_u32(wg_smem_raw);
+    const uint32_t base = (raw + 127u) & ~127u;
+    unsigned char* gbase = wg_smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + C::STAGES * C::A_BYTES;
+    const uint32_t bars = sB + C::STAGES * C::B_BYTES;   // STAGES mbarriers
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (bars - base) + 8 * C::STAGES);
+    unsigned char* gA = gbase;
+    unsigned char* gB = gbase + C::STAGES * C::A_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cpt = Cin / 32;
-    const int tap = blockIdx.x / cpt, cch = blockIdx.x - tap * cpt;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int tg = blockIdx.x / cpt, cch = blockIdx.x - tg * cpt;   // taps 4 tg .. 4 tg + 3, channel chunk
     const int n0 = blockIdx.y * BN;
-    const long long HW = (long long)H * W;
-    const long long M = (long long)B * HW;
+    const long long HW = (long long)H * W, M = (long long)B * HW;
     const long long pb = (long long)blockIdx.z * chunk;
     const long long pe = pb + chunk < M ? pb + chunk : M;
-    const int nst = pe > pb ? (int)((pe - pb + PX - 1) / PX) : 0;
+    const int nst = pe > pb ? (int)((pe - pb + C::PX - 1) / C::PX) : 0;
 
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < C::STAGES; ++i) mbar_init(bars + 8 * i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // (image, row, column) of the stage's pixels, computed once per stage
+    __shared__ int s_pix[C::PX][3];
     auto load_stage = [&](int st, int it) {
-        const long long p0 = pb + (long long)it * PX;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int sid = tid + 128 * k;
-            const int row = sid >> 2, seg = sid & 3;
-            const long long p = p0 + row;
-            const bf16* src = nullptr;
+        const long long p0 = pb + (long long)it * C::PX;
+        __syncthreads();   // the previous stage's copies have read s_pix
+        if (tid < C::PX) {
+            const long long p = p0 + tid;
+            int n = -1, y = 0, x = 0;
             if (p < pe) {
-                const int n = (int)(p / HW);
+                n = (int)(p / HW);
                 const int rem = (int)(p - (long long)n * HW);
-                const int y = rem / W, x = rem - (rem / W) * W;
-                src = in_at(in, n, y + dy, x + dx, H, W, cch * 32 + seg * 8);
+                y = rem / W;
+                x = rem - y * W;
             }
-            cp16(sX + st * XS + row * 32 + (swz4(row, seg) << 3), src ? src : in.a, src ? 16 : 0);
+            s_pix[tid][0] = n;
+            s_pix[tid][1] = y;
+            s_pix[tid][2] = x;
         }
-        constexpr int SEGS = BN / 8;
-#pragma unroll
-        for (int sid = tid; sid < PX * SEGS; sid += 128) {
-            const int row = sid / SEGS, seg = sid - row * SEGS;
-            const long long p = p0 + row;
+        __syncthreads();
+        unsigned char* a_st = gA + st * C::A_BYTES;
+        for (int sidx = tid; sidx < C::PX * 16; sidx += 128) {   // (pixel, lane group = tap * 4 + channel group)
+            const int k = sidx >> 4, mg = sidx & 15;
+            const int t = tg * 4 + (mg >> 2);
+            const int n = s_pix[k][0];
+            const bf16* src = nullptr;
+            if (n >= 0 && t < 9)
+                src = in_at(in, n, s_pix[k][1] + t / 3 - 1, s_pix[k][2] + t % 3 - 1, H, W, cch * 32 + (mg & 3) * 8);
+            cp16(a_st + (k >> 3) * C::A_LBO + mg * C::A_SBO + (k & 7) * 16, src ? src : in.a, src ? 16 : 0);
+        }
+        unsigned char* b_st = gB + st * C::B_BYTES;
+        constexpr int NG = BN / 8;
+        for (int sidx = tid; sidx < C::PX * NG; sidx += 128) {   // (pixel, channel group)
+            const int k = sidx / NG, ng = sidx - k * NG;
+            const long long p = p0 + k;
             const bool ok = p < pe;
-            cp16(sG + st * GS + row * BN + (swzB<BN>(row, seg) << 3),
-                 ok ? G + p * N + n0 + seg * 8 : G, ok ? 16 : 0);
+            cp16(b_st + (k >> 3) * C::B_LBO + ng * C::B_SBO + (k & 7) * 16, ok ? G + p * N + n0 + ng * 8 : G,
+                 ok ? 16 : 0);
         }
     };
 
-    constexpr int NI = BN / 8;
-    float acc[2][NI][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < NI; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-
-#pragma unroll
-    for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < nst) load_stage(s, s);
+    bool ok = true;
+    int waited = -1;   // the last item whose MMAs were waited for
+#pragma unroll 1
+    for (int sg = 0; sg < C::STAGES - 1; ++sg) {
+        if (sg < nst) load_stage(sg, sg);
         cp_commit();
     }
+#pragma unroll 1
     for (int it = 0; it < nst; ++it) {
-        cp_wait<STAGES - 2>();
-        __syncthreads();
-        const int nx = it + STAGES - 1;
-        if (nx < nst) load_stage(nx % STAGES, nx);
-        cp_commit();
-        const bf16* xs = sX + (it % STAGES) * XS;
-        const bf16* gs = sG + (it % STAGES) * GS;
-        uint32_t af[2][4];
+        const int st = it % C::STAGES;
+        cp_wait<C::STAGES - 2>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();   // every thread's copies of item it have landed
+        tc_fence_after();
+        if (tid == 0) {
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-            const int krow = warp * 16 + (lane & 7) + ((lane >> 4) << 3);
-            const int mseg = mi * 2 + ((lane >> 3) & 1);
-            ldsm_x4_t(af[mi], xs + krow * 32 + (swz4(krow, mseg) << 3));
+            for (int ks = 0; ks < C::PX / 16; ++ks) {
+                const uint64_t ad = plain_desc(sA + st * C::A_BYTES + 2 * ks * C::A_LBO, C::A_LBO, C::A_SBO);
+                const uint64_t bd = plain_desc(sB + st * C::B_BYTES + 2 * ks * C::B_LBO, C::B_LBO, C::B_SBO);
+                tc_mma(tmem, ad, bd, C::IDESC, (it > 0 || ks > 0) ? 1u : 0u);
+            }
+            tc_commit(bars + 8 * st);
         }
+        // refill the stage of item it - 1 once its MMAs are done
+        const int nx = it + C::STAGES - 1;
+        if (nx < nst) {
+            if (it >= 1) {
+                if (tid == 0)
+                    ok = mbar_wait(bars + 8 * ((it - 1) % C::STAGES), (uint32_t)(((it - 1) / C::STAGES) & 1));
+                if (!__syncthreads_and(ok)) {
+                    ok = false;
+                    break;
+                }
+                waited = it - 1;
+            }
+            load_stage(nx % C::STAGES, nx);
+        }
+        cp_commit();
+    }
+    // the last item: its MMAs complete after all earlier ones
+    if (ok && nst > 0) {
+        const int j = nst - 1;
+        if (tid == 0) ok = mbar_wait(bars + 8 * (j % C::STAGES), (uint32_t)((j / C::STAGES) & 1));
+        ok = __syncthreads_and(ok) != 0;
+        if (ok) waited = j;
+    }
+    tc_fence_after();
+    if (ok) {
+        // TMEM lane 32 w + l: tap 4 tg + w, channel cch * 32 + l
+        const int t = tg * 4 + warp;
+        const long long K = 9LL * Cin;
+        float* dst = part + (long long)blockIdx.z * K * N + ((long long)t * Cin + cch * 32 + lane) * N + n0;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 8) {
+            float v[8];
+            if (nst > 0) {
+                tc_ld8(trow + (uint32_t)c0, v);
+            } else {
 #pragma unroll
-        for (int nb = 0; nb < NI / 2; ++nb) {
-            const int krow = warp * 16 + (lane & 15);
-            const int nseg = nb * 2 + (lane >> 4);
-            uint32_t r[4];
-            ldsm_x4_t(r, gs + krow * BN + (swzB<BN>(krow, nseg) << 3));
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                mma16816(acc[mi][2 * nb], af[mi], r[0], r[1]);
-                mma16816(acc[mi][2 * nb + 1], af[mi], r[2], r[3]);
+                for (int i = 0; i < 8; ++i) v[i] = 0.f;
+            }
+            if (t < 9) {
+                reinterpret_cast<float4*>(dst + c0)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                reinterpret_cast<float4*>(dst + c0)[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
         }
     }
     cp_wait<0>();
+    if (!ok && tid == 0) {
+        // MMAs of the items after the last one waited for may still run: one
+        // more bounded wait on the newest committed item before TMEM is freed
+        const int j = nst - 1;
+        bool drained = true;
+        if (j > waited && j >= 0) drained = mbar_wait(bars + 8 * (j % C::STAGES), (uint32_t)((j / C::STAGES) & 1));
+        atomicMax(err, drained ? 1 : 2);
+    }
+    tc_fence_before();
     __syncthreads();
-    // sum the four warps' 32 x BN tiles
-    float* red = reinterpret_cast<float*>(smem);
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < NI; ++ni)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int r = mi * 16 + g + (c >> 1) * 8;
-                const int col = ni * 8 + 2 * t + (c & 1);
-                red[(warp * 32 + r) * BN + col] = acc[mi][ni][c];
-            }
-    __syncthreads();
-    const long long K = 9LL * Cin;
-    float* dst = part + (long long)blockIdx.z * K * N;
-    for (int i = tid; i < 32 * BN; i += 128) {
-        const int r = i / BN, col = i - r * BN;
-        const float v = red[r * BN + col] + red[(32 + r) * BN + col] + red[(64 + r) * BN + col] +
-                        red[(96 + r) * BN + col];
-        dst[((long long)tap * Cin + cch * 32 + r) * N + n0 + col] = v;
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
     }
 }
 
 cudaError_t launch_wgrad3(const ConvIn& in, const bf16* G, int Cin, int N, int B, int H, int W,
-                          float* part, size_t part_cap, int* splits, cudaStream_t s) {
+                          float* part, size_t part_cap, int* splits, int* err, cudaStream_t s) {
     if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 ||
-        (in.up && ((H | W) & 1)))
+        (in.up && ((H | W) & 1)) || !err)
         return cudaErrorInvalidValue;
     const long long M = (long long)B * H * W;
-    const int BN = N % 64 == 0 ? 64 : 32;
-    const long long tiles = 9LL * (Cin / 32) * (N / BN);
+    const int BN = N % 128 == 0 ? 128 : N % 64 == 0 ? 64 : 32;
+    const long long tiles = 3LL * (Cin / 32) * (N / BN);
     const long long per = 9LL * Cin * N;
-    long long S = (4 * 152 + tiles - 1) / tiles;
+    const int sms = device_sms();
+    long long S = ((long long)2 * (sms > 0 ? sms : 152) + tiles - 1) / tiles;
     const long long max_s = (M + 63) / 64;
     if (S > max_s) S = max_s;
     if (S > (long long)(part_cap / per)) S = (long long)(part_cap / per);
@@ -559,12 +637,18 @@ cudaError_t launch_wgrad3(const ConvIn& in, const bf16* G, int Cin, int N, int B
     chunk = (chunk + 63) / 64 * 64;
     S = (M + chunk - 1) / chunk;
     *splits = (int)S;
-    dim3 grid((unsigned)(9 * (Cin / 32)), N / BN, (unsigned)S);
-    if (BN == 64)
-        wgrad3_kernel<64><<<grid, 128, 0, s>>>(in, G, Cin, N, B, H, W, chunk, part);
-    else
-        wgrad3_kernel<32><<<grid, 128, 0, s>>>(in, G, Cin, N, B, H, W, chunk, part);
-    return cudaGetLastError();
+    dim3 grid((unsigned)(3 * (Cin / 32)), N / BN, (unsigned)S);
+    auto go = [&](auto tag) -> cudaError_t {
+        constexpr int bn = decltype(tag)::value;
+        using C = WgCfg<bn>;
+        const cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(wgrad_tc_kernel<bn>), C::SMEM);
+        if (e != cudaSuccess) return e;
+        wgrad_tc_kernel<bn><<<grid, 128, C::SMEM, s>>>(in, G, Cin, N, B, H, W, chunk, part, err);
+        return cudaGetLastError();
+    };
+    if (BN == 128) return go(std::integral_constant<int, 128>{});
+    if (BN == 64) return go(std::integral_constant<int, 64>{});
+    return go(std::integral_constant<int, 32>{});
 }
 
 // ------------------------------------------------------------ column sums

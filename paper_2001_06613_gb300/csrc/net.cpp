@@ -236,7 +236,8 @@ cudaError_t layer_wgrad(stml_net* n, int l, const bf16* G, int B, int H8, int W8
     const int lv = kDefs[l].level;
     const int H = H8 >> lv, W = W8 >> lv;
     int ws = 0, bs = 0;
-    ECK(launch_wgrad3(layer_input(n, l), G, kDefs[l].cin, kDefs[l].cout, B, H, W, n->wpart, n->wpart_cap, &ws, s));
+    ECK(launch_wgrad3(layer_input(n, l), G, kDefs[l].cin, kDefs[l].cout, B, H, W, n->wpart, n->wpart_cap, &ws,
+                      n->err_d, s));
     ECK(launch_colsum(G, (long long)B * H * W, kDefs[l].cout, n->bpart, n->bpart_cap, &bs, s));
     ECK(launch_reduce_grad(n->wpart, ws, kDefs[l].cin, kDefs[l].cin_real, kDefs[l].cout, n->bpart, bs, n->grad,
                            n->w_off[l], n->b_off[l], s));
@@ -545,7 +546,7 @@ stml_status stml_net_conv3_block(int mode, const float* x, const float* a, const
             ECK(nalloc(&wpart, wcap));
             ECK(nalloc(&bpart, bcap));
             int ws = 0, bs = 0;
-            ECK(launch_wgrad3(cin1(ab, Cin), xb, Cin, Cout, B, H, W_, wpart, wcap, &ws, s));
+            ECK(launch_wgrad3(cin1(ab, Cin), xb, Cin, Cout, B, H, W_, wpart, wcap, &ws, errd, s));
             ECK(launch_colsum(xb, P, Cout, bpart, bcap, &bs, s));
             ECK(launch_reduce_grad(wpart, ws, Cin, Cin, Cout, bpart, bs, y, 0, nw, s));
         }

@@ -89,9 +89,10 @@ cudaError_t launch_assemble(const Sample* smp, int B, int H, int W, int H8, int 
 cudaError_t launch_conv3(const ConvIn& in, const bf16* Wh, int Cin, int N, int B, int H, int W,
                          const ConvOut& out, int* err, cudaStream_t s);
 // Partial weight gradients: part[s][9 Cin][N] (FP32) = sum over the s-th slice
-// of pixels of im2col(in)^T G; returns the number of slices used in *splits.
+// of pixels of im2col(in)^T G (tcgen05 tensor cores); returns the number of
+// slices used in *splits; *err (device) as for launch_conv3.
 cudaError_t launch_wgrad3(const ConvIn& in, const bf16* G, int Cin, int N, int B, int H, int W,
-                          float* part, size_t part_cap, int* splits, cudaStream_t s);
+                          float* part, size_t part_cap, int* splits, int* err, cudaStream_t s);
 // Partial column sums part[s][N] of G [P][N].
 cudaError_t launch_colsum(const bf16* G, long long P, int N, float* part, size_t part_cap,
                           int* splits, cudaStream_t s);
