@@ -13,7 +13,15 @@ timed call.
     python -m paper_2001_06613_gb300.opbench --op net_forward --shape 256 256 --frames 32
 
 times the learned predictor's forward pass on a batch of `frames` canvases
-(TFLOP/s of its 3x3 convolutions against the measured BF16 peak).
+(TFLOP/s of its 3x3 convolutions against the measured BF16 peak);
+`--op net_train` one training step (forward, input and weight gradients,
+Adam) on `frames` crops of the given shape.
+
+    python -m paper_2001_06613_gb300.opbench --op batch --frames 8
+
+registers `frames` sequences of uneven length and size (the first of the
+batching workload's seeded draws, scaled down by 4 in each axis) with the
+persistent batched solver and reports the time of each stage.
 """
 from __future__ import annotations
 
@@ -37,7 +45,8 @@ def _peak():
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="all",
-                    choices=["all", "hessvec", "eval", "objective", "trial", "predict_ls", "net_forward"])
+                    choices=["all", "hessvec", "eval", "objective", "trial", "predict_ls", "net_forward",
+                             "net_train", "batch"])
     ap.add_argument("--shape", type=int, nargs="+", default=[256, 256])
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--iters", type=int, default=20)
@@ -51,6 +60,10 @@ def main(argv=None):
     dev = torch.device("cuda", 0)
     if args.op == "net_forward":
         return net_forward(S, torch, synthetic, dev, args)
+    if args.op == "net_train":
+        return net_train(S, torch, synthetic, dev, args)
+    if args.op == "batch":
+        return batch(S, torch, synthetic, dev, args)
     shape = tuple(args.shape)
     d = len(shape)
     n = args.frames
@@ -163,6 +176,61 @@ def net_forward(S, torch, synthetic, dev, args):
     print(json.dumps({"op": "net_forward", "batch": B, "shape": [H, W], "ms": ms, "GFLOP": flops / 1e9,
                       "TFLOP/s": tf, "frac_of_measured_bf16": tf / peak}), flush=True)
     return 0
+
+
+
+def net_train(S, torch, synthetic, dev, args):
+    """One Adam step of the predictor network on B = --frames crops."""
+    H, W = args.shape[0], args.shape[1]
+    B = args.frames
+    rng = np.random.default_rng(1)
+    f = torch.from_numpy(synthetic.random_field(rng, 3 * B, 2, (H, W), amp=2.0)).to(dev)
+    T = torch.rand((3, B, H, W), device=dev)
+    net = S.Net(synthetic.net_init_params(0, head_scale=0.1), max_batch=B, max_h=H, max_w=W)
+    smp = S.net_samples(f[:B].contiguous(), f[B:2 * B].contiguous(), T[0], T[1], T[2], 1.0, 0.5,
+                        target=f[2 * B:].contiguous())
+    for _ in range(args.warmup):
+        S.stml_net_train_step(net, smp, H, W, lr=1e-6, want_loss=False)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.iters):
+        S.stml_net_train_step(net, smp, H, W, lr=1e-6, want_loss=False)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.iters
+    convs = [(0, 7, 32), (0, 32, 32), (1, 32, 64), (1, 64, 64), (2, 64, 96), (2, 96, 96), (3, 96, 128),
+             (3, 128, 128), (2, 224, 96), (2, 96, 96), (1, 160, 64), (1, 64, 64), (0, 96, 32), (0, 32, 32)]
+    flops = sum(2.0 * B * (H >> lv) * (W >> lv) * 9 * ci * co * (2 if i == 0 else 3)
+                for i, (lv, ci, co) in enumerate(convs))
+    print(json.dumps({"op": "net_train", "batch": B, "shape": [H, W], "ms": ms,
+                      "tflops_algorithmic": flops / (ms / 1e3) / 1e12}), flush=True)
+    net.close()
+
+
+def batch(S, torch, synthetic, dev, args):
+    """stml_batch_register on --frames sequences: 20-300 frames of 32^2-128^2."""
+    rng = np.random.default_rng(1000)
+    seqs = []
+    for i in range(args.frames):
+        n = int(rng.integers(20, 301))
+        m = int(rng.choice([32, 48, 64, 96, 128]))
+        seqs.append(torch.from_numpy(synthetic.make_sequence(synthetic.SequenceSpec(
+            n=n, shape=(m, m), n_modes=4, amp=1.0, periods=[(16.0, 0.0)], noise_sd=0.01, seed=1000 + i)))
+            .to(dev))
+    prm = S.stml_default_params(n_levels=3, n_tlevels=3)
+    ctxs = [S.Context(prm) for _ in seqs]
+    for c, R in zip(ctxs, seqs):
+        S.stml_load_sequence(c.ptr, R)
+        S.stml_build_pyramid(c.ptr)
+    bt = S.Batch(ctxs)
+    for _ in range(max(1, args.warmup)):
+        bt.register(0)
+    torch.cuda.synchronize()
+    print(json.dumps({"op": "batch", "sequences": len(seqs), "frames": sum(int(r.shape[0]) for r in seqs),
+                      "stages": bt.report()}), flush=True)
+    bt.close()
+    for c in ctxs:
+        c.close()
 
 
 if __name__ == "__main__":

@@ -166,14 +166,33 @@ def _register_timed(S, R, params, net=None, repeats: int = 3):
     return best, stats, J
 
 
-def compare(S, net, sequences, params, repeats: int = 3) -> dict:
+def _with_target(S, params, target: float):
+    import ctypes
+    p = type(params)()
+    ctypes.memmove(ctypes.byref(p), ctypes.byref(params), ctypes.sizeof(params))
+    p.target_J = target
+    return p
+
+
+def compare(S, net, sequences, params, repeats: int = 3, equal_objective: bool = True) -> dict:
     """Registration of each sequence with and without the network: frames/s,
-    PCG and Gauss-Newton iterations, learned proposals kept, final objective."""
+    PCG and Gauss-Newton iterations, learned proposals kept, final objective;
+    with equal_objective also both runs to a common target per sequence (the
+    higher of the two natural final objectives, which each reaches on its own
+    path; the last GIR lands on it by regula falsi): frames/s at equal final
+    objective."""
     rows = []
     for R in sequences:
         t1, st1, J1 = _register_timed(S, R, params, net, repeats)
         t0, st0, J0 = _register_timed(S, R, params, None, repeats)
-        rows.append(dict(
+        eq = None
+        if equal_objective:
+            target = max(J0, J1)
+            u1, s1, K1 = _register_timed(S, R, _with_target(S, params, target), net, repeats)
+            u0, s0, K0 = _register_timed(S, R, _with_target(S, params, target), None, repeats)
+            eq = dict(target=target, seconds_learned=u1, seconds_classic=u0, J_learned=K1, J_classic=K0,
+                      cg_learned=sum(s["cg_iters"] for s in s1), cg_classic=sum(s["cg_iters"] for s in s0))
+        rows.append(dict(eq=eq,
             frames=int(R.shape[0]), seconds_learned=t1, seconds_classic=t0, J_learned=J1, J_classic=J0,
             cg_learned=sum(s["cg_iters"] for s in st1), cg_classic=sum(s["cg_iters"] for s in st0),
             gn_learned=sum(s["gn_iters"] for s in st1), gn_classic=sum(s["gn_iters"] for s in st0),
@@ -191,7 +210,13 @@ def compare(S, net, sequences, params, repeats: int = 3) -> dict:
                                       sum(1 for r in rows for (l, _, d) in r["decisions"] if l == lv)]
                             for lv in sorted({l for r in rows for (l, _, _) in r["decisions"]})},
         max_rel_J_change=max(abs(r["J_learned"] - r["J_classic"]) / abs(r["J_classic"]) for r in rows),
-        mean_rel_J_change=float(np.mean([(r["J_learned"] - r["J_classic"]) / abs(r["J_classic"]) for r in rows])))
+        mean_rel_J_change=float(np.mean([(r["J_learned"] - r["J_classic"]) / abs(r["J_classic"]) for r in rows])),
+        equal_objective=None if not equal_objective else dict(
+            frames_per_s_learned=frames / sum(r["eq"]["seconds_learned"] for r in rows),
+            frames_per_s_classic=frames / sum(r["eq"]["seconds_classic"] for r in rows),
+            cg_learned=sum(r["eq"]["cg_learned"] for r in rows), cg_classic=sum(r["eq"]["cg_classic"] for r in rows),
+            max_rel_J_diff=max(abs(r["eq"]["J_learned"] / r["eq"]["J_classic"] - 1.0) for r in rows),
+            how="both runs to a common target per sequence: the higher of the two natural final objectives"))
 
 
 def main(argv=None):
