@@ -355,6 +355,40 @@ def run_reference(args):
 BATCH_LEVELS = (4, 3)
 
 
+class RawStreams:
+    """Distinct CUDA streams, one per context (torch's stream pool repeats
+    after 32 streams, and contexts of stml_register_batch may not share one)."""
+
+    def __init__(self, torch, n: int):
+        import ctypes
+        self.rt = None
+        for name in ("libcudart.so", "libcudart.so.13", "libcudart.so.12"):
+            try:
+                self.rt = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        self.handles = []
+        if self.rt is None:   # fall back to torch streams when n fits its pool
+            if n > 32:
+                raise RuntimeError("no CUDA runtime library to create more than 32 streams")
+            self.torch_streams = [torch.cuda.Stream() for _ in range(n)]
+            self.handles = [st.cuda_stream for st in self.torch_streams]
+            return
+        for _ in range(n):
+            h = ctypes.c_void_p()
+            if self.rt.cudaStreamCreateWithFlags(ctypes.byref(h), 1) != 0:   # cudaStreamNonBlocking
+                raise RuntimeError("cudaStreamCreateWithFlags failed")
+            self.handles.append(h.value)
+
+    def close(self):
+        if self.rt is not None:
+            import ctypes
+            for h in self.handles:
+                self.rt.cudaStreamDestroy(ctypes.c_void_p(h))
+        self.handles = []
+
+
 def batch_specs(count: int):
     """The batching workload: 64 seeded sequences, frame counts uniform in
     20-300, sizes drawn from 128^2 ... 512^2, each with its own smooth motion
@@ -386,8 +420,9 @@ def run_batch_small(S, torch, dev, mode, count: int = 64):
             n=n, shape=(m, m), n_modes=4, amp=1.5, periods=[(16.0, 0.0)], noise_sd=0.01, seed=2000 + i),
             device=dev)).to(dev))
     frames = sum(int(r.shape[0]) for r in seqs)
-    streams = [torch.cuda.Stream(dev) for _ in seqs]
-    ctxs = [S.Context(S.stml_default_params(n_levels=3, n_tlevels=3), st.cuda_stream) for st in streams]
+    torch.cuda.synchronize()   # the contexts' streams do not wait for torch's stream
+    raw = RawStreams(torch, len(seqs))
+    ctxs = [S.Context(S.stml_default_params(n_levels=3, n_tlevels=3), st) for st in raw.handles]
 
     def timed(fn):
         for _ in range(2):
@@ -411,6 +446,8 @@ def run_batch_small(S, torch, dev, mode, count: int = 64):
     t_str = timed(lambda: S.stml_register_batch(ctxs, mode))
     for c in ctxs:
         c.close()
+    torch.cuda.synchronize()
+    raw.close()
     return {"sequences": count, "frames": frames, "sizes": "20-60 frames of 32^2/48^2/64^2, 3 x 3 levels",
             "sequential_frames_per_s": frames / t_seq, "streams_frames_per_s": frames / t_str,
             "persistent_frames_per_s": frames / t_per, "persistent_kernel_steps": steps,
@@ -432,12 +469,14 @@ def run_batch(S, torch, dev, mode, count: int, with_combined: bool):
     specs = batch_specs(count)
     t0 = time.perf_counter()
     seqs = [torch.from_numpy(synthetic.make_sequence(sp, device=dev)).to(dev) for sp in specs]
+    torch.cuda.synchronize()   # the contexts' streams do not wait for torch's stream
     gen_s = time.perf_counter() - t0
     frames = sum(sp.n for sp in specs)
     pixel_frames = sum(sp.n * sp.shape[0] * sp.shape[1] for sp in specs)
-    streams = [torch.cuda.Stream(dev) for _ in seqs]
+    raw = RawStreams(torch, len(seqs))
+    streams = raw.handles
     prm = S.stml_default_params(n_levels=L, n_tlevels=Q)
-    ctxs = [S.Context(prm, st.cuda_stream) for st in streams]
+    ctxs = [S.Context(prm, st) for st in streams]
 
     def load_all(cs):
         for c, R in zip(cs, seqs):
@@ -493,8 +532,8 @@ def run_batch(S, torch, dev, mode, count: int, with_combined: bool):
         # objective difference measured at its own natural result.
         params = np.fromfile(WEIGHTS, dtype=np.float32)
         cprm = lambda **kw: S.stml_default_params(n_levels=L, n_tlevels=Q, image_dtype=2, pcg_cooperative=0, **kw)
-        comb = [S.Context(cprm(), st.cuda_stream) for st in streams]
-        nets = [S.Net(params, max_batch=32, max_h=256, max_w=256, stream=st.cuda_stream) for st in streams]
+        comb = [S.Context(cprm(), st) for st in streams]
+        nets = [S.Net(params, max_batch=32, max_h=256, max_w=256, stream=st) for st in streams]
         for c, net in zip(comb, nets):
             S.stml_set_predictor_net(c, net)
         t_comb = timed(lambda: S.stml_register_batch(comb, mode), comb)
@@ -547,6 +586,8 @@ def run_batch(S, torch, dev, mode, count: int, with_combined: bool):
                 "max_abs_rel_diff": max(abs(r) for r in rel)}}
     for c in ctxs:
         c.close()
+    torch.cuda.synchronize()
+    raw.close()
     return out
 
 

@@ -226,8 +226,16 @@ def batch(S, torch, synthetic, dev, args):
     for _ in range(max(1, args.warmup)):
         bt.register(0)
     torch.cuda.synchronize()
+    reports = []
+    for _ in range(max(1, args.iters)):
+        for c, R in zip(ctxs, seqs):
+            S.stml_load_sequence(c.ptr, R)
+            S.stml_build_pyramid(c.ptr)
+        bt.register(0)
+        reports.append(bt.report())
+    torch.cuda.synchronize()
     print(json.dumps({"op": "batch", "sequences": len(seqs), "frames": sum(int(r.shape[0]) for r in seqs),
-                      "stages": bt.report()}), flush=True)
+                      "shapes": [list(r.shape) for r in seqs], "stages": reports}), flush=True)
     bt.close()
     for c in ctxs:
         c.close()

@@ -234,3 +234,25 @@ def test_batch_target_objective_lands_per_sequence(S, mode):
         batch.close()
         for c in ctxs:
             c.close()
+
+
+def test_batch_of_one_and_a_stationary_sequence(S):
+    """Degenerate batches: a single sequence (its GIRs get the whole grid),
+    and a sequence of identical frames, where u = 0 is stationary and every
+    GIR stops at its first evaluation with the fields exactly zero."""
+    base = synthetic.make_sequence(synthetic.spec_custom(1, (32, 32), seed=3))
+    still = np.repeat(base, 6, axis=0)
+    one = _uneven_2d(True)[1]
+    for seqs in ([one], [still, one]):
+        ctxs, prm = _contexts(S, seqs, n_levels=2, n_tlevels=2)
+        batch = S.Batch(ctxs)
+        try:
+            assert batch.register(0) == [0] * len(seqs)
+            _check_against_oracle(S, ctxs, seqs, prm, 0)
+            if len(seqs) == 2:
+                assert all(s["gn_iters"] == 0 and s["cg_iters"] == 0 for s in S.stml_last_stats(ctxs[0].ptr))
+                assert float(np.abs(_field(S, ctxs[0], still)).max()) == 0.0
+        finally:
+            batch.close()
+            for c in ctxs:
+                c.close()
