@@ -178,6 +178,24 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
+// 32 consecutive columns of the thread's TMEM lane: the load and its wait in
+// one asm statement, so no instruction can read the registers early.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
@@ -291,10 +309,17 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
         const int y = y0 + (tid >> 3), x = x0 + (tid & 7);
         const bool valid = y < H && x < W;
         const long long m = ((long long)pn * H + y) * W + x;
+        // 32 columns per TMEM load and wait
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 8) {
+        for (int c32 = 0; c32 < BN; c32 += 32) {
+        float vv[32];
+        tc_ld32(trow + (uint32_t)c32, vv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
             float v[8];
-            tc_ld8(trow + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = vv[8 * i + j];
+            const int c0 = c32 + 8 * i;
             if (!valid) continue;
             const int n = n0 + c0;
             if (out.mode == CONV_FWD) {
@@ -312,6 +337,7 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
                 reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
                 reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
+        }
         }
         tc_fence_before();   // ordered before the barrier that precedes the buffer's next MMA
     };
@@ -354,13 +380,15 @@ __global__ void __launch_bounds__(128) conv3_kernel(ConvIn in, const bf16* __res
                 }
                 tc_commit(bars + 8 * st);
             }
-            if (c == 0 && prev_tile >= 0) epilogue(prev_tile, buf ^ 1);
-            // prefetch the next item (this tile's next chunk, or the next tile's first)
+            // prefetch the next item (this tile's next chunk, or the next tile's
+            // first) before the previous tile's epilogue, so that the copies
+            // proceed while the epilogue reads TMEM
             if (c + 1 < nch)
                 load_stage(st ^ 1, tile, c + 1);
             else if (tile + (int)gridDim.x < tiles)
                 load_stage(st ^ 1, tile + gridDim.x, 0);
             cp_commit();
+            if (c == 0 && prev_tile >= 0) epilogue(prev_tile, buf ^ 1);
         }
         prev_tile = tile;
     }
@@ -422,59 +450,65 @@ cudaError_t launch_conv3(const ConvIn& in, const bf16* Wh, int Cin, int N, int B
 }
 
 // --------------------------------------------------------- weight gradient
-// dW[tap][ci][co] = sum_p X[p + off(tap)][ci] G[p][co] as a tensor-core GEMM
-// (tcgen05.mma kind::f16, BF16 operands, FP32 accumulator in TMEM) with
-// M = 4 taps x 32 input channels (TMEM lane = tap-in-group * 32 + ci),
-// N = BN output channels and K = pixels.  A CTA owns one group of four taps
-// (the third group holds tap 8 and three zero taps), one chunk of 32 input
-// channels, BN output channels and one slice of pixels, in stages of 64
-// pixels: the shifted inputs of its four taps and the output gradients are
-// gathered (cp.async; zero outside the image and past the slice) straight
-// from the channels-last maps into the no-swizzle MN-major core-matrix layout
-// -- a core matrix holds 8 pixels (rows of 16 bytes) x 8 consecutive
-// channels, core matrices along M (or N) 128 bytes apart, along K (8-pixel
-// groups) one stage row apart -- and one thread issues 4 MMAs (K = 16) per
-// stage, committed to the stage's mbarrier; three stages in flight.  Every
-// wait is bounded (*err as in conv3_kernel).
-template <int BN>
+// dW[tap][ci][co] = sum_p G[p][co] X[p + off(tap)][ci] as tensor-core GEMMs
+// (tcgen05.mma kind::f16, BF16 operands, FP32 accumulators in TMEM), one per
+// tap: M = 128 output channels (TMEM lanes; rows past the layer's channels
+// are zero), N = 32 input channels, K = pixels.  A CTA owns one block of 128
+// output channels, one chunk of 32 input channels and a run of 8 x 8 pixel
+// tiles; the nine taps accumulate in TMEM columns 32 tap .. 32 tap + 31.  Per
+// tile the output gradients G (64 pixels x 128 channels) and the input's
+// 10 x 10 halo (32 channels) are gathered once by cp.async (zero outside the
+// image) into no-swizzle MN-major core-matrix layouts: G as [8 tile rows]
+// [16 channel groups][8 pixels][8 ch], the halo as [4 channel groups]
+// [10 x 10 pixels][8 ch].  The B operand of tap (dy, dx) is the halo seen
+// through a descriptor that starts at halo pixel (1 + dy, 1 + dx): its 8-pixel
+// core-matrix rows are 8 consecutive halo pixels, the next tile row is 10
+// pixels on, the next channel group 100 pixels on.  36 MMAs (9 taps x 4 steps
+// of 16 pixels) per tile, issued by one thread and committed to the stage's
+// mbarrier; three stages; every wait bounded (*err as in conv3_kernel).
+namespace {
+constexpr int kWgHalo = 10;                                   // 8 x 8 tile + 1-pixel border
+constexpr int kWgHaloPx = kWgHalo * kWgHalo;
+}  // namespace
+
 struct WgCfg {
-    static constexpr int PX = 64;                      // pixels per stage
     static constexpr int STAGES = 3;
-    static constexpr uint32_t A_SBO = 128;             // between 8-lane groups (M)
-    static constexpr uint32_t A_LBO = 16 * 128;        // between 8-pixel groups (K)
-    static constexpr uint32_t B_SBO = 128;             // between 8-channel groups (N)
-    static constexpr uint32_t B_LBO = (BN / 8) * 128;
-    static constexpr int A_BYTES = (PX / 8) * (int)A_LBO;   // 16 KB
-    static constexpr int B_BYTES = (PX / 8) * (int)B_LBO;
-    static constexpr int SMEM = 128 + STAGES * (A_BYTES + B_BYTES) + 64;
-    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : 128;
-    // F32 accumulator, BF16 A and B, both MN-major (transposed), N = BN, M = 128
+    static constexpr uint32_t A_SBO = 128;                    // between 8-channel groups (M)
+    static constexpr uint32_t A_LBO = 16 * 128;               // between tile rows (K)
+    static constexpr int A_BYTES = 8 * (int)A_LBO;            // 64 pixels x 128 channels
+    static constexpr uint32_t B_LBO = kWgHalo * 16;           // next tile row in the halo (K)
+    static constexpr uint32_t B_SBO = kWgHaloPx * 16;         // next channel group (N)
+    static constexpr int B_BYTES = 4 * kWgHaloPx * 16;        // 10 x 10 pixels x 32 channels
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    // at least half the SM's shared memory: one CTA per SM, which owns all
+    // 512 TMEM columns (nine accumulators of 32)
+    static constexpr int SMEM_USED = 128 + STAGES * STAGE + 64;
+    static constexpr int SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
+    static constexpr int TMEM_COLS = 512;
+    // F32 accumulator, BF16 A and B, both MN-major (transposed), N = 32, M = 128
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                                      ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+                                      ((uint32_t)(32 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 };
 
-template <int BN>
 __global__ void __launch_bounds__(128) wgrad_tc_kernel(ConvIn in, const bf16* __restrict__ G, int Cin, int N,
-                                                       int B, int H, int W, long long chunk,
+                                                       int B, int H, int W, int tiles_per_slice,
                                                        float* __restrict__ part, int* __restrict__ err) {
-    using C = WgCfg<BN>;
+    using C = WgCfg;
     extern __shared__ unsigned char wg_smem_raw[];
     const uint32_t raw = smem_u32(wg_smem_raw);
     const uint32_t base = (raw + 127u) & ~127u;
     unsigned char* gbase = wg_smem_raw + (base - raw);
-    const uint32_t sA = base, sB = base + C::STAGES * C::A_BYTES;
-    const uint32_t bars = sB + C::STAGES * C::B_BYTES;   // STAGES mbarriers
+    const uint32_t bars = base + C::STAGES * C::STAGE;          // STAGES mbarriers
     uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (bars - base) + 8 * C::STAGES);
-    unsigned char* gA = gbase;
-    unsigned char* gB = gbase + C::STAGES * C::A_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cpt = Cin / 32;
-    const int tg = blockIdx.x / cpt, cch = blockIdx.x - tg * cpt;   // taps 4 tg .. 4 tg + 3, channel chunk
-    const int n0 = blockIdx.y * BN;
-    const long long HW = (long long)H * W, M = (long long)B * HW;
-    const long long pb = (long long)blockIdx.z * chunk;
-    const long long pe = pb + chunk < M ? pb + chunk : M;
-    const int nst = pe > pb ? (int)((pe - pb + C::PX - 1) / C::PX) : 0;
+    const int cch = blockIdx.x;                                  // input-channel chunk
+    const int co0 = blockIdx.y * 128;                            // output-channel block
+    const int ncol = N - co0 < 128 ? N - co0 : 128;              // real output channels (multiple of 8)
+    const int tx = (W + 7) >> 3, ty = (H + 7) >> 3;
+    const int ntiles = B * ty * tx;
+    const int t_begin = blockIdx.z * tiles_per_slice;
+    const int t_end = t_begin + tiles_per_slice < ntiles ? t_begin + tiles_per_slice : ntiles;
+    const int nst = t_end > t_begin ? t_end - t_begin : 0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -486,53 +520,46 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(ConvIn in, const bf16* __
         for (int i = 0; i < C::STAGES; ++i) mbar_init(bars + 8 * i, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    // channel groups past the layer's channels stay zero in every stage
+    for (int i = tid; i < C::STAGES * 64 * 16; i += 128) {   // (stage, tile row, pixel, channel group)
+        const int g = i & 15, rest = i >> 4;
+        if (g * 8 < ncol) continue;
+        const int st = rest / 64, r = (rest % 64) >> 3, k = rest & 7;
+        *reinterpret_cast<uint4*>(gbase + st * C::STAGE + r * C::A_LBO + g * C::A_SBO + k * 16) =
+            make_uint4(0, 0, 0, 0);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    // (image, row, column) of the stage's pixels, computed once per stage
-    __shared__ int s_pix[C::PX][3];
     auto load_stage = [&](int st, int it) {
-        const long long p0 = pb + (long long)it * C::PX;
-        __syncthreads();   // the previous stage's copies have read s_pix
-        if (tid < C::PX) {
-            const long long p = p0 + tid;
-            int n = -1, y = 0, x = 0;
-            if (p < pe) {
-                n = (int)(p / HW);
-                const int rem = (int)(p - (long long)n * HW);
-                y = rem / W;
-                x = rem - y * W;
-            }
-            s_pix[tid][0] = n;
-            s_pix[tid][1] = y;
-            s_pix[tid][2] = x;
+        int t = t_begin + it;
+        const int txi = t % tx;
+        t /= tx;
+        const int tyi = t % ty;
+        const int pn = t / ty;
+        const int y0 = tyi * 8, x0 = txi * 8;
+        unsigned char* a_st = gbase + st * C::STAGE;
+        unsigned char* b_st = a_st + C::A_BYTES;
+        const int ng = ncol >> 3;
+        for (int i = tid; i < 64 * ng; i += 128) {              // G: (pixel, channel group)
+            const int k = i / ng, g = i - k * ng;
+            const int y = y0 + (k >> 3), x = x0 + (k & 7);
+            const bool ok = y < H && x < W;
+            const bf16* src = ok ? G + (((long long)pn * H + y) * W + x) * N + co0 + g * 8 : G;
+            cp16(a_st + (k >> 3) * C::A_LBO + g * C::A_SBO + (k & 7) * 16, src, ok ? 16 : 0);
         }
-        __syncthreads();
-        unsigned char* a_st = gA + st * C::A_BYTES;
-        for (int sidx = tid; sidx < C::PX * 16; sidx += 128) {   // (pixel, lane group = tap * 4 + channel group)
-            const int k = sidx >> 4, mg = sidx & 15;
-            const int t = tg * 4 + (mg >> 2);
-            const int n = s_pix[k][0];
-            const bf16* src = nullptr;
-            if (n >= 0 && t < 9)
-                src = in_at(in, n, s_pix[k][1] + t / 3 - 1, s_pix[k][2] + t % 3 - 1, H, W, cch * 32 + (mg & 3) * 8);
-            cp16(a_st + (k >> 3) * C::A_LBO + mg * C::A_SBO + (k & 7) * 16, src ? src : in.a, src ? 16 : 0);
-        }
-        unsigned char* b_st = gB + st * C::B_BYTES;
-        constexpr int NG = BN / 8;
-        for (int sidx = tid; sidx < C::PX * NG; sidx += 128) {   // (pixel, channel group)
-            const int k = sidx / NG, ng = sidx - k * NG;
-            const long long p = p0 + k;
-            const bool ok = p < pe;
-            cp16(b_st + (k >> 3) * C::B_LBO + ng * C::B_SBO + (k & 7) * 16, ok ? G + p * N + n0 + ng * 8 : G,
-                 ok ? 16 : 0);
+        for (int i = tid; i < kWgHaloPx * 4; i += 128) {        // halo: (pixel, channel group)
+            const int hp = i >> 2, g = i & 3;
+            const int hy = hp / kWgHalo, hx = hp - hy * kWgHalo;
+            const bf16* src = in_at(in, pn, y0 - 1 + hy, x0 - 1 + hx, H, W, cch * 32 + g * 8);
+            cp16(b_st + g * C::B_SBO + hp * 16, src ? src : in.a, src ? 16 : 0);
         }
     };
 
     bool ok = true;
-    int waited = -1;   // the last item whose MMAs were waited for
+    int waited = -1;
 #pragma unroll 1
     for (int sg = 0; sg < C::STAGES - 1; ++sg) {
         if (sg < nst) load_stage(sg, sg);
@@ -543,21 +570,26 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(ConvIn in, const bf16* __
         const int st = it % C::STAGES;
         cp_wait<C::STAGES - 2>();
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();   // every thread's copies of item it have landed
+        __syncthreads();   // every thread's copies of tile it have landed
         tc_fence_after();
         if (tid == 0) {
+            const uint32_t a0 = base + st * C::STAGE, b0 = a0 + C::A_BYTES;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - 3 * (tap / 3);   // halo offsets 0..2
 #pragma unroll
-            for (int ks = 0; ks < C::PX / 16; ++ks) {
-                const uint64_t ad = plain_desc(sA + st * C::A_BYTES + 2 * ks * C::A_LBO, C::A_LBO, C::A_SBO);
-                const uint64_t bd = plain_desc(sB + st * C::B_BYTES + 2 * ks * C::B_LBO, C::B_LBO, C::B_SBO);
-                tc_mma(tmem, ad, bd, C::IDESC, (it > 0 || ks > 0) ? 1u : 0u);
+                for (int ks = 0; ks < 4; ++ks) {                    // tile rows 2 ks, 2 ks + 1
+                    const uint64_t ad = plain_desc(a0 + 2 * ks * C::A_LBO, C::A_LBO, C::A_SBO);
+                    const uint64_t bd =
+                        plain_desc(b0 + ((2 * ks + dy) * kWgHalo + dx) * 16, C::B_LBO, C::B_SBO);
+                    tc_mma(tmem + (uint32_t)(tap * 32), ad, bd, C::IDESC, (it > 0 || ks > 0) ? 1u : 0u);
+                }
             }
             tc_commit(bars + 8 * st);
         }
-        // refill the stage of item it - 1 once its MMAs are done
         const int nx = it + C::STAGES - 1;
         if (nx < nst) {
-            if (it >= 1) {
+            if (it >= 1) {   // the stage of tile it - 1 is refilled once its MMAs are done
                 if (tid == 0)
                     ok = mbar_wait(bars + 8 * ((it - 1) % C::STAGES), (uint32_t)(((it - 1) / C::STAGES) & 1));
                 if (!__syncthreads_and(ok)) {
@@ -570,7 +602,6 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(ConvIn in, const bf16* __
         }
         cp_commit();
     }
-    // the last item: its MMAs complete after all earlier ones
     if (ok && nst > 0) {
         const int j = nst - 1;
         if (tid == 0) ok = mbar_wait(bars + 8 * (j % C::STAGES), (uint32_t)((j / C::STAGES) & 1));
@@ -579,30 +610,28 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(ConvIn in, const bf16* __
     }
     tc_fence_after();
     if (ok) {
-        // TMEM lane 32 w + l: tap 4 tg + w, channel cch * 32 + l
-        const int t = tg * 4 + warp;
+        // TMEM lane 32 w + l = output channel co0 + 32 w + l; column 32 tap + i = input channel cch * 32 + i
+        const int co = co0 + warp * 32 + lane;
         const long long K = 9LL * Cin;
-        float* dst = part + (long long)blockIdx.z * K * N + ((long long)t * Cin + cch * 32 + lane) * N + n0;
+        float* dst = part + (long long)blockIdx.z * K * N;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 8) {
-            float v[8];
+        for (int tap = 0; tap < 9; ++tap) {
+            float v[32];
             if (nst > 0) {
-                tc_ld8(trow + (uint32_t)c0, v);
+                tc_ld32(trow + (uint32_t)(tap * 32), v);
             } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = 0.f;
+                for (int i = 0; i < 32; ++i) v[i] = 0.f;
             }
-            if (t < 9) {
-                reinterpret_cast<float4*>(dst + c0)[0] = make_float4(v[0], v[1], v[2], v[3]);
-                reinterpret_cast<float4*>(dst + c0)[1] = make_float4(v[4], v[5], v[6], v[7]);
+            if (co < N) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) dst[((long long)tap * Cin + cch * 32 + i) * N + co] = v[i];
             }
         }
     }
     cp_wait<0>();
     if (!ok && tid == 0) {
-        // MMAs of the items after the last one waited for may still run: one
-        // more bounded wait on the newest committed item before TMEM is freed
         const int j = nst - 1;
         bool drained = true;
         if (j > waited && j >= 0) drained = mbar_wait(bars + 8 * (j % C::STAGES), (uint32_t)((j / C::STAGES) & 1));
@@ -620,35 +649,28 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(ConvIn in, const bf16* __
 
 cudaError_t launch_wgrad3(const ConvIn& in, const bf16* G, int Cin, int N, int B, int H, int W,
                           float* part, size_t part_cap, int* splits, int* err, cudaStream_t s) {
-    if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 ||
+    if (Cin % 32 || N % 32 || in.ca % 32 || in.cb % 32 || in.ca + in.cb != Cin || B <= 0 || H <= 0 || W <= 0 ||
         (in.up && ((H | W) & 1)) || !err)
         return cudaErrorInvalidValue;
-    const long long M = (long long)B * H * W;
-    const int BN = N % 128 == 0 ? 128 : N % 64 == 0 ? 64 : 32;
-    const long long tiles = 3LL * (Cin / 32) * (N / BN);
+    const long long ntiles = (long long)B * ((H + 7) / 8) * ((W + 7) / 8);
+    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int cblocks = (N + 127) / 128;
+    const long long ctas = (long long)(Cin / 32) * cblocks;
     const long long per = 9LL * Cin * N;
     const int sms = device_sms();
-    long long S = ((long long)2 * (sms > 0 ? sms : 152) + tiles - 1) / tiles;
-    const long long max_s = (M + 63) / 64;
-    if (S > max_s) S = max_s;
+    long long S = ((sms > 0 ? sms : 152) + ctas - 1) / ctas;   // about one CTA per SM
+    if (S > ntiles) S = ntiles;
     if (S > (long long)(part_cap / per)) S = (long long)(part_cap / per);
     if (S < 1) return cudaErrorInvalidValue;
-    long long chunk = (M + S - 1) / S;
-    chunk = (chunk + 63) / 64 * 64;
-    S = (M + chunk - 1) / chunk;
+    const long long tps = (ntiles + S - 1) / S;
+    S = (ntiles + tps - 1) / tps;
     *splits = (int)S;
-    dim3 grid((unsigned)(3 * (Cin / 32)), N / BN, (unsigned)S);
-    auto go = [&](auto tag) -> cudaError_t {
-        constexpr int bn = decltype(tag)::value;
-        using C = WgCfg<bn>;
-        const cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(wgrad_tc_kernel<bn>), C::SMEM);
-        if (e != cudaSuccess) return e;
-        wgrad_tc_kernel<bn><<<grid, 128, C::SMEM, s>>>(in, G, Cin, N, B, H, W, chunk, part, err);
-        return cudaGetLastError();
-    };
-    if (BN == 128) return go(std::integral_constant<int, 128>{});
-    if (BN == 64) return go(std::integral_constant<int, 64>{});
-    return go(std::integral_constant<int, 32>{});
+    using C = WgCfg;
+    const cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(wgrad_tc_kernel), C::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(Cin / 32), (unsigned)cblocks, (unsigned)S);
+    wgrad_tc_kernel<<<grid, 128, C::SMEM, s>>>(in, G, Cin, N, B, H, W, (int)tps, part, err);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ column sums
@@ -687,48 +709,51 @@ cudaError_t launch_colsum(const bf16* G, long long P, int N, float* part, size_t
     return cudaGetLastError();
 }
 
-__global__ void reduce_grad_kernel(const float* __restrict__ wpart, int ws, int cin, int cin_real, int N,
-                                   const float* __restrict__ bpart, int bs, float* __restrict__ grad,
-                                   long long w_off, long long b_off) {
+// Fixed-order sum of the slice partials.  A block owns 32 consecutive output
+// elements; warp w adds slices w, w + 8, w + 16, ... in order (each load a
+// coalesced 128-byte row), and warp 0 adds the eight warp sums in order: the
+// result depends only on the slice count, never on timing.
+__global__ void __launch_bounds__(256) reduce_grad_kernel(const float* __restrict__ wpart, int ws, int cin,
+                                                          int cin_real, int N, const float* __restrict__ bpart,
+                                                          int bs, float* __restrict__ grad, long long w_off,
+                                                          long long b_off) {
+    __shared__ float red[8][33];
     const long long nW = 9LL * cin_real * N;
     const long long per = 9LL * cin * N;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nW + N;
-         i += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (long long blk = blockIdx.x; blk * 32 < nW + N; blk += gridDim.x) {
+        const long long i = blk * 32 + lane;
+        float v = 0.f;
         if (i < nW) {
             const int co = (int)(i % N);
             const long long k = i / N;
             const int ci = (int)(k % cin_real);
             const int tap = (int)(k / cin_real);
-            const long long src = ((long long)tap * cin + ci) * N + co;
-            // slices summed in order; loads issued eight at a time
-            float v = 0.f;
-            int s = 0;
-            for (; s + 8 <= ws; s += 8) {
-                float t[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) t[k] = wpart[(s + k) * per + src];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v += t[k];
-            }
-            for (; s < ws; ++s) v += wpart[s * per + src];
-            grad[w_off + i] = v;
-        } else {
-            const int co = (int)(i - nW);
-            float v = 0.f;
-            for (int s = 0; s < bs; ++s) v += bpart[(long long)s * N + co];
-            grad[b_off + co] = v;
+            const float* src = wpart + ((long long)tap * cin + ci) * N + co;
+#pragma unroll 4
+            for (int sl = w; sl < ws; sl += 8) v += __ldg(src + (long long)sl * per);
+        } else if (i < nW + N) {
+            const float* src = bpart + (i - nW);
+            for (int sl = w; sl < bs; sl += 8) v += __ldg(src + (long long)sl * N);
         }
+        red[w][lane] = v;
+        __syncthreads();
+        if (w == 0 && i < nW + N) {
+            float t = red[0][lane];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) t += red[k][lane];
+            grad[i < nW ? w_off + i : b_off + (i - nW)] = t;
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_reduce_grad(const float* wpart, int ws, int cin, int cin_real, int N,
                                const float* bpart, int bs, float* grad, long long w_off,
                                long long b_off, cudaStream_t s) {
-    const long long n = 9LL * cin_real * N + N;
-    long long blocks = (n + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    reduce_grad_kernel<<<(unsigned)blocks, 256, 0, s>>>(wpart, ws, cin, cin_real, N, bpart, bs, grad,
-                                                        w_off, b_off);
+    const long long nblk = (9LL * cin_real * N + N + 31) / 32;
+    const unsigned blocks = (unsigned)(nblk < 8192 ? nblk : 8192);
+    reduce_grad_kernel<<<blocks, 256, 0, s>>>(wpart, ws, cin, cin_real, N, bpart, bs, grad, w_off, b_off);
     return cudaGetLastError();
 }
 
