@@ -679,8 +679,8 @@ def run_learned(S, torch, dev, peaks):
                                 "unit": "TFLOP/s", "frac": alg / step_s / 1e12 / peak,
                                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)" if peaks
                                 else "fallback 1.9 PFLOP/s (of fallback)",
-                                "note": "whole training step (mma.sync BF16 convolutions plus "
-                                        "the FP32 elementwise and reduction kernels)"},
+                                "note": "whole training step (tcgen05 BF16 convolutions and weight "
+                                        "gradients plus the FP32 elementwise and reduction kernels)"},
             "forward": {"batch": "16 canvases of 256x256", "ms": fwd_ms,
                         "tflops_algorithmic": fwd_flops / (fwd_ms / 1e3) / 1e12,
                         "frac_of_bf16_peak": fwd_flops / (fwd_ms / 1e3) / 1e12 / peak,
