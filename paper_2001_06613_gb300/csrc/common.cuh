@@ -14,6 +14,20 @@ enum StoreType { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 
 inline size_t store_bytes(int st) { return st == ST_F32 ? 4 : 2; }
 
+// Entry of a kernel that may be launched as a programmatic dependent launch
+// (the launch starts its CTAs while the previous kernel of the stream is
+// still finishing).  griddepcontrol.wait blocks until every grid this launch
+// depends on has completed and its memory is visible, so it comes before
+// any global load or store and before any early return (a kernel that left
+// without waiting could complete before its predecessor, and the kernel
+// after it would then no longer be ordered after that predecessor).  Then
+// launch_dependents lets the next kernel of the stream start its own CTAs,
+// which wait in turn.  Both are no-ops in a launch without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // One value of a stored array, as float (read-only path), and its store
 // (round to nearest even).
 __device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }

@@ -168,6 +168,7 @@ obj_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, 
            const float* __restrict__ du, float t, const float* __restrict__ gdot, float* __restrict__ abar,
            float* __restrict__ ubar, double* __restrict__ partials, unsigned int* ticket, double* out,
            LineSearchArgs ls) {
+    pdl_enter();
     // a later Armijo trial has nothing to do once an earlier one decided
     if (ls.S && ls.k > 0 && (ls.S->ls_accepted || ls.S->ls_nodescent)) return;
     constexpr int FG = kThreads / 32, SEG = 32 * VEC;
@@ -463,6 +464,7 @@ grad_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FastDiv chunks, long 
             Coef cf, FView U, const float* __restrict__ abar, const float* __restrict__ ubar,
             float* __restrict__ grad, TD* __restrict__ dTout, float* __restrict__ unew,
             double* __restrict__ partials, unsigned int* ticket, double* out, const DevScalars* gate) {
+    pdl_enter();
     if (gate) {   // the accepted step of a line search decided on the device
         if (!gate->ls_accepted) return;
         U.t = gate->ls_t;
@@ -684,13 +686,18 @@ static cudaError_t obj_go(const ObjShape& sh, cudaStream_t s, const TI* T, const
         if (e != cudaSuccess) return e;
         lc.dynamicSmemBytes = ring;
     }
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 1;
-    at[0].val.clusterDim.y = (unsigned)sh.splits;
-    at[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute at[2];
+    unsigned na = 0;
+    if (sh.splits > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = 1;
+        at[na].val.clusterDim.y = (unsigned)sh.splits;
+        at[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    na += pdl_attr(s, at + na);
     lc.attrs = at;
-    lc.numAttrs = sh.splits > 1 ? 1 : 0;
+    lc.numAttrs = na;
     return cudaLaunchKernelEx(&lc, obj_kernel<D, VEC, TRIAL, GDOT, TI>, T, g, pi, fs, cf, u, du, t, gdot, abar, ubar,
                               partials, ticket, out, ls);
 }
@@ -768,8 +775,9 @@ cudaError_t launch_gradient(const Stored& T, const Geom& g, const FrameSet& fs, 
         auto k = grad_kernel<D_, V_, TI, TD>;                                                             \
         const unsigned blocks = resident_grid((const void*)k, items, kGridStride);                        \
         if ((size_t)blocks * 2 > partials_cap) return cudaErrorInvalidValue;                              \
-        k<<<blocks, kThreads, 0, s>>>(Ti, g, pi, chunks, items, fs, cf, U, abar, ubar, grad, Td, unew, partials, \
-                                      ticket, out, gate);                                                 \
+        const cudaError_t le = launch_pdl(k, dim3(blocks), dim3(kThreads), 0, s, Ti, g, pi, chunks, items, fs, cf, U, \
+                                          abar, ubar, grad, Td, unew, partials, ticket, out, gate);       \
+        if (le != cudaSuccess) return le;                                                                 \
     } while (0)
         if (g.d == 2) {
             if (v4) STML_GRAD(2, 4); else STML_GRAD(2, 1);

@@ -46,6 +46,7 @@ tile_kernel(Geom g, PixIndex pi, FrameSet fs, Coef cf, const TD* __restrict__ dT
             float* __restrict__ mean_s, float* __restrict__ sum_v, double* __restrict__ partials, DevScalars* S,
             PcgArgs a, const int* gate) {
     static_assert(MODE != TILE_UPDATE, "the update runs as a grid-stride stream");
+    pdl_enter();
     if (MODE == TILE_DIR && !S->cg_active) return;
     if (gate && !*gate) return;
     __shared__ float sh[(kThreads / TPR) * (1 + D) * TPR * VEC];
@@ -107,6 +108,7 @@ update_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs,
               const TD* __restrict__ dT, float* __restrict__ x, float* __restrict__ r,
               const float* __restrict__ p, const float* __restrict__ q, double* __restrict__ partials,
               const double* __restrict__ pq_partials, DevScalars* S, PcgArgs a) {
+    pdl_enter();
     if (!S->cg_active) return;
     CgState st = cg_load(S);
     {
@@ -148,6 +150,7 @@ __global__ void __launch_bounds__(kThreads, (apply_min_ctas<D, VEC>()))
 apply_kernel(Geom g, PixIndex pi, FastDiv chunks, long long items, FrameSet fs, Coef cf,
              const TD* __restrict__ dT, DirSrc src, float* __restrict__ Hv, double* __restrict__ partials,
              unsigned int* ticket, double* out, DevScalars* pcg) {
+    pdl_enter();
     if (pcg && !pcg->cg_active) return;
     float acc[1] = {0.f};
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
@@ -266,8 +269,9 @@ cudaError_t tile_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const
     const int seg = v4 ? (narrow ? 16 : 64) : (narrow ? 8 : 32);
     const unsigned blocks = (unsigned)((g.N + seg - 1) / seg);
 #define STML_TILE(D_, V_, T_)                                                                                      \
-    tile_kernel<D_, V_, MODE, T_, TD><<<blocks, kThreads, 0, s>>>(g, pi, fs, cf, Td, v, r, grad, x, mean_s, sum_v, \
-                                                                  partials, S, a, gate)
+    e = launch_pdl(tile_kernel<D_, V_, MODE, T_, TD>, dim3(blocks), dim3(kThreads), 0, s, g, pi, fs, cf, Td, v, r,  \
+                   grad, x, mean_s, sum_v, partials, S, a, gate)
+    cudaError_t e = cudaSuccess;
     with_store_type(dT.type, [&](auto tag) {
         using TD = decltype(tag);
         const TD* Td = static_cast<const TD*>(dT.p);
@@ -283,7 +287,7 @@ cudaError_t tile_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const
     });
 #undef STML_TILE
     count_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t apply_launch(const Geom& g, const FrameSet& fs, const Coef& cf, const Stored& dT, const DirSrc& src,
@@ -302,9 +306,11 @@ cudaError_t apply_launch(const Geom& g, const FrameSet& fs, const Coef& cf, cons
                           : (v4 ? apply_kernel<3, 4, TD> : apply_kernel<3, 1, TD>);
         const unsigned grid = resident_grid((const void*)k, items, kGridStride);
         if ((size_t)grid > partials_cap) return cudaErrorInvalidValue;
-        k<<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, src, Hv, partials, ticket, out, pcg);
+        const cudaError_t e =
+            launch_pdl(k, dim3(grid), dim3(kThreads), 0, s, g, pi, chunks, items, fs, cf, Td, src, Hv, partials, ticket,
+                       out, pcg);
         count_launches(1);
-        return cudaGetLastError();
+        return e != cudaSuccess ? e : cudaGetLastError();
     });
 }
 
@@ -362,10 +368,10 @@ cudaError_t launch_pcg_update(const Geom& g, const FrameSet& fs, const Coef& cf,
                           : (v4 ? update_kernel<3, 4, TD> : update_kernel<3, 1, TD>);
         const unsigned grid = resident_grid((const void*)k, items, kGridStride);
         if ((size_t)grid * 2 > kPqOffset || partials_cap < kPqOffset + kGridStride) return cudaErrorInvalidValue;
-        k<<<grid, kThreads, 0, s>>>(g, pi, chunks, items, fs, cf, Td, b.x, b.r, b.p[0], b.q, partials,
-                                    partials + kPqOffset, S, a);
+        const cudaError_t e = launch_pdl(k, dim3(grid), dim3(kThreads), 0, s, g, pi, chunks, items, fs, cf, Td, b.x,
+                                         b.r, b.p[0], b.q, partials, partials + kPqOffset, S, a);
         count_launches(1);
-        return cudaGetLastError();
+        return e != cudaSuccess ? e : cudaGetLastError();
     });
 }
 

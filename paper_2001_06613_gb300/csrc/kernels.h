@@ -27,6 +27,40 @@ auto with_store_type(int st, F&& f) {
     return f(float{});
 }
 
+// Launch attributes of a programmatic dependent launch on stream s: the
+// kernel may start its CTAs while the previous kernel of the stream is still
+// finishing (it waits in pdl_enter until that kernel has completed).  This
+// hides the ~2 us between the end of one kernel and the start of the next in
+// a chain of dependent launches.  Left out while s is being captured into a
+// graph, where the launches keep plain stream order.  Returns the number of
+// attributes written to at (0 or 1).
+inline unsigned pdl_attr(cudaStream_t s, cudaLaunchAttribute* at) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    at->id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at->val.programmaticStreamSerializationAllowed = 1;
+    return 1;
+}
+
+// Launches kernel k (whose first statement is pdl_enter()) on `grid` x
+// `block` threads with `smem` bytes of dynamic shared memory on stream s as
+// a programmatic dependent launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    lc.numAttrs = pdl_attr(s, at);
+    lc.attrs = at;
+    return cudaLaunchKernelEx(&lc, k, static_cast<KArgs>(args)...);
+}
+
 // Sets the text stml_last_error(NULL) returns (errors of context-free calls).
 void set_context_free_error(const std::string& msg);
 
