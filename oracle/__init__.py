@@ -19,6 +19,10 @@ Layout of the oracle:
 * ``predictor``  -- the coarse-level linear predictor (Sec. 3) and the
                     least-squares predictor of eq. (2), by Thomas' algorithm and
                     by a dense solve.
+* ``ugrid``      -- displacements on a grid 2^s times coarser than the images:
+                    the prolongation P_s, its transpose (the gradient's
+                    adjoint gather) and the objective, Hessian product and
+                    Jacobi diagonal of the unknowns on that grid.
 * ``multilevel`` -- image pyramid, STML predictor-corrector driver with the
                     stopping rule of eq. (3), and the spatial-only (SpML) driver.
 * ``affine``     -- affine-linear transformations per frame (Sec. 4) solved by
@@ -36,4 +40,4 @@ Every function works in float64 on numpy arrays.  Where the paper is silent the
 oracle follows one stated reading, documented on the function.
 """
 from .params import Params  # noqa: F401
-from . import grid, objective, solver, predictor, multilevel, net, affine  # noqa: F401
+from . import grid, objective, solver, predictor, multilevel, net, affine, ugrid  # noqa: F401

@@ -18,6 +18,11 @@ predictor-corrector sweep over the temporal sets K_0 ... K_T:
 
 SpML: one GIR over all frames per level, started from the prolongated result
 of the previous level (Id on the coarsest).
+
+With ``p.u_coarsen = s > 0`` the fields of every level live on its image grid
+coarsened by 2^s per axis (:mod:`ugrid`); the drivers are unchanged (the
+level-to-level prolongation and the predictors act on those grids, which
+halve from level to level like the images).
 """
 from __future__ import annotations
 
@@ -26,7 +31,7 @@ from typing import List
 
 import numpy as np
 
-from . import grid, objective, predictor, solver
+from . import grid, objective, predictor, solver, ugrid
 from .params import Params
 
 
@@ -70,6 +75,11 @@ def _fill(ell: int, yK, K, z_all, beta):
     return out
 
 
+def _model(T, K, h, p: Params):
+    """The objective of a GIR: None (image-grid fields) or the coarse-grid model."""
+    return ugrid.Model(T, K, h, p.u_coarsen, p) if p.u_coarsen else None
+
+
 def register(R: np.ndarray, p: Params, mode: str = "stml") -> Result:
     n = R.shape[0]
     d = R.ndim - 1
@@ -82,11 +92,11 @@ def register(R: np.ndarray, p: Params, mode: str = "stml") -> Result:
     for ell in range(L):
         T = pyr[ell]
         h = grid.level_h(L, ell)
-        m = T.shape[1:]
+        m = tuple(x // 2 ** p.u_coarsen for x in T.shape[1:])   # grid of the fields
         z_all = np.zeros((n, d) + m) if ell == 0 else grid.prolong_fields(y_prev)
         target = p.target_J if ell == L - 1 else 0.0     # the last GIR over all frames
         if mode == "spml":
-            y_all, st = solver.gauss_newton(T, z_all, allK, h, p, target)
+            y_all, st = solver.gauss_newton(T, z_all, allK, h, p, target, _model(T, allK, h, p))
             res.stats.append(LevelStats(ell, p.n_tlevels - 1, n, st.gn_iters, st.cg_iters,
                                         st.ls_trials, st.J, st.D, st.S, st.P))
         elif mode == "stml":
@@ -94,7 +104,7 @@ def register(R: np.ndarray, p: Params, mode: str = "stml") -> Result:
             dhat_prev = None
             for q, K in enumerate(sets):
                 yK, st = solver.gauss_newton(T[K], z_all[K], K, h, p,
-                                             target if q == len(sets) - 1 else 0.0)
+                                             target if q == len(sets) - 1 else 0.0, _model(T[K], K, h, p))
                 dhat = st.D / len(K)
                 stop = (q > 0 and p.stop_rule and
                         abs(dhat - dhat_prev) <= p.eps_stop * abs(dhat_prev))
@@ -123,6 +133,10 @@ def register(R: np.ndarray, p: Params, mode: str = "stml") -> Result:
 def final_objective(R: np.ndarray, y: np.ndarray, p: Params) -> dict:
     """J, D, S, P over all frames on the finest level at fields y."""
     n = R.shape[0]
+    if p.u_coarsen:
+        ev = ugrid.evaluate(np.asarray(R, dtype=np.float64), y, list(range(n)), 1.0, p.u_coarsen, p,
+                            want_grad=False)
+        return {k: ev[k] for k in ("J", "D", "S", "P")}
     ev = objective.evaluate(np.asarray(R, dtype=np.float64), y, list(range(n)), 1.0, p,
                             want_grad=False)
     return {k: ev[k] for k in ("J", "D", "S", "P")}

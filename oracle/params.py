@@ -34,6 +34,10 @@ class Params:
     # distance of the affine variant: "ssd" (eq. 1 as in the non-parametric
     # path) or "nc" (normalised-correlation reading of the SqN distance, Sec. 2)
     distance: str = "ssd"
+    # displacement grid: the unknowns of every level live on its image grid
+    # coarsened by 2^u_coarsen per axis and are prolonged onto the image grid
+    # (0: the image grid itself); see :mod:`ugrid`
+    u_coarsen: int = 0
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)

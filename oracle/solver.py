@@ -147,12 +147,33 @@ class GirStats:
     cg_residuals: list = field(default_factory=list)   # ||r|| / ||g|| after each CG step, per solve
 
 
+class ImageGridModel:
+    """Eq. (1) with S and P over the fields of the frames in K on the image
+    grid of the level (the default reading): what the Gauss-Newton loop
+    evaluates.  Another discretisation of the unknowns provides the same three
+    methods (``evaluate``, ``hessvec``, ``jacobi``)."""
+
+    def __init__(self, T: np.ndarray, frames: Sequence[int], h: float, p: Params):
+        self.T, self.frames, self.h, self.p = T, frames, h, p
+
+    def evaluate(self, u: np.ndarray, want_grad: bool = True) -> dict:
+        return objective.evaluate(self.T, u, self.frames, self.h, self.p, want_grad=want_grad)
+
+    def hessvec(self, dT: np.ndarray, v: np.ndarray) -> np.ndarray:
+        return objective.hessvec(dT, v, self.frames, self.h, self.p)
+
+    def jacobi(self, dT: np.ndarray) -> np.ndarray:
+        return objective.jacobi_diag(dT, self.frames, self.h, self.p)
+
+
 def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float, p: Params,
-                 target: float = 0.0):
+                 target: float = 0.0, model=None):
     """GIR(K): minimise eq. (1) over the fields of the frames in K, from u0
-    (with target > 0: until J reaches the target objective, see above)."""
+    (with target > 0: until J reaches the target objective, see above).
+    ``model`` replaces the image-grid objective (:class:`ImageGridModel`)."""
+    mdl = model if model is not None else ImageGridModel(T, frames, h, p)
     u = np.array(u0, dtype=np.float64, copy=True)
-    ev = objective.evaluate(T, u, frames, h, p)
+    ev = mdl.evaluate(u)
     J0 = ev["J"]
     st = GirStats(J0=J0)
     J, g = ev["J"], ev["g"]
@@ -174,10 +195,10 @@ def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float,
                 break
         if gnorm <= p.g_abs * (1.0 + abs(J0)) or it >= p.max_gn:
             break
-        Minv = 1.0 / objective.jacobi_diag(ev["dT"], frames, h, p)
+        Minv = 1.0 / mdl.jacobi(ev["dT"])
         dT = ev["dT"]
         rec = []
-        d, steps, _ = pcg(lambda v: objective.hessvec(dT, v, frames, h, p), -g, Minv,
+        d, steps, _ = pcg(lambda v: mdl.hessvec(dT, v), -g, Minv,
                           p.tol_cg, p.max_cg, rec)
         st.cg_residuals.append(rec)
         st.cg_iters += steps
@@ -186,7 +207,7 @@ def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float,
             st.status = "no-descent"
             break
         t, trials, accepted = armijo(
-            lambda s: objective.evaluate(T, u + s * d, frames, h, p, want_grad=False)["J"],
+            lambda s: mdl.evaluate(u + s * d, want_grad=False)["J"],
             J, gTd, p.armijo_c, p.max_ls)
         st.ls_trials += trials
         st.steps.append((steps, trials))
@@ -194,20 +215,20 @@ def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float,
             st.status = "line-search"
             break
         if target > 0.0:
-            Jt = objective.evaluate(T, u + t * d, frames, h, p, want_grad=False)["J"]
+            Jt = mdl.evaluate(u + t * d, want_grad=False)["J"]
             if Jt <= target:
                 t, _, st.landing_evals = land(
-                    lambda s: objective.evaluate(T, u + s * d, frames, h, p, want_grad=False)["J"],
+                    lambda s: mdl.evaluate(u + s * d, want_grad=False)["J"],
                     J, t, Jt, target, p.target_tol)
                 u = u + t * d
-                ev = objective.evaluate(T, u, frames, h, p)
+                ev = mdl.evaluate(u)
                 it += 1
                 st.status = "target"
                 break
         u = u + t * d
         step_norm = t * float(np.sqrt(np.sum(d * d)))
         J_old = J
-        ev = objective.evaluate(T, u, frames, h, p)
+        ev = mdl.evaluate(u)
         J, g = ev["J"], ev["g"]
         it += 1
     st.J, st.D, st.S, st.P = ev["J"], ev["D"], ev["S"], ev["P"]
