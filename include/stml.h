@@ -116,6 +116,19 @@ typedef struct {
                               * Lets registrations that follow different paths
                               * end at the same objective.  0: off (default) */
     double target_tol;       /* relative tolerance of that landing (default 1e-5) */
+    int u_coarsen;           /* s in 0..4: the unknown fields of every level live on its image
+                              * grid coarsened by 2^s per axis (cell width 2^s h) and warp the
+                              * images through u = P_s w, P_s the cell-centred multilinear
+                              * interpolation with clamp-to-edge; the distance of eq. (1) is
+                              * taken on the image grid, S and P of Sec. 2 on the coarse grid,
+                              * and the gradient gathers the image-grid distance gradient
+                              * through P_s^T (a reading of Sec. 2, which leaves the
+                              * discretisation of the transformation to FAIR).  Fields
+                              * (stml_get_field, stml_gir) are then on the coarse grid.  s > 0
+                              * needs transform 0, image_dtype F32 and target_J 0; the
+                              * predictor network is not used and stml_batch_register
+                              * refuses the context; every image axis must be a multiple of
+                              * 2^(n_levels-1+s).  0: the image grid (default) */
 } stml_params;
 
 typedef struct {
@@ -237,9 +250,31 @@ stml_status stml_hessvec(stml_ctx* ctx, int level, const int* frames, int nK,
                          const float* dT, const float* v, float* Hv, double* vHv);
 
 /* Runs the Gauss-Newton/PCG/Armijo scheme on the frames of K starting from
- * u (device, nK * d * N floats, overwritten with the result). */
+ * u (device, nK * d * N floats, overwritten with the result; with
+ * params.u_coarsen = s > 0 the fields are on the coarse grid, nK * d * N / 2^(s d)
+ * floats). */
 stml_status stml_gir(stml_ctx* ctx, int level, const int* frames, int nK, float* u,
                      stml_stats* stats);
+
+/* Coarse displacement grid (params.u_coarsen = s > 0; see stml_params).  The
+ * unknowns w (device, nK * d * Nc floats, Nc = N / 2^(s d) cells of the
+ * coarse grid of the level, layout [frame][component][cells]) warp the images
+ * through u = P_s w.  stml_eval_ugrid: out (host, 6 doubles) = J, D, S, P,
+ * ||g||^2, ||w||^2 with D the distance of eq. (1) at u on the image grid and S,
+ * P of Sec. 2 on the coarse grid; g (coarse, may be NULL) = P_s^T (hd r_k grad
+ * T_k) + alpha hd_w B^T B w_k + alpha_t hd_w (L_t w)_k + 2 lambda hd_w wbar / |K|
+ * (hd_w = (2^s h)^d); dT (image grid, nK * d * N floats, may be NULL) = grad T
+ * at the warped positions; Minv (coarse, may be NULL) = the inverse Jacobi
+ * diagonal of the Gauss-Newton Hessian, (P_s o P_s)^T of the image-grid
+ * distance diagonal plus the regulariser and penalty diagonal.
+ * stml_hessvec_ugrid: Hv = P_s^T H_D P_s v + alpha hd_w B^T B v + alpha_t hd_w
+ * L_t v + 2 lambda hd_w / |K|^2 sum_j v_j (H_D the distance part of the
+ * image-grid Hessian at dT); Hv must not alias v; *vHv (host, may be NULL)
+ * = <v, Hv>.  STML_EINVAL when u_coarsen is 0. */
+stml_status stml_eval_ugrid(stml_ctx* ctx, int level, const int* frames, int nK, const float* w,
+                            double* out, float* g, float* dT, float* Minv);
+stml_status stml_hessvec_ugrid(stml_ctx* ctx, int level, const int* frames, int nK, const float* dT,
+                               const float* v, float* Hv, double* vHv);
 
 /* Affine-linear variant (params.transform = 1; Sec. 4 transformations, Sec. 2
  * L-BFGS).  Frame k's displacement is u_k(x) = W_k (x - c) / rho + b_k with x
@@ -291,6 +326,18 @@ stml_status stml_prolong(const float* coarse, float* fine, int planes, int dim,
 /* Transpose P^T of stml_prolong, as a gather with a fixed summation order. */
 stml_status stml_prolong_adjoint(const float* fine, float* coarse, int planes, int dim,
                                  const int* coarse_shape, void* cuda_stream);
+
+/* The interpolation P_s of the coarse displacement grid (params.u_coarsen):
+ * `planes` planes of fine_shape / 2^s (s in 1..4, every axis of fine_shape a
+ * multiple of 2^s) to fine_shape; per axis, fine cell j takes
+ * (1 - f) w[clamp(i0)] + f w[clamp(i0 + 1)] with i0 + f = (j + 1/2) / 2^s - 1/2.
+ * stml_ugrid_adjoint is its transpose P_s^T, a gather over the 2^(s+1) fine
+ * cells per axis of every coarse cell in a fixed order (no atomics).  Device
+ * arrays; STML_EINVAL for bad shapes. */
+stml_status stml_ugrid_prolong(const float* w, float* u, int planes, int dim, const int* fine_shape, int s,
+                               void* cuda_stream);
+stml_status stml_ugrid_adjoint(const float* u, float* w, int planes, int dim, const int* fine_shape, int s,
+                               void* cuda_stream);
 
 /* Linear temporal predictor (Sec. 3, coarsest level): for every target frame
  * t in `targets` (host, nT frames) z[t] = yK[t] if t is in K, else the linear

@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("armijo_c", C.c_double),
                 ("image_dtype", C.c_int), ("pcg_cooperative", C.c_int), ("autotune", C.c_int),
                 ("transform", C.c_int), ("lbfgs_m", C.c_int), ("max_lbfgs", C.c_int), ("distance", C.c_int),
-                ("target_J", C.c_double), ("target_tol", C.c_double)]
+                ("target_J", C.c_double), ("target_tol", C.c_double), ("u_coarsen", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -131,6 +131,10 @@ _SIGS = {
     "stml_net_conv3_block": (C.c_int, [C.c_int, _fp, _fp, _fp, _fp, _fp, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_int, _vp]),
     "stml_check_bounded_wait": (C.c_int, [_vp, _ip]),
+    "stml_eval_ugrid": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _vp, _dp, _vp, _vp, _vp]),
+    "stml_hessvec_ugrid": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _vp, _vp, _vp, _dp]),
+    "stml_ugrid_prolong": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _ip, C.c_int, _vp]),
+    "stml_ugrid_adjoint": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _ip, C.c_int, _vp]),
 }
 
 
@@ -404,6 +408,31 @@ def stml_gir(ctx, level: int, frames: Sequence[int], u) -> dict:
     st = Stats()
     _check(load().stml_gir(ctx, level, _ints(frames), len(frames), _dev(u), C.byref(st)), ctx)
     return st.as_dict()
+
+
+def stml_eval_ugrid(ctx, level: int, frames: Sequence[int], w, g=None, dT=None, Minv=None) -> np.ndarray:
+    """Objective (J, D, S, P, |g|^2, |w|^2) at coarse-grid fields w (params.u_coarsen > 0)."""
+    out = (C.c_double * 6)()
+    _check(load().stml_eval_ugrid(ctx, level, _ints(frames), len(frames), _dev(w), out, _dev(g), _dev(dT),
+                                  _dev(Minv)), ctx)
+    return np.array(out[:])
+
+
+def stml_hessvec_ugrid(ctx, level: int, frames: Sequence[int], dT, v, Hv) -> float:
+    vhv = C.c_double()
+    _check(load().stml_hessvec_ugrid(ctx, level, _ints(frames), len(frames), _dev(dT), _dev(v), _dev(Hv),
+                                     C.byref(vhv)), ctx)
+    return vhv.value
+
+
+def stml_ugrid_prolong(w, u, planes: int, fine_shape: Sequence[int], s: int, stream=None):
+    _check(load().stml_ugrid_prolong(_dev(w), _dev(u), planes, len(fine_shape), _ints(fine_shape), s,
+                                     _stream(stream)))
+
+
+def stml_ugrid_adjoint(u, w, planes: int, fine_shape: Sequence[int], s: int, stream=None):
+    _check(load().stml_ugrid_adjoint(_dev(u), _dev(w), planes, len(fine_shape), _ints(fine_shape), s,
+                                     _stream(stream)))
 
 
 def stml_corr_coeff(ctx, level: int, n: int) -> np.ndarray:

@@ -131,6 +131,15 @@ struct stml_ctx {
     int pred_learned = -1;
     double J0_classic = 0.0;
 
+    // coarse displacement grid (params.u_coarsen > 0): vectors on the coarse
+    // grid of the finest level for all frames (gradient, PCG x, r, z, p, q,
+    // Jacobi inverse, accepted point) and the reduction scratch of its passes
+    float *ug_g = nullptr, *ug_x = nullptr, *ug_r = nullptr, *ug_z = nullptr, *ug_p = nullptr, *ug_q = nullptr,
+          *ug_m = nullptr, *ug_w = nullptr;
+    double *ug_part = nullptr, *ug_out = nullptr, *ug_outh = nullptr;
+    size_t ug_part_cap = 0;
+    unsigned int* ug_tk = nullptr;
+
     std::vector<stml_stats> last_stats;   // per GIR of the last registration
     std::string err;
 };
@@ -201,6 +210,11 @@ bool valid_params(const stml_params* p, std::string& why) {
         why = "image_dtype must be STML_DTYPE_F32, _F16 or _BF16";
         return false;
     }
+    if (p->u_coarsen < 0 || p->u_coarsen > 4) { why = "u_coarsen must be in 0..4"; return false; }
+    if (p->u_coarsen > 0 && (p->transform != 0 || p->image_dtype != STML_DTYPE_F32 || p->target_J != 0.0)) {
+        why = "u_coarsen > 0 needs transform 0, image_dtype STML_DTYPE_F32 and target_J 0";
+        return false;
+    }
     return true;
 }
 
@@ -220,6 +234,16 @@ Coef make_coef(const Geom& g, const stml_params& p, int nK) {
     return c;
 }
 
+// Grid the fields of a level live on: its image grid, or with u_coarsen =
+// s > 0 that grid coarsened by 2^s per axis (cell width 2^s h).
+Geom field_geom(const stml_ctx* c, int level) {
+    const Geom& g = c->lv[level].g;
+    const int s = c->p.u_coarsen;
+    if (s == 0) return g;
+    int sh3[3] = {g.d == 3 ? g.nz >> s : 1, g.ny >> s, g.nx >> s};
+    return make_geom(sh3, g.d, g.h * (float)(1 << s));
+}
+
 void free_buffers(stml_ctx* c) {
     for (auto& L : c->lv) {
         dfree(L.img);
@@ -230,6 +254,13 @@ void free_buffers(stml_ctx* c) {
     dfree(c->w_p); dfree(c->w_q); dfree(c->w_ut); dfree(c->w_abar); dfree(c->w_ubar); dfree(c->w_m1);
     dfree(c->w_m2); dfree(c->w_z); dfree(c->w_z2); dfree(c->partials);
     dfree(c->w_p2); dfree(c->w_cz); dfree(c->w_sp0); dfree(c->w_sp1);
+    for (float** fp : {&c->ug_g, &c->ug_x, &c->ug_r, &c->ug_z, &c->ug_p, &c->ug_q, &c->ug_m, &c->ug_w}) dfree(*fp);
+    dfree(c->ug_part);
+    dfree(c->ug_out);
+    dfree(c->ug_tk);
+    if (c->ug_outh) cudaFreeHost(c->ug_outh);
+    c->ug_outh = nullptr;
+    c->ug_part_cap = 0;
     dfree(c->d_frames); dfree(c->d_wnext); dfree(c->d_idx); dfree(c->d_lsf);
     dfree(c->d_kidx); dfree(c->d_taps); dfree(c->d_rho);
     dfree(c->d_theta); dfree(c->d_gth); dfree(c->d_aff_part);
@@ -415,8 +446,11 @@ const ObjShapeChoice* obj_choice(stml_ctx* c, int level, const Geom& g, const Fr
 // J <= target, after shortening that step (Illinois regula falsi on its
 // length) so that J lands within params.target_tol * target of the target; a
 // start with J0 <= target takes no step.
+stml_status run_gir_ugrid(stml_ctx* c, int level, const std::vector<int>& K, float* w_io, stml_stats* st);
+
 stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_io, stml_stats* st,
                     double target = 0.0) {
+    if (c->p.u_coarsen > 0) return run_gir_ugrid(c, level, K, u_io, st);
     Range rg("GIR level %d |K| %d", level, (int)K.size());
     const auto t_start = std::chrono::steady_clock::now();
     LevelBuf& L = c->lv[level];
@@ -768,6 +802,260 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
     return STML_OK;
 }
 
+// ------------------------------------------------------- coarse displacement grid
+// Buffers of the coarse-grid solver (allocated on first use, sized for the
+// finest level and all frames).
+stml_status ensure_ugrid(stml_ctx* c) {
+    if (c->ug_g) return STML_OK;
+    const size_t M = (size_t)c->n * c->d * field_geom(c, (int)c->lv.size() - 1).N;
+    bool ok = true;
+    for (float** fp : {&c->ug_g, &c->ug_x, &c->ug_r, &c->ug_z, &c->ug_p, &c->ug_q, &c->ug_m, &c->ug_w})
+        ok = ok && dalloc(fp, M) == cudaSuccess;
+    c->ug_part_cap = (size_t)152 * 8 * 8;
+    ok = ok && dalloc(&c->ug_part, c->ug_part_cap) == cudaSuccess;
+    ok = ok && dalloc(&c->ug_out, 16) == cudaSuccess;
+    ok = ok && dalloc(&c->ug_tk, 8) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&c->ug_outh, 16 * sizeof(double)) == cudaSuccess;
+    if (!ok) return fail(c, STML_ENOMEM, "device allocation of the coarse-grid solver buffers failed");
+    CK(c, cudaMemsetAsync(c->ug_tk, 0, 8 * sizeof(unsigned int), c->stream));
+    return STML_OK;
+}
+
+// The first n reduced values of the coarse-grid passes (ug_out) on the host.
+stml_status ug_read(stml_ctx* c, int n) {
+    CK(c, cudaMemcpyAsync(c->ug_outh, c->ug_out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+// One objective evaluation with the unknowns w on the coarse grid of the
+// level: u = P_s w on the image grid, the distance of eq. (1) there (with
+// the gradient: hd r grad T, gathered to the coarse grid by P_s^T), S and P
+// on the coarse grid.  o6 = J, D, S, P, |g|^2, |w|^2.  With grad the coarse
+// gradient goes to c->ug_g and grad T (image grid) to c->w_dT; with dw the
+// objective is taken at w + t dw (no gradient).
+struct UgEval {
+    stml_ctx* c;
+    int level;
+    Geom g, gw;
+    UGrid ug;
+    FrameSet fs;
+    Coef cf0, cw;
+    long long planes;
+
+    stml_status run(const float* w, const float* dw, float t, bool grad, double* o6) {
+        const LevelBuf& L = c->lv[level];
+        const Stored img{L.img, c->img_type};
+        const double pf = (double)fs.nK * (double)g.N;
+        long pe = prof_begin(c, PC_PROLONG, level);
+        CK(c, launch_ugrid_prolong(w, dw, t, c->w_ut, planes, ug, c->stream));
+        prof_end(c, pe, 4.0 * g.d * pf, pf);
+        pe = prof_begin(c, PC_TRIAL, level);
+        CK(c, launch_objective(img, g, fs, cf0, c->w_ut, nullptr, 0.f, nullptr, c->w_abar, c->w_ubar, c->partials,
+                               c->partials_cap, &c->S->ticket[0], c->S->red, c->stream));
+        prof_end(c, pe, pf * (4.0 + 4.0 * g.d), pf);
+        if (grad) {
+            pe = prof_begin(c, PC_EVAL, level);
+            CK(c, launch_gradient(img, g, fs, cf0, c->w_ut, nullptr, 0.f, c->w_abar, c->w_ubar, c->w_g, c->w_dT,
+                                  ST_F32, nullptr, c->partials, c->partials_cap, &c->S->ticket[4], c->S->red,
+                                  c->stream));
+            prof_end(c, pe, pf * (4.0 + 20.0 * g.d), pf);
+            pe = prof_begin(c, PC_PROLONG, level);
+            CK(c, launch_ugrid_adjoint(c->w_g, c->ug_g, planes, ug, c->stream));
+            prof_end(c, pe, 4.0 * g.d * pf, pf);
+        }
+        CK(c, launch_ugrid_reg(0, gw, fs, cw, w, dw, t, grad ? c->ug_g : nullptr, grad ? c->ug_g : nullptr,
+                               c->ug_part, c->ug_part_cap, &c->ug_tk[0], c->ug_out, c->stream));
+        TRY(read_scalars(c));
+        TRY(ug_read(c, 5));
+        const stml_params& p = c->p;
+        const double* r = c->ug_outh;
+        const double hdw = gw.hd, inv_h2 = 1.0 / ((double)gw.h * gw.h), K = fs.nK;
+        const double D = c->Sh->red[1];
+        const double Sv = 0.5 * p.alpha * hdw * inv_h2 * r[0] + 0.5 * p.alpha_t * hdw * r[1];
+        const double Pv = p.lambda * hdw * r[2] / (K * K);
+        o6[0] = D + Sv + Pv;
+        o6[1] = D;
+        o6[2] = Sv;
+        o6[3] = Pv;
+        o6[4] = grad ? r[3] : 0.0;
+        o6[5] = r[4];
+        return STML_OK;
+    }
+
+    // q = H p (coarse grid): P_s^T H_D P_s p + the regulariser and penalty
+    // Hessian; *pq = <p, q>.
+    stml_status hess(const float* pv, float* qv, double* pq) {
+        const double pf = (double)fs.nK * (double)g.N;
+        long pe = prof_begin(c, PC_PROLONG, level);
+        CK(c, launch_ugrid_prolong(pv, nullptr, 0.f, c->w_p, planes, ug, c->stream));
+        prof_end(c, pe, 4.0 * g.d * pf, pf);
+        TRY(hessvec_launch(c, level, g, fs, cf0, c->w_dT, c->w_p, c->w_q, nullptr));
+        pe = prof_begin(c, PC_PROLONG, level);
+        CK(c, launch_ugrid_adjoint(c->w_q, qv, planes, ug, c->stream));
+        prof_end(c, pe, 4.0 * g.d * pf, pf);
+        CK(c, launch_ugrid_reg(1, gw, fs, cw, pv, nullptr, 0.f, qv, qv, c->ug_part, c->ug_part_cap, &c->ug_tk[1],
+                               c->ug_out + 5, c->stream));
+        if (pq) {
+            CK(c, cudaMemcpyAsync(c->ug_outh + 5, c->ug_out + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+            *pq = c->ug_outh[5];
+        }
+        return STML_OK;
+    }
+
+    stml_status jacobi() {
+        CK(c, launch_ugrid_jacobi(c->w_dT, c->ug_m, ug, fs, cf0, cw, c->stream));
+        return STML_OK;
+    }
+};
+
+stml_status ug_setup(stml_ctx* c, int level, const std::vector<int>& K, UgEval& E) {
+    TRY(ensure_ugrid(c));
+    E.c = c;
+    E.level = level;
+    E.g = c->lv[level].g;
+    E.gw = field_geom(c, level);
+    E.ug = make_ugrid(E.g, c->p.u_coarsen);
+    TRY(upload_frameset(c, K, E.fs));
+    stml_params p0 = c->p;
+    p0.alpha = p0.alpha_t = p0.lambda = 0.0;
+    E.cf0 = make_coef(E.g, p0, (int)K.size());
+    E.cw = make_coef(E.gw, c->p, (int)K.size());
+    E.planes = (long long)K.size() * E.g.d;
+    return STML_OK;
+}
+
+// Deterministic dot product of two coarse-grid vectors of n values.
+stml_status ug_dot(stml_ctx* c, long long n, const float* a, const float* b, double* out) {
+    CK(c, launch_ugrid_vec(VEC_DOT, n, 0.f, nullptr, const_cast<float*>(a), nullptr, nullptr, const_cast<float*>(b),
+                           nullptr, nullptr, c->ug_part, c->ug_part_cap, &c->ug_tk[3], c->ug_out + 8, c->stream));
+    CK(c, cudaMemcpyAsync(c->ug_outh + 8, c->ug_out + 8, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *out = c->ug_outh[8];
+    return STML_OK;
+}
+
+// GIR(K) with the unknowns on the coarse grid (u_coarsen = s > 0): the same
+// Gauss-Newton / Jacobi-PCG / Armijo scheme and stopping tests as run_gir,
+// with the PCG coefficients taken on the host from the device reductions.
+stml_status run_gir_ugrid(stml_ctx* c, int level, const std::vector<int>& K, float* w_io, stml_stats* st) {
+    Range rg("GIR on the coarse field grid, level %d |K| %d", level, (int)K.size());
+    const auto t_start = std::chrono::steady_clock::now();
+    UgEval E;
+    TRY(ug_setup(c, level, K, E));
+    const stml_params& p = c->p;
+    const long long M = E.planes * E.gw.N;
+    stml_stats s{};
+    s.level = level;
+    s.n_frames = (int)K.size();
+    s.status = STML_OK;
+    float* w = w_io;
+    float* wt = c->ug_w;
+    double ev[6];
+    TRY(E.run(w, nullptr, 0.f, true, ev));
+    const double J0 = ev[0];
+    double J = ev[0], gnorm2 = ev[4], wnorm2 = ev[5], J_old = 0.0, step_norm = 0.0;
+    s.J0 = J0;
+    int it = 0;
+    double last[4] = {ev[0], ev[1], ev[2], ev[3]};
+    for (;;) {
+        if (!std::isfinite(J) || !std::isfinite(gnorm2)) {
+            s.status = STML_ENONFINITE;
+            break;
+        }
+        const double gnorm = std::sqrt(gnorm2);
+        if (it > 0) {
+            const bool c1 = std::fabs(J_old - J) <= p.tol_J * (1.0 + std::fabs(J0));
+            const bool c2 = step_norm <= p.tol_Y * (1.0 + std::sqrt(wnorm2));
+            const bool c3 = gnorm <= p.tol_G * (1.0 + std::fabs(J0));
+            if (c1 && c2 && c3) break;
+        }
+        if (gnorm <= p.g_abs * (1.0 + std::fabs(J0)) || it >= p.max_gn) break;
+        // --- Jacobi-PCG for H x = -g from x = 0
+        Range rit("Gauss-Newton iteration %d", it);
+        TRY(E.jacobi());
+        int steps = 0;
+        if (gnorm > 0.0) {
+            CK(c, launch_ugrid_vec(VEC_INIT, M, 0.f, c->ug_m, c->ug_x, c->ug_r, c->ug_z, c->ug_p, nullptr, c->ug_g,
+                                   c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6, c->stream));
+            TRY(ug_read(c, 8));
+            double rho = c->ug_outh[6];
+            while (steps < p.max_cg) {
+                double pq = 0.0;
+                TRY(E.hess(c->ug_p, c->ug_q, &pq));
+                if (pq <= 0.0) {   // breakdown: the iterate so far, or the preconditioned gradient on the first step
+                    if (steps == 0)
+                        CK(c, cudaMemcpyAsync(c->ug_x, c->ug_z, (size_t)M * sizeof(float), cudaMemcpyDeviceToDevice,
+                                              c->stream));
+                    break;
+                }
+                const double alpha = rho / pq;
+                CK(c, launch_ugrid_vec(VEC_STEP, M, (float)alpha, c->ug_m, c->ug_x, c->ug_r, c->ug_z, c->ug_p,
+                                       c->ug_q, nullptr, c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6,
+                                       c->stream));
+                TRY(ug_read(c, 8));
+                ++steps;
+                if (std::sqrt(c->ug_outh[6]) <= p.tol_cg * gnorm) break;
+                const double rho_new = c->ug_outh[7];
+                const double beta = rho_new / rho;
+                rho = rho_new;
+                CK(c, launch_ugrid_vec(VEC_DIR, M, (float)beta, nullptr, nullptr, nullptr, c->ug_z, c->ug_p, nullptr,
+                                       nullptr, c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6, c->stream));
+            }
+        } else {
+            CK(c, cudaMemsetAsync(c->ug_x, 0, (size_t)M * sizeof(float), c->stream));
+        }
+        s.cg_iters += steps;
+        double gTd = 0.0, dd = 0.0;
+        TRY(ug_dot(c, M, c->ug_g, c->ug_x, &gTd));
+        if (!(gTd < 0.0)) {
+            s.status = STML_EBREAKDOWN;
+            break;
+        }
+        TRY(ug_dot(c, M, c->ug_x, c->ug_x, &dd));
+        // --- Armijo back-tracking on t = 1, 1/2, ...
+        bool accepted = false;
+        double t = 1.0, tr[6];
+        for (int k = 0; k < p.max_ls; ++k) {
+            TRY(E.run(w, c->ug_x, (float)t, false, tr));
+            ++s.ls_trials;
+            if (tr[0] <= J + p.armijo_c * t * gTd) {
+                accepted = true;
+                break;
+            }
+            if (k + 1 < p.max_ls) t *= 0.5;
+        }
+        if (!accepted) {
+            s.status = STML_ELINESEARCH;
+            break;
+        }
+        CK(c, launch_ugrid_vec(VEC_AXPY, M, (float)t, nullptr, w, nullptr, wt, c->ug_x, nullptr, nullptr, c->ug_part,
+                               c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6, c->stream));
+        std::swap(w, wt);
+        step_norm = t * std::sqrt(dd);
+        J_old = J;
+        TRY(E.run(w, nullptr, 0.f, true, ev));
+        J = ev[0];
+        gnorm2 = ev[4];
+        wnorm2 = ev[5];
+        for (int i = 0; i < 4; ++i) last[i] = ev[i];
+        ++it;
+    }
+    if (w != w_io) {
+        CK(c, cudaMemcpyAsync(w_io, w, (size_t)M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    s.gn_iters = it;
+    s.J = last[0];
+    s.D = last[1];
+    s.S = last[2];
+    s.P = last[3];
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (st) *st = s;
+    return STML_OK;
+}
+
 // ------------------------------------------------------------------ predictors
 stml_status upload_idx(stml_ctx* c, const std::vector<int>& K) {
     CK(c, cudaMemcpyAsync(c->d_idx, K.data(), K.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -880,7 +1168,8 @@ stml_status learned_fill(stml_ctx* c, int level, const std::vector<int>& Kp, con
                          double* J_classic, double* J_kept) {
     *decision = -1;
     LevelBuf& L = c->lv[level];
-    if (!c->net || c->d != 2 || targets.empty() || !net::fits(c->net, L.g.ny, L.g.nx)) return STML_OK;
+    if (!c->net || c->d != 2 || c->p.u_coarsen || targets.empty() || !net::fits(c->net, L.g.ny, L.g.nx))
+        return STML_OK;
     const size_t plane = (size_t)L.g.d * L.g.N;
     const size_t img_frame = (size_t)L.g.N * store_bytes(c->img_type);
     const char* img = static_cast<const char*>(L.img);
@@ -1426,7 +1715,8 @@ stml_status register_affine(stml_ctx* c, stml_mode mode, const std::function<voi
 // ------------------------------------------------------------------ STML steps
 stml_status do_predict(stml_ctx* c, int level, int q) {
     LevelBuf& L = c->lv[level];
-    const size_t plane = (size_t)L.g.d * L.g.N;    // one frame of a field
+    const Geom gf = field_geom(c, level);
+    const size_t plane = (size_t)gf.d * gf.N;      // one frame of a field
     const size_t total = (size_t)c->n * plane;
     if (q == 0) {
         if (level == 0) {
@@ -1434,9 +1724,10 @@ stml_status do_predict(stml_ctx* c, int level, int q) {
         } else {
             const LevelBuf& C = c->lv[level - 1];
             if (L.g.nx != 2 * C.g.nx) return fail(c, STML_EINVAL, "level shapes do not halve");
+            const Geom gc = field_geom(c, level - 1);
             const long pe = prof_begin(c, PC_PROLONG, level);
-            CK(c, launch_prolong(C.y, c->w_z, c->n * c->d, C.g, c->stream));
-            prof_end(c, pe, 4.0 * c->n * c->d * (double)(L.g.N + C.g.N), (double)c->n * L.g.N);
+            CK(c, launch_prolong(C.y, c->w_z, c->n * c->d, gc, c->stream));
+            prof_end(c, pe, 4.0 * c->n * c->d * (double)(gf.N + gc.N), (double)c->n * gf.N);
         }
         c->cur_level = level;
         c->last_q = -1;
@@ -1468,13 +1759,13 @@ stml_status do_predict(stml_ctx* c, int level, int q) {
 stml_status correct_begin(stml_ctx* c, int level, int q) {
     if (c->cur_level != level || c->last_q != q - 1 || c->level_done)
         return fail(c, STML_ESTATE, "stml_correct(level, q) needs stml_predict(level, q) first");
-    LevelBuf& L = c->lv[level];
-    const size_t plane = (size_t)L.g.d * L.g.N;
+    const Geom gf = field_geom(c, level);
+    const size_t plane = (size_t)gf.d * gf.N;
     const std::vector<int>& K = c->sets[q];
     TRY(upload_idx(c, K));
     long pe = prof_begin(c, PC_GATHER, level);
     CK(c, launch_gather_planes(c->w_z, c->w_u, c->d_idx, (int)K.size(), plane, c->stream));
-    prof_end(c, pe, 8.0 * plane * K.size(), (double)K.size() * L.g.N);
+    prof_end(c, pe, 8.0 * plane * K.size(), (double)K.size() * gf.N);
     return STML_OK;
 }
 
@@ -1491,7 +1782,8 @@ stml_status do_correct(stml_ctx* c, int level, int q, stml_stats* st, int* finis
 
 stml_status correct_end(stml_ctx* c, int level, int q, stml_stats s, stml_stats* st, int* finished) {
     LevelBuf& L = c->lv[level];
-    const size_t plane = (size_t)L.g.d * L.g.N;
+    const Geom gf = field_geom(c, level);
+    const size_t plane = (size_t)gf.d * gf.N;
     const std::vector<int>& K = c->sets[q];
     const int Q = (int)c->sets.size();
     s.tlevel = q;
@@ -1704,6 +1996,7 @@ stml_status batch_register(stml_batch* b, stml_mode mode, stml_status* status) {
         if (!c->built) return bfail(b, STML_ESTATE, "stml_batch_register: a context has no pyramid");
         if (c->device != b->device) return bfail(b, STML_EINVAL, "stml_batch_register: contexts on several devices");
         if (c->p.transform != 0) return bfail(b, STML_EINVAL, "stml_batch_register: transform 0 only");
+        if (c->p.u_coarsen != 0) return bfail(b, STML_EINVAL, "stml_batch_register: u_coarsen 0 only");
         if (c->d != c0->d || c->img_type != c0->img_type || !same_solver(c->p, c0->p) ||
             c->lv.size() != c0->lv.size() || c->sets.size() != c0->sets.size())
             return bfail(b, STML_EINVAL,
@@ -2036,6 +2329,12 @@ stml_status stml_set_params(stml_ctx* c, const stml_params* p) {
     if (!valid_params(p, why)) return fail(c, STML_EINVAL, why);
     if (c->loaded && (p->n_levels != c->p.n_levels || p->n_tlevels != c->p.n_tlevels))
         return fail(c, STML_EINVAL, "level counts cannot change after stml_load_sequence");
+    if (c->loaded) {
+        const int f = 1 << (p->n_levels - 1 + p->u_coarsen);
+        for (int i = 3 - c->d; i < 3; ++i)
+            if (c->shape[i] % f)
+                return fail(c, STML_EINVAL, "the loaded shape is not a multiple of 2^(n_levels-1+u_coarsen)");
+    }
     c->p = *p;
     return STML_OK;
 }
@@ -2073,10 +2372,11 @@ stml_status stml_load_sequence(stml_ctx* c, const float* frames, int on_device, 
         return fail(c, STML_EINVAL, "need frames, shape, n_frames >= 1 and dim 2 or 3");
     cudaSetDevice(c->device);
     const int L = c->p.n_levels;
-    const long long f = 1LL << (L - 1);
+    const long long f = 1LL << (L - 1 + c->p.u_coarsen);
     int sh3[3] = {1, 1, 1};
     for (int i = 0; i < dim; ++i) {
-        if (shape[i] < 1 || shape[i] % f) return fail(c, STML_EINVAL, "every axis must be a positive multiple of 2^(n_levels-1)");
+        if (shape[i] < 1 || shape[i] % f)
+            return fail(c, STML_EINVAL, "every axis must be a positive multiple of 2^(n_levels-1+u_coarsen)");
         if (shape[i] > 65535) return fail(c, STML_EINVAL, "an axis has more than 65535 cells");
         sh3[3 - dim + i] = shape[i];
     }
@@ -2192,7 +2492,7 @@ stml_status stml_get_field(stml_ctx* c, int level, float* dst, int dst_on_device
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
     TRY(check_level(c, level));
     cudaSetDevice(c->device);
-    const size_t cnt = (size_t)c->n * c->d * c->lv[level].g.N;
+    const size_t cnt = (size_t)c->n * c->d * field_geom(c, level).N;
     CK(c, cudaMemcpyAsync(dst, c->lv[level].y, cnt * sizeof(float),
                           dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -2203,7 +2503,7 @@ stml_status stml_set_field(stml_ctx* c, int level, const float* src, int src_on_
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
     TRY(check_level(c, level));
     cudaSetDevice(c->device);
-    const size_t cnt = (size_t)c->n * c->d * c->lv[level].g.N;
+    const size_t cnt = (size_t)c->n * c->d * field_geom(c, level).N;
     CK(c, cudaMemcpyAsync(c->lv[level].y, src, cnt * sizeof(float),
                           src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -2254,7 +2554,7 @@ stml_status stml_register(stml_ctx* c, stml_mode mode, stml_stats* stats, int ca
         if (mode == STML_MODE_SPML) {
             TRY(do_predict(c, l, 0));
             LevelBuf& B = c->lv[l];
-            const size_t total = (size_t)c->n * c->d * B.g.N;
+            const size_t total = (size_t)c->n * c->d * field_geom(c, l).N;
             CK(c, cudaMemcpyAsync(B.y, c->w_z, total * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
             stml_stats s{};
             TRY(run_gir(c, l, all, B.y, &s, l == L - 1 ? c->p.target_J : 0.0));
@@ -2412,6 +2712,49 @@ stml_status stml_gir(stml_ctx* c, int level, const int* frames, int nK, float* u
     return run_gir(c, level, K, u, stats, c->p.target_J);
 }
 
+stml_status stml_eval_ugrid(stml_ctx* c, int level, const int* frames, int nK, const float* w, double* out,
+                            float* g, float* dT, float* Minv) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (c->p.u_coarsen < 1) return fail(c, STML_EINVAL, "stml_eval_ugrid needs params.u_coarsen > 0");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!w || !out) return fail(c, STML_EINVAL, "w and out are required");
+    cudaSetDevice(c->device);
+    std::vector<int> K(frames, frames + nK);
+    UgEval E;
+    TRY(ug_setup(c, level, K, E));
+    const bool grad = g || dT || Minv;
+    TRY(E.run(w, nullptr, 0.f, grad, out));
+    const size_t Mc = (size_t)E.planes * E.gw.N, Mf = (size_t)E.planes * E.g.N;
+    if (g) CK(c, cudaMemcpyAsync(g, c->ug_g, Mc * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (dT) CK(c, cudaMemcpyAsync(dT, c->w_dT, Mf * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (Minv) {
+        TRY(E.jacobi());
+        CK(c, cudaMemcpyAsync(Minv, c->ug_m, Mc * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return STML_OK;
+}
+
+stml_status stml_hessvec_ugrid(stml_ctx* c, int level, const int* frames, int nK, const float* dT, const float* v,
+                               float* Hv, double* vHv) {
+    if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
+    if (c->p.u_coarsen < 1) return fail(c, STML_EINVAL, "stml_hessvec_ugrid needs params.u_coarsen > 0");
+    TRY(check_level(c, level));
+    TRY(check_frames(c, frames, nK));
+    if (!dT || !v || !Hv || v == Hv) return fail(c, STML_EINVAL, "dT, v and Hv (distinct from v) are required");
+    cudaSetDevice(c->device);
+    std::vector<int> K(frames, frames + nK);
+    UgEval E;
+    TRY(ug_setup(c, level, K, E));
+    CK(c, cudaMemcpyAsync(c->w_dT, dT, (size_t)E.planes * E.g.N * sizeof(float), cudaMemcpyDeviceToDevice,
+                          c->stream));
+    double pq = 0.0;
+    TRY(E.hess(v, Hv, &pq));
+    if (vHv) *vHv = pq;
+    return STML_OK;
+}
+
 stml_status stml_eval_affine(stml_ctx* c, int level, const int* frames, int nK, const double* theta, double* out,
                              double* grad) {
     if (!c) return fail(nullptr, STML_EINVAL, "ctx is NULL");
@@ -2515,6 +2858,33 @@ stml_status stml_prolong_adjoint(const float* fine, float* coarse, int planes, i
     const Geom gc = make_geom(sh3, dim, 2.f);
     cudaError_t e = launch_prolong_adjoint(fine, coarse, planes, gc, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_prolong_adjoint");
+}
+
+static stml_status ugrid_args(const char* who, const float* a, const float* b, int planes, int dim,
+                              const int* fine_shape, int s, UGrid& ug) {
+    int sh3[3];
+    if (!a || !b || planes < 0 || s < 1 || s > 4 || !shape_ok(dim, fine_shape, sh3))
+        return fail(nullptr, STML_EINVAL, std::string(who) + ": bad arguments");
+    for (int i = 3 - dim; i < 3; ++i)
+        if (sh3[i] % (1 << s)) return fail(nullptr, STML_EINVAL, std::string(who) + ": an axis is not a multiple of 2^s");
+    ug = make_ugrid(make_geom(sh3, dim, 1.f), s);
+    return STML_OK;
+}
+
+stml_status stml_ugrid_prolong(const float* w, float* u, int planes, int dim, const int* fine_shape, int s,
+                               void* cuda_stream) {
+    UGrid ug;
+    TRY(ugrid_args("stml_ugrid_prolong", w, u, planes, dim, fine_shape, s, ug));
+    cudaError_t e = launch_ugrid_prolong(w, nullptr, 0.f, u, planes, ug, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_ugrid_prolong");
+}
+
+stml_status stml_ugrid_adjoint(const float* u, float* w, int planes, int dim, const int* fine_shape, int s,
+                               void* cuda_stream) {
+    UGrid ug;
+    TRY(ugrid_args("stml_ugrid_adjoint", u, w, planes, dim, fine_shape, s, ug));
+    cudaError_t e = launch_ugrid_adjoint(u, w, planes, ug, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? STML_OK : cuda_fail(nullptr, e, "stml_ugrid_adjoint");
 }
 
 static bool increasing(const int* K, int nK) {

@@ -360,4 +360,36 @@ cudaError_t launch_batch_gir(const BatchSeq* seqs_dev, int nseq, BatchState* sta
                              int vec, int img_type, const BatchShape& sh, float2* part, BatchSync* sync,
                              int max_steps, cudaStream_t s);
 
+// ------------------------------------------------- coarse displacement grid (k_ugrid.cu)
+// The image grid (nx, ny, nz; N cells per plane) and the grid of the
+// unknowns, coarser by F = 2^s per axis (cx, cy, cz; Nc cells per plane).
+struct UGrid {
+    int nx, ny, nz;
+    int cx, cy, cz;
+    int d, F;
+    float inv_F;
+    long long N, Nc;
+};
+UGrid make_ugrid(const Geom& fine, int s);
+// u = P_s (w + t dw) for `planes` planes (dw may be null).
+cudaError_t launch_ugrid_prolong(const float* w, const float* dw, float t, float* u, long long planes,
+                                 const UGrid& ug, cudaStream_t s);
+// out = P_s^T f (fixed-order gather per coarse value).
+cudaError_t launch_ugrid_adjoint(const float* f, float* out, long long planes, const UGrid& ug, cudaStream_t s);
+// Minv = 1 / Jacobi diagonal of the coarse-grid Hessian from the image-grid
+// grad T (float), cf the image grid's and cw the coarse grid's coefficients.
+cudaError_t launch_ugrid_jacobi(const float* dT, float* Minv, const UGrid& ug, const FrameSet& fs, const Coef& cf,
+                                const Coef& cw, cudaStream_t s);
+// S and P on the coarse grid gw at w + t dw; mode 0: objective sums (5
+// values to out) and, with gout, the gradient gin + regulariser/penalty
+// gradient; mode 1: gout = gin + their Hessian product, out[0] = <w, gout>.
+cudaError_t launch_ugrid_reg(int mode, const Geom& gw, const FrameSet& fs, const Coef& cw, const float* w,
+                             const float* dw, float t, const float* gin, float* gout, double* partials,
+                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s);
+enum UgridVecMode { VEC_INIT = 0, VEC_STEP = 1, VEC_DIR = 2, VEC_DOT = 3, VEC_AXPY = 4 };
+// PCG vector steps and dot products over n coarse values (see k_ugrid.cu).
+cudaError_t launch_ugrid_vec(int mode, long long n, float a, const float* Minv, float* x, float* r, float* z,
+                             float* p, const float* q, const float* g, double* partials, size_t partials_cap,
+                             unsigned int* ticket, double* out, cudaStream_t s);
+
 }  // namespace stml

@@ -15,7 +15,7 @@ STRUCTS = {
     "stml_params": ("Params", ["alpha", "alpha_t", "lambda", "beta", "eps_stop", "stop_rule", "n_levels",
                                "n_tlevels", "tol_J", "tol_Y", "tol_G", "g_abs", "max_gn", "tol_cg", "max_cg",
                                "max_ls", "armijo_c", "image_dtype", "pcg_cooperative", "autotune", "transform",
-                               "lbfgs_m", "max_lbfgs", "distance", "target_J", "target_tol"]),
+                               "lbfgs_m", "max_lbfgs", "distance", "target_J", "target_tol", "u_coarsen"]),
     "stml_stats": ("Stats", ["level", "tlevel", "n_frames", "gn_iters", "cg_iters", "ls_trials", "stopped_early",
                              "status", "J0", "J", "D", "S", "P", "seconds", "pred_learned", "fill_learned",
                              "J0_classic", "J_fill_classic", "J_fill"]),
