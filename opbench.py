@@ -1,6 +1,6 @@
 """Per-operation throughput of the library on one grid level (CUDA events).
 
-    python -m paper_2001_06613_gb300.opbench --op all --shape 256 256 --frames 200
+    python opbench.py --op all --shape 256 256 --frames 200
 
 Each operation is timed through the C ABI on device-resident data (the call,
 including its host work) and reported as achieved GB/s of its algorithmic bytes (every array it must read or write
@@ -10,14 +10,14 @@ time of each kernel class from the library's own CUDA-event profiling.
 Inputs are larger than L2 at the default size, and L2 is flushed before every
 timed call.
 
-    python -m paper_2001_06613_gb300.opbench --op net_forward --shape 256 256 --frames 32
+    python opbench.py --op net_forward --shape 256 256 --frames 32
 
 times the learned predictor's forward pass on a batch of `frames` canvases
 (TFLOP/s of its 3x3 convolutions against the measured BF16 peak);
 `--op net_train` one training step (forward, input and weight gradients,
 Adam) on `frames` crops of the given shape.
 
-    python -m paper_2001_06613_gb300.opbench --op batch --frames 8
+    python opbench.py --op batch --frames 8
 
 registers `frames` sequences of uneven length and size (the first of the
 batching workload's seeded draws, scaled down by 4 in each axis) with the
@@ -32,7 +32,9 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 
 
 def _peak():
