@@ -56,6 +56,8 @@ class LevelStats:
     S: float
     P: float
     stopped_early: bool = False
+    cg_margin: float = float("inf")    # see solver.GirStats.cg_margin
+    cg_residuals: list = field(default_factory=list)   # ||r|| / ||g|| after each CG step, per solve
 
 
 @dataclass
@@ -80,7 +82,10 @@ def _model(T, K, h, p: Params):
     return ugrid.Model(T, K, h, p.u_coarsen, p) if p.u_coarsen else None
 
 
-def register(R: np.ndarray, p: Params, mode: str = "stml") -> Result:
+def register(R: np.ndarray, p: Params, mode: str = "stml", flips=None) -> Result:
+    """``flips``: {GIR index: set of (solve, k)} -- CG stopping decisions that
+    take their other branch (:func:`solver.gauss_newton`); GIRs are numbered
+    in the order they run."""
     n = R.shape[0]
     d = R.ndim - 1
     L = p.n_levels
@@ -96,20 +101,24 @@ def register(R: np.ndarray, p: Params, mode: str = "stml") -> Result:
         z_all = np.zeros((n, d) + m) if ell == 0 else grid.prolong_fields(y_prev)
         target = p.target_J if ell == L - 1 else 0.0     # the last GIR over all frames
         if mode == "spml":
-            y_all, st = solver.gauss_newton(T, z_all, allK, h, p, target, _model(T, allK, h, p))
+            y_all, st = solver.gauss_newton(T, z_all, allK, h, p, target, _model(T, allK, h, p),
+                                            (flips or {}).get(len(res.stats)))
             res.stats.append(LevelStats(ell, p.n_tlevels - 1, n, st.gn_iters, st.cg_iters,
-                                        st.ls_trials, st.J, st.D, st.S, st.P))
+                                        st.ls_trials, st.J, st.D, st.S, st.P,
+                                        cg_margin=st.cg_margin(p.tol_cg), cg_residuals=st.cg_residuals))
         elif mode == "stml":
             y_all = None
             dhat_prev = None
             for q, K in enumerate(sets):
                 yK, st = solver.gauss_newton(T[K], z_all[K], K, h, p,
-                                             target if q == len(sets) - 1 else 0.0, _model(T[K], K, h, p))
+                                             target if q == len(sets) - 1 else 0.0, _model(T[K], K, h, p),
+                                             (flips or {}).get(len(res.stats)))
                 dhat = st.D / len(K)
                 stop = (q > 0 and p.stop_rule and
                         abs(dhat - dhat_prev) <= p.eps_stop * abs(dhat_prev))
                 res.stats.append(LevelStats(ell, q, len(K), st.gn_iters, st.cg_iters,
-                                            st.ls_trials, st.J, st.D, st.S, st.P, stop))
+                                            st.ls_trials, st.J, st.D, st.S, st.P, stop,
+                                            cg_margin=st.cg_margin(p.tol_cg), cg_residuals=st.cg_residuals))
                 if q == len(sets) - 1:
                     y_all = yK
                     break

@@ -38,11 +38,14 @@ from .params import Params
 
 
 def pcg(apply_H: Callable[[np.ndarray], np.ndarray], b: np.ndarray, Minv: np.ndarray,
-        tol: float, maxit: int, record: list | None = None):
+        tol: float, maxit: int, record: list | None = None, flip: int | None = None):
     """Jacobi-preconditioned CG for H x = b from x = 0; returns (x, steps, flag).
 
     With ``record`` given, ||r|| / ||b|| after every step is appended to it
-    (the quantity the stopping test compares with ``tol``)."""
+    (the quantity the stopping test compares with ``tol``).  ``flip`` = k
+    inverts the stopping decision taken after step k + 1 (the other branch of
+    a decision whose ratio sits within rounding of ``tol``: several results
+    of the method are then correct, and a test may compare with either)."""
     x = np.zeros_like(b)
     bnorm = float(np.sqrt(np.sum(b * b)))
     if bnorm == 0.0:
@@ -67,7 +70,10 @@ def pcg(apply_H: Callable[[np.ndarray], np.ndarray], b: np.ndarray, Minv: np.nda
         steps += 1
         if record is not None:
             record.append(float(np.sqrt(np.sum(r * r))) / bnorm)
-        if float(np.sqrt(np.sum(r * r))) <= tol * bnorm:
+        stop = float(np.sqrt(np.sum(r * r))) <= tol * bnorm
+        if flip is not None and steps - 1 == flip:
+            stop = not stop
+        if stop:
             flag = "converged"
             break
         z = Minv * r
@@ -146,6 +152,13 @@ class GirStats:
     steps: list = field(default_factory=list)      # (CG steps, Armijo trials) of every GN step
     cg_residuals: list = field(default_factory=list)   # ||r|| / ||g|| after each CG step, per solve
 
+    def cg_margin(self, tol: float) -> float:
+        """Smallest relative distance |ratio - tol| / tol of any CG stopping
+        decision of this GIR from its threshold (inf without CG steps): how
+        far the solve is from a decision that FP32 rounding could flip."""
+        r = [abs(x - tol) / tol for rec in self.cg_residuals for x in rec]
+        return min(r) if r else float("inf")
+
 
 class ImageGridModel:
     """Eq. (1) with S and P over the fields of the frames in K on the image
@@ -167,10 +180,13 @@ class ImageGridModel:
 
 
 def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float, p: Params,
-                 target: float = 0.0, model=None):
+                 target: float = 0.0, model=None, flips=None):
     """GIR(K): minimise eq. (1) over the fields of the frames in K, from u0
     (with target > 0: until J reaches the target objective, see above).
-    ``model`` replaces the image-grid objective (:class:`ImageGridModel`)."""
+    ``model`` replaces the image-grid objective (:class:`ImageGridModel`).
+    ``flips``: set of (solve, k) -- the CG stopping decision after step k + 1
+    of the solve-th PCG solve of this GIR takes its other branch (see
+    :func:`pcg`)."""
     mdl = model if model is not None else ImageGridModel(T, frames, h, p)
     u = np.array(u0, dtype=np.float64, copy=True)
     ev = mdl.evaluate(u)
@@ -198,8 +214,10 @@ def gauss_newton(T: np.ndarray, u0: np.ndarray, frames: Sequence[int], h: float,
         Minv = 1.0 / mdl.jacobi(ev["dT"])
         dT = ev["dT"]
         rec = []
+        solve = len(st.cg_residuals)
+        fk = [k for (si, k) in (flips or ()) if si == solve]
         d, steps, _ = pcg(lambda v: mdl.hessvec(dT, v), -g, Minv,
-                          p.tol_cg, p.max_cg, rec)
+                          p.tol_cg, p.max_cg, rec, fk[0] if fk else None)
         st.cg_residuals.append(rec)
         st.cg_iters += steps
         gTd = float(np.sum(g * d))

@@ -235,3 +235,55 @@ def test_gauss_newton_stops_at_the_target_objective():
     # a start at or below the target takes no step
     _, st0 = solver.gauss_newton(R, u0, K, 1.0, Params(), Js[0] * 1.01)
     assert st0.gn_iters == 0 and st0.status == "target"
+
+
+def test_pcg_flip_takes_the_other_branch_of_one_stopping_decision():
+    """flip=k inverts only the decision after step k + 1: a stop becomes a
+    further step, a further step becomes a stop; the ratios before it are
+    unchanged."""
+    rng = np.random.default_rng(12)
+    A = rng.normal(size=(30, 30))
+    H = A @ A.T + 3.0 * np.eye(30)
+    b = rng.normal(size=30)
+    Minv = 1.0 / np.diag(H)
+    rec = []
+    x, n, flag = solver.pcg(lambda v: H @ v, b, Minv, 0.1, 50, rec)
+    assert flag == "converged" and n >= 3
+    rec_stop = []
+    _, n1, _ = solver.pcg(lambda v: H @ v, b, Minv, 0.1, 50, rec_stop, flip=n - 1)
+    assert n1 > n and rec_stop[:n] == rec
+    rec_go = []
+    _, n2, _ = solver.pcg(lambda v: H @ v, b, Minv, 0.1, 50, rec_go, flip=n - 2)
+    assert n2 == n - 1 and rec_go == rec[:n - 1]
+
+
+def test_oracle_branch_follows_only_near_threshold_decisions():
+    """The test helper reruns the oracle with a near-threshold CG decision on
+    its other branch when that explains the GPU's counts, and refuses
+    differences that no such decision explains (3-D sequence whose oracle
+    run has a CG ratio 0.14 % above tol_cg in its second GIR)."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from _util import CG_BRANCH_DELTA, gir_counts, oracle_branch
+    from oracle import multilevel
+    from paper_2001_06613_gb300 import synthetic
+    R3 = synthetic.make_sequence(synthetic.spec_custom(5, (16, 16, 16), seed=4, amp=1.0)).astype(np.float64)
+    op = Params(n_levels=2, n_tlevels=2)
+    reg = lambda fl: multilevel.register(R3, op, "stml", flips=fl)
+    base = reg({})
+    want = gir_counts(base.stats)
+    res, flips = oracle_branch(reg, want, op.tol_cg)
+    assert flips == {} and gir_counts(res.stats) == want
+    rec = base.stats[1].cg_residuals
+    near = [(i, k) for i, r in enumerate(rec) for k, x in enumerate(r)
+            if abs(x - op.tol_cg) / op.tol_cg < CG_BRANCH_DELTA]
+    assert near and abs(rec[near[0][0]][near[0][1]] / op.tol_cg - 1.0) < 2e-3
+    # counts of the other branch at that decision: found again by the helper
+    other = gir_counts(reg({1: {near[0]}}).stats)
+    assert other != want and other[0] == want[0]
+    res, flips = oracle_branch(reg, other, op.tol_cg)
+    assert gir_counts(res.stats) == other and flips == {1: {near[0]}}
+    # a count difference that no near-threshold decision explains is refused
+    bogus = [c if i != 0 else c[:4] + (c[4] + 7,) + c[5:] for i, c in enumerate(want)]
+    with pytest.raises(AssertionError):
+        oracle_branch(reg, bogus, op.tol_cg)
