@@ -17,6 +17,28 @@ namespace stml {
 namespace {
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+// Streaming (evict-first) loads and stores for arrays a pass touches once and
+// no pass reads again before several others have streamed through L2.
+__device__ __forceinline__ float4 ld4cs(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void ldcs4f(const float* p, float (&o)[4]) {
+    const float4 q = ld4cs(p);
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+}
+__device__ __forceinline__ void ldcs4f(const __half* p, float (&o)[4]) {
+    const uint2 q = __ldcs(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ldcs4f(const __nv_bfloat16* p, float (&o)[4]) {
+    const uint2 q = __ldcs(reinterpret_cast<const uint2*>(p));
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ float ldcs1(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldcs1(const __half* p) { return __half2float(__ldcs(p)); }
+__device__ __forceinline__ float ldcs1(const __nv_bfloat16* p) { return __bfloat162float(__ldcs(p)); }
 __device__ __forceinline__ float4 ld4rw(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
@@ -37,6 +59,12 @@ struct V<4> {
     __device__ __forceinline__ void zero() { a[0] = a[1] = a[2] = a[3] = 0.f; }
     template <typename T>
     __device__ __forceinline__ void load_t(const T* p) { ld4f(p, a); }   // stored type -> float
+    __device__ __forceinline__ void load_cs(const float* p) { ldcs4f(p, a); }
+    template <typename T>
+    __device__ __forceinline__ void load_t_cs(const T* p) { ldcs4f(p, a); }
+    __device__ __forceinline__ void store_cs(float* p) const {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(a[0], a[1], a[2], a[3]));
+    }
 };
 template <>
 struct V<1> {
@@ -47,6 +75,10 @@ struct V<1> {
     __device__ __forceinline__ void zero() { a[0] = 0.f; }
     template <typename T>
     __device__ __forceinline__ void load_t(const T* p) { a[0] = ldf(p); }
+    __device__ __forceinline__ void load_cs(const float* p) { a[0] = __ldcs(p); }
+    template <typename T>
+    __device__ __forceinline__ void load_t_cs(const T* p) { a[0] = ldcs1(p); }
+    __device__ __forceinline__ void store_cs(float* p) const { __stcs(p, a[0]); }
 };
 
 // Position of pixel p: x, y, z via multiply-high division.
@@ -124,7 +156,10 @@ __device__ __forceinline__ void tile_pass(const Geom& g, const PixIndex& pi, con
             for (int c = 0; c < D; ++c) {
                 const size_t e0 = ((size_t)j * D + c) * N + px;
                 V<VEC> dt, wv;
-                dt.load_t(dT + e0);
+                if constexpr (MODE == TILE_DIR)
+                    dt.load_t_cs(dT + e0);
+                else
+                    dt.load_t(dT + e0);
                 if constexpr (MODE == TILE_SUMS) {
                     wv.load(v + e0);
                 } else if constexpr (MODE == TILE_DIR) {
@@ -253,7 +288,7 @@ __device__ __forceinline__ void apply_item(const Geom& g, const PixIndex& pi, co
         const size_t e0 = ((size_t)j * D + c) * N + p;
         if (valid) {
             ldw(e0, vc[c]);
-            dt[c].load_t(dT + e0);
+            dt[c].load_t_cs(dT + e0);
             if (FUSED) vc[c].store(src.pout + e0);
         } else {
             vc[c].zero();

@@ -80,10 +80,10 @@ __device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, c
     pix_pos(pi, px, xx, yy, zz);
     const size_t e0 = (size_t)plane * g.N + px;
     V<VEC> dt, pv, qv, xv, rv;
-    dt.load_t(dT + e0);
-    pv.load(p + e0);
-    qv.load(q + e0);
-    xv.load_rw(x + e0);
+    dt.load_t_cs(dT + e0);   // grad T, q and x: next read after the other passes of the step
+    pv.load(p + e0);         // p: read again by the direction step that follows
+    qv.load_cs(q + e0);
+    xv.load_cs(x + e0);
     rv.load_rw(r + e0);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
@@ -93,8 +93,8 @@ __device__ __forceinline__ void update_item(const Geom& g, const PixIndex& pi, c
         rz = fmaf(rv.a[e], zv, rz);
         rr = fmaf(rv.a[e], rv.a[e], rr);
     }
-    xv.store(x + e0);
-    rv.store(r + e0);
+    xv.store_cs(x + e0);
+    rv.store(r + e0);        // r: read by the direction step that follows
 }
 
 // The PCG update.  It first completes the Hessian-product pass before it:
