@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-affine", action="store_true")
     ap.add_argument("--no-volume", action="store_true")
+    ap.add_argument("--no-ugrid", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time launch shapes and PCG paths on first use (warm-up steps)")
     ap.add_argument("--cpu-sample-frames", type=int, default=25)
@@ -153,16 +154,25 @@ def measured_peaks():
         return None
 
 
+MATVEC_SOURCES = ("k_gn.cu", "gn_items.cuh")   # the Hessian-product kernel and its per-item body
+
+
+def matvec_source_digest():
+    h = hashlib.sha256()
+    for name in MATVEC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2001_06613_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def matvec_traffic_per_pixel_frame():
     """DRAM bytes per pixel-frame of the Hessian-product kernel from the ncu
     capture recorded in profiles/gn_matvec_paper_scale.json, if that capture
-    was taken on the current kernel source (same hash of csrc/k_gn.cu)."""
+    was taken on the current kernel source (same hash of csrc/k_gn.cu and
+    csrc/gn_items.cuh)."""
     path = os.path.join(ROOT, "profiles", "gn_matvec_paper_scale.json")
-    src = os.path.join(ROOT, "paper_2001_06613_gb300", "csrc", "k_gn.cu")
     try:
         rec = json.load(open(path))
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("k_gn_cu_sha256_16") != digest:
+        if rec.get("kernel_source_sha256_16") != matvec_source_digest():
             return None
         return float(rec["dram_bytes_per_pixel_frame"])
     except Exception:
@@ -766,6 +776,46 @@ def run_volume(S, torch, dev, peak_gbs: float):
     return out
 
 
+def run_ugrid(S, torch, dev, R_dev, n, shape, L, Q, s: int = 1, repeats: int = 2):
+    """The paper-scale sequence registered (STML) with the unknowns of every
+    level on its image grid coarsened by 2^s (params.u_coarsen): frames/s
+    (one warm-up, then the mean of `repeats` registrations, L2 flushed before
+    each), Gauss-Newton / CG counts and the final objective of that
+    discretisation, beside the field-grid size."""
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = S.Context(S.stml_default_params(n_levels=L, n_tlevels=Q, u_coarsen=s), stream.cuda_stream)
+    try:
+        def reg():
+            S.stml_load_sequence(ctx.ptr, R_dev)
+            S.stml_build_pyramid(ctx.ptr)
+            return S.stml_register(ctx.ptr, S.MODE_STML)
+
+        reg()
+        times = []
+        for _ in range(repeats):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stats = reg()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        cshape = tuple(m // 2 ** s for m in shape)
+        w = torch.empty((n, len(shape)) + cshape, dtype=torch.float32, device=dev)
+        S.stml_get_field(ctx.ptr, L - 1, w)
+        J = S.stml_eval_ugrid(ctx.ptr, L - 1, list(range(n)), w)[0]
+        return {"workload": f"{n} frames {'x'.join(map(str, shape))} fp32, {L} spatial x {Q} temporal levels, "
+                            f"STML, unknowns on the image grid coarsened by 2^{s} (finest {'x'.join(map(str, cshape))})",
+                "u_coarsen": s, "frames_per_s": n / (statistics.mean(times) / 1e3), "ms": times,
+                "final_J": J, "gn_iters": sum(t["gn_iters"] for t in stats),
+                "cg_iters": sum(t["cg_iters"] for t in stats),
+                "note": "PCG coefficients taken on the host (two waits per CG step); J is the coarse-grid "
+                        "objective (S and P on the coarse grid), not comparable with the headline's"}
+    finally:
+        ctx.close()
+
+
 def run_affine(S, torch, dev, repeats: int = 2):
     """The paper's own setting (Sec. 4): one affine-linear map per frame,
     L-BFGS (Sec. 2), 129 frames with |K_0| = 17, |K_1| = 33 (4 temporal
@@ -978,6 +1028,10 @@ def run_native(args):
         pk = measured_peaks()
         volume = run_volume(S, torch, dev, pk["hbm_gbs"] if pk else 6800.0)
 
+    ugrid = None
+    if not args.no_ugrid and rank == 0 and world == 1 and args.image_dtype == "f32":
+        ugrid = run_ugrid(S, torch, dev, R_dev, n, shape, L, Q)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         frames = min(args.cpu_sample_frames, n)
@@ -1056,7 +1110,7 @@ def run_native(args):
                 "gir_stats": [{k: s[k] for k in ("level", "tlevel", "n_frames", "gn_iters", "cg_iters",
                                                  "ls_trials", "stopped_early")} for s in stats],
                 "spml": spml, "batch": batch, "learned": learned, "affine": affine, "volume": volume,
-                "tuning": tuning}
+                "ugrid": ugrid, "tuning": tuning}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
