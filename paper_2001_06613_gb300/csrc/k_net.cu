@@ -5,9 +5,9 @@
 // only where the objective of eq. (1) is lower there than at the classical
 // predictor's.
 //
-// Convolutions are implicit GEMMs on the tensor cores.  Forward and input
-// gradient: tcgen05.mma into tensor memory (conv3_kernel); weight gradient:
-// mma.sync m16n8k16 from ldmatrix fragments (wgrad3_kernel).
+// Convolutions are implicit GEMMs on the tensor cores, tcgen05.mma into
+// tensor memory: forward and input gradient (conv3_kernel), weight gradient
+// (wgrad_tc_kernel).
 //   forward:        Y[p][co]  = sum_{tap, ci} X[p + off(tap)][ci] W[tap][ci][co]
 //   input gradient: dX[p][ci] = sum_{tap, co} G[p + off(tap)][co] W[8 - tap][ci][co]
 //                   (the same kernel with the flipped, transposed weights)
@@ -43,30 +43,6 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// XOR swizzles of 16-byte segments: rows of 64 bytes (4 segments) and of
-// 128 bytes (8 segments); eight consecutive rows at one logical segment land
-// on 32 distinct banks, so ldmatrix phases are conflict-free.
-__device__ __forceinline__ int swz4(int row, int seg) { return seg ^ ((row >> 1) & 3); }
-__device__ __forceinline__ int swz8(int row, int seg) { return seg ^ (row & 7); }
-template <int BN>
-__device__ __forceinline__ int swzB(int row, int seg) {
-    return BN == 64 ? swz8(row, seg) : swz4(row, seg);
 }
 
 __device__ __forceinline__ float slope(float y) { return y > 0.f ? 1.f : kSlope; }
@@ -194,17 +170,6 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
         : "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 }  // namespace
@@ -427,7 +392,8 @@ static cudaError_t conv3_go(const ConvIn& in, const bf16* Wh, int Cin, int N, in
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)B * ((H + 15) / 16) * ((W + 7) / 8);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    // a few CTAs per SM, each running a sequence of tiles
+    // a few CTAs per SM, each running a sequence of tiles (twice the CTAs
+    // that fit at once: measured faster than one wave of resident CTAs)
     const long long per_sm = BN <= 32 ? 3 : BN <= 64 ? 2 : 1;
     const int sms = device_sms();
     long long ctas = (long long)(sms > 0 ? sms : 152) * per_sm * 2 / (N / BN);
