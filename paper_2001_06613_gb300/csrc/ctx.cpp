@@ -139,6 +139,7 @@ struct stml_ctx {
     double *ug_part = nullptr, *ug_out = nullptr, *ug_outh = nullptr;
     size_t ug_part_cap = 0;
     unsigned int* ug_tk = nullptr;
+    UgCg *ug_cg = nullptr, *ug_cgh = nullptr;   // device state of the coarse-grid PCG solve, pinned host copy
 
     std::vector<stml_stats> last_stats;   // per GIR of the last registration
     std::string err;
@@ -258,8 +259,11 @@ void free_buffers(stml_ctx* c) {
     dfree(c->ug_part);
     dfree(c->ug_out);
     dfree(c->ug_tk);
+    dfree(c->ug_cg);
     if (c->ug_outh) cudaFreeHost(c->ug_outh);
+    if (c->ug_cgh) cudaFreeHost(c->ug_cgh);
     c->ug_outh = nullptr;
+    c->ug_cgh = nullptr;
     c->ug_part_cap = 0;
     dfree(c->d_frames); dfree(c->d_wnext); dfree(c->d_idx); dfree(c->d_lsf);
     dfree(c->d_kidx); dfree(c->d_taps); dfree(c->d_rho);
@@ -816,8 +820,16 @@ stml_status ensure_ugrid(stml_ctx* c) {
     ok = ok && dalloc(&c->ug_out, 16) == cudaSuccess;
     ok = ok && dalloc(&c->ug_tk, 8) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->ug_outh, 16 * sizeof(double)) == cudaSuccess;
+    ok = ok && dalloc(&c->ug_cg, 1) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&c->ug_cgh, sizeof(UgCg)) == cudaSuccess;
     if (!ok) return fail(c, STML_ENOMEM, "device allocation of the coarse-grid solver buffers failed");
     CK(c, cudaMemsetAsync(c->ug_tk, 0, 8 * sizeof(unsigned int), c->stream));
+    // the PCG state mirrors its `active` word into the context's cg_active,
+    // which gates the image-grid kernels of the Hessian product
+    std::memset(c->ug_cgh, 0, sizeof(UgCg));
+    c->ug_cgh->mirror = &c->S->cg_active;
+    CK(c, cudaMemcpyAsync(c->ug_cg, c->ug_cgh, sizeof(UgCg), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
     return STML_OK;
 }
 
@@ -904,6 +916,23 @@ struct UgEval {
         return STML_OK;
     }
 
+    // One PCG step's Hessian product q = H p, every launch gated on the solve
+    // still running; the last CTA of the regulariser pass takes alpha.
+    stml_status hess_step(const float* pv, float* qv) {
+        const double pf = (double)fs.nK * (double)g.N;
+        const int* gate = &c->S->cg_active;
+        long pe = prof_begin(c, PC_PROLONG, level);
+        CK(c, launch_ugrid_prolong(pv, nullptr, 0.f, c->w_p, planes, ug, c->stream, gate));
+        prof_end(c, pe, 4.0 * g.d * pf, pf);
+        TRY(hessvec_launch(c, level, g, fs, cf0, c->w_dT, c->w_p, c->w_q, c->S));
+        pe = prof_begin(c, PC_PROLONG, level);
+        CK(c, launch_ugrid_adjoint(c->w_q, qv, planes, ug, c->stream, gate));
+        prof_end(c, pe, 4.0 * g.d * pf, pf);
+        CK(c, launch_ugrid_reg(1, gw, fs, cw, pv, nullptr, 0.f, qv, qv, c->ug_part, c->ug_part_cap, &c->ug_tk[1],
+                               c->ug_out + 5, c->stream, c->ug_cg));
+        return STML_OK;
+    }
+
     stml_status jacobi() {
         CK(c, launch_ugrid_jacobi(c->w_dT, c->ug_m, ug, fs, cf0, cw, c->stream));
         return STML_OK;
@@ -937,8 +966,10 @@ stml_status ug_dot(stml_ctx* c, long long n, const float* a, const float* b, dou
 }
 
 // GIR(K) with the unknowns on the coarse grid (u_coarsen = s > 0): the same
-// Gauss-Newton / Jacobi-PCG / Armijo scheme and stopping tests as run_gir,
-// with the PCG coefficients taken on the host from the device reductions.
+// Gauss-Newton / Jacobi-PCG / Armijo scheme and stopping tests as run_gir;
+// the PCG coefficients and stopping decisions are taken on the device (FP64
+// from the deterministic reductions), the host reads the solve's state once
+// per chunk of queued steps.
 stml_status run_gir_ugrid(stml_ctx* c, int level, const std::vector<int>& K, float* w_io, stml_stats* st) {
     Range rg("GIR on the coarse field grid, level %d |K| %d", level, (int)K.size());
     const auto t_start = std::chrono::steady_clock::now();
@@ -957,7 +988,7 @@ stml_status run_gir_ugrid(stml_ctx* c, int level, const std::vector<int>& K, flo
     const double J0 = ev[0];
     double J = ev[0], gnorm2 = ev[4], wnorm2 = ev[5], J_old = 0.0, step_norm = 0.0;
     s.J0 = J0;
-    int it = 0;
+    int it = 0, predict_cg = 8;
     double last[4] = {ev[0], ev[1], ev[2], ev[3]};
     for (;;) {
         if (!std::isfinite(J) || !std::isfinite(gnorm2)) {
@@ -977,32 +1008,36 @@ stml_status run_gir_ugrid(stml_ctx* c, int level, const std::vector<int>& K, flo
         TRY(E.jacobi());
         int steps = 0;
         if (gnorm > 0.0) {
+            // the coefficients stay on the device; the host queues the
+            // previous solve's step count, then chunks of 4, and reads the
+            // state once per chunk (launches after the stop return at once)
             CK(c, launch_ugrid_vec(VEC_INIT, M, 0.f, c->ug_m, c->ug_x, c->ug_r, c->ug_z, c->ug_p, nullptr, c->ug_g,
-                                   c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6, c->stream));
-            TRY(ug_read(c, 8));
-            double rho = c->ug_outh[6];
-            while (steps < p.max_cg) {
-                double pq = 0.0;
-                TRY(E.hess(c->ug_p, c->ug_q, &pq));
-                if (pq <= 0.0) {   // breakdown: the iterate so far, or the preconditioned gradient on the first step
-                    if (steps == 0)
-                        CK(c, cudaMemcpyAsync(c->ug_x, c->ug_z, (size_t)M * sizeof(float), cudaMemcpyDeviceToDevice,
-                                              c->stream));
-                    break;
+                                   c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6, c->stream, c->ug_cg,
+                                   p.tol_cg * gnorm, p.max_cg));
+            int launched = 0, chunk = std::max(2, predict_cg);
+            for (;;) {
+                const int nq = std::min(chunk, p.max_cg - launched);
+                for (int i = 0; i < nq; ++i) {
+                    TRY(E.hess_step(c->ug_p, c->ug_q));
+                    CK(c, launch_ugrid_vec(VEC_STEP, M, 0.f, c->ug_m, c->ug_x, c->ug_r, c->ug_z, c->ug_p, c->ug_q,
+                                           nullptr, c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6,
+                                           c->stream, c->ug_cg));
+                    CK(c, launch_ugrid_vec(VEC_DIR, M, 0.f, nullptr, nullptr, nullptr, c->ug_z, c->ug_p, nullptr,
+                                           nullptr, c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6,
+                                           c->stream, c->ug_cg));
                 }
-                const double alpha = rho / pq;
-                CK(c, launch_ugrid_vec(VEC_STEP, M, (float)alpha, c->ug_m, c->ug_x, c->ug_r, c->ug_z, c->ug_p,
-                                       c->ug_q, nullptr, c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6,
-                                       c->stream));
-                TRY(ug_read(c, 8));
-                ++steps;
-                if (std::sqrt(c->ug_outh[6]) <= p.tol_cg * gnorm) break;
-                const double rho_new = c->ug_outh[7];
-                const double beta = rho_new / rho;
-                rho = rho_new;
-                CK(c, launch_ugrid_vec(VEC_DIR, M, (float)beta, nullptr, nullptr, nullptr, c->ug_z, c->ug_p, nullptr,
-                                       nullptr, c->ug_part, c->ug_part_cap, &c->ug_tk[2], c->ug_out + 6, c->stream));
+                launched += nq;
+                CK(c, cudaMemcpyAsync(c->ug_cgh, c->ug_cg, sizeof(UgCg), cudaMemcpyDeviceToHost, c->stream));
+                CK(c, cudaStreamSynchronize(c->stream));
+                if (!c->ug_cgh->active || launched >= p.max_cg) break;
+                chunk = 4;
             }
+            steps = c->ug_cgh->iter;
+            predict_cg = steps;
+            // breakdown on the first step: the preconditioned gradient
+            if (c->ug_cgh->flag == CG_BREAKDOWN && steps == 0)
+                CK(c, cudaMemcpyAsync(c->ug_x, c->ug_z, (size_t)M * sizeof(float), cudaMemcpyDeviceToDevice,
+                                      c->stream));
         } else {
             CK(c, cudaMemsetAsync(c->ug_x, 0, (size_t)M * sizeof(float), c->stream));
         }

@@ -324,10 +324,10 @@ size_t gn_partials(const Geom& g, int nK) {
 }
 
 cudaError_t launch_hess_sums(const Geom& g, const FrameSet& fs, const float* dT, const float* v, float* mean_s,
-                             float* sum_v, cudaStream_t s) {
+                             float* sum_v, cudaStream_t s, const int* gate) {
     Coef cf{};
     return tile_launch<TILE_SUMS>(g, fs, cf, Stored{dT, ST_F32}, const_cast<float*>(v), nullptr, nullptr, nullptr, mean_s, sum_v,
-                                  nullptr, nullptr, PcgArgs{0.f, 0}, s);
+                                  nullptr, nullptr, PcgArgs{0.f, 0}, s, gate);
 }
 
 cudaError_t launch_hess_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const float* v,

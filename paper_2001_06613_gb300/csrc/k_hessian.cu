@@ -11,7 +11,8 @@ cudaError_t launch_hessvec(const Geom& g, const FrameSet& fs, const Coef& cf, co
                            const float* v, float* Hv, HessWork& w, unsigned int* ticket,
                            double* out, DevScalars* pcg, cudaStream_t s) {
     if (fs.nK <= 0) return cudaErrorInvalidValue;
-    cudaError_t e = launch_hess_sums(g, fs, dT, v, w.mean_s, w.sum_v, s);
+    // a PCG step (pcg given) does nothing once the solve has stopped
+    cudaError_t e = launch_hess_sums(g, fs, dT, v, w.mean_s, w.sum_v, s, pcg ? &pcg->cg_active : nullptr);
     if (e != cudaSuccess) return e;
     return launch_hess_apply(g, fs, cf, dT, v, w.mean_s, w.sum_v, Hv, w.partials, w.partials_cap, ticket, out, pcg, s);
 }

@@ -54,8 +54,9 @@ __device__ __forceinline__ void coords(long long p, int nx, int ny, int& x, int&
 
 __global__ void __launch_bounds__(kThreads)
 ugrid_prolong_kernel(const float* __restrict__ w, const float* __restrict__ dw, float t, float* __restrict__ u,
-                     long long planes, UGrid ug) {
+                     long long planes, UGrid ug, const int* gate) {
     pdl_enter();
+    if (gate && !*gate) return;
     const long long total = planes * ug.N;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
@@ -96,8 +97,9 @@ ugrid_prolong_kernel(const float* __restrict__ w, const float* __restrict__ dw, 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads)
 ugrid_gather_kernel(const float* __restrict__ f, float* __restrict__ out, long long planes, UGrid ug, FrameSet fs,
-                    Coef cf, Coef cw) {
+                    Coef cf, Coef cw, const int* gate) {
     pdl_enter();
+    if (gate && !*gate) return;
     const long long total = planes * ug.Nc;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const int hF = ug.F / 2, F3 = 3 * ug.F / 2;
@@ -160,8 +162,10 @@ ugrid_gather_kernel(const float* __restrict__ f, float* __restrict__ out, long l
 template <int MODE>
 __global__ void __launch_bounds__(kThreads)
 ugrid_reg_kernel(Geom gw, FrameSet fs, Coef cw, const float* __restrict__ w, const float* __restrict__ dw, float t,
-                 const float* gin, float* gout, double* __restrict__ partials, unsigned int* ticket, double* out) {
+                 const float* gin, float* gout, double* __restrict__ partials, unsigned int* ticket, double* out,
+                 UgCg* cg) {
     pdl_enter();
+    if (cg && !cg->active) return;
     const long long Nc = gw.N;
     const long long items = Nc * gw.d;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -223,7 +227,17 @@ ugrid_reg_kernel(Geom gw, FrameSet fs, Coef cw, const float* __restrict__ w, con
         grid_reduce<5>(acc, partials, ticket, out);
     } else {
         float acc[1] = {(float)a_pq};
-        grid_reduce<1>(acc, partials, ticket, out);
+        if (grid_reduce<1>(acc, partials, ticket, out) && threadIdx.x == 0 && cg) {
+            const double pq = out[0];   // the PCG decision of this step: alpha or breakdown
+            cg->pq = pq;
+            if (!(pq > 0.0)) {
+                cg->flag = CG_BREAKDOWN;
+                cg->active = 0;
+                if (cg->mirror) *cg->mirror = 0;
+            } else {
+                cg->alpha = cg->rho / pq;
+            }
+        }
     }
 }
 
@@ -237,8 +251,13 @@ ugrid_reg_kernel(Geom gw, FrameSet fs, Coef cw, const float* __restrict__ w, con
 template <int MODE>
 __global__ void __launch_bounds__(kThreads)
 ugrid_vec_kernel(long long n, float a, const float* Minv, float* x, float* r, float* z, float* p, const float* q,
-                 const float* g, double* __restrict__ partials, unsigned int* ticket, double* out) {
+                 const float* g, double* __restrict__ partials, unsigned int* ticket, double* out, UgCg* cg,
+                 double thr, int max_cg) {
     pdl_enter();
+    if (cg && (MODE == VEC_STEP || MODE == VEC_DIR)) {
+        if (!cg->active) return;
+        a = (float)(MODE == VEC_STEP ? cg->alpha : cg->beta);
+    }
     const long long stride = (long long)gridDim.x * blockDim.x;
     double s0 = 0.0, s1 = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -267,7 +286,32 @@ ugrid_vec_kernel(long long n, float a, const float* Minv, float* x, float* r, fl
     }
     if (MODE == VEC_INIT || MODE == VEC_STEP) {
         float acc[2] = {(float)s0, (float)s1};
-        grid_reduce<2>(acc, partials, ticket, out);
+        if (grid_reduce<2>(acc, partials, ticket, out) && threadIdx.x == 0 && cg) {
+            if (MODE == VEC_INIT) {   // start: rho = <r, z>; stop at ||r|| <= thr
+                cg->rho = out[0];
+                cg->thr = thr;
+                cg->iter = 0;
+                cg->max_cg = max_cg;
+                cg->pq = 0.0;
+                cg->rnorm2 = out[1];
+                cg->flag = !(out[1] > 0.0) ? CG_ZERO : max_cg <= 0 ? CG_MAXIT : CG_RUNNING;
+                cg->active = cg->flag == CG_RUNNING;
+            } else {                  // after x += alpha p, r -= alpha q: stop, or beta = <r, z> / rho
+                cg->iter += 1;
+                cg->rnorm2 = out[0];
+                if (sqrt(out[0]) <= cg->thr) {
+                    cg->flag = CG_CONVERGED;
+                    cg->active = 0;
+                } else if (cg->iter >= cg->max_cg) {
+                    cg->flag = CG_MAXIT;
+                    cg->active = 0;
+                } else {
+                    cg->beta = out[1] / cg->rho;
+                    cg->rho = out[1];
+                }
+            }
+            if (cg->mirror) *cg->mirror = cg->active;
+        }
     } else if (MODE == VEC_DOT) {
         float acc[1] = {(float)s0};
         grid_reduce<1>(acc, partials, ticket, out);
@@ -293,21 +337,22 @@ UGrid make_ugrid(const Geom& fine, int s) {
 }
 
 cudaError_t launch_ugrid_prolong(const float* w, const float* dw, float t, float* u, long long planes,
-                                 const UGrid& ug, cudaStream_t s) {
+                                 const UGrid& ug, cudaStream_t s, const int* gate) {
     const long long total = planes * ug.N;
     if (total <= 0) return cudaSuccess;
     const unsigned grid = resident_grid((const void*)ugrid_prolong_kernel, (total + kThreads - 1) / kThreads, 152 * 8);
     count_launches(1);
-    return launch_pdl(ugrid_prolong_kernel, dim3(grid), dim3(kThreads), 0, s, w, dw, t, u, planes, ug);
+    return launch_pdl(ugrid_prolong_kernel, dim3(grid), dim3(kThreads), 0, s, w, dw, t, u, planes, ug, gate);
 }
 
-cudaError_t launch_ugrid_adjoint(const float* f, float* out, long long planes, const UGrid& ug, cudaStream_t s) {
+cudaError_t launch_ugrid_adjoint(const float* f, float* out, long long planes, const UGrid& ug, cudaStream_t s,
+                                 const int* gate) {
     const long long total = planes * ug.Nc;
     if (total <= 0) return cudaSuccess;
     const unsigned grid = resident_grid((const void*)ugrid_gather_kernel<0>, (total + kThreads - 1) / kThreads, 152 * 8);
     count_launches(1);
     return launch_pdl(ugrid_gather_kernel<0>, dim3(grid), dim3(kThreads), 0, s, f, out, planes, ug, FrameSet{},
-                      Coef{}, Coef{});
+                      Coef{}, Coef{}, gate);
 }
 
 cudaError_t launch_ugrid_jacobi(const float* dT, float* Minv, const UGrid& ug, const FrameSet& fs, const Coef& cf,
@@ -317,23 +362,25 @@ cudaError_t launch_ugrid_jacobi(const float* dT, float* Minv, const UGrid& ug, c
     if (total <= 0) return cudaSuccess;
     const unsigned grid = resident_grid((const void*)ugrid_gather_kernel<1>, (total + kThreads - 1) / kThreads, 152 * 8);
     count_launches(1);
-    return launch_pdl(ugrid_gather_kernel<1>, dim3(grid), dim3(kThreads), 0, s, dT, Minv, planes, ug, fs, cf, cw);
+    return launch_pdl(ugrid_gather_kernel<1>, dim3(grid), dim3(kThreads), 0, s, dT, Minv, planes, ug, fs, cf, cw,
+                      (const int*)nullptr);
 }
 
 cudaError_t launch_ugrid_reg(int mode, const Geom& gw, const FrameSet& fs, const Coef& cw, const float* w,
                              const float* dw, float t, const float* gin, float* gout, double* partials,
-                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s) {
+                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s, UgCg* cg) {
     const long long items = gw.N * gw.d;
     auto k = mode == 0 ? ugrid_reg_kernel<0> : ugrid_reg_kernel<1>;
     const unsigned grid = resident_grid((const void*)k, (items + kThreads - 1) / kThreads, 152 * 8);
     if ((size_t)grid * 5 > partials_cap) return cudaErrorInvalidValue;
     count_launches(1);
-    return launch_pdl(k, dim3(grid), dim3(kThreads), 0, s, gw, fs, cw, w, dw, t, gin, gout, partials, ticket, out);
+    return launch_pdl(k, dim3(grid), dim3(kThreads), 0, s, gw, fs, cw, w, dw, t, gin, gout, partials, ticket, out,
+                      mode == 1 ? cg : nullptr);
 }
 
 cudaError_t launch_ugrid_vec(int mode, long long n, float a, const float* Minv, float* x, float* r, float* z,
                              float* p, const float* q, const float* g, double* partials, size_t partials_cap,
-                             unsigned int* ticket, double* out, cudaStream_t s) {
+                             unsigned int* ticket, double* out, cudaStream_t s, UgCg* cg, double thr, int max_cg) {
     if (n <= 0) return cudaErrorInvalidValue;
     const void* kp = nullptr;
     switch (mode) {
@@ -349,7 +396,7 @@ cudaError_t launch_ugrid_vec(int mode, long long n, float a, const float* Minv, 
     count_launches(1);
 #define STML_VEC(M_) \
     return launch_pdl(ugrid_vec_kernel<M_>, dim3(grid), dim3(kThreads), 0, s, n, a, Minv, x, r, z, p, q, g, partials, \
-                      ticket, out)
+                      ticket, out, cg, thr, max_cg)
     switch (mode) {
         case VEC_INIT: STML_VEC(VEC_INIT);
         case VEC_STEP: STML_VEC(VEC_STEP);

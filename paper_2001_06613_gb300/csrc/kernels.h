@@ -230,7 +230,7 @@ size_t gn_partials(const Geom& g, int nK);
 // The two halves of the Hessian product (k_gn.cu): per-pixel frame sums of v
 // (mean of grad T . v, sum of v) and the stencil stream that uses them.
 cudaError_t launch_hess_sums(const Geom& g, const FrameSet& fs, const float* dT, const float* v, float* mean_s,
-                             float* sum_v, cudaStream_t s);
+                             float* sum_v, cudaStream_t s, const int* gate = nullptr);
 cudaError_t launch_hess_apply(const Geom& g, const FrameSet& fs, const Coef& cf, const float* dT, const float* v,
                               const float* mean_s, const float* sum_v, float* Hv, double* partials,
                               size_t partials_cap, unsigned int* ticket, double* out, DevScalars* pcg,
@@ -371,25 +371,43 @@ struct UGrid {
     long long N, Nc;
 };
 UGrid make_ugrid(const Geom& fine, int s);
-// u = P_s (w + t dw) for `planes` planes (dw may be null).
+// Device-resident state of a coarse-grid PCG solve: the coefficients (FP64,
+// applied in float), the stopping threshold tol_cg ||g||, the step count and
+// the CG_* flag.  `mirror` (may be null) receives `active` as well, for the
+// image-grid kernels of the Hessian product that are gated on it.
+struct UgCg {
+    double rho, thr, alpha, beta, pq, rnorm2;
+    int active, iter, flag, max_cg;
+    int* mirror;
+};
+// u = P_s (w + t dw) for `planes` planes (dw may be null); nothing when
+// gate != null and *gate == 0.
 cudaError_t launch_ugrid_prolong(const float* w, const float* dw, float t, float* u, long long planes,
-                                 const UGrid& ug, cudaStream_t s);
-// out = P_s^T f (fixed-order gather per coarse value).
-cudaError_t launch_ugrid_adjoint(const float* f, float* out, long long planes, const UGrid& ug, cudaStream_t s);
+                                 const UGrid& ug, cudaStream_t s, const int* gate = nullptr);
+// out = P_s^T f (fixed-order gather per coarse value); gated like the prolongation.
+cudaError_t launch_ugrid_adjoint(const float* f, float* out, long long planes, const UGrid& ug, cudaStream_t s,
+                                 const int* gate = nullptr);
 // Minv = 1 / Jacobi diagonal of the coarse-grid Hessian from the image-grid
 // grad T (float), cf the image grid's and cw the coarse grid's coefficients.
 cudaError_t launch_ugrid_jacobi(const float* dT, float* Minv, const UGrid& ug, const FrameSet& fs, const Coef& cf,
                                 const Coef& cw, cudaStream_t s);
 // S and P on the coarse grid gw at w + t dw; mode 0: objective sums (5
 // values to out) and, with gout, the gradient gin + regulariser/penalty
-// gradient; mode 1: gout = gin + their Hessian product, out[0] = <w, gout>.
+// gradient; mode 1: gout = gin + their Hessian product, out[0] = <w, gout>;
+// with cg (mode 1, a PCG step): nothing once cg->active is 0, and the last
+// CTA takes alpha = rho / <p, Hp> or the breakdown decision.
 cudaError_t launch_ugrid_reg(int mode, const Geom& gw, const FrameSet& fs, const Coef& cw, const float* w,
                              const float* dw, float t, const float* gin, float* gout, double* partials,
-                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s);
+                             size_t partials_cap, unsigned int* ticket, double* out, cudaStream_t s,
+                             UgCg* cg = nullptr);
 enum UgridVecMode { VEC_INIT = 0, VEC_STEP = 1, VEC_DIR = 2, VEC_DOT = 3, VEC_AXPY = 4 };
 // PCG vector steps and dot products over n coarse values (see k_ugrid.cu).
+// With cg: VEC_INIT starts the solve (thr = tol_cg ||g||), VEC_STEP and
+// VEC_DIR take alpha / beta from it and do nothing once it stopped, and
+// VEC_STEP's last CTA takes the stopping decision.
 cudaError_t launch_ugrid_vec(int mode, long long n, float a, const float* Minv, float* x, float* r, float* z,
                              float* p, const float* q, const float* g, double* partials, size_t partials_cap,
-                             unsigned int* ticket, double* out, cudaStream_t s);
+                             unsigned int* ticket, double* out, cudaStream_t s, UgCg* cg = nullptr,
+                             double thr = 0.0, int max_cg = 0);
 
 }  // namespace stml
