@@ -810,8 +810,8 @@ def run_ugrid(S, torch, dev, R_dev, n, shape, L, Q, s: int = 1, repeats: int = 2
                 "u_coarsen": s, "frames_per_s": n / (statistics.mean(times) / 1e3), "ms": times,
                 "final_J": J, "gn_iters": sum(t["gn_iters"] for t in stats),
                 "cg_iters": sum(t["cg_iters"] for t in stats),
-                "note": "PCG coefficients taken on the host (two waits per CG step); J is the coarse-grid "
-                        "objective (S and P on the coarse grid), not comparable with the headline's"}
+                "note": "J is the coarse-grid objective (S and P on the coarse grid), not comparable with the "
+                        "headline's"}
     finally:
         ctx.close()
 
