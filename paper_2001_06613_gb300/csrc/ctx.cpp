@@ -140,6 +140,7 @@ struct stml_ctx {
     size_t ug_part_cap = 0;
     unsigned int* ug_tk = nullptr;
     UgCg *ug_cg = nullptr, *ug_cgh = nullptr;   // device state of the coarse-grid PCG solve, pinned host copy
+    size_t ug_cap = 0;                           // floats each coarse-grid vector holds
 
     std::vector<stml_stats> last_stats;   // per GIR of the last registration
     std::string err;
@@ -264,6 +265,7 @@ void free_buffers(stml_ctx* c) {
     if (c->ug_cgh) cudaFreeHost(c->ug_cgh);
     c->ug_outh = nullptr;
     c->ug_cgh = nullptr;
+    c->ug_cap = 0;
     c->ug_part_cap = 0;
     dfree(c->d_frames); dfree(c->d_wnext); dfree(c->d_idx); dfree(c->d_lsf);
     dfree(c->d_kidx); dfree(c->d_taps); dfree(c->d_rho);
@@ -810,8 +812,21 @@ stml_status run_gir(stml_ctx* c, int level, const std::vector<int>& K, float* u_
 // Buffers of the coarse-grid solver (allocated on first use, sized for the
 // finest level and all frames).
 stml_status ensure_ugrid(stml_ctx* c) {
-    if (c->ug_g) return STML_OK;
     const size_t M = (size_t)c->n * c->d * field_geom(c, (int)c->lv.size() - 1).N;
+    if (c->ug_g && c->ug_cap >= M) return STML_OK;
+    if (c->ug_g) {   // u_coarsen was lowered since the buffers were made: make them again, larger
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (float** fp : {&c->ug_g, &c->ug_x, &c->ug_r, &c->ug_z, &c->ug_p, &c->ug_q, &c->ug_m, &c->ug_w}) dfree(*fp);
+        dfree(c->ug_part);
+        dfree(c->ug_out);
+        dfree(c->ug_tk);
+        dfree(c->ug_cg);
+        if (c->ug_outh) cudaFreeHost(c->ug_outh);
+        if (c->ug_cgh) cudaFreeHost(c->ug_cgh);
+        c->ug_outh = nullptr;
+        c->ug_cgh = nullptr;
+    }
+    c->ug_cap = 0;
     bool ok = true;
     for (float** fp : {&c->ug_g, &c->ug_x, &c->ug_r, &c->ug_z, &c->ug_p, &c->ug_q, &c->ug_m, &c->ug_w})
         ok = ok && dalloc(fp, M) == cudaSuccess;
@@ -823,6 +838,7 @@ stml_status ensure_ugrid(stml_ctx* c) {
     ok = ok && dalloc(&c->ug_cg, 1) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->ug_cgh, sizeof(UgCg)) == cudaSuccess;
     if (!ok) return fail(c, STML_ENOMEM, "device allocation of the coarse-grid solver buffers failed");
+    c->ug_cap = M;
     CK(c, cudaMemsetAsync(c->ug_tk, 0, 8 * sizeof(unsigned int), c->stream));
     // the PCG state mirrors its `active` word into the context's cg_active,
     // which gates the image-grid kernels of the Hessian product

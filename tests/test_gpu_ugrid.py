@@ -183,3 +183,29 @@ def test_invalid_combinations_are_refused(S):
             S.stml_eval_ugrid(ctx.ptr, 1, [0, 1], _dev(np.zeros((2, 2, 10, 10))))
     finally:
         ctx.close()
+
+
+def test_lowering_u_coarsen_on_a_loaded_context(S):
+    """The coarse-grid buffers made for 2^2 coarsening are made again, larger,
+    when stml_set_params lowers u_coarsen to 1 on the loaded context: the
+    evaluation equals that of a context created with u_coarsen = 1."""
+    import torch
+    R = synthetic.make_sequence(synthetic.spec_custom(4, (64, 48), seed=9, amp=1.2))
+    frames = [0, 1, 2, 3]
+    rng = np.random.default_rng(3)
+    w1 = _dev(synthetic.random_field(rng, 4, 2, (32, 24), amp=1.0, rough=0.3))
+    w2 = _dev(synthetic.random_field(rng, 4, 2, (16, 12), amp=1.0, rough=0.3))
+    ref = _ctx(S, R, n_levels=1, u_coarsen=1)
+    ctx = _ctx(S, R, n_levels=1, u_coarsen=2)
+    try:
+        g_ref = torch.empty_like(w1)
+        out_ref = S.stml_eval_ugrid(ref.ptr, 0, frames, w1, g_ref)
+        S.stml_eval_ugrid(ctx.ptr, 0, frames, w2, torch.empty_like(w2))   # buffers for s = 2
+        S.stml_set_params(ctx.ptr, S.stml_default_params(n_levels=1, u_coarsen=1))
+        g = torch.empty_like(w1)
+        out = S.stml_eval_ugrid(ctx.ptr, 0, frames, w1, g)
+        assert np.array_equal(out, out_ref)
+        assert torch.equal(g, g_ref)
+    finally:
+        ctx.close()
+        ref.close()
