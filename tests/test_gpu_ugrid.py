@@ -225,3 +225,41 @@ def test_register_3d_matches_oracle(S):
     Jo = multilevel.final_objective(R.astype(np.float64), res.y, op)["J"]
     assert abs(Jg - Jo) <= 1e-4 * Jo, (Jg, Jo)
     assert float(np.sqrt(np.mean((y - res.y) ** 2))) <= 1e-3
+
+
+def test_full_size_finest_level(S):
+    """All 200 frames of 256 x 256 (the paper-scale sequence) with the unknowns
+    on the 128 x 128 grid: objective, gradient, Jacobi inverse and Hessian
+    product element by element against the oracle."""
+    import torch
+    R = synthetic.make_sequence(synthetic.spec_paper_scale())
+    ctx = _ctx(S, R, n_levels=4, u_coarsen=1)
+    try:
+        frames = list(range(200))
+        rng = np.random.default_rng(11)
+        # values on a 2^-10 grid: their interpolation (weights 1/4, 3/4) is exact
+        # in FP32 as in FP64, so both sides sample the images at the same
+        # positions (on 26 M sample points some lie within FP32 rounding of a
+        # cell edge, where grad T is one-sided and a rounding would pick the
+        # other cell)
+        w = synthetic.random_field(rng, 200, 2, (128, 128), amp=3.0, rough=0.2, modes=2)
+        w = (np.round(w * 1024.0) / 1024.0).astype(np.float32)
+        g = torch.empty((200, 2, 128, 128), device="cuda")
+        Minv = torch.empty_like(g)
+        dT = torch.empty((200, 2, 256, 256), device="cuda")
+        out = S.stml_eval_ugrid(ctx.ptr, 3, frames, _dev(w), g, dT, Minv)
+        op = _oparams(ctx.params)
+        T = R.astype(np.float64)
+        ev = ugrid.evaluate(T, w.astype(np.float64), frames, 1.0, 1, op)
+        for i, k in enumerate(("J", "D", "S", "P")):
+            assert_scalar(out[i], ev[k], what=k)
+        assert_array(dT.cpu().numpy(), ev["dT"], what="grad T")
+        assert_array(g.cpu().numpy(), ev["g"], what="coarse gradient")
+        dTg = dT.cpu().numpy().astype(np.float64)
+        assert_array(Minv.cpu().numpy(), 1.0 / ugrid.jacobi_diag(dTg, frames, 1.0, 1, op), what="Jacobi inverse")
+        v = synthetic.random_field(rng, 200, 2, (128, 128), amp=1.0, rough=0.5, modes=2)
+        Hv = torch.empty_like(g)
+        S.stml_hessvec_ugrid(ctx.ptr, 3, frames, dT, _dev(v), Hv)
+        assert_array(Hv.cpu().numpy(), ugrid.hessvec(dTg, v.astype(np.float64), frames, 1.0, 1, op), what="Hv")
+    finally:
+        ctx.close()
