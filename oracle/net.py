@@ -17,7 +17,7 @@ neighbour and h the cell width of the level (fields in cells inside the
 network, so one network serves every level).  With the head's weights zero
 the network returns linear interpolation exactly.  The registration keeps the
 proposal only where the objective of eq. (1) at the proposal is lower than at
-the classical predictor's (the objective is the judge).
+the classical predictor's (the objective decides).
 
 Architecture (2-D, channels-first arrays (B, C, H, W) here):
 
