@@ -462,6 +462,21 @@ stml_status stml_tuning_report(const stml_ctx* ctx, char* buf, size_t cap, size_
 /* Number of this library's kernel launches since the context was created. */
 long long stml_launch_count(const stml_ctx* ctx);
 
+/* Latency floor of one CG step of the cooperative PCG solve (the Jacobi-PCG
+ * inner iterations of the Gauss-Newton GIR, Sec. 2, run in one launch on
+ * small levels): times `iters` iterations of the solve's synchronisation
+ * alone -- per iteration two rounds of CTA partial sums, a grid-wide barrier
+ * and the fixed-order total of the partials in every CTA, with no vector
+ * work -- in one cooperative launch of `blocks` CTAs of 256 threads (at most
+ * two per SM, as the solve), after one untimed launch, and writes the
+ * microseconds per iteration to *us_per_iter (host).  A measurement utility;
+ * the paper has no counterpart.  No context is needed; the call allocates
+ * and frees its own small buffers, runs on a stream of its own on the current
+ * device and synchronises it.  blocks beyond what can be resident at once,
+ * blocks or iters below 1, or a NULL pointer return STML_EINVAL; errors are
+ * reported through stml_last_error(NULL). */
+stml_status stml_coop_sync_floor(int blocks, int iters, double* us_per_iter);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,11 @@ Adam) on `frames` crops of the given shape.
 registers `frames` sequences of uneven length and size (the first of the
 batching workload's seeded draws, scaled down by 4 in each axis) with the
 persistent batched solver and reports the time of each stage.
+
+    python opbench.py --op coop_floor
+
+sets the cooperative PCG solves of the paper-scale registration (the small
+levels) against the latency floor of their grid barriers and reductions.
 """
 from __future__ import annotations
 
@@ -48,7 +53,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="all",
                     choices=["all", "hessvec", "eval", "objective", "trial", "predict_ls", "net_forward",
-                             "net_train", "batch"])
+                             "net_train", "batch", "coop_floor"])
     ap.add_argument("--shape", type=int, nargs="+", default=[256, 256])
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--iters", type=int, default=20)
@@ -66,6 +71,8 @@ def main(argv=None):
         return net_train(S, torch, synthetic, dev, args)
     if args.op == "batch":
         return batch(S, torch, synthetic, dev, args)
+    if args.op == "coop_floor":
+        return coop_floor(S, torch, synthetic, dev, args)
     shape = tuple(args.shape)
     d = len(shape)
     n = args.frames
@@ -241,6 +248,65 @@ def batch(S, torch, synthetic, dev, args):
     bt.close()
     for c in ctxs:
         c.close()
+
+
+def _coop_blocks(shape, nK, sms):
+    """CTAs of the cooperative PCG solve of nK frames on a 2-D level `shape`:
+    the larger of its (frame, 1024-pixel chunk) items and its pixel tiles
+    (16 pixels with the float4 path), at most two per SM -- the grid rule of
+    the solve's launcher."""
+    N = int(np.prod(shape))
+    vec = 4 if shape[-1] % 4 == 0 else 1
+    tpr = 4 if vec == 4 else 8
+    items = -(-N // (256 * vec)) * nK
+    tiles = -(-N // (tpr * vec))
+    return max(1, min(max(items, tiles), 2 * sms))
+
+
+def coop_floor(S, torch, synthetic, dev, args):
+    """The cooperative PCG solves of the paper-scale STML registration (200
+    frames of 256^2, 4 spatial and 3 temporal levels) against their latency
+    floor: per level, the solve's device time per CG step (each solve's start
+    and end amortised over its steps; every launch timed with CUDA events) and
+    the time of the synchronisation alone (stml_coop_sync_floor) on the grid
+    of each GIR, weighted by the GIR's CG steps."""
+    L, Q = 4, 3
+    R = torch.from_numpy(synthetic.make_sequence(synthetic.spec_paper_scale())).to(dev)
+    finest = tuple(R.shape[1:])
+    ctx = S.Context(S.stml_default_params(n_levels=L, n_tlevels=Q))
+
+    def run():
+        S.stml_load_sequence(ctx.ptr, R)
+        S.stml_build_pyramid(ctx.ptr)
+        return S.stml_register(ctx.ptr, S.MODE_STML)
+
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    S.stml_profile_enable(ctx.ptr, 1)
+    stats = run()
+    table = S.stml_profile_report(ctx.ptr)
+    S.stml_profile_enable(ctx.ptr, 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    for lev in range(L):
+        shape = tuple(m >> (L - 1 - lev) for m in finest)
+        N = int(np.prod(shape))
+        rows = [r for r in table if r["kernel"] == "pcg_solve_cooperative" and r["level"] == lev]
+        girs = [s for s in stats if s["level"] == lev and N * s["n_frames"] <= (1 << 21)]
+        if not rows or not girs:
+            continue
+        cg = sum(s["cg_iters"] for s in girs)
+        blocks = [_coop_blocks(shape, s["n_frames"], sms) for s in girs]
+        floors = [S.stml_coop_sync_floor(b, 20 * args.iters) for b in blocks]
+        floor = sum(f * s["cg_iters"] for f, s in zip(floors, girs)) / max(1, cg)
+        us = 1e3 * sum(r["ms"] for r in rows) / max(1, cg)
+        print(json.dumps({"op": "coop_floor", "level": lev, "shape": list(shape),
+                          "frames": [s["n_frames"] for s in girs], "cg_steps": [s["cg_iters"] for s in girs],
+                          "solves": sum(r["launches"] for r in rows), "blocks": blocks,
+                          "floor_us_per_step": [round(f, 3) for f in floors],
+                          "us_per_cg_step": round(us, 3), "floor_us_per_cg_step": round(floor, 3),
+                          "floor_share": round(floor / us, 3)}), flush=True)
+    ctx.close()
 
 
 if __name__ == "__main__":

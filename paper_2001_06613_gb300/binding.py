@@ -111,6 +111,7 @@ _SIGS = {
     "stml_profile_read": (C.c_int, [_vp, C.POINTER(C.c_longlong), _dp, _dp, _dp]),
     "stml_profile_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "stml_launch_count": (C.c_longlong, [_vp]),
+    "stml_coop_sync_floor": (C.c_int, [C.c_int, C.c_int, _dp]),
     "stml_tuning_report": (C.c_int, [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "stml_eval_affine": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _dp, _dp, _dp]),
     "stml_affine_field": (C.c_int, [_vp, C.c_int, _ip, C.c_int, _dp, _fp]),
@@ -508,6 +509,14 @@ def stml_tuning_report(ctx) -> list:
 
 def stml_launch_count(ctx=None) -> int:
     return int(load().stml_launch_count(ctx))
+
+
+def stml_coop_sync_floor(blocks: int, iters: int = 200) -> float:
+    """Microseconds per CG step of the cooperative PCG solve's synchronisation
+    alone (two partial-sum / grid-barrier / total rounds) on `blocks` CTAs."""
+    us = C.c_double()
+    _check(load().stml_coop_sync_floor(int(blocks), int(iters), C.byref(us)))
+    return us.value
 
 
 class Context:

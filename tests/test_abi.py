@@ -44,3 +44,11 @@ def test_invalid_parameters_are_rejected_before_any_device_work(lib):
     bad = lib.stml_default_params(alpha=-1.0)
     with pytest.raises(lib.StmlError):
         lib.stml_create(bad)
+
+
+def test_coop_sync_floor_rejects_bad_arguments_before_any_device_work(lib):
+    for blocks, iters in ((0, 10), (4, 0), (-1, -1)):
+        with pytest.raises(lib.StmlError) as e:
+            lib.stml_coop_sync_floor(blocks, iters)
+        assert e.value.status == -1
+        assert "stml_coop_sync_floor" in lib.stml_last_error(None)

@@ -257,3 +257,19 @@ def test_autotune_is_reproducible_and_close(S, tiny):
         assert float(np.sqrt(np.mean((ys[0] - y_ref) ** 2))) <= E2E_RMS
     finally:
         ctx.close()
+
+
+def test_coop_sync_floor_on_the_solve_grids():
+    """The latency floor of a cooperative CG step is measured on grids up to
+    the solve's largest (two CTAs per SM); a grid that cannot be resident is
+    refused before any launch."""
+    S = cuda_lib()
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for blocks in (1, 64, 2 * sms):
+        us = S.stml_coop_sync_floor(blocks, 200)
+        assert 0.0 < us < 1000.0
+    with pytest.raises(S.StmlError) as e:
+        S.stml_coop_sync_floor(1000 * sms, 10)
+    assert e.value.status == -1
+    assert "resident" in S.stml_last_error(None)
