@@ -110,6 +110,20 @@ __device__ __forceinline__ void ldv(const float* __restrict__ q, size_t i, float
     }
 }
 
+// VEC consecutive floats from shared memory, aligned to 4 VEC bytes.
+template <int VEC>
+__device__ __forceinline__ void lds_vec(const float* p, float (&o)[VEC]) {
+    if constexpr (VEC == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    } else if constexpr (VEC == 2) {
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        o[0] = q.x; o[1] = q.y;
+    } else {
+        o[0] = p[0];
+    }
+}
+
 // The field of one frame at a thread's pixels: the pixels, the next row, the
 // next plane (3-D) and, in lane 31, the first pixel of the next run.
 template <int D, int VEC, bool TRIAL>
@@ -299,12 +313,23 @@ obj_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, 
             for (int k = 0; k < D; ++k) {
                 const float* r0 = b + (k * 2) * STG::kRow + lane * VEC;
                 const float* r1 = b + ((STG::kSrc - 1) * D + k) * 2 * STG::kRow + lane * VEC;   // du rows
+                // one vector load per row piece (a lane's VEC floats are
+                // contiguous and aligned): scalar loads at a lane stride of
+                // VEC words would conflict on the banks; slots a lane did not
+                // copy are read but not used
+                float c0[VEC], n0[VEC], c1[VEC], n1[VEC];
+                lds_vec<VEC>(r0, c0);
+                lds_vec<VEC>(r0 + STG::kRow, n0);
+                if constexpr (TRIAL) {
+                    lds_vec<VEC>(r1, c1);
+                    lds_vec<VEC>(r1 + STG::kRow, n1);
+                }
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
-                    float cv = valid ? r0[e] : 0.f, nv = has_y ? r0[STG::kRow + e] : 0.f;
+                    float cv = valid ? c0[e] : 0.f, nv = has_y ? n0[e] : 0.f;
                     if constexpr (TRIAL) {
-                        if (valid) cv = fmaf(t, r1[e], cv);
-                        if (has_y) nv = fmaf(t, r1[STG::kRow + e], nv);
+                        if (valid) cv = fmaf(t, c1[e], cv);
+                        if (has_y) nv = fmaf(t, n1[e], nv);
                     }
                     cur.c[k][e] = cv;
                     cur.ny[k][e] = nv;
