@@ -110,6 +110,12 @@ __device__ __forceinline__ void ldv(const float* __restrict__ q, size_t i, float
     }
 }
 
+// A hint to fetch the line holding p into L2 (no register is written, so
+// nothing waits for it); p must lie inside an allocation.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // VEC consecutive floats from shared memory, aligned to 4 VEC bytes.
 template <int VEC>
 __device__ __forceinline__ void lds_vec(const float* p, float (&o)[VEC]) {
@@ -349,7 +355,14 @@ obj_kernel(const TI* __restrict__ T, Geom g, PixIndex pi, FrameSet fs, Coef cf, 
         int stage = 0;
         for (int j = j0; j < fs.nK; j += TG) {
             const int jf = j + (kObjStages - 1) * TG;
-            if (jf < fs.nK) issue(jf, (stage + kObjStages - 1) % kObjStages);
+            if (jf < fs.nK) {
+                issue(jf, (stage + kObjStages - 1) % kObjStages);
+                // the image rows its gathers start from (warped positions
+                // stay within a few pixels), into L2 two frames ahead
+                const TI* Tf = T + (size_t)__ldg(fs.frames + jf) * N + (valid ? p : 0u);
+                prefetch_l2(Tf);
+                if (has_y) prefetch_l2(Tf + g.nx);
+            }
             cp_async_commit();
             const int fr = __ldg(fs.frames + j);
             cp_async_wait<kObjStages - 1>();
