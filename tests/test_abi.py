@@ -52,3 +52,36 @@ def test_coop_sync_floor_rejects_bad_arguments_before_any_device_work(lib):
             lib.stml_coop_sync_floor(blocks, iters)
         assert e.value.status == -1
         assert "stml_coop_sync_floor" in lib.stml_last_error(None)
+
+
+@pytest.mark.parametrize("overrides, message", [
+    ({"n_levels": 13}, "n_levels"),
+    ({"n_tlevels": 0}, "n_tlevels"),
+    ({"alpha_t": -0.5}, "alpha_t"),
+    ({"lam": float("nan")}, "lambda"),
+    ({"max_ls": 0}, "iteration limits"),
+    ({"max_cg": -1}, "iteration limits"),
+    ({"tol_cg": 0.0}, "tol_cg"),
+    ({"armijo_c": 1.0}, "armijo_c"),
+    ({"pcg_cooperative": 2}, "pcg_cooperative"),
+    ({"autotune": -1}, "autotune"),
+    ({"transform": 2}, "transform"),
+    ({"distance": 1, "transform": 0}, "distance 1"),
+    ({"lbfgs_m": 65}, "lbfgs_m"),
+    ({"target_J": -1.0}, "target_J"),
+    ({"target_tol": 1.0}, "target_tol"),
+    ({"image_dtype": 3}, "image_dtype"),
+    ({"u_coarsen": 5}, "u_coarsen must be in 0..4"),
+    ({"u_coarsen": 1, "transform": 1}, "u_coarsen > 0 needs"),
+    ({"u_coarsen": 2, "image_dtype": 1}, "u_coarsen > 0 needs"),
+    ({"u_coarsen": 1, "target_J": 10.0}, "u_coarsen > 0 needs"),
+])
+def test_every_parameter_rule_is_checked_before_any_device_work(lib, overrides, message):
+    """Each documented parameter constraint of stml_params is refused by
+    stml_create with STML_EINVAL and a message naming it, before any CUDA
+    call (so this runs without a GPU)."""
+    bad = lib.stml_default_params(**overrides)
+    with pytest.raises(lib.StmlError) as e:
+        lib.stml_create(bad)
+    assert e.value.status == -1
+    assert message in lib.stml_last_error(None)
