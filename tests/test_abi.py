@@ -85,3 +85,54 @@ def test_every_parameter_rule_is_checked_before_any_device_work(lib, overrides, 
         lib.stml_create(bad)
     assert e.value.status == -1
     assert message in lib.stml_last_error(None)
+
+
+# The context-free operators check their arguments before they touch the
+# device: these calls pass stand-in device addresses that are never used.
+_P = 256          # a 16-byte aligned stand-in address
+_MIS = 260        # one that is not 16-byte aligned
+
+
+def _ia(*v):
+    return (ctypes.c_int * len(v))(*v)
+
+
+@pytest.mark.parametrize("call, message", [
+    (lambda L: L.stml_restrict(_P, _P, 1, 2, _ia(8, 7), None), "stml_restrict: odd axis"),
+    (lambda L: L.stml_restrict(None, _P, 1, 2, _ia(8, 8), None), "stml_restrict: bad arguments"),
+    (lambda L: L.stml_restrict(_P, _P, 1, 4, _ia(8, 8, 8, 8), None), "stml_restrict: bad arguments"),
+    (lambda L: L.stml_prolong(_P, _P, -1, 2, _ia(8, 8), None), "stml_prolong: bad arguments"),
+    (lambda L: L.stml_prolong_adjoint(_P, _P, 1, 2, _ia(0, 8), None), "stml_prolong_adjoint: bad arguments"),
+    (lambda L: L.stml_ugrid_prolong(_P, _P, 1, 2, _ia(16, 16), 5, None), "stml_ugrid_prolong: bad arguments"),
+    (lambda L: L.stml_ugrid_adjoint(_P, _P, 1, 2, _ia(16, 12), 3, None),
+     "stml_ugrid_adjoint: an axis is not a multiple of 2^s"),
+    (lambda L: L.stml_predict_linear(_P, _ia(0, 4, 2), 3, _P, _ia(1), 1, 64, None),
+     "stml_predict_linear: bad arguments"),
+    (lambda L: L.stml_predict_linear(_P, _ia(0, 4), 2, _P, _ia(5), 1, 64, None),
+     "stml_predict_linear: target outside the span of K"),
+    (lambda L: L.stml_predict_ls(_P, _ia(0, 4), 2, _P, _P, 5, 1.0, 64, None),
+     "stml_predict_ls: omega and zeta must differ"),
+    (lambda L: L.stml_predict_ls(_P, _ia(0, 5), 2, _P, _P + 64, 5, 1.0, 64, None), "stml_predict_ls: bad arguments"),
+    (lambda L: L.stml_predict_ls(_P, _ia(0, 4), 2, _P, _P + 64, 5, -1.0, 64, None), "stml_predict_ls: bad arguments"),
+])
+def test_context_free_operators_refuse_bad_arguments_before_any_device_work(lib, call, message):
+    L = lib.load()
+    assert call(L) == -1
+    assert message in lib.stml_last_error(None)
+
+
+def test_allocation_free_hessian_product_refuses_before_any_device_work(lib):
+    L = lib.load()
+    p = lib.stml_default_params()
+    cases = [
+        ((_MIS, _P, _P, 2, _ia(8, 8), 1.0, _ia(0, 1), 2), "16-byte aligned"),
+        ((_P, _P, _P, 2, _ia(8, 8), 1.0, _ia(1, 1), 2), "frames must increase"),
+        ((_P, _P, _P, 2, _ia(8, 0), 1.0, _ia(0, 1), 2), "bad shape"),
+        ((_P, _P, _P, 2, _ia(8, 8), 0.0, _ia(0, 1), 2), "bad arguments"),
+        # 4096 x 4096 pixels need 192 MiB of per-pixel sums: more than the static array
+        ((_P, _P, _P, 2, _ia(4096, 4096), 1.0, _ia(0, 1), 2), "scratch bytes"),
+    ]
+    for (dT, v, Hv, dim, shape, h, frames, nK), message in cases:
+        st = L.stml_hessvec_noalloc(dT, v, Hv, dim, shape, h, frames, nK, ctypes.byref(p), None, None)
+        assert st == -1, message
+        assert message in lib.stml_last_error(None)
