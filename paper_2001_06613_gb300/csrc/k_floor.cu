@@ -93,16 +93,20 @@ extern "C" stml_status stml_coop_sync_floor(int blocks, int iters, double* us_pe
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // a warm-up launch, then the timed one
         void* args[] = {(void*)&partials, (void*)&iters, (void*)&sink};
         if (rep == 1) e = cudaEventRecord(a, s);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess) {
             e = cudaLaunchCooperativeKernel((const void*)coop_floor_kernel, dim3(blocks), dim3(kThreads), args,
                                             kFloorSmem, s);
-        count_launches(1);
+            if (e == cudaSuccess) count_launches(1);
+        }
         if (e == cudaSuccess && rep == 1) e = cudaEventRecord(b, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
     release();
-    if (e != cudaSuccess) return floor_err(STML_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // a refused launch leaves no error behind for later calls
+        return floor_err(STML_ECUDA, cudaGetErrorString(e));
+    }
     *us_per_iter = 1e3 * (double)ms / iters;
     return STML_OK;
 }
