@@ -90,3 +90,15 @@ def test_both_bench_arms_name_the_workload_alike():
                                           "4 spatial x 3 temporal levels, STML")
     args.mode = "spml"
     assert bench.workload_label(args).endswith("SPML")
+
+
+def test_coop_floor_grid_rule_gives_the_solve_grids_of_the_paper_scale_levels():
+    """The CTA counts opbench sets the cooperative PCG's latency floor on (the
+    solve launcher's rule: the larger of the (frame, 1024-pixel chunk) items
+    and the 16-pixel tiles, at most two CTAs per SM), on 152 SMs."""
+    import opbench
+    grids = {(m, n): opbench._coop_blocks((m, m), n, 152) for m in (32, 64, 128) for n in (51, 101, 200)}
+    assert [grids[32, n] for n in (51, 101, 200)] == [64, 101, 200]      # 64 tiles, one chunk per frame
+    assert [grids[64, n] for n in (51, 101, 200)] == [256, 304, 304]     # 256 tiles, 4 chunks per frame
+    assert [grids[128, n] for n in (51, 101)] == [304, 304]
+    assert opbench._coop_blocks((30, 30), 4, 152) == 113                 # scalar path: 8-pixel tiles
